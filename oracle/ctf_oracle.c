@@ -1,0 +1,640 @@
+/*
+ * ctf_oracle.c -- plain, slow CPU oracle for Collaborative Texture Filtering
+ * (Akenine-Moller, Ebelin, Pharr, Wronski: "Collaborative Texture Filtering",
+ * HPG 2025, arXiv 2506.17770).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline / reference leg of bench.py load this library.  The product
+ * library (paper_2506_17770_gb300) never links, loads or calls it, and the two
+ * share no source, header, table or constant generator.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC.
+ * -ffp-contract=off matters: every float operation below is one IEEE
+ * round-to-nearest operation, and the only fused multiply-adds are the explicit
+ * fmaf() calls of the filter step.
+ *
+ * What is here, each with the passage it follows:
+ *   - Philox4x32-10 and Philox4x64-10 counter-based generators (Salmon et al.,
+ *     "Parallel random numbers: as easy as 1, 2, 3", SC'11), written from the
+ *     published round function.  The paper itself names no generator; the STF
+ *     fallback draws its two uniforms from Philox4x32-10.
+ *   - the bijection h(i,B) (i-th set bit) and its inverse (number of set bits
+ *     below t), Sec. 3.3 and Fig. 3.
+ *   - exact decode of the project's 4x4-texel block format (the paper only says
+ *     "a texel stored in a custom format", Sec. 3): two RGB565 endpoints,
+ *     bit-replicated to 8 bits, 4-colour palette (c0, c1, (2c0+c1+1)/3,
+ *     (c0+2c1+1)/3), 2-bit index per texel, alpha 255.
+ *   - per-pixel 4-tap bilinear (Sec. 3, the filter every success path must
+ *     reproduce), one-tap STF (Sec. 3.4 opening: a texel chosen with probability
+ *     equal to its filter weight), and the three collaborative algorithms:
+ *     List Merge (Sec. 3.1), Box Sampling (Sec. 3.2, Appendix code of Box
+ *     Sampling) and Mask Sampling (Sec. 3.3), with edge remapping (supplemental
+ *     Sec. 2, "Edge Remapping": producer lane = h(i, A)).
+ *
+ * Coordinates (Appendix code, first lines): floatCoords = uv*dim - 0.5,
+ * upperLeft = floor, st = frac.  Warp tiles are tile_w x tile_h pixels aligned
+ * to the frame origin, lane = ty*tile_w + tx.
+ */
+#include <stdint.h>
+#include <stddef.h>
+#include <string.h>
+#include <stdlib.h>
+#include <math.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox (Salmon et al. SC'11).  One round: two multiplications split into  */
+/* high and low halves, xor with the other two words and the round key; the  */
+/* key is bumped by the Weyl constants between rounds.                        */
+/* ------------------------------------------------------------------------ */
+#define PHILOX_M4x32_0 0xD2511F53u
+#define PHILOX_M4x32_1 0xCD9E8D57u
+#define PHILOX_W32_0 0x9E3779B9u
+#define PHILOX_W32_1 0xBB67AE85u
+#define PHILOX_M4x64_0 0xD2E7470EE14C6C93ull
+#define PHILOX_M4x64_1 0xCA5A826395121157ull
+#define PHILOX_W64_0 0x9E3779B97F4A7C15ull
+#define PHILOX_W64_1 0xBB67AE8584CAA73Bull
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W32_0;
+            k1 += PHILOX_W32_1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M4x32_0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)PHILOX_M4x32_1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void oracle_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W64_0;
+            k1 += PHILOX_W64_1;
+        }
+        unsigned __int128 p0 = (unsigned __int128)PHILOX_M4x64_0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)PHILOX_M4x64_1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t y0 = hi1 ^ x1 ^ k0;
+        uint64_t y1 = lo1;
+        uint64_t y2 = hi0 ^ x3 ^ k1;
+        uint64_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The bijection of Sec. 3.3 / Fig. 3 over a bit set stored as 32-bit words  */
+/* (bit t lives in word t/32, bit t%32).                                      */
+/* ------------------------------------------------------------------------ */
+
+/* h(i, B): position of the i-th set bit of B, counting from 0; -1 if B has
+ * at most i set bits. */
+int oracle_h(const uint32_t *B, int nwords, int i)
+{
+    int seen = 0;
+    for (int t = 0; t < nwords * 32; ++t) {
+        if ((B[t / 32] >> (t % 32)) & 1u) {
+            if (seen == i)
+                return t;
+            ++seen;
+        }
+    }
+    return -1;
+}
+
+/* h^{-1}(t, B): number of set bits of B strictly below position t. */
+int oracle_hinv(const uint32_t *B, int nwords, int t)
+{
+    int count = 0;
+    for (int u = 0; u < t && u < nwords * 32; ++u)
+        if ((B[u / 32] >> (u % 32)) & 1u)
+            ++count;
+    return count;
+}
+
+static int popcount_words(const uint32_t *B, int nwords)
+{
+    int c = 0;
+    for (int t = 0; t < nwords * 32; ++t)
+        c += (int)((B[t / 32] >> (t % 32)) & 1u);
+    return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact decode of the 4x4-texel block format.                               */
+/* Block (bx, by) of a Wt x Ht texture sits at byte 8*(by*(Wt/4)+bx); bytes  */
+/* 0-1 = c0 (RGB565, little endian), 2-3 = c1, 4-7 = 32 index bits; texel    */
+/* (x&3, y&3) uses index bits 2*(4*(y&3)+(x&3)) and the next one.            */
+/* ------------------------------------------------------------------------ */
+static void expand565(unsigned c, int rgb[3])
+{
+    unsigned r5 = (c >> 11) & 31u, g6 = (c >> 5) & 63u, b5 = c & 31u;
+    rgb[0] = (int)((r5 << 3) | (r5 >> 2));
+    rgb[1] = (int)((g6 << 2) | (g6 >> 4));
+    rgb[2] = (int)((b5 << 3) | (b5 >> 2));
+}
+
+/* Decode texel (x, y) to RGBA8.  Coordinates are clamped to the texture
+ * (clamp-to-edge): the appendix omits clamping, and this is the one place the
+ * oracle applies it. */
+void oracle_decode_rgba8(const uint8_t *blocks, int Wt, int Ht, int x, int y, uint8_t rgba[4])
+{
+    if (x < 0) x = 0;
+    if (x > Wt - 1) x = Wt - 1;
+    if (y < 0) y = 0;
+    if (y > Ht - 1) y = Ht - 1;
+    size_t bx = (size_t)(x / 4), by = (size_t)(y / 4), nbx = (size_t)(Wt / 4);
+    const uint8_t *b = blocks + 8 * (by * nbx + bx);
+    unsigned c0 = (unsigned)b[0] | ((unsigned)b[1] << 8);
+    unsigned c1 = (unsigned)b[2] | ((unsigned)b[3] << 8);
+    uint32_t bits = (uint32_t)b[4] | ((uint32_t)b[5] << 8) | ((uint32_t)b[6] << 16) | ((uint32_t)b[7] << 24);
+    int texel = 4 * (y % 4) + (x % 4);
+    int sel = (int)((bits >> (2 * texel)) & 3u);
+    int e0[3], e1[3];
+    expand565(c0, e0);
+    expand565(c1, e1);
+    for (int ch = 0; ch < 3; ++ch) {
+        int v;
+        switch (sel) {
+        case 0: v = e0[ch]; break;
+        case 1: v = e1[ch]; break;
+        case 2: v = (2 * e0[ch] + e1[ch] + 1) / 3; break;
+        default: v = (e0[ch] + 2 * e1[ch] + 1) / 3; break;
+        }
+        rgba[ch] = (uint8_t)v;
+    }
+    rgba[3] = 255;
+}
+
+/* RGBA8 -> float, each channel v/255 correctly rounded (IEEE division). */
+static void decode_texel_f32(const uint8_t *blocks, int Wt, int Ht, int x, int y, float out[4])
+{
+    uint8_t c[4];
+    oracle_decode_rgba8(blocks, Wt, Ht, x, y, c);
+    for (int k = 0; k < 4; ++k)
+        out[k] = (float)c[k] / 255.0f;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Texel sources.  The filter below asks a source for texel values; the     */
+/* exact source is the block decode, the learned source (ctf_oracle_mlp.c)  */
+/* is the FP64 MLP over the latent grids.                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int kind;                 /* 0 = exact blocks, 1 = learned (FP64 MLP) */
+    int Wt, Ht;
+    const uint8_t *blocks;    /* kind 0 */
+    const void *mlp;          /* kind 1: struct oracle_mlp (ctf_oracle_mlp.c) */
+} texel_source;
+
+void oracle_mlp_texel_f64(const void *mlp, int Wt, int Ht, int x, int y, double out[4]);
+
+static void fetch_texel(const texel_source *src, int x, int y, float vf[4], double vd[4])
+{
+    if (src->kind == 0) {
+        decode_texel_f32(src->blocks, src->Wt, src->Ht, x, y, vf);
+        for (int k = 0; k < 4; ++k)
+            vd[k] = (double)vf[k];
+    } else {
+        int xc = x < 0 ? 0 : (x > src->Wt - 1 ? src->Wt - 1 : x);
+        int yc = y < 0 ? 0 : (y > src->Ht - 1 ? src->Ht - 1 : y);
+        oracle_mlp_texel_f64(src->mlp, src->Wt, src->Ht, xc, yc, vd);
+        for (int k = 0; k < 4; ++k)
+            vf[k] = (float)vd[k];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-pixel setup (Appendix code, first lines; minification rule).          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int active;
+    int px, py;
+    int ulx, uly;     /* upper-left integer texel of the 2x2 footprint */
+    float s, t;       /* local coordinates in the 2x2 footprint, in [0,1) */
+    int minified;
+} pixel_setup;
+
+/* Range guard: |uv*dim - 0.5| must stay below 2^22 so that floor() and the
+ * integer bounding box never overflow.  Pixels outside it, with non-finite
+ * UVs, outside the frame or with coverage 0 are inactive. */
+#define COORD_LIMIT 4194304.0f
+
+static void setup_pixel(const float *uv, const float *jac, const uint8_t *cov, int W, int H,
+                        int Wt, int Ht, int px, int py, pixel_setup *p)
+{
+    memset(p, 0, sizeof(*p));
+    p->px = px;
+    p->py = py;
+    if (px >= W || py >= H)
+        return;
+    size_t idx = (size_t)py * (size_t)W + (size_t)px;
+    if (cov && cov[idx] == 0)
+        return;
+    float u = uv[2 * idx + 0], v = uv[2 * idx + 1];
+    float fW = (float)Wt, fH = (float)Ht;
+    float xf = u * fW;         /* one rounding */
+    xf = xf - 0.5f;            /* one rounding */
+    float yf = v * fH;
+    yf = yf - 0.5f;
+    if (!(fabsf(xf) < COORD_LIMIT) || !(fabsf(yf) < COORD_LIMIT))
+        return; /* also rejects NaN */
+    float fx = floorf(xf), fy = floorf(yf);
+    p->ulx = (int)fx;
+    p->uly = (int)fy;
+    p->s = xf - fx;
+    p->t = yf - fy;
+    /* Minification: rho_x^2 = (du/dx*Wt)^2 + (dv/dx*Ht)^2, rho_y^2 likewise;
+     * the pixel is minified unless both are <= 1 (NaN counts as minified). */
+    float a = jac[4 * idx + 0] * fW;
+    float b = jac[4 * idx + 1] * fH;
+    float c = jac[4 * idx + 2] * fW;
+    float d = jac[4 * idx + 3] * fH;
+    float aa = a * a, bb = b * b, cc = c * c, dd = d * d;
+    float rx = aa + bb;
+    float ry = cc + dd;
+    p->minified = !(rx <= 1.0f && ry <= 1.0f);
+    p->active = 1;
+}
+
+/* Bilinear weights for taps k = (k%2, k/2): (1-s)(1-t), s(1-t), (1-s)t, st.
+ * Appendix code names computeBilinearWeights without defining it. */
+static void bilinear_weights(float s, float t, float w[4])
+{
+    float os = 1.0f - s, ot = 1.0f - t;
+    w[0] = os * ot;
+    w[1] = s * ot;
+    w[2] = os * t;
+    w[3] = s * t;
+}
+
+/* Filter of Sec. 3 step 3: acc = 0; acc = fma(w_k, p_k, acc) for k = 0..3.
+ * FP32 mode uses fmaf; FP64 mode accumulates in double. */
+static void filter4(const float w[4], float p[4][4], double pd[4][4], int fp64, float out[4], double outd[4])
+{
+    for (int ch = 0; ch < 4; ++ch) {
+        if (!fp64) {
+            float acc = 0.0f;
+            for (int k = 0; k < 4; ++k)
+                acc = fmaf(w[k], p[k][ch], acc);
+            out[ch] = acc;
+            outd[ch] = (double)acc;
+        } else {
+            double acc = 0.0;
+            for (int k = 0; k < 4; ++k)
+                acc += (double)w[k] * pd[k][ch];
+            outd[ch] = acc;
+            out[ch] = (float)acc;
+        }
+    }
+}
+
+/* One-tap STF texel choice: Philox4x32-10 with counter (px, py, view, 0) and
+ * key (seed low, seed high); xi = (r >> 8) * 2^-24; the right neighbour is
+ * taken when xi0 < s, the lower one when xi1 < t.  Each of the 4 taps is thus
+ * chosen with probability equal to its bilinear weight (up to the 2^-24
+ * quantisation of xi). */
+void oracle_stf_offset(int px, int py, int view, uint64_t seed, float s, float t, int *dx, int *dy)
+{
+    uint32_t ctr[4] = {(uint32_t)px, (uint32_t)py, (uint32_t)view, 0u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    oracle_philox4x32_10(ctr, key, r);
+    float xi0 = (float)(r[0] >> 8) * 0x1p-24f;
+    float xi1 = (float)(r[1] >> 8) * 0x1p-24f;
+    *dx = xi0 < s ? 1 : 0;
+    *dy = xi1 < t ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithms and per-tile outcome codes (shared numbering with the public  */
+/* interface; the numbers are the only thing the two sides agree on).       */
+/* ------------------------------------------------------------------------ */
+enum { ALG_4TAP = 0, ALG_STF = 1, ALG_LIST_MERGE = 2, ALG_BOX = 3, ALG_MASK = 4 };
+enum { PATH_EMPTY = 0, PATH_SUCCESS = 1, PATH_FALLBACK_BUDGET = 2, PATH_FALLBACK_MINIFIED = 3, PATH_DIRECT = 4 };
+
+typedef struct {
+    int64_t tiles_total, tiles_empty, tiles_direct, tiles_success;
+    int64_t tiles_fallback_budget, tiles_fallback_minified;
+    int64_t pixels_active, texel_evals;
+} oracle_stats;
+
+/* Output for one active lane on the STF path: its own STF texel, count 1. */
+static void stf_lane(const texel_source *src, const pixel_setup *p, int view, uint64_t seed, int fp64,
+                     float *out, double *outd, uint8_t *evals, size_t idx)
+{
+    int dx, dy;
+    oracle_stf_offset(p->px, p->py, view, seed, p->s, p->t, &dx, &dy);
+    float vf[4];
+    double vd[4];
+    fetch_texel(src, p->ulx + dx, p->uly + dy, vf, vd);
+    for (int ch = 0; ch < 4; ++ch) {
+        if (out) out[4 * idx + ch] = fp64 ? (float)vd[ch] : vf[ch];
+        if (outd) outd[4 * idx + ch] = fp64 ? vd[ch] : (double)vf[ch];
+    }
+    evals[idx] = 1;
+}
+
+/* Set of unique texel coordinates, kept in insertion order. */
+typedef struct {
+    int n;
+    int x[128], y[128];
+} texel_list;
+
+static int list_find(const texel_list *L, int x, int y)
+{
+    for (int i = 0; i < L->n; ++i)
+        if (L->x[i] == x && L->y[i] == y)
+            return i;
+    return -1;
+}
+
+/*
+ * oracle_filter_ex: filter one frame.
+ *   src            texel source (exact blocks or learned)
+ *   uv   [H][W][2] float, jac [H][W][4] float = (du/dx, dv/dx, du/dy, dv/dy)
+ *   cov  [H][W] uint8 or NULL
+ *   out  [H][W][4] float (FP32 result; may be NULL), outd [H][W][4] double (may be NULL)
+ *   evals[H][W] uint8 per-pixel texel evaluations
+ *   tile_path / tile_n: per tile outcome code and texel-set size (may be NULL)
+ * Returns 0 on success, -1 on bad arguments.
+ */
+static int oracle_filter_ex(const texel_source *src, const float *uv, const float *jac, const uint8_t *cov,
+                            int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h,
+                            int budget, int mask_dim, int edge_remap, int fp64, float *out, double *outd,
+                            uint8_t *evals, int32_t *tile_path, int32_t *tile_n, int64_t *stats_out)
+{
+    if (W < 0 || H < 0 || tile_w <= 0 || tile_h <= 0 || tile_w * tile_h != 32)
+        return -1;
+    if (alg < 0 || alg > 4 || budget < 1 || budget > 32)
+        return -1;
+    if (alg == ALG_MASK && mask_dim != 16 && mask_dim != 11)
+        return -1;
+    oracle_stats st;
+    memset(&st, 0, sizeof(st));
+    int tiles_x = (W + tile_w - 1) / tile_w, tiles_y = (H + tile_h - 1) / tile_h;
+    for (int by = 0; by < tiles_y; ++by) {
+        for (int bx = 0; bx < tiles_x; ++bx) {
+            int tile_id = by * tiles_x + bx;
+            pixel_setup lane[32];
+            uint32_t A = 0;
+            int any_minified = 0;
+            for (int l = 0; l < 32; ++l) {
+                int px = bx * tile_w + l % tile_w, py = by * tile_h + l / tile_w;
+                setup_pixel(uv, jac, cov, W, H, src->Wt, src->Ht, px, py, &lane[l]);
+                if (lane[l].active) {
+                    A |= 1u << l;
+                    any_minified |= lane[l].minified;
+                    st.pixels_active++;
+                }
+                if (px < W && py < H) {
+                    size_t idx = (size_t)py * W + px;
+                    evals[idx] = 0;
+                    for (int ch = 0; ch < 4; ++ch) {
+                        if (out) out[4 * idx + ch] = 0.0f;
+                        if (outd) outd[4 * idx + ch] = 0.0;
+                    }
+                }
+            }
+            st.tiles_total++;
+            int path = PATH_EMPTY, nset = 0;
+            if (A == 0) {
+                st.tiles_empty++;
+                if (tile_path) tile_path[tile_id] = PATH_EMPTY;
+                if (tile_n) tile_n[tile_id] = 0;
+                continue;
+            }
+            int nactive = popcount_words(&A, 1);
+
+            if (alg == ALG_4TAP || alg == ALG_STF) {
+                path = PATH_DIRECT;
+                for (int l = 0; l < 32; ++l) {
+                    if (!lane[l].active) continue;
+                    const pixel_setup *p = &lane[l];
+                    size_t idx = (size_t)p->py * W + p->px;
+                    if (alg == ALG_STF) {
+                        stf_lane(src, p, view, seed, fp64, out, outd, evals, idx);
+                    } else {
+                        float w[4], pv[4][4], o[4];
+                        double pd[4][4], od[4];
+                        bilinear_weights(p->s, p->t, w);
+                        for (int k = 0; k < 4; ++k)
+                            fetch_texel(src, p->ulx + k % 2, p->uly + k / 2, pv[k], pd[k]);
+                        filter4(w, pv, pd, fp64, o, od);
+                        for (int ch = 0; ch < 4; ++ch) {
+                            if (out) out[4 * idx + ch] = o[ch];
+                            if (outd) outd[4 * idx + ch] = od[ch];
+                        }
+                        evals[idx] = 4;
+                    }
+                }
+                st.tiles_direct++;
+                if (tile_path) tile_path[tile_id] = path;
+                if (tile_n) tile_n[tile_id] = alg == ALG_STF ? nactive : 4 * nactive;
+                continue;
+            }
+
+            /* Collaborative algorithms.  Step 1: collect the wave's needs. */
+            texel_list L;
+            L.n = 0;
+            int fits = 1;
+            if (any_minified) {
+                fits = 0;
+                path = PATH_FALLBACK_MINIFIED;
+                nset = -1;
+            } else {
+                /* Wave bounding box: min of upper-left corners, max of
+                 * upper-left + (1,1) (Appendix code of Box Sampling). */
+                int minx = 0, miny = 0, maxx = 0, maxy = 0, first = 1;
+                for (int l = 0; l < 32; ++l) {
+                    if (!lane[l].active) continue;
+                    int ux = lane[l].ulx, uy = lane[l].uly;
+                    if (first || ux < minx) minx = ux;
+                    if (first || uy < miny) miny = uy;
+                    if (first || ux + 1 > maxx) maxx = ux + 1;
+                    if (first || uy + 1 > maxy) maxy = uy + 1;
+                    first = 0;
+                }
+                int64_t bw = (int64_t)maxx - minx + 1, bh = (int64_t)maxy - miny + 1;
+                if (alg == ALG_BOX) {
+                    /* n = area of the bounding box; texel i = UL + (i % w, i / w). */
+                    int64_t area = bw * bh;
+                    nset = area > 0x7fffffff ? 0x7fffffff : (int)area;
+                    if (area <= budget) {
+                        for (int i = 0; i < (int)area; ++i) {
+                            L.x[L.n] = minx + (int)(i % bw);
+                            L.y[L.n] = miny + (int)(i / bw);
+                            L.n++;
+                        }
+                    } else {
+                        fits = 0;
+                    }
+                } else if (alg == ALG_MASK) {
+                    /* Bit (dy*M + dx) for each of the 2x2 texels of each lane,
+                     * OR over the wave; texel i = the i-th set bit, h(i, B). */
+                    int M = mask_dim;
+                    if (bw > M || bh > M) {
+                        fits = 0;
+                        nset = -1;
+                    } else {
+                        uint32_t B[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                        int nwords = (M * M + 31) / 32;
+                        for (int l = 0; l < 32; ++l) {
+                            if (!lane[l].active) continue;
+                            int dx = lane[l].ulx - minx, dy = lane[l].uly - miny;
+                            for (int k = 0; k < 4; ++k) {
+                                int tb = (dy + k / 2) * M + (dx + k % 2);
+                                B[tb / 32] |= 1u << (tb % 32);
+                            }
+                        }
+                        nset = popcount_words(B, nwords);
+                        if (nset <= budget) {
+                            for (int i = 0; i < nset; ++i) {
+                                int tb = oracle_h(B, nwords, i);
+                                L.x[L.n] = minx + tb % M;
+                                L.y[L.n] = miny + tb / M;
+                                L.n++;
+                            }
+                        } else {
+                            fits = 0;
+                        }
+                    }
+                } else { /* ALG_LIST_MERGE: the exact set union of all 2x2 lists. */
+                    for (int l = 0; l < 32; ++l) {
+                        if (!lane[l].active) continue;
+                        for (int k = 0; k < 4; ++k) {
+                            int x = lane[l].ulx + k % 2, y = lane[l].uly + k / 2;
+                            if (list_find(&L, x, y) < 0) {
+                                L.x[L.n] = x;
+                                L.y[L.n] = y;
+                                L.n++;
+                            }
+                        }
+                    }
+                    nset = L.n;
+                    if (nset > budget)
+                        fits = 0;
+                }
+                /* Enough lanes to produce n texels?  With edge remapping any n
+                 * active lanes do (producer of texel i is lane h(i, A));
+                 * without it, lanes 0..n-1 must all be active. */
+                if (fits) {
+                    if (edge_remap) {
+                        if (L.n > nactive) fits = 0;
+                    } else {
+                        uint32_t need = L.n >= 32 ? 0xffffffffu : ((1u << L.n) - 1u);
+                        if ((A & need) != need) fits = 0;
+                    }
+                }
+                path = fits ? PATH_SUCCESS : PATH_FALLBACK_BUDGET;
+            }
+            if (tile_path) tile_path[tile_id] = path;
+            if (tile_n) tile_n[tile_id] = nset;
+
+            if (!fits) {
+                if (path == PATH_FALLBACK_MINIFIED) st.tiles_fallback_minified++;
+                else st.tiles_fallback_budget++;
+                for (int l = 0; l < 32; ++l) {
+                    if (!lane[l].active) continue;
+                    size_t idx = (size_t)lane[l].py * W + lane[l].px;
+                    stf_lane(src, &lane[l], view, seed, fp64, out, outd, evals, idx);
+                }
+                continue;
+            }
+            st.tiles_success++;
+            /* Step 2: texel i is produced once, by lane h(i, A) (or lane i). */
+            float valf[128][4];
+            double vald[128][4];
+            for (int i = 0; i < L.n; ++i) {
+                int producer = edge_remap ? oracle_h(&A, 1, i) : i;
+                const pixel_setup *p = &lane[producer];
+                size_t idx = (size_t)p->py * W + p->px;
+                fetch_texel(src, L.x[i], L.y[i], valf[i], vald[i]);
+                evals[idx] = 1;
+            }
+            /* Step 3: every active lane gathers its four taps and filters. */
+            for (int l = 0; l < 32; ++l) {
+                if (!lane[l].active) continue;
+                const pixel_setup *p = &lane[l];
+                size_t idx = (size_t)p->py * W + p->px;
+                float w[4], pv[4][4], o[4];
+                double pd[4][4], od[4];
+                bilinear_weights(p->s, p->t, w);
+                for (int k = 0; k < 4; ++k) {
+                    int j = list_find(&L, p->ulx + k % 2, p->uly + k / 2);
+                    if (j < 0)
+                        return -2; /* cannot happen: the set covers every tap */
+                    for (int ch = 0; ch < 4; ++ch) {
+                        pv[k][ch] = valf[j][ch];
+                        pd[k][ch] = vald[j][ch];
+                    }
+                }
+                filter4(w, pv, pd, fp64, o, od);
+                for (int ch = 0; ch < 4; ++ch) {
+                    if (out) out[4 * idx + ch] = o[ch];
+                    if (outd) outd[4 * idx + ch] = od[ch];
+                }
+            }
+        }
+    }
+    /* Total evaluations = sum of the per-pixel counts. */
+    int64_t tot = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            tot += evals[(size_t)y * W + x];
+    st.texel_evals = tot;
+    if (stats_out) {
+        stats_out[0] = st.tiles_total;
+        stats_out[1] = st.tiles_empty;
+        stats_out[2] = st.tiles_direct;
+        stats_out[3] = st.tiles_success;
+        stats_out[4] = st.tiles_fallback_budget;
+        stats_out[5] = st.tiles_fallback_minified;
+        stats_out[6] = st.pixels_active;
+        stats_out[7] = st.texel_evals;
+    }
+    return 0;
+}
+
+/* Exact block decode, FP32 arithmetic with the rounding described above. */
+int oracle_filter(const uint8_t *blocks, int Wt, int Ht, const float *uv, const float *jac, const uint8_t *cov,
+                  int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h, int budget,
+                  int mask_dim, int edge_remap, float *out, uint8_t *evals, int32_t *tile_path,
+                  int32_t *tile_n, int64_t *stats)
+{
+    if (Wt <= 0 || Ht <= 0 || Wt % 4 || Ht % 4 || !blocks)
+        return -1;
+    texel_source src = {0, Wt, Ht, blocks, NULL};
+    return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
+                            edge_remap, 0, out, NULL, evals, tile_path, tile_n, stats);
+}
+
+/* Learned decode: texel values from the FP64 MLP, filter in double. */
+int oracle_filter_learned_f64(const void *mlp, int Wt, int Ht, const float *uv, const float *jac,
+                              const uint8_t *cov, int W, int H, int view, int alg, uint64_t seed, int tile_w,
+                              int tile_h, int budget, int mask_dim, int edge_remap, double *outd,
+                              uint8_t *evals, int32_t *tile_path, int32_t *tile_n, int64_t *stats)
+{
+    if (Wt <= 0 || Ht <= 0 || !mlp)
+        return -1;
+    texel_source src = {1, Wt, Ht, NULL, mlp};
+    return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
+                            edge_remap, 1, NULL, outd, evals, tile_path, tile_n, stats);
+}
