@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Throughput of collaborative texture filtering on one GB300 (or N, one
+process per GPU, each filtering its own view: weak scaling, no collective on
+the data path).
+
+Workload (default "frame1080"): one 1920x1080 view of a perspective ground
+plane plus three tilted quads (magnification about 0.1 to 20, 9.5% of pixels
+minified), texture 2048x2048 in 4x4-texel blocks with seeded random endpoints
+and indices.  A step filters the whole view with the headline collaborative
+algorithm (Mask Sampling, 11x11 mask, one-tap STF fallback, 8x4 warps).  The
+same view is also timed with per-pixel 4-tap bilinear, Box Sampling, List
+Merge and the 16x16 mask, each reported beside the headline.
+
+Timing: W warm-up steps, then K timed steps; before every step a 256 MiB
+buffer is written to flush L2 (the view's I/O, 87 MB, would otherwise stay in
+the 129 MB L2), and each step's kernel is timed with CUDA events on the
+launching stream.  One JSON line on rank 0.
+
+--impl reference times the CPU oracle (plain C, one thread) on the same view
+and algorithm: each step is one full view.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filtered pixels/s and texel evals/pixel, collaborative vs 4-tap on one GB300 at tol"
+HEADLINE = ("mask", {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 11, "edge_remap": 1})
+OTHERS = [("4tap", {}), ("box", {}), ("list_merge", {}), ("mask", {"mask_dim": 16})]
+ALG_ID = {"4tap": 0, "stf": 1, "list_merge": 2, "box": 3, "mask": 4}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["frame1080", "frame2160", "plane128"], default="frame1080")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="headline only (for profiling)")
+    return ap.parse_args()
+
+
+def workload(name: str, rank: int):
+    from paper_2506_17770_gb300 import synth
+    seed = synth.SEED_SCENE + rank
+    if name == "plane128":
+        Wt = Ht = 64
+        sc = synth.magnified_plane(128, 128, Wt, Ht, scale=0.25, seed=seed)
+        desc = "128x128 magnified plane (4x), texture 64x64 random blocks"
+    elif name == "frame2160":
+        Wt = Ht = 2048
+        sc = synth.ground_plane_with_quads(3840, 2160, Wt, Ht, seed=seed)
+        desc = "3840x2160 ground plane + 3 tilted quads, texture 2048x2048 random blocks"
+    else:
+        Wt = Ht = 2048
+        sc = synth.ground_plane_with_quads(1920, 1080, Wt, Ht, seed=seed)
+        desc = "1920x1080 ground plane + 3 tilted quads, texture 2048x2048 random blocks"
+    blocks = synth.random_blocks(Wt, Ht, seed=synth.SEED_TEXTURE)
+    return sc, blocks, Wt, Ht, desc
+
+
+def algorithmic_bytes(alg: str, npix: int, tex_bytes: int, has_cov: bool) -> int:
+    """Bytes a kernel must move: per pixel uv 8 + (jac 16 for the collaborative
+    algorithms, which vote on minification) + coverage 1 + RGBA32F 16 + count 1,
+    plus the texture read once."""
+    per = 8 + 16 + 1 + (1 if has_cov else 0)
+    if alg not in ("4tap", "stf"):
+        per += 16
+    return npix * per + tex_bytes
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ctf_filter.cu", "ctf_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2506_17770_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload_name: str, alg_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(f"{workload_name}:{alg_key}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return int(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_cpu_oracle(sc, blocks, Wt, Ht, alg, opts, seconds: float, max_frames: int = 1000):
+    import oracle
+    o = {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 16, "edge_remap": 1}
+    o.update(opts)
+    frames, t0 = 0, time.perf_counter()
+    ev_total = 0
+    while True:
+        _, ev, st = oracle.filter_frame(blocks, Wt, Ht, sc.uv, sc.jac, sc.coverage, view=0, alg=ALG_ID[alg],
+                                        seed=0, **o)
+        frames += 1
+        ev_total += st["texel_evals"]
+        el = time.perf_counter() - t0
+        if el >= seconds or frames >= max_frames:
+            break
+    return frames, el, ev_total
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    sys.path.insert(0, ROOT)
+    import oracle
+    oracle.build()
+    sc, blocks, Wt, Ht, desc = workload(args.workload, 0)
+    alg, opts = HEADLINE
+    npix = sc.W * sc.H
+    for _ in range(max(args.warmup, 0)):
+        run_cpu_oracle(sc, blocks, Wt, Ht, alg, opts, 0.0, 1)
+    t0 = time.perf_counter()
+    ev = 0
+    for _ in range(args.steps):
+        _, _, e = run_cpu_oracle(sc, blocks, Wt, Ht, alg, opts, 0.0, 1)
+        ev += e
+    el = time.perf_counter() - t0
+    value = npix * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {desc}", "algorithm": "mask11+stf", "tile": "8x4",
+                       "l2": "n/a (CPU)"},
+            "evals_per_pixel": ev / (npix * args.steps),
+            "cpu_baseline": {"value": value, "unit": "pixels/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full views, single thread"},
+            "e2e": {"value": value, "unit": "pixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_arm(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2506_17770_gb300 import _ctf, build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    _ctf.load()
+
+    sc, blocks, Wt, Ht, desc = workload(args.workload, rank)
+    W, H = sc.W, sc.H
+    npix = W * H
+    dev = torch.device("cuda", torch.cuda.current_device())
+    uv = torch.from_numpy(sc.uv).to(dev)
+    jac = torch.from_numpy(sc.jac).to(dev)
+    cov = torch.from_numpy(sc.coverage).to(dev) if sc.coverage is not None else None
+    out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    ev = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    tex = _ctf.ctf_texture_create(Wt, Ht, blocks)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    tex_bytes = blocks.nbytes
+
+    def launch(alg, opts):
+        _ctf.ctf_filter(tex, uv, jac, cov, W, H, rank, alg, 0, opts, out, ev, stream=stream)
+
+    def timed(alg, opts, steps, warmup, barrier=False):
+        for _ in range(warmup):
+            flush.zero_()
+            launch(alg, opts)
+        torch.cuda.synchronize()
+        if barrier and world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        w0 = time.perf_counter()
+        for i in range(steps):
+            flush.zero_()
+            starts[i].record(stream)
+            launch(alg, opts)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        if barrier and world > 1:
+            torch.distributed.barrier()
+        wall = time.perf_counter() - w0
+        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        return ms, wall
+
+    def stats_of(alg, opts):
+        return _ctf.ctf_filter(tex, uv, jac, cov, W, H, rank, alg, 0, opts, out, ev, stats=True, stream=stream)
+
+    alg, opts = HEADLINE
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, wall = timed(alg, opts, args.steps, args.warmup, barrier=True)
+    clk = clocks.stop()
+    ms_per_step = ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms_per_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    st = stats_of(alg, opts)
+    value = world * npix / (ms_per_step * 1e-3)
+    evpp = st["texel_evals"] / max(1, st["pixels_active"])
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return 0
+
+    # --- side measurements (rank 0 only) ---
+    extras = {}
+    if not args.no_extras:
+        k = min(args.steps, 1000)
+        for a, o in OTHERS:
+            oo = dict(HEADLINE[1])
+            oo.update(o)
+            ms_a, _ = timed(a, oo, k, 5)
+            sa = stats_of(a, oo)
+            key = a if a != "mask" else f"mask{oo['mask_dim']}"
+            extras[key] = {"pixels_per_s": npix / (ms_a / k * 1e-3), "ms_per_view": ms_a / k,
+                           "evals_per_pixel": sa["texel_evals"] / max(1, sa["pixels_active"]),
+                           "tiles_success": sa["tiles_success"], "tiles_fallback_budget": sa["tiles_fallback_budget"],
+                           "tiles_fallback_minified": sa["tiles_fallback_minified"],
+                           "achieved_gbs": algorithmic_bytes(a, npix, tex_bytes, cov is not None) / (ms_a / k * 1e-3) / 1e9}
+    # end-to-end through the host entry point (pinned host buffers)
+    h_uv = torch.from_numpy(sc.uv).pin_memory()
+    h_jac = torch.from_numpy(sc.jac).pin_memory()
+    h_cov = torch.from_numpy(sc.coverage).pin_memory() if sc.coverage is not None else None
+    h_out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+    h_ev = torch.empty((H, W), dtype=torch.uint8).pin_memory()
+    k_e2e = max(3, min(args.steps, 200))
+    for _ in range(3):
+        _ctf.ctf_filter_host(tex, h_uv, h_jac, h_cov, W, H, 0, alg, 0, opts, h_out, h_ev, stream=stream)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        _ctf.ctf_filter_host(tex, h_uv, h_jac, h_cov, W, H, 0, alg, 0, opts, h_out, h_ev, stream=stream)
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+    h2d = npix * (8 + 16 + (1 if h_cov is not None else 0))
+    d2h = npix * (16 + 1)
+
+    peak, peak_kind = measured_peaks()
+    abytes = algorithmic_bytes(alg, npix, tex_bytes, cov is not None)
+    achieved = abytes / (ms_per_step * 1e-3) / 1e9
+    traffic = ncu_traffic(args.workload, "mask11")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": abytes,
+                "kernel": "exact_filter_kernel<MASK, 8x4, 11>"}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        frames, el, evs = run_cpu_oracle(sc, blocks, Wt, Ht, alg, opts, seconds=10.0)
+        cpu = {"value": frames * npix / el, "unit": "pixels/s", "cores": 1, "kind": "oracle",
+               "sample": f"{frames} full {W}x{H} views of the same workload, mask11+stf, single thread, "
+                         f"{el:.1f} s"}
+
+    fourtap = extras.get("4tap")
+    line = {"metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {desc}", "algorithm": "mask11+stf", "tile": "8x4",
+                       "budget": 32, "views_per_step": world, "l2": "flushed (256 MiB write) before every step"},
+            "evals_per_pixel": evpp,
+            "texel_evals_per_s": value * evpp,
+            "vs_4tap": (value / world) / fourtap["pixels_per_s"] if fourtap else None,
+            "algorithms": extras,
+            "stats": st,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": npix / e2e_s, "unit": "pixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "entry_point": "ctf_filter_host"},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "wall_s_timed_region": wall}
+    print(json.dumps(line), flush=True)
+    _ctf.ctf_texture_destroy(tex)
+    if world > 1:
+        torch.distributed.barrier()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * ctf.h -- C ABI of the GB300 collaborative texture filtering library.
+ *
+ * Collaborative texture filtering (Akenine-Moller, Ebelin, Pharr, Wronski,
+ * "Collaborative Texture Filtering", HPG 2025, arXiv 2506.17770): the 32
+ * pixels of a warp find the texels their bilinear footprints need, each
+ * needed texel is evaluated ("produced") once by one lane, and every pixel
+ * gathers its four taps from the lanes that produced them (Sec. 3, the
+ * three-step flow: collect, produce, gather and filter).  Warps whose texel
+ * set is too large, or that contain a minified pixel, fall back to one-tap
+ * stochastic texture filtering (STF, Sec. 3.4 opening).
+ *
+ * Conventions shared by every call:
+ *  - Pixel arrays are row-major [height][width]:
+ *      uv       float[2] per pixel, texture coordinates in [0,1]-normalised
+ *               texture space (texel x covers u in [x/Wt, (x+1)/Wt));
+ *      jac      float[4] per pixel = (du/dx, dv/dx, du/dy, dv/dy), the UV
+ *               Jacobian in normalised UV per pixel;
+ *      coverage uint8 per pixel, 0 = not covered (nullable = all covered);
+ *      out_rgba float[4] per pixel (RGBA, values in [0,1]);
+ *      out_evals uint8 per pixel: texel evaluations made by that pixel's lane.
+ *  - Texel-space position of a pixel: (u*Wt - 0.5, v*Ht - 0.5), upper-left
+ *    texel = floor, (s,t) = fraction (Appendix code, first lines), each a
+ *    single IEEE float32 operation.
+ *  - A pixel is active when it is inside the frame, covered, and its
+ *    texel-space position is finite with magnitude below 2^22; inactive
+ *    pixels get RGBA (0,0,0,0) and 0 evaluations.
+ *  - Warp tiles are tile_w x tile_h pixels (tile_w*tile_h = 32) aligned to
+ *    the frame origin; lane = ty*tile_w + tx.  Partial tiles at the right
+ *    and bottom edges have inactive lanes.
+ *  - Device pointers are CUDA device (or managed) memory on the current
+ *    device; "host" entry points take host memory.  The library never keeps
+ *    a caller pointer after a call returns.  The stream is borrowed; NULL is
+ *    the legacy default stream.
+ *  - Every function returns CTF_OK (0) or a negative ctf_status.  Arguments
+ *    are validated before any work is queued; errors of kernels already
+ *    queued show up as CTF_ERR_CUDA on a later synchronising call.
+ *    ctf_last_error() gives a thread-local message for the last failure.
+ */
+#ifndef CTF_H
+#define CTF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CTF_OK = 0,
+    CTF_ERR_ARG = -1,         /* bad argument (null, size, enum, shape) */
+    CTF_ERR_ALIGN = -2,       /* pointer not aligned as documented */
+    CTF_ERR_UNSUPPORTED = -3, /* combination not built */
+    CTF_ERR_OOM = -4,         /* device allocation failed */
+    CTF_ERR_CUDA = -5,        /* CUDA runtime error */
+    CTF_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+    CTF_ERR_CORRUPT = -7      /* corrupt or mismatched file */
+} ctf_status;
+
+/* Filtering algorithm.
+ *  CTF_ALG_4TAP        per-pixel bilinear: every pixel evaluates its 4 texels
+ *                      (the reference every collaborative success must equal).
+ *  CTF_ALG_STF         one-tap STF for every pixel (Sec. 3.4 opening).
+ *  CTF_ALG_LIST_MERGE  exact union of the wave's 2x2 texel lists (Sec. 3.1).
+ *  CTF_ALG_BOX         bounding box of the wave's footprints, texel i at
+ *                      (i mod w, i div w) from its corner (Sec. 3.2).
+ *  CTF_ALG_MASK        bit mask over the bounding box, texel i = i-th set bit
+ *                      h(i,B) (Sec. 3.3, Fig. 3); mask_dim 16 or 11. */
+typedef enum {
+    CTF_ALG_4TAP = 0,
+    CTF_ALG_STF = 1,
+    CTF_ALG_LIST_MERGE = 2,
+    CTF_ALG_BOX = 3,
+    CTF_ALG_MASK = 4
+} ctf_algorithm;
+
+/* How a texel value is produced ("texel evaluation", Sec. 3, step 2). */
+typedef enum {
+    CTF_EVAL_BLOCK = 0,    /* exact decode of 4x4-texel blocks */
+    CTF_EVAL_MLP_FP16 = 1, /* learned decode, FP16 MLP over latent grids */
+    CTF_EVAL_MLP_FP8 = 2   /* learned decode, FP8 E4M3 with per-channel scales */
+} ctf_eval_mode;
+
+typedef struct ctf_texture_s *ctf_texture;
+
+/* Texture description for ctf_texture_create.
+ * CTF_EVAL_BLOCK: width and height multiples of 4 in [4, 65536]; blocks
+ *   points to (width/4)*(height/4) records of 8 bytes, row-major by block:
+ *   bytes 0-1 endpoint c0 (RGB565, little endian), bytes 2-3 endpoint c1,
+ *   bytes 4-7 the 2-bit palette indices, texel (x&3, y&3) at bits
+ *   2*(4*(y&3)+(x&3)).  Decode: endpoints bit-replicated to 8 bits, palette
+ *   c0, c1, (2c0+c1+1)/3, (c0+2c1+1)/3 per channel, alpha 255; value = v/255
+ *   correctly rounded.  The paper leaves the format open ("a texel stored in
+ *   a custom format", Sec. 3); this one is the library's.
+ *   blocks may be host or device memory; it is copied. */
+typedef struct {
+    int width, height;
+    ctf_eval_mode mode;
+    const void *blocks;
+} ctf_texture_desc;
+
+/* Filter options; NULL means the defaults in brackets.
+ *   tile_w, tile_h  warp pixel tile, 8x4, 4x8 or 16x2            [8 x 4]
+ *   budget          texels one warp may produce, 1..32 (one per lane,
+ *                   Sec. 3 "at most one texel evaluation per lane") [32]
+ *   mask_dim        Mask Sampling mask side, 16 or 11 (Sec. 3.3)  [16]
+ *   edge_remap      1: producer of texel i is the i-th active lane h(i,A)
+ *                   (supplemental Sec. 2), success needs n <= popcount(A);
+ *                   0: lane i produces texel i and lanes 0..n-1 must be
+ *                   active                                        [1] */
+typedef struct {
+    int tile_w, tile_h;
+    int budget;
+    int mask_dim;
+    int edge_remap;
+} ctf_filter_opts;
+
+/* Per-call counters (filled only when a stats pointer is given). */
+typedef struct {
+    int64_t tiles_total;             /* warp tiles in the frame */
+    int64_t tiles_empty;             /* tiles with no active pixel */
+    int64_t tiles_direct;            /* tiles filtered by 4TAP or STF algorithms */
+    int64_t tiles_success;           /* collaborative tiles on the success path */
+    int64_t tiles_fallback_budget;   /* collaborative tiles over budget -> STF */
+    int64_t tiles_fallback_minified; /* collaborative tiles with a minified pixel -> STF */
+    int64_t pixels_active;
+    int64_t texel_evals;             /* sum of out_evals */
+} ctf_stats;
+
+/* Library and device information. */
+const char *ctf_version(void);
+const char *ctf_status_string(int status);
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *ctf_last_error(void);
+
+/* Create a texture; the library copies the data into its own device memory
+ * on the current device.  *out receives the handle.  Errors: CTF_ERR_ARG,
+ * CTF_ERR_UNSUPPORTED (mode not built), CTF_ERR_OOM, CTF_ERR_CUDA. */
+int ctf_texture_create(const ctf_texture_desc *desc, ctf_texture *out);
+
+/* Destroy a texture (synchronises the device first).  NULL is accepted. */
+int ctf_texture_destroy(ctf_texture tex);
+
+/* Filter one view (Sec. 3 flow for the collaborative algorithms).
+ *   uv [H][W][2], jac [H][W][4], coverage [H][W] (nullable): device memory;
+ *   uv 8-byte and jac 16-byte aligned (else CTF_ERR_ALIGN).
+ *   width, height in [0, 32768] (0 = nothing to do).
+ *   view_id: third word of the STF counter (px, py, view_id, 0).
+ *   seed: Philox4x32-10 key (low word, high word) of the STF choice; pixel
+ *   (px,py) takes the right neighbour when (r0>>8)*2^-24 < s and the lower
+ *   one when (r1>>8)*2^-24 < t, so each tap is chosen with probability equal
+ *   to its bilinear weight (Sec. 3.4 opening).
+ *   out_rgba [H][W][4] device, 16-byte aligned; out_evals [H][W] device or
+ *   NULL.
+ *   stats: host pointer or NULL; when given, the call waits for the stream
+ *   and fills it.
+ *   stream: cudaStream_t or NULL.
+ * The call is asynchronous unless stats is given. */
+int ctf_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t *coverage, int width,
+               int height, int view_id, ctf_algorithm alg, uint64_t seed, const ctf_filter_opts *opts,
+               float *out_rgba, uint8_t *out_evals, ctf_stats *stats, void *stream);
+
+/* ctf_filter on HOST buffers: copies uv, jac (and coverage) to device memory
+ * that the library owns and reuses, filters, copies the image and counts
+ * back, and waits for the stream before returning.  Host buffers that are
+ * page-locked (cudaHostAlloc / cudaHostRegister) copy fastest. */
+int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host, const uint8_t *coverage_host,
+                    int width, int height, int view_id, ctf_algorithm alg, uint64_t seed,
+                    const ctf_filter_opts *opts, float *out_rgba_host, uint8_t *out_evals_host,
+                    ctf_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTF_H */

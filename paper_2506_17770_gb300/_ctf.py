@@ -1,0 +1,183 @@
+"""Thin ctypes binding of the C ABI in include/ctf.h.
+
+Argument marshalling only: every step of the filtering path runs in the CUDA
+library (_build/libctf.so).  There is no CPU fallback: if the library is not
+built, loading raises.  Tensors are torch tensors on the current CUDA device
+(or host tensors for the *_host entry points); their data pointers are passed
+through unchanged.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libctf.so")
+
+CTF_OK, CTF_ERR_ARG, CTF_ERR_ALIGN, CTF_ERR_UNSUPPORTED = 0, -1, -2, -3
+CTF_ERR_OOM, CTF_ERR_CUDA, CTF_ERR_TIMEOUT, CTF_ERR_CORRUPT = -4, -5, -6, -7
+CTF_ALG_4TAP, CTF_ALG_STF, CTF_ALG_LIST_MERGE, CTF_ALG_BOX, CTF_ALG_MASK = 0, 1, 2, 3, 4
+CTF_EVAL_BLOCK, CTF_EVAL_MLP_FP16, CTF_EVAL_MLP_FP8 = 0, 1, 2
+ALGORITHMS = {"4tap": 0, "stf": 1, "list_merge": 2, "box": 3, "mask": 4}
+
+
+class CtfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class ctf_texture_desc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("mode", ctypes.c_int),
+                ("blocks", ctypes.c_void_p)]
+
+
+class ctf_filter_opts(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("budget", ctypes.c_int),
+                ("mask_dim", ctypes.c_int), ("edge_remap", ctypes.c_int)]
+
+
+class ctf_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "tiles_total", "tiles_empty", "tiles_direct", "tiles_success", "tiles_fallback_budget",
+        "tiles_fallback_minified", "pixels_active", "texel_evals")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                                  "(run paper_2506_17770_gb300.build.build())")
+            lib = ctypes.CDLL(LIB_PATH)
+            P, I, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
+            lib.ctf_version.restype = ctypes.c_char_p
+            lib.ctf_status_string.restype = ctypes.c_char_p
+            lib.ctf_status_string.argtypes = [I]
+            lib.ctf_last_error.restype = ctypes.c_char_p
+            lib.ctf_texture_create.argtypes = [P, P]
+            lib.ctf_texture_destroy.argtypes = [P]
+            sig = [P, P, P, P, I, I, I, I, U64, P, P, P, P, P]
+            lib.ctf_filter.argtypes = sig
+            lib.ctf_filter_host.argtypes = sig
+            for fn in ("ctf_texture_create", "ctf_texture_destroy", "ctf_filter", "ctf_filter_host"):
+                getattr(lib, fn).restype = I
+            _bind_optional(lib)
+            _lib = lib
+    return _lib
+
+
+def _bind_optional(lib):
+    """Signatures of the entry points added by later modules, when present."""
+    P, I, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
+    table = {}
+    for name, (argtypes, restype) in table.items():
+        if hasattr(lib, name):
+            f = getattr(lib, name)
+            f.argtypes, f.restype = argtypes, restype
+
+
+def _check(rc: int):
+    if rc != CTF_OK:
+        lib = load()
+        raise CtfError(rc, f"{lib.ctf_status_string(rc).decode()}: {lib.ctf_last_error().decode()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    raise TypeError(f"cannot take a data pointer of {type(t)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _opts(opts):
+    if opts is None or isinstance(opts, ctf_filter_opts):
+        return opts
+    d = {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 16, "edge_remap": 1}
+    d.update(opts)
+    return ctf_filter_opts(**d)
+
+
+def _alg(alg):
+    return ALGORITHMS[alg] if isinstance(alg, str) else int(alg)
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def ctf_version() -> str:
+    return load().ctf_version().decode()
+
+
+def ctf_status_string(status: int) -> str:
+    return load().ctf_status_string(status).decode()
+
+
+def ctf_last_error() -> str:
+    return load().ctf_last_error().decode()
+
+
+def ctf_texture_create(width: int, height: int, blocks, mode: int = CTF_EVAL_BLOCK) -> ctypes.c_void_p:
+    """Block texture from a uint8 tensor/array of (width/4)*(height/4)*8 bytes."""
+    lib = load()
+    desc = ctf_texture_desc(width, height, mode, _ptr(blocks))
+    out = ctypes.c_void_p()
+    _check(lib.ctf_texture_create(ctypes.byref(desc), ctypes.byref(out)))
+    return out
+
+
+def ctf_texture_destroy(tex) -> None:
+    _check(load().ctf_texture_destroy(tex))
+
+
+def ctf_filter(tex, uv, jac, coverage, width, height, view_id, alg, seed, opts, out_rgba, out_evals,
+               stats: bool = False, stream=None):
+    """Filter one view on device buffers.  Returns the stats dict when stats=True."""
+    st = ctf_stats() if stats else None
+    rc = load().ctf_filter(tex, _ptr(uv), _ptr(jac), _ptr(coverage), int(width), int(height), int(view_id),
+                           _alg(alg), int(seed) % 2**64, ctypes.byref(_opts(opts)) if opts is not None else None,
+                           _ptr(out_rgba), _ptr(out_evals), ctypes.byref(st) if st is not None else None,
+                           _stream(stream))
+    _check(rc)
+    return st.as_dict() if st is not None else None
+
+
+def ctf_filter_host(tex, uv, jac, coverage, width, height, view_id, alg, seed, opts, out_rgba, out_evals,
+                    stats: bool = False, stream=None):
+    """ctf_filter on host buffers (copies in and out inside the call)."""
+    st = ctf_stats() if stats else None
+    rc = load().ctf_filter_host(tex, _ptr(uv), _ptr(jac), _ptr(coverage), int(width), int(height),
+                                int(view_id), _alg(alg), int(seed) % 2**64,
+                                ctypes.byref(_opts(opts)) if opts is not None else None, _ptr(out_rgba),
+                                _ptr(out_evals), ctypes.byref(st) if st is not None else None, _stream(stream))
+    _check(rc)
+    return st.as_dict() if st is not None else None

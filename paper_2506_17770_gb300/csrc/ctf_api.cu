@@ -1,0 +1,325 @@
+// ctf_api.cu -- the C ABI (include/ctf.h): argument validation, texture
+// objects, per-device scratch, error reporting.  No exception crosses the ABI.
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ctf.h"
+#include "ctf_internal.h"
+
+struct ctf_texture_s {
+    int width = 0, height = 0;
+    ctf_eval_mode mode = CTF_EVAL_BLOCK;
+    int device = 0;
+    void *blocks = nullptr;  // device copy (BLOCK mode)
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) return fail(CTF_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(CTF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Per-device scratch owned by the library: the stats counters and the
+// staging buffers of ctf_filter_host.  Grown on demand, kept until exit.
+struct DeviceScratch {
+    unsigned long long *stats = nullptr;
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+};
+constexpr int kMaxDevices = 64;
+DeviceScratch g_scratch[kMaxDevices];
+std::mutex g_scratch_mutex;
+
+int current_device(int *dev) {
+    cudaError_t e = cudaGetDevice(dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (*dev < 0 || *dev >= kMaxDevices) return fail(CTF_ERR_UNSUPPORTED, "device ordinal %d too large", *dev);
+    return CTF_OK;
+}
+
+int scratch_stats(unsigned long long **out) {
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_scratch_mutex);
+    DeviceScratch &s = g_scratch[dev];
+    if (!s.stats) {
+        cudaError_t e = cudaMalloc(&s.stats, sizeof(unsigned long long) * ctf::kNumStats);
+        if (e != cudaSuccess) {
+            s.stats = nullptr;
+            return cuda_fail(e, "cudaMalloc(stats)");
+        }
+    }
+    *out = s.stats;
+    return CTF_OK;
+}
+
+int scratch_stage(size_t bytes, void **out) {
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_scratch_mutex);
+    DeviceScratch &s = g_scratch[dev];
+    if (s.stage_bytes < bytes) {
+        if (s.stage) {
+            cudaDeviceSynchronize();
+            cudaFree(s.stage);
+        }
+        s.stage = nullptr;
+        s.stage_bytes = 0;
+        cudaError_t e = cudaMalloc(&s.stage, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(stage)");
+        s.stage_bytes = bytes;
+    }
+    *out = s.stage;
+    return CTF_OK;
+}
+
+struct ResolvedOpts {
+    int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1;
+};
+
+int resolve_opts(const ctf_filter_opts *o, ResolvedOpts *r) {
+    *r = ResolvedOpts();
+    if (!o) return CTF_OK;
+    r->tile_w = o->tile_w;
+    r->tile_h = o->tile_h;
+    r->budget = o->budget;
+    r->mask_dim = o->mask_dim;
+    r->edge_remap = o->edge_remap;
+    const bool shape_ok = (r->tile_w == 8 && r->tile_h == 4) || (r->tile_w == 4 && r->tile_h == 8) ||
+                          (r->tile_w == 16 && r->tile_h == 2);
+    if (!shape_ok) return fail(CTF_ERR_ARG, "tile %dx%d not one of 8x4, 4x8, 16x2", r->tile_w, r->tile_h);
+    if (r->budget < 1 || r->budget > 32) return fail(CTF_ERR_ARG, "budget %d outside [1, 32]", r->budget);
+    if (r->mask_dim != 16 && r->mask_dim != 11) return fail(CTF_ERR_ARG, "mask_dim %d not 16 or 11", r->mask_dim);
+    if (r->edge_remap != 0 && r->edge_remap != 1) return fail(CTF_ERR_ARG, "edge_remap must be 0 or 1");
+    return CTF_OK;
+}
+
+int check_frame(int width, int height) {
+    if (width < 0 || height < 0 || width > 32768 || height > 32768)
+        return fail(CTF_ERR_ARG, "frame %dx%d outside [0, 32768]^2", width, height);
+    return CTF_OK;
+}
+
+int validate_filter_args(ctf_texture tex, const float *uv, const float *jac, int width, int height,
+                         ctf_algorithm alg, float *out, ResolvedOpts *ro, const ctf_filter_opts *opts) {
+    if (!tex) return fail(CTF_ERR_ARG, "texture is NULL");
+    int rc = check_frame(width, height);
+    if (rc) return rc;
+    if ((int)alg < CTF_ALG_4TAP || (int)alg > CTF_ALG_MASK) return fail(CTF_ERR_ARG, "unknown algorithm %d", (int)alg);
+    rc = resolve_opts(opts, ro);
+    if (rc) return rc;
+    if ((size_t)width * (size_t)height == 0) return CTF_OK;
+    if (!uv || !jac || !out) return fail(CTF_ERR_ARG, "uv, jac and out_rgba must not be NULL");
+    if (!aligned(uv, 8)) return fail(CTF_ERR_ALIGN, "uv must be 8-byte aligned");
+    if (!aligned(jac, 16)) return fail(CTF_ERR_ALIGN, "jac must be 16-byte aligned");
+    if (!aligned(out, 16)) return fail(CTF_ERR_ALIGN, "out_rgba must be 16-byte aligned");
+    return CTF_OK;
+}
+
+int run_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t *coverage, int width, int height,
+               int view_id, ctf_algorithm alg, uint64_t seed, const ResolvedOpts &ro, float *out,
+               uint8_t *evals, unsigned long long *dstats, cudaStream_t stream) {
+    if (tex->mode != CTF_EVAL_BLOCK) return fail(CTF_ERR_UNSUPPORTED, "texture mode %d not handled here", tex->mode);
+    ctf::ExactParams p;
+    p.blocks = static_cast<const uint2 *>(tex->blocks);
+    p.Wt = tex->width;
+    p.Ht = tex->height;
+    p.nbx = tex->width / 4;
+    p.uv = reinterpret_cast<const float2 *>(uv);
+    p.jac = reinterpret_cast<const float4 *>(jac);
+    p.cov = coverage;
+    p.W = width;
+    p.H = height;
+    p.tiles_x = (width + ro.tile_w - 1) / ro.tile_w;
+    const int tiles_y = (height + ro.tile_h - 1) / ro.tile_h;
+    p.n_tiles = (long long)p.tiles_x * tiles_y;
+    p.view = view_id;
+    p.k0 = (uint32_t)(seed & 0xffffffffu);
+    p.k1 = (uint32_t)(seed >> 32);
+    p.budget = ro.budget;
+    p.edge_remap = ro.edge_remap;
+    p.out = reinterpret_cast<float4 *>(out);
+    p.evals = evals;
+    p.stats = dstats;
+    cudaError_t e = ctf::launch_exact_filter(p, (int)alg, ro.tile_w, ro.mask_dim, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "filter launch");
+    return CTF_OK;
+}
+
+int read_stats(unsigned long long *dstats, ctf_stats *stats, cudaStream_t stream) {
+    unsigned long long h[ctf::kNumStats];
+    cudaError_t e = cudaMemcpyAsync(h, dstats, sizeof(h), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading stats");
+    stats->tiles_total = (int64_t)h[ctf::kStatTilesTotal];
+    stats->tiles_empty = (int64_t)h[ctf::kStatTilesEmpty];
+    stats->tiles_direct = (int64_t)h[ctf::kStatTilesDirect];
+    stats->tiles_success = (int64_t)h[ctf::kStatTilesSuccess];
+    stats->tiles_fallback_budget = (int64_t)h[ctf::kStatTilesFallbackBudget];
+    stats->tiles_fallback_minified = (int64_t)h[ctf::kStatTilesFallbackMinified];
+    stats->pixels_active = (int64_t)h[ctf::kStatPixelsActive];
+    stats->texel_evals = (int64_t)h[ctf::kStatTexelEvals];
+    return CTF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ctf_version(void) { return "ctf-gb300 0.1 (sm_103a)"; }
+
+const char *ctf_status_string(int status) {
+    switch (status) {
+    case CTF_OK: return "CTF_OK";
+    case CTF_ERR_ARG: return "CTF_ERR_ARG";
+    case CTF_ERR_ALIGN: return "CTF_ERR_ALIGN";
+    case CTF_ERR_UNSUPPORTED: return "CTF_ERR_UNSUPPORTED";
+    case CTF_ERR_OOM: return "CTF_ERR_OOM";
+    case CTF_ERR_CUDA: return "CTF_ERR_CUDA";
+    case CTF_ERR_TIMEOUT: return "CTF_ERR_TIMEOUT";
+    case CTF_ERR_CORRUPT: return "CTF_ERR_CORRUPT";
+    default: return "CTF_ERR_UNKNOWN";
+    }
+}
+
+const char *ctf_last_error(void) { return g_last_error.c_str(); }
+
+int ctf_texture_create(const ctf_texture_desc *desc, ctf_texture *out) {
+    g_last_error.clear();
+    if (!desc || !out) return fail(CTF_ERR_ARG, "desc and out must not be NULL");
+    *out = nullptr;
+    if (desc->mode != CTF_EVAL_BLOCK)
+        return fail(CTF_ERR_UNSUPPORTED, "mode %d needs ctf_texture_create_mlp", (int)desc->mode);
+    const int W = desc->width, H = desc->height;
+    if (W < 4 || H < 4 || W > 65536 || H > 65536 || W % 4 || H % 4)
+        return fail(CTF_ERR_ARG, "texture %dx%d: sides must be multiples of 4 in [4, 65536]", W, H);
+    if (!desc->blocks) return fail(CTF_ERR_ARG, "blocks must not be NULL");
+    ctf_texture t = new (std::nothrow) ctf_texture_s();
+    if (!t) return fail(CTF_ERR_OOM, "host allocation");
+    t->width = W;
+    t->height = H;
+    t->mode = CTF_EVAL_BLOCK;
+    cudaGetDevice(&t->device);
+    const size_t bytes = (size_t)(W / 4) * (size_t)(H / 4) * 8;
+    cudaError_t e = cudaMalloc(&t->blocks, bytes);
+    if (e != cudaSuccess) {
+        delete t;
+        return cuda_fail(e, "cudaMalloc(blocks)");
+    }
+    e = cudaMemcpy(t->blocks, desc->blocks, bytes, cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+        cudaFree(t->blocks);
+        delete t;
+        return cuda_fail(e, "copying blocks");
+    }
+    *out = t;
+    return CTF_OK;
+}
+
+int ctf_texture_destroy(ctf_texture tex) {
+    g_last_error.clear();
+    if (!tex) return CTF_OK;
+    cudaDeviceSynchronize();
+    if (tex->blocks) cudaFree(tex->blocks);
+    delete tex;
+    return CTF_OK;
+}
+
+int ctf_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t *coverage, int width, int height,
+               int view_id, ctf_algorithm alg, uint64_t seed, const ctf_filter_opts *opts, float *out_rgba,
+               uint8_t *out_evals, ctf_stats *stats, void *stream) {
+    g_last_error.clear();
+    ResolvedOpts ro;
+    int rc = validate_filter_args(tex, uv, jac, width, height, alg, out_rgba, &ro, opts);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long *dstats = nullptr;
+    if (stats) {
+        rc = scratch_stats(&dstats);
+        if (rc) return rc;
+        cudaError_t e = cudaMemsetAsync(dstats, 0, sizeof(unsigned long long) * ctf::kNumStats, s);
+        if (e != cudaSuccess) return cuda_fail(e, "clearing stats");
+    }
+    if ((size_t)width * (size_t)height > 0) {
+        rc = run_filter(tex, uv, jac, coverage, width, height, view_id, alg, seed, ro, out_rgba, out_evals, dstats, s);
+        if (rc) return rc;
+    }
+    if (stats) return read_stats(dstats, stats, s);
+    return CTF_OK;
+}
+
+int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host, const uint8_t *coverage_host,
+                    int width, int height, int view_id, ctf_algorithm alg, uint64_t seed,
+                    const ctf_filter_opts *opts, float *out_rgba_host, uint8_t *out_evals_host, ctf_stats *stats,
+                    void *stream) {
+    g_last_error.clear();
+    ResolvedOpts ro;
+    int rc = validate_filter_args(tex, uv_host, jac_host, width, height, alg, out_rgba_host, &ro, opts);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t np = (size_t)width * (size_t)height;
+    if (np == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return CTF_OK;
+    }
+    const bool need_jac = alg != CTF_ALG_4TAP && alg != CTF_ALG_STF;
+    // staging layout: uv | jac | out | coverage | evals, each 256-byte aligned
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_uv = up(np * 8), b_jac = up(np * 16), b_out = up(np * 16), b_cov = up(np), b_ev = up(np);
+    void *stage = nullptr;
+    rc = scratch_stage(b_uv + b_jac + b_out + b_cov + b_ev, &stage);
+    if (rc) return rc;
+    char *base = static_cast<char *>(stage);
+    float *d_uv = reinterpret_cast<float *>(base);
+    float *d_jac = reinterpret_cast<float *>(base + b_uv);
+    float *d_out = reinterpret_cast<float *>(base + b_uv + b_jac);
+    uint8_t *d_cov = reinterpret_cast<uint8_t *>(base + b_uv + b_jac + b_out);
+    uint8_t *d_ev = reinterpret_cast<uint8_t *>(base + b_uv + b_jac + b_out + b_cov);
+    cudaError_t e = cudaMemcpyAsync(d_uv, uv_host, np * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && need_jac) e = cudaMemcpyAsync(d_jac, jac_host, np * 16, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && coverage_host) e = cudaMemcpyAsync(d_cov, coverage_host, np, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    unsigned long long *dstats = nullptr;
+    if (stats) {
+        rc = scratch_stats(&dstats);
+        if (rc) return rc;
+        e = cudaMemsetAsync(dstats, 0, sizeof(unsigned long long) * ctf::kNumStats, s);
+        if (e != cudaSuccess) return cuda_fail(e, "clearing stats");
+    }
+    rc = run_filter(tex, d_uv, d_jac, coverage_host ? d_cov : nullptr, width, height, view_id, alg, seed, ro, d_out,
+                    out_evals_host ? d_ev : nullptr, dstats, s);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(out_rgba_host, d_out, np * 16, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && out_evals_host) e = cudaMemcpyAsync(out_evals_host, d_ev, np, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    if (stats) return read_stats(dstats, stats, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+    return CTF_OK;
+}
+
+}  // extern "C"
