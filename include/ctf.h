@@ -170,6 +170,33 @@ int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host
                     const ctf_filter_opts *opts, float *out_rgba_host, uint8_t *out_evals_host,
                     ctf_stats *stats, void *stream);
 
+/* ctf_filter_host for callers that cannot let the library allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant.
+ * ctf_filter_host stages the host arrays in device buffers that the library
+ * allocates (and re-allocates for larger views) with cudaMalloc; a renderer
+ * or plug-in whose video memory is reserved up front by its own allocator,
+ * or a frame loop that cannot afford the device-wide synchronisation that
+ * cudaMalloc and cudaFree may cause, cannot allow that.  This call keeps all
+ * of its scratch (staging of uv, jac, coverage, image and counts, plus the
+ * stats counters) in one fixed __device__ array of CTF_NOALLOC_SCRATCH_BYTES
+ * that exists on every GPU that loads the library until the process exits,
+ * and it never calls cudaMalloc, cudaFree or any other allocating routine.
+ * Same arguments and results as ctf_filter_host, with these limits:
+ *  - the view must fit: 256 bytes plus, each rounded up to 256 bytes,
+ *    8 + 16 + 16 + 1 + 1 bytes per pixel (about 798,000 pixels; 1024x768
+ *    fits); larger views return CTF_ERR_ARG and queue nothing;
+ *  - all calls on a device share the array and it keeps the last call's
+ *    contents (the stats counters are cleared at the start of each call);
+ *    calls whose GPU work overlaps (other streams, other threads) race on
+ *    it, so serialise them;
+ *  - the first call on a device looks up the array's device address and
+ *    caches it; make that first call before any stream capture. */
+#define CTF_NOALLOC_SCRATCH_BYTES (32u << 20)
+int ctf_filter_host_noalloc(ctf_texture tex, const float *uv_host, const float *jac_host,
+                            const uint8_t *coverage_host, int width, int height, int view_id, ctf_algorithm alg,
+                            uint64_t seed, const ctf_filter_opts *opts, float *out_rgba_host,
+                            uint8_t *out_evals_host, ctf_stats *stats, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,7 +70,9 @@ def load() -> ctypes.CDLL:
             sig = [P, P, P, P, I, I, I, I, U64, P, P, P, P, P]
             lib.ctf_filter.argtypes = sig
             lib.ctf_filter_host.argtypes = sig
-            for fn in ("ctf_texture_create", "ctf_texture_destroy", "ctf_filter", "ctf_filter_host"):
+            lib.ctf_filter_host_noalloc.argtypes = sig
+            for fn in ("ctf_texture_create", "ctf_texture_destroy", "ctf_filter", "ctf_filter_host",
+                       "ctf_filter_host_noalloc"):
                 getattr(lib, fn).restype = I
             _bind_optional(lib)
             _lib = lib
@@ -179,5 +181,19 @@ def ctf_filter_host(tex, uv, jac, coverage, width, height, view_id, alg, seed, o
                                 int(view_id), _alg(alg), int(seed) % 2**64,
                                 ctypes.byref(_opts(opts)) if opts is not None else None, _ptr(out_rgba),
                                 _ptr(out_evals), ctypes.byref(st) if st is not None else None, _stream(stream))
+    _check(rc)
+    return st.as_dict() if st is not None else None
+
+
+def ctf_filter_host_noalloc(tex, uv, jac, coverage, width, height, view_id, alg, seed, opts, out_rgba, out_evals,
+                            stats: bool = False, stream=None):
+    """ctf_filter_host without device allocation: scratch in the library's
+    fixed static device array (views up to about 798,000 pixels)."""
+    st = ctf_stats() if stats else None
+    rc = load().ctf_filter_host_noalloc(tex, _ptr(uv), _ptr(jac), _ptr(coverage), int(width), int(height),
+                                        int(view_id), _alg(alg), int(seed) % 2**64,
+                                        ctypes.byref(_opts(opts)) if opts is not None else None, _ptr(out_rgba),
+                                        _ptr(out_evals), ctypes.byref(st) if st is not None else None,
+                                        _stream(stream))
     _check(rc)
     return st.as_dict() if st is not None else None

@@ -188,6 +188,44 @@ int read_stats(unsigned long long *dstats, ctf_stats *stats, cudaStream_t stream
 
 }  // namespace
 
+// Helpers for the no-allocation entry point (ctf_noalloc.cu), which keeps its
+// scratch in a static device array instead of the buffers above.
+namespace ctf {
+
+int noalloc_validate(ctf_texture tex, const float *uv, const float *jac, int width, int height, ctf_algorithm alg,
+                     const ctf_filter_opts *opts, float *out) {
+    g_last_error.clear();
+    ResolvedOpts ro;
+    return validate_filter_args(tex, uv, jac, width, height, alg, out, &ro, opts);
+}
+
+int noalloc_fail(int status, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+int noalloc_cuda_fail(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+
+int noalloc_run(ctf_texture tex, const float *uv, const float *jac, const uint8_t *coverage, int width, int height,
+                int view_id, ctf_algorithm alg, uint64_t seed, const ctf_filter_opts *opts, float *out,
+                uint8_t *evals, unsigned long long *dstats, cudaStream_t stream) {
+    ResolvedOpts ro;
+    int rc = resolve_opts(opts, &ro);
+    if (rc) return rc;
+    return run_filter(tex, uv, jac, coverage, width, height, view_id, alg, seed, ro, out, evals, dstats, stream);
+}
+
+int noalloc_read_stats(unsigned long long *dstats, ctf_stats *stats, cudaStream_t stream) {
+    return read_stats(dstats, stats, stream);
+}
+
+}  // namespace ctf
+
 extern "C" {
 
 const char *ctf_version(void) { return "ctf-gb300 0.1 (sm_103a)"; }

@@ -45,3 +45,19 @@ cudaError_t launch_exact_filter(const ExactParams &p, int alg, int tile_w, int m
 int device_sm_count();
 
 }  // namespace ctf
+
+#include "../../include/ctf.h"
+
+namespace ctf {
+
+// Used by ctf_filter_host_noalloc (ctf_noalloc.cu); defined in ctf_api.cu.
+int noalloc_validate(ctf_texture tex, const float *uv, const float *jac, int width, int height, ctf_algorithm alg,
+                     const ctf_filter_opts *opts, float *out);
+int noalloc_fail(int status, const char *fmt, ...);
+int noalloc_cuda_fail(cudaError_t e, const char *what);
+int noalloc_run(ctf_texture tex, const float *uv, const float *jac, const uint8_t *coverage, int width, int height,
+                int view_id, ctf_algorithm alg, uint64_t seed, const ctf_filter_opts *opts, float *out,
+                uint8_t *evals, unsigned long long *dstats, cudaStream_t stream);
+int noalloc_read_stats(unsigned long long *dstats, ctf_stats *stats, cudaStream_t stream);
+
+}  // namespace ctf
