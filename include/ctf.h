@@ -170,6 +170,63 @@ int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host
                     const ctf_filter_opts *opts, float *out_rgba_host, uint8_t *out_evals_host,
                     ctf_stats *stats, void *stream);
 
+/* Learned texel decode (the paper's costly texel evaluation, Sec. 4.3.1:
+ * a neural decompressor run "on sample").  Texel (x, y) of a W x H texture
+ * is decoded as
+ *   f    = concat over grids g = 0, 1 of the bilinear sample of latent grid
+ *          L_g (latent_w[g] x latent_h[g] texels, 8 channels, clamp-to-edge)
+ *          at grid position ((x+0.5)*latent_w[g]/W - 0.5, (y+0.5)*latent_h[g]/H - 0.5)
+ *   h1   = relu(W1 f + b1), h2 = relu(W2 h1 + b2)       (16 -> 64 -> 64)
+ *   rgba = clamp(W3 h2 + b3, 0, 1)                     (64 -> 4)
+ * on the tensor cores, FP32 accumulation.  CTF_EVAL_MLP_FP16: latents and
+ * weights rounded to FP16 (nearest), activations FP16.  CTF_EVAL_MLP_FP8:
+ * latents FP16; every layer input k is scaled by a_k = act_absmax_k / 448
+ * and rounded to E4M3 (nearest, saturating); weights W'[o][k] = W[o][k]*a_k
+ * are stored as E4M3 after division by s_o = max_k |W'[o][k]| / 448, and the
+ * layer output is s_o * sum_k + b_o.  Biases stay FP32.
+ * All arrays are FP32, row-major, host or device memory; they are copied and
+ * quantised by the library.  latent[g] is [latent_h][latent_w][8]; w1 [64][16],
+ * w2 [64][64], w3 [4][64] (output x input); act_absmax[l] (FP8 only) holds
+ * the largest |input| of layer l per input channel (16, 64, 64 values). */
+typedef struct {
+    int width, height;
+    ctf_eval_mode mode;
+    int latent_w[2], latent_h[2];
+    const float *latent[2];
+    const float *w1, *b1, *w2, *b2, *w3, *b3;
+    const float *act_absmax[3];
+} ctf_mlp_desc;
+
+/* Create a learned-decode texture (copies and quantises the parameters).
+ * Errors: CTF_ERR_ARG (sizes, NULL or non-finite values), CTF_ERR_OOM,
+ * CTF_ERR_CUDA.  ctf_filter on such a texture runs every algorithm with the
+ * learned decode as texel evaluation; alpha comes from the network. */
+int ctf_texture_create_mlp(const ctf_mlp_desc *desc, ctf_texture *out);
+
+/* The parameters exactly as stored, as floats, into caller-owned host
+ * arrays (any pointer may be NULL): latents (FP16 values), weights (FP16
+ * values, or E4M3 values before scaling), biases, and for FP8 the weight
+ * scales s (64, 64, 4) and activation scales a (16, 64, 64).  The effective
+ * FP8 weight is s_o * q[o][k] / a_k. */
+typedef struct {
+    float *latent[2];
+    float *w1, *b1, *w2, *b2, *w3, *b3;
+    float *weight_scale[3];
+    float *act_scale[3];
+} ctf_mlp_params;
+int ctf_mlp_export(ctf_texture tex, const ctf_mlp_params *out);
+
+/* Decode n texels of a learned-decode texture: xy is int32 [n][2] (x, y),
+ * clamped to the texture; out_rgba float [n][4].  Device memory, xy 8-byte
+ * and out 16-byte aligned.  Asynchronous on the stream. */
+int ctf_mlp_decode(ctf_texture tex, const int32_t *xy, int n, float *out_rgba, void *stream);
+
+/* Wait for the stream and report any failure of work queued on it:
+ * CTF_ERR_CUDA for CUDA errors, CTF_ERR_TIMEOUT if a kernel of this library
+ * on the current device gave up a bounded wait since the last check (the
+ * record is then cleared). */
+int ctf_sync_check(void *stream);
+
 /* ctf_filter_host for callers that cannot let the library allocate device
  * memory.  The paper has no counterpart: this is a deployment variant.
  * ctf_filter_host stages the host arrays in device buffers that the library

@@ -79,10 +79,31 @@ def load() -> ctypes.CDLL:
     return _lib
 
 
+class ctf_mlp_desc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("mode", ctypes.c_int),
+                ("latent_w", ctypes.c_int * 2), ("latent_h", ctypes.c_int * 2),
+                ("latent", ctypes.c_void_p * 2),
+                ("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("w2", ctypes.c_void_p),
+                ("b2", ctypes.c_void_p), ("w3", ctypes.c_void_p), ("b3", ctypes.c_void_p),
+                ("act_absmax", ctypes.c_void_p * 3)]
+
+
+class ctf_mlp_params(ctypes.Structure):
+    _fields_ = [("latent", ctypes.c_void_p * 2), ("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p),
+                ("w2", ctypes.c_void_p), ("b2", ctypes.c_void_p), ("w3", ctypes.c_void_p),
+                ("b3", ctypes.c_void_p), ("weight_scale", ctypes.c_void_p * 3),
+                ("act_scale", ctypes.c_void_p * 3)]
+
+
 def _bind_optional(lib):
-    """Signatures of the entry points added by later modules, when present."""
+    """Signatures of the entry points of the learned decode and later modules."""
     P, I, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
-    table = {}
+    table = {
+        "ctf_texture_create_mlp": ([P, P], I),
+        "ctf_mlp_export": ([P, P], I),
+        "ctf_mlp_decode": ([P, P, I, P, P], I),
+        "ctf_sync_check": ([P], I),
+    }
     for name, (argtypes, restype) in table.items():
         if hasattr(lib, name):
             f = getattr(lib, name)
@@ -197,3 +218,64 @@ def ctf_filter_host_noalloc(tex, uv, jac, coverage, width, height, view_id, alg,
                                         _stream(stream))
     _check(rc)
     return st.as_dict() if st is not None else None
+
+
+# ---------------------------------------------------------------------------
+# Learned decode
+# ---------------------------------------------------------------------------
+def ctf_texture_create_mlp(width, height, mode, latents, w1, b1, w2, b2, w3, b3, act_absmax=None):
+    """Learned-decode texture from FP32 parameters (numpy arrays or device
+    tensors).  latents = (L0 [h0,w0,8], L1 [h1,w1,8])."""
+    import numpy as np
+    keep = []
+
+    def arr(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            keep.append(a)
+            return a.data_ptr()
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        keep.append(a)
+        return a.ctypes.data
+
+    d = ctf_mlp_desc()
+    d.width, d.height, d.mode = int(width), int(height), int(mode)
+    for g in range(2):
+        d.latent_h[g], d.latent_w[g] = int(latents[g].shape[0]), int(latents[g].shape[1])
+        d.latent[g] = arr(latents[g])
+    d.w1, d.b1, d.w2, d.b2, d.w3, d.b3 = (arr(a) for a in (w1, b1, w2, b2, w3, b3))
+    if act_absmax is not None:
+        for l in range(3):
+            d.act_absmax[l] = arr(act_absmax[l])
+    out = ctypes.c_void_p()
+    _check(load().ctf_texture_create_mlp(ctypes.byref(d), ctypes.byref(out)))
+    return out
+
+
+def ctf_mlp_export(tex, latent_shapes, hidden=64, nin=16, nout=4):
+    """The stored (quantised) parameters as float32 numpy arrays."""
+    import numpy as np
+    res = {"lat0": np.zeros(latent_shapes[0], np.float32), "lat1": np.zeros(latent_shapes[1], np.float32),
+           "w1": np.zeros((hidden, nin), np.float32), "b1": np.zeros(hidden, np.float32),
+           "w2": np.zeros((hidden, hidden), np.float32), "b2": np.zeros(hidden, np.float32),
+           "w3": np.zeros((nout, hidden), np.float32), "b3": np.zeros(nout, np.float32),
+           "ws0": np.zeros(hidden, np.float32), "ws1": np.zeros(hidden, np.float32),
+           "ws2": np.zeros(nout, np.float32), "as0": np.zeros(nin, np.float32),
+           "as1": np.zeros(hidden, np.float32), "as2": np.zeros(hidden, np.float32)}
+    p = ctf_mlp_params()
+    p.latent[0], p.latent[1] = res["lat0"].ctypes.data, res["lat1"].ctypes.data
+    p.w1, p.b1, p.w2, p.b2, p.w3, p.b3 = (res[k].ctypes.data for k in ("w1", "b1", "w2", "b2", "w3", "b3"))
+    for l in range(3):
+        p.weight_scale[l] = res[f"ws{l}"].ctypes.data
+        p.act_scale[l] = res[f"as{l}"].ctypes.data
+    _check(load().ctf_mlp_export(tex, ctypes.byref(p)))
+    return res
+
+
+def ctf_mlp_decode(tex, xy, n, out_rgba, stream=None):
+    _check(load().ctf_mlp_decode(tex, _ptr(xy), int(n), _ptr(out_rgba), _stream(stream)))
+
+
+def ctf_sync_check(stream=None):
+    _check(load().ctf_sync_check(_stream(stream)))

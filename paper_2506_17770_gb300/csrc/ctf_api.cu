@@ -13,13 +13,6 @@
 #include "../../include/ctf.h"
 #include "ctf_internal.h"
 
-struct ctf_texture_s {
-    int width = 0, height = 0;
-    ctf_eval_mode mode = CTF_EVAL_BLOCK;
-    int device = 0;
-    void *blocks = nullptr;  // device copy (BLOCK mode)
-};
-
 namespace {
 
 thread_local std::string g_last_error;
@@ -47,6 +40,7 @@ struct DeviceScratch {
     unsigned long long *stats = nullptr;
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    int *err = nullptr;  // set by bounded device waits that gave up
 };
 constexpr int kMaxDevices = 64;
 DeviceScratch g_scratch[kMaxDevices];
@@ -143,7 +137,6 @@ int validate_filter_args(ctf_texture tex, const float *uv, const float *jac, int
 int run_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t *coverage, int width, int height,
                int view_id, ctf_algorithm alg, uint64_t seed, const ResolvedOpts &ro, float *out,
                uint8_t *evals, unsigned long long *dstats, cudaStream_t stream) {
-    if (tex->mode != CTF_EVAL_BLOCK) return fail(CTF_ERR_UNSUPPORTED, "texture mode %d not handled here", tex->mode);
     ctf::ExactParams p;
     p.blocks = static_cast<const uint2 *>(tex->blocks);
     p.Wt = tex->width;
@@ -165,7 +158,15 @@ int run_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t
     p.out = reinterpret_cast<float4 *>(out);
     p.evals = evals;
     p.stats = dstats;
-    cudaError_t e = ctf::launch_exact_filter(p, (int)alg, ro.tile_w, ro.mask_dim, stream);
+    cudaError_t e;
+    if (tex->mode == CTF_EVAL_BLOCK) {
+        e = ctf::launch_exact_filter(p, (int)alg, ro.tile_w, ro.mask_dim, stream);
+    } else {
+        int *err = nullptr;
+        int rc = ctf::device_error_word(&err);
+        if (rc) return rc;
+        e = ctf::launch_mlp_filter(p, ctf::mlp_device_view(tex), (int)alg, ro.tile_w, ro.mask_dim, err, stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "filter launch");
     return CTF_OK;
 }
@@ -187,6 +188,44 @@ int read_stats(unsigned long long *dstats, ctf_stats *stats, cudaStream_t stream
 }
 
 }  // namespace
+
+// Error reporting and the per-device error word, shared with the other
+// translation units of the library.
+namespace ctf {
+
+int report(int status, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+int report_cuda(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+
+void clear_error() { g_last_error.clear(); }
+
+int device_error_word(int **out) {
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_scratch_mutex);
+    DeviceScratch &s = g_scratch[dev];
+    if (!s.err) {
+        cudaError_t e = cudaMalloc(&s.err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(s.err, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            s.err = nullptr;
+            return cuda_fail(e, "cudaMalloc(error word)");
+        }
+    }
+    *out = s.err;
+    return CTF_OK;
+}
+
+}  // namespace ctf
 
 // Helpers for the no-allocation entry point (ctf_noalloc.cu), which keeps its
 // scratch in a static device array instead of the buffers above.
@@ -246,6 +285,24 @@ const char *ctf_status_string(int status) {
 
 const char *ctf_last_error(void) { return g_last_error.c_str(); }
 
+int ctf_sync_check(void *stream) {
+    g_last_error.clear();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+    int *err = nullptr;
+    int rc = ctf::device_error_word(&err);
+    if (rc) return rc;
+    int h = 0;
+    e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the error word");
+    if (h != 0) {
+        cudaMemset(err, 0, sizeof(int));
+        return fail(h, "a device wait gave up (status %d recorded by a kernel)", h);
+    }
+    return CTF_OK;
+}
+
 int ctf_texture_create(const ctf_texture_desc *desc, ctf_texture *out) {
     g_last_error.clear();
     if (!desc || !out) return fail(CTF_ERR_ARG, "desc and out must not be NULL");
@@ -283,6 +340,9 @@ int ctf_texture_destroy(ctf_texture tex) {
     if (!tex) return CTF_OK;
     cudaDeviceSynchronize();
     if (tex->blocks) cudaFree(tex->blocks);
+    for (int g = 0; g < 2; ++g)
+        if (tex->lat[g]) cudaFree(tex->lat[g]);
+    if (tex->img) cudaFree(tex->img);
     delete tex;
     return CTF_OK;
 }

@@ -26,6 +26,7 @@
 
 #include "ctf_device.cuh"
 #include "ctf_internal.h"
+#include "ctf_select.cuh"
 
 namespace ctf {
 namespace {
@@ -33,39 +34,10 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
-enum { ALG_4TAP = 0, ALG_STF = 1, ALG_LIST = 2, ALG_BOX = 3, ALG_MASK = 4 };
-
-// List Merge table of one warp: open addressing over 256 slots (at most 128
-// distinct keys are ever inserted, so probing always ends).
-struct ListTable {
-    unsigned long long keys[256];
-    unsigned char index[256];
-    unsigned long long list[32];
-};
-constexpr unsigned long long kEmpty = ~0ull;
-
-__device__ __forceinline__ unsigned hash_key(unsigned long long k) {
-    unsigned lo = (unsigned)k, hi = (unsigned)(k >> 32);
-    return ((lo * 0x9E3779B1u) ^ (hi * 0x85EBCA77u)) >> 24;
-}
-
-// ceil(4096 / w) for w = 0..32: t / w == (t * kDiv[w]) >> 12 for every
-// t < 32 and w <= 32, and for every t < 256 and w <= 16 (checked
-// exhaustively when the table was made).
-__constant__ unsigned short kDiv[33] = {0,   4096, 2048, 1366, 1024, 820, 683, 586, 512, 456, 410,
-                                        373, 342,  316,  293,  274,  256, 241, 228, 216, 205, 196,
-                                        187, 179,  171,  164,  158,  152, 147, 142, 137, 133, 128};
-
-__device__ __forceinline__ int div_small(int t, int w) { return (t * (int)kDiv[w]) >> 12; }
-
 struct Inputs {
     float2 uv;
     float4 jac;
     bool covered;  // inside the frame and covered
-};
-
-struct Counters {
-    uint32_t v[kNumStats];
 };
 
 template <bool kJac>
@@ -104,321 +76,64 @@ __device__ __forceinline__ float4 filter4(const float w[4], const float3 t[4]) {
     return make_float4(r, g, b, a);
 }
 
-// Mask Sampling words: lane bits at t00, t00+1 (row dy) and t00+S, t00+S+1
-// (row dy+1) for row stride S, OR-reduced over the warp one 32-bit word at a
-// time.
-template <int NW>
-__device__ __forceinline__ void mask_words(bool active, int t00, int S, uint32_t Bw[NW]) {
-    const int tA = t00, tB = t00 + S;
-    const uint32_t sA = (uint32_t)tA & 31u, sB = (uint32_t)tB & 31u;
-    const uint32_t loA = 3u << sA, hiA = sA == 31u ? 1u : 0u;
-    const uint32_t loB = 3u << sB, hiB = sB == 31u ? 1u : 0u;
-    const int wA = tA >> 5, wB = tB >> 5;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        uint32_t m = 0;
-        if (active) {
-            m = (w == wA ? loA : 0u) | (w == wA + 1 ? hiA : 0u) | (w == wB ? loB : 0u) | (w == wB + 1 ? hiB : 0u);
-        }
-        Bw[w] = __reduce_or_sync(FULL, m);
-    }
-}
-
-// h^{-1}(q, B): set bits of B below bit q.
-template <int NW>
-__device__ __forceinline__ int mask_rank(const uint32_t Bw[NW], const int pre[NW], int q) {
-    const int qw = q >> 5;
-    uint32_t word = Bw[0];
-    int base = 0;
-#pragma unroll
-    for (int w = 1; w < NW; ++w) {
-        word = qw == w ? Bw[w] : word;
-        base = qw == w ? pre[w] : base;
-    }
-    return base + __popc(word & ((1u << (q & 31)) - 1u));
-}
-
-// h(i, B): position of the i-th set bit of B (i < popcount(B)).
-template <int NW>
-__device__ __forceinline__ int mask_select(const uint32_t Bw[NW], const int pre[NW], int i) {
-    uint32_t word = Bw[0];
-    int base = 0, wsel = 0;
-#pragma unroll
-    for (int w = 1; w < NW; ++w) {
-        const bool ge = i >= pre[w];
-        word = ge ? Bw[w] : word;
-        base = ge ? pre[w] : base;
-        wsel = ge ? w : wsel;
-    }
-    return 32 * wsel + (int)__fns(word, 0, i - base + 1);
-}
-
 template <int ALG, int TW, int MD>
 __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &in, int px, int py, bool inside,
                                             uint32_t idx, int lane, uint32_t lt, const float *lut, ListTable *T,
                                             Counters &cnt) {
-    constexpr bool kCollab = ALG >= ALG_LIST;
-    constexpr int NW = (MD * MD + 31) / 32;
-    const float fW = (float)p.Wt, fH = (float)p.Ht;
-
     PixelSetup ps;
     ps.active = in.covered;
-    setup_coords(in.uv, fW, fH, ps);
-    const uint32_t A = __ballot_sync(FULL, ps.active);
-    cnt.v[kStatTilesTotal] += 1;
-    if (A == 0) {
-        cnt.v[kStatTilesEmpty] += 1;
-        if (inside) store_pixel(p, idx, make_float4(0.f, 0.f, 0.f, 0.f), 0);
-        return;
-    }
-    const int nactive = __popc(A);
-    cnt.v[kStatPixelsActive] += nactive;
+    setup_coords(in.uv, (float)p.Wt, (float)p.Ht, ps);
 
-    if (!kCollab) {
-        // ---------------- per-pixel 4-tap or one-tap STF ----------------
-        cnt.v[kStatTilesDirect] += 1;
-        cnt.v[kStatTexelEvals] += (ALG == ALG_4TAP ? 4 : 1) * nactive;
-        if (ps.active) {
-            if (ALG == ALG_4TAP) {
-                float3 t[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    t[k] = to_float3(fetch_block_texel(p.blocks, p.nbx, p.Wt, p.Ht, ps.ulx + (k & 1), ps.uly + (k >> 1)),
-                                     lut);
-                float w[4];
-                bilinear_weights(ps.s, ps.t, w);
-                store_pixel(p, idx, filter4(w, t), 4);
-            } else {
-                int dx, dy;
-                stf_offset(px, py, p.view, p.k0, p.k1, ps.s, ps.t, dx, dy);
-                const float3 v = to_float3(fetch_block_texel(p.blocks, p.nbx, p.Wt, p.Ht, ps.ulx + dx, ps.uly + dy), lut);
-                store_pixel(p, idx, make_float4(v.x, v.y, v.z, 1.0f), 1);
-            }
-        } else if (inside) {
-            store_pixel(p, idx, make_float4(0.f, 0.f, 0.f, 0.f), 0);
-        }
-        return;
-    }
-
-    // ---------------- collaborative: step 1, collect ----------------
-    const bool mini = __any_sync(FULL, ps.active && is_minified(in.jac, fW, fH));
-    bool fits = false;
-    int n = 0, minx = 0, miny = 0, bw = 0, mcls = 0;
-    uint32_t Bw[NW];
-    int pre[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        Bw[w] = 0;
-        pre[w] = 0;
-    }
-    if (!mini) {
-        minx = __reduce_min_sync(FULL, ps.active ? ps.ulx : INT_MAX);
-        miny = __reduce_min_sync(FULL, ps.active ? ps.uly : INT_MAX);
-        const int maxx = __reduce_max_sync(FULL, ps.active ? ps.ulx + 1 : INT_MIN);
-        const int maxy = __reduce_max_sync(FULL, ps.active ? ps.uly + 1 : INT_MIN);
-        bw = maxx - minx + 1;
-        const int bh = maxy - miny + 1;
-        if (ALG == ALG_BOX) {
-            if (bw <= p.budget && bh <= p.budget && bw * bh <= p.budget) {
-                n = bw * bh;
-                fits = true;
-            }
-        } else if (ALG == ALG_MASK) {
-            // The mask covers the M x M square of Sec. 3.3; its bits are laid
-            // out with the bounding-box width bw as row stride, so that the
-            // common small boxes need one or two words.  The set, hence n and
-            // every output, is the same as with row stride M.
-            if (bw <= MD && bh <= MD) {
-                const int area = bw * bh;
-                const int t00 = (ps.uly - miny) * bw + (ps.ulx - minx);
-                if (area <= 32) {
-                    mcls = 1;
-                    const uint32_t m = ps.active ? ((3u << t00) | (3u << (t00 + bw))) : 0u;
-                    Bw[0] = __reduce_or_sync(FULL, m);
-                    n = __popc(Bw[0]);
-                } else if (area <= 64) {
-                    mcls = 2;
-                    const unsigned long long m = ps.active ? ((3ull << t00) | (3ull << (t00 + bw))) : 0ull;
-                    Bw[0] = __reduce_or_sync(FULL, (uint32_t)m);
-                    Bw[1] = __reduce_or_sync(FULL, (uint32_t)(m >> 32));
-                    pre[1] = __popc(Bw[0]);
-                    n = pre[1] + __popc(Bw[1]);
-                } else {
-                    mcls = 3;
-                    mask_words<NW>(ps.active, t00, bw, Bw);
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) {
-                        pre[w] = n;
-                        n += __popc(Bw[w]);
-                    }
-                }
-                fits = n <= p.budget;
-            }
-        } else {  // List Merge: exact union through the warp's hash table
-            int base = 0;
-            bool over = false;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const unsigned long long key =
-                    ps.active ? (((unsigned long long)(uint32_t)(ps.uly + (k >> 1) - miny) << 32) |
-                                 (uint32_t)(ps.ulx + (k & 1) - minx))
-                              : (kEmpty - 1ull - (unsigned long long)lane);
-                const uint32_t grp = __match_any_sync(FULL, key);
-                const bool leader = ps.active && (__ffs(grp) - 1) == lane;
-                bool inserted = false;
-                unsigned slot = 0;
-                if (leader) {
-                    unsigned h = hash_key(key) & 255u;
-                    for (int probe = 0; probe < 256; ++probe) {
-                        const unsigned long long old = atomicCAS(&T->keys[h], kEmpty, key);
-                        if (old == kEmpty) {
-                            inserted = true;
-                            slot = h;
-                            break;
-                        }
-                        if (old == key) break;
-                        h = (h + 1) & 255u;
-                    }
-                }
-                const uint32_t newm = __ballot_sync(FULL, inserted);
-                if (inserted) {
-                    const int index = base + __popc(newm & lt);
-                    T->index[slot] = (unsigned char)index;
-                    if (index < 32) T->list[index] = key;
-                }
-                base += __popc(newm);
-                __syncwarp();
-                if (base > p.budget) {
-                    over = true;
-                    break;
-                }
-            }
-            n = base;
-            fits = !over;
-        }
-        if (fits) {
-            if (p.edge_remap) {
-                fits = n <= nactive;
-            } else {
-                const uint32_t need = n >= 32 ? FULL : ((1u << n) - 1u);
-                fits = (A & need) == need;
-            }
-        }
-    }
-
-    if (!fits) {
-        // ---------------- fallback: one-tap STF for every active lane ----------------
-        cnt.v[kStatTilesFallbackMinified] += mini ? 1 : 0;
-        cnt.v[kStatTilesFallbackBudget] += mini ? 0 : 1;
-        cnt.v[kStatTexelEvals] += nactive;
-        if (ps.active) {
-            int dx, dy;
-            stf_offset(px, py, p.view, p.k0, p.k1, ps.s, ps.t, dx, dy);
-            const float3 v = to_float3(fetch_block_texel(p.blocks, p.nbx, p.Wt, p.Ht, ps.ulx + dx, ps.uly + dy), lut);
-            store_pixel(p, idx, make_float4(v.x, v.y, v.z, 1.0f), 1);
-        } else if (inside) {
-            store_pixel(p, idx, make_float4(0.f, 0.f, 0.f, 0.f), 0);
-        }
-    } else {
-        cnt.v[kStatTilesSuccess] += 1;
-        cnt.v[kStatTexelEvals] += n;
-        // ---------------- step 2: produce texel i on lane h(i, A) ----------------
-        const bool full = A == FULL;
-        const int my_i = (full || !p.edge_remap) ? lane : (((A >> lane) & 1u) ? __popc(A & lt) : 32);
-        float3 val = make_float3(0.f, 0.f, 0.f);
-        if (my_i < n) {
-            int x, y;
-            if (ALG == ALG_BOX) {
-                const int q = div_small(my_i, bw);
-                x = minx + (my_i - q * bw);
-                y = miny + q;
-            } else if (ALG == ALG_MASK) {
-                int t;
-                if (mcls == 1) {
-                    t = (int)__fns(Bw[0], 0, my_i + 1);
-                } else if (mcls == 2) {
-                    t = my_i < pre[1] ? (int)__fns(Bw[0], 0, my_i + 1) : 32 + (int)__fns(Bw[1], 0, my_i - pre[1] + 1);
-                } else {
-                    t = mask_select<NW>(Bw, pre, my_i);
-                }
-                const int q = div_small(t, bw);
-                x = minx + (t - q * bw);
-                y = miny + q;
-            } else {
-                const unsigned long long key = T->list[my_i];
-                x = minx + (int)(uint32_t)key;
-                y = miny + (int)(uint32_t)(key >> 32);
-            }
-            val = to_float3(fetch_block_texel(p.blocks, p.nbx, p.Wt, p.Ht, x, y), lut);
-        }
-        // ---------------- step 3: gather the 2x2 taps and filter ----------------
-        int j[4];
-        const int dx0 = ps.ulx - minx, dy0 = ps.uly - miny;
-        if (ALG == ALG_BOX) {
-            j[0] = dx0 + dy0 * bw;
-            j[1] = j[0] + 1;
-            j[2] = j[0] + bw;
-            j[3] = j[2] + 1;
-        } else if (ALG == ALG_MASK) {
-            const int t00 = dy0 * bw + dx0, t01 = t00 + bw;
-            if (mcls == 1) {
-                j[0] = __popc(Bw[0] & ((1u << t00) - 1u));
-                j[2] = __popc(Bw[0] & ((1u << t01) - 1u));
-            } else if (mcls == 2) {
-                const unsigned long long B = ((unsigned long long)Bw[1] << 32) | Bw[0];
-                j[0] = __popcll(B & ((1ull << t00) - 1ull));
-                j[2] = __popcll(B & ((1ull << t01) - 1ull));
-            } else {
-                j[0] = mask_rank<NW>(Bw, pre, t00);
-                j[2] = mask_rank<NW>(Bw, pre, t01);
-            }
-            j[1] = j[0] + 1;
-            j[3] = j[2] + 1;
+    if (ALG == ALG_4TAP) {
+        // ---------------- per-pixel 4-tap ----------------
+        const uint32_t A = __ballot_sync(FULL, ps.active);
+        cnt.v[kStatTilesTotal] += 1;
+        if (A == 0) {
+            cnt.v[kStatTilesEmpty] += 1;
         } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                j[k] = 0;
-                if (ps.active) {
-                    const unsigned long long key =
-                        ((unsigned long long)(uint32_t)(dy0 + (k >> 1)) << 32) | (uint32_t)(dx0 + (k & 1));
-                    unsigned h = hash_key(key) & 255u;
-                    for (int probe = 0; probe < 256; ++probe) {
-                        const unsigned long long kk = T->keys[h];
-                        if (kk == key) {
-                            j[k] = T->index[h];
-                            break;
-                        }
-                        if (kk == kEmpty) break;
-                        h = (h + 1) & 255u;
-                    }
-                }
-            }
+            const int nactive = __popc(A);
+            cnt.v[kStatPixelsActive] += nactive;
+            cnt.v[kStatTilesDirect] += 1;
+            cnt.v[kStatTexelEvals] += 4 * nactive;
         }
-        if (!full && p.edge_remap) {
+        if (ps.active) {
+            float3 t[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) j[k] = nth_set_lane(A, j[k]);
+            for (int k = 0; k < 4; ++k)
+                t[k] = to_float3(fetch_block_texel(p.blocks, p.nbx, p.Wt, p.Ht, ps.ulx + (k & 1), ps.uly + (k >> 1)), lut);
+            float w[4];
+            bilinear_weights(ps.s, ps.t, w);
+            store_pixel(p, idx, filter4(w, t), 4);
+        } else if (inside) {
+            store_pixel(p, idx, make_float4(0.f, 0.f, 0.f, 0.f), 0);
         }
+        return;
+    }
+
+    const Selection sel = select_tile<ALG, MD>(p, ps, in.jac, px, py, lane, lt, T, cnt);
+    // step 2: exact decode of the lane's texel (clamped to the texture)
+    float3 val = make_float3(0.f, 0.f, 0.f);
+    if (sel.produce) val = to_float3(fetch_block_texel(p.blocks, p.nbx, p.Wt, p.Ht, sel.tx, sel.ty), lut);
+    if (sel.path == PATH_SUCCESS) {
+        // step 3: gather the 2x2 taps from their producers and filter
         float3 t[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int src = j[k] & 31;
-            t[k].x = __shfl_sync(FULL, val.x, src);
-            t[k].y = __shfl_sync(FULL, val.y, src);
-            t[k].z = __shfl_sync(FULL, val.z, src);
+            t[k].x = __shfl_sync(FULL, val.x, sel.src[k]);
+            t[k].y = __shfl_sync(FULL, val.y, sel.src[k]);
+            t[k].z = __shfl_sync(FULL, val.z, sel.src[k]);
         }
         if (ps.active) {
             float w[4];
             bilinear_weights(ps.s, ps.t, w);
-            store_pixel(p, idx, filter4(w, t), my_i < n ? 1 : 0);
+            store_pixel(p, idx, filter4(w, t), sel.count);
         } else if (inside) {
             store_pixel(p, idx, make_float4(0.f, 0.f, 0.f, 0.f), 0);
         }
-    }
-    if (ALG == ALG_LIST) {
-        __syncwarp();
-#pragma unroll
-        for (int s = 0; s < 8; ++s) T->keys[lane * 8 + s] = kEmpty;
-        __syncwarp();
+    } else if (ps.active) {
+        store_pixel(p, idx, make_float4(val.x, val.y, val.z, 1.0f), 1);
+    } else if (inside) {
+        store_pixel(p, idx, make_float4(0.f, 0.f, 0.f, 0.f), 0);
     }
 }
 

@@ -2,7 +2,26 @@
 // the CUDA library (not part of the public ABI).
 #pragma once
 #include <cstdint>
+#include <vector>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
+
+#include "../../include/ctf.h"
+#include "ctf_mlp.cuh"
+
+// Texture object behind the opaque ctf_texture handle.
+struct ctf_texture_s {
+    int width = 0, height = 0;
+    ctf_eval_mode mode = CTF_EVAL_BLOCK;
+    int device = 0;
+    void *blocks = nullptr;  // BLOCK: device copy of the blocks
+    // learned decode
+    __half *lat[2] = {nullptr, nullptr};  // device latent grids [gh][gw][8]
+    int gw[2] = {0, 0}, gh[2] = {0, 0};
+    void *img = nullptr;                  // device operand image (kImgBytes)
+    // stored (quantised) parameters as floats, for ctf_mlp_export
+    std::vector<float> s_lat[2], s_w1, s_b1, s_w2, s_b2, s_w3, s_b3, s_wscale[3], s_ascale[3];
+};
 
 namespace ctf {
 
@@ -43,6 +62,20 @@ cudaError_t launch_exact_filter(const ExactParams &p, int alg, int tile_w, int m
 
 // Number of SMs of the current device (cached).
 int device_sm_count();
+
+// Learned decode (ctf_mlp.cu).
+cudaError_t launch_mlp_decode(const MlpDevice &m, int Wt, int Ht, const int2 *xy, int n, float4 *out, int *err,
+                              cudaStream_t stream);
+cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
+                              cudaStream_t stream);
+MlpDevice mlp_device_view(const ctf_texture_s *t);
+
+// Error reporting shared by the C ABI translation units (ctf_api.cu).
+int report(int status, const char *fmt, ...);
+int report_cuda(cudaError_t e, const char *what);
+void clear_error();
+// Per-device error word that bounded device waits set (ctf_api.cu).
+int device_error_word(int **out);
 
 }  // namespace ctf
 

@@ -1,0 +1,202 @@
+"""GPU parity of the learned texel decode (tcgen05 MLP) against the FP64 oracle.
+
+Tolerance, derived from the arithmetic of the FP16 path: the features are
+rounded to FP16 and so are both hidden activations (unit roundoff u = 2^-11);
+products are exact and sums are FP32 on the tensor cores.  To first order the
+output error of a texel is bounded by
+    e_f  = u |f|,  e_h1 = u |h1| + |W1| e_f,  e_h2 = u |h2| + |W2| e_h1,
+    e_y  = |W3| e_h2
+(ReLU and the final clamp are 1-Lipschitz).  Each test allows 1.5 e_y + 1e-5,
+computed per texel from the oracle's FP64 activations with the stored
+weights.  Texel-evaluation counts must match the oracle bit-exactly: the
+selection uses the same FP32 coordinate arithmetic as the exact path.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_17770_gb300 import _ctf, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+U16 = 2.0 ** -11
+ALGS = {"4tap": 0, "stf": 1, "list_merge": 2, "box": 3, "mask": 4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2506_17770_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def random_params(seed, Wt, Ht, r0=4, r1=8):
+    g = np.random.default_rng(seed)
+    lat = [g.normal(0, 1.0, (Ht // r0, Wt // r0, 8)).astype(np.float32),
+           g.normal(0, 1.0, (Ht // r1, Wt // r1, 8)).astype(np.float32)]
+    w1 = g.normal(0, math.sqrt(2 / 16), (64, 16)).astype(np.float32)
+    b1 = g.normal(0, 0.1, 64).astype(np.float32)
+    w2 = g.normal(0, math.sqrt(2 / 64), (64, 64)).astype(np.float32)
+    b2 = g.normal(0, 0.1, 64).astype(np.float32)
+    w3 = g.normal(0, 0.04, (4, 64)).astype(np.float32)
+    b3 = np.array([0.5, 0.45, 0.55, 0.9], np.float32)
+    return lat, (w1, b1, w2, b2, w3, b3)
+
+
+class LearnedTex:
+    def __init__(self, Wt, Ht, seed=1, mode=_ctf.CTF_EVAL_MLP_FP16):
+        self.Wt, self.Ht = Wt, Ht
+        lat, p = random_params(seed, Wt, Ht)
+        self.h = _ctf.ctf_texture_create_mlp(Wt, Ht, mode, lat, *p)
+        st = _ctf.ctf_mlp_export(self.h, (lat[0].shape, lat[1].shape))
+        self.stored = st
+        self.mlp = oracle.MLP((st["lat0"], st["lat1"]), st["w1"], st["b1"], st["w2"], st["b2"], st["w3"], st["b3"])
+        self.bound = self._texel_bounds()
+
+    def _texel_bounds(self):
+        st = self.stored
+        ys, xs = np.meshgrid(np.arange(self.Ht), np.arange(self.Wt), indexing="ij")
+        xs, ys = xs.ravel(), ys.ravel()
+        F = np.stack([oracle.mlp_features(self.mlp, self.Wt, self.Ht, int(x), int(y)) for x, y in zip(xs, ys)])
+        w1, w2, w3 = (st[k].astype(np.float64) for k in ("w1", "w2", "w3"))
+        h1 = np.maximum(F @ w1.T + st["b1"], 0)
+        h2 = np.maximum(h1 @ w2.T + st["b2"], 0)
+        e_f = U16 * np.abs(F)
+        e_h1 = U16 * h1 + e_f @ np.abs(w1).T
+        e_h2 = U16 * h2 + e_h1 @ np.abs(w2).T
+        e_y = e_h2 @ np.abs(w3).T
+        return (1.5 * e_y + 1e-5).reshape(self.Ht, self.Wt, 4)
+
+    def close(self):
+        _ctf.ctf_texture_destroy(self.h)
+
+
+@pytest.fixture(scope="module")
+def tex64():
+    t = LearnedTex(64, 64, seed=1)
+    yield t
+    t.close()
+
+
+def test_export_round_trips_fp16(tex64):
+    lat, (w1, b1, w2, b2, w3, b3) = random_params(1, 64, 64)
+    st = tex64.stored
+    np.testing.assert_array_equal(st["w2"], w2.astype(np.float16).astype(np.float32))
+    np.testing.assert_array_equal(st["lat1"], lat[1].astype(np.float16).astype(np.float32))
+    np.testing.assert_array_equal(st["b2"], b2)
+
+
+def test_mlp_decode_matches_fp64_oracle(tex64):
+    g = np.random.default_rng(4)
+    n = 3000
+    xy = np.stack([g.integers(-5, 70, n), g.integers(-5, 70, n)], -1).astype(np.int32)
+    d_xy = torch.from_numpy(xy).cuda()
+    out = torch.full((n, 4), -1.0, device="cuda")
+    _ctf.ctf_mlp_decode(tex64.h, d_xy, n, out)
+    _ctf.ctf_sync_check()
+    got = out.cpu().numpy()
+    xc, yc = np.clip(xy[:, 0], 0, 63), np.clip(xy[:, 1], 0, 63)
+    ref = oracle.mlp_decode(tex64.mlp, 64, 64, xc, yc)
+    tol = tex64.bound[yc, xc]
+    err = np.abs(got - ref)
+    assert np.all(err <= tol), (err.max(), (err / tol).max())
+    assert err.max() > 0  # FP16 rounding is visible: the kernel is not an FP64 copy
+
+
+def test_mlp_decode_is_row_independent(tex64):
+    """A texel's value does not depend on which row of the 128-row tile it
+    lands in or on the other rows (needed for collaborative == 4-tap)."""
+    g = np.random.default_rng(5)
+    base = np.stack([g.integers(0, 64, 200), g.integers(0, 64, 200)], -1).astype(np.int32)
+    perm = g.permutation(200)
+    outs = []
+    for arr in (base, base[perm], np.concatenate([base[:7], base])[7:]):
+        d = torch.from_numpy(np.ascontiguousarray(arr)).cuda()
+        o = torch.empty((len(arr), 4), device="cuda")
+        _ctf.ctf_mlp_decode(tex64.h, d, len(arr), o)
+        outs.append(o.cpu().numpy())
+    _ctf.ctf_sync_check()
+    inv = np.argsort(perm)
+    assert np.array_equal(outs[0].view(np.uint32), outs[1][inv].view(np.uint32))
+    assert np.array_equal(outs[0].view(np.uint32), outs[2].view(np.uint32))
+
+
+def _scene(W, H, seed):
+    g = np.random.default_rng(seed)
+    uv = np.zeros((H, W, 2))
+    jac = np.zeros((H, W, 4))
+    for ty in range(0, H, 4):
+        for tx in range(0, W, 8):
+            m = math.exp(g.uniform(math.log(0.6), math.log(8.0)))
+            r = g.uniform(0, 2 * math.pi)
+            c, s = math.cos(r), math.sin(r)
+            o = g.uniform(-2, 62, 2)
+            ly, lx = np.meshgrid(np.arange(4) + 0.5, np.arange(8) + 0.5, indexing="ij")
+            X = (c * lx - s * ly) / m + o[0]
+            Y = (s * lx + c * ly) / m + o[1]
+            hh, ww = min(4, H - ty), min(8, W - tx)
+            sl = (slice(ty, ty + hh), slice(tx, tx + ww))
+            uv[sl + (0,)] = (X / 64)[:hh, :ww]
+            uv[sl + (1,)] = (Y / 64)[:hh, :ww]
+            jac[sl] = np.array([c / m / 64, s / m / 64, -s / m / 64, c / m / 64])
+    cov = (g.uniform(size=(H, W)) > 0.1).astype(np.uint8)
+    return uv.astype(np.float32), jac.astype(np.float32), cov
+
+
+def _pixel_bounds(tex, uv):
+    xf = uv[..., 0] * np.float32(tex.Wt) - np.float32(0.5)
+    yf = uv[..., 1] * np.float32(tex.Ht) - np.float32(0.5)
+    ok = np.isfinite(xf) & np.isfinite(yf) & (np.abs(xf) < 2 ** 22) & (np.abs(yf) < 2 ** 22)
+    x0 = np.floor(np.where(ok, xf, 0)).astype(np.int64)
+    y0 = np.floor(np.where(ok, yf, 0)).astype(np.int64)
+    b = np.zeros(uv.shape[:2] + (4,))
+    for dy in (0, 1):
+        for dx in (0, 1):
+            xx = np.clip(x0 + dx, 0, tex.Wt - 1)
+            yy = np.clip(y0 + dy, 0, tex.Ht - 1)
+            b = np.maximum(b, tex.bound[yy, xx])
+    return b
+
+
+def gpu_filter(tex, uv, jac, cov, alg, opts=None, seed=0):
+    H, W = uv.shape[:2]
+    d_uv, d_jac = torch.from_numpy(uv).cuda(), torch.from_numpy(jac).cuda()
+    d_cov = None if cov is None else torch.from_numpy(cov).cuda()
+    out = torch.full((H, W, 4), -3.0, device="cuda")
+    ev = torch.full((H, W), 77, dtype=torch.uint8, device="cuda")
+    st = _ctf.ctf_filter(tex.h, d_uv, d_jac, d_cov, W, H, 0, alg, seed, opts, out, ev, stats=True)
+    _ctf.ctf_sync_check()
+    return out.cpu().numpy(), ev.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("alg", list(ALGS))
+@pytest.mark.parametrize("W,H,seed", [(128, 64, 11), (37, 21, 12)])
+def test_learned_filter_matches_fp64_oracle(tex64, alg, W, H, seed):
+    uv, jac, cov = _scene(W, H, seed)
+    for opts in (None, {"tile_w": 4, "tile_h": 8, "mask_dim": 11}):
+        o = {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 16, "edge_remap": 1}
+        o.update(opts or {})
+        out, ev, st = gpu_filter(tex64, uv, jac, cov, alg, opts)
+        ref, ref_ev, ref_st = oracle.filter_frame_learned_f64(tex64.mlp, 64, 64, uv, jac, cov, alg=ALGS[alg],
+                                                              seed=0, **o)
+        np.testing.assert_array_equal(ev, ref_ev)
+        assert st == ref_st
+        tol = _pixel_bounds(tex64, uv)
+        err = np.abs(out - ref)
+        assert np.all(err <= tol), (alg, opts, err.max())
+
+
+def test_learned_success_equals_learned_4tap_bitwise(tex64):
+    sc = synth.magnified_plane(128, 128, 64, 64, scale=0.25)
+    ref = gpu_filter(tex64, sc.uv, sc.jac, None, "4tap")[0]
+    for alg in ("box", "mask", "list_merge"):
+        out, ev, st = gpu_filter(tex64, sc.uv, sc.jac, None, alg)
+        assert st["tiles_success"] == st["tiles_total"]
+        assert np.array_equal(out.view(np.uint32), ref.view(np.uint32)), alg
+        assert st["texel_evals"] < 0.75 * st["pixels_active"]
