@@ -227,6 +227,77 @@ int ctf_mlp_decode(ctf_texture tex, const int32_t *xy, int n, float *out_rgba, v
  * record is then cleared). */
 int ctf_sync_check(void *stream);
 
+/* Training of the learned decode on texels of an exact block texture (the
+ * decoder the network stands in for, which also judges its error).  A
+ * trainer holds FP32 master parameters (latents, weights, biases) and Adam
+ * moments on the device.  One step draws `batch` texels with Philox4x32-10
+ * (counter (i, step, 0x5A4D, 0), key = seed; x = (r0 * W) >> 32,
+ * y = (r1 * H) >> 32), decodes their exact values as targets, and minimises
+ * L = (1/batch) sum_i sum_c (y_ic - target_ic)^2 over the unclamped network
+ * output, all four channels.  Gradients are summed in 64-bit fixed point
+ * (2^-44 resolution), so every step is deterministic and a run resumed from
+ * a checkpoint is bit-identical to an uninterrupted one.  Learning rates
+ * decay linearly from lr_* to lr_* * lr_final_frac over `total_steps`.
+ * The paper trains no network; this is the project's stand-in for the
+ * neural decompressor of Sec. 4.3.1. */
+typedef struct {
+    int latent_w[2], latent_h[2]; /* latent grid sizes, e.g. W/4 x H/4 and W/8 x H/8 */
+    int batch;                    /* texels per step, 1 .. 4194304 */
+    int64_t total_steps;          /* length of the learning-rate schedule */
+    float lr_weights, lr_latents; /* Adam step sizes */
+    float lr_final_frac;          /* final fraction of the step sizes */
+    float beta1, beta2, eps;      /* Adam */
+    uint64_t seed;                /* sampling and initialisation */
+} ctf_train_desc;
+
+typedef struct ctf_trainer_s *ctf_trainer;
+
+/* Create a trainer on an exact block texture (which must outlive it), with
+ * seeded initial parameters: latents ~ N(0, 0.5^2), weights uniform in
+ * +-sqrt(6 / fan_in), biases 0 except b3 = 0.5. */
+int ctf_trainer_create(ctf_texture exact_src, const ctf_train_desc *desc, ctf_trainer *out);
+int ctf_trainer_destroy(ctf_trainer tr);
+
+/* Run `steps` optimisation steps on the stream (asynchronous). */
+int ctf_trainer_step(ctf_trainer tr, int64_t steps, void *stream);
+
+/* Steps taken so far. */
+int64_t ctf_trainer_steps_done(ctf_trainer tr);
+
+/* Loss and gradients for explicit texels without updating anything:
+ * xy int32 [n][2] (device), targets from the exact texture.  Gradients go
+ * to host arrays (any may be NULL) shaped like the parameters; loss to a
+ * host double.  Synchronises the stream. */
+typedef struct {
+    float *latent[2];
+    float *w1, *b1, *w2, *b2, *w3, *b3;
+} ctf_mlp_arrays;
+int ctf_trainer_gradients(ctf_trainer tr, const int32_t *xy, int n, double *loss, const ctf_mlp_arrays *grads,
+                          void *stream);
+
+/* Copy the FP32 master parameters to host arrays, or replace them from host
+ * or device arrays (Adam moments are kept).  Synchronous. */
+int ctf_trainer_get_params(ctf_trainer tr, const ctf_mlp_arrays *out);
+int ctf_trainer_set_params(ctf_trainer tr, const ctf_mlp_arrays *in);
+
+/* Quantise the current parameters into a learned-decode texture of the
+ * given mode.  For CTF_EVAL_MLP_FP8 the activation ranges are measured on
+ * the GPU over every texel of the texture first. */
+int ctf_trainer_export(ctf_trainer tr, ctf_eval_mode mode, ctf_texture *out);
+
+/* Checkpoint: parameters, Adam moments, step count and description in a
+ * versioned binary file with an FNV-1a checksum.  Loading checks the
+ * magic, version, sizes and checksum (CTF_ERR_CORRUPT on mismatch) and
+ * needs the same exact source texture size. */
+int ctf_trainer_save(ctf_trainer tr, const char *path);
+int ctf_trainer_load(ctf_texture exact_src, const char *path, ctf_trainer *out);
+
+/* Error of a learned-decode texture against an exact block texture of the
+ * same size over every texel: mean squared error of RGB (alpha excluded)
+ * and the largest absolute channel difference.  PSNR = -10 log10(mse).
+ * Synchronous. */
+int ctf_texture_compare(ctf_texture exact_ref, ctf_texture learned, double *mse_rgb, double *max_abs, void *stream);
+
 /* ctf_filter_host for callers that cannot let the library allocate device
  * memory.  The paper has no counterpart: this is a deployment variant.
  * ctf_filter_host stages the host arrays in device buffers that the library

@@ -103,6 +103,17 @@ def _bind_optional(lib):
         "ctf_mlp_export": ([P, P], I),
         "ctf_mlp_decode": ([P, P, I, P, P], I),
         "ctf_sync_check": ([P], I),
+        "ctf_trainer_create": ([P, P, P], I),
+        "ctf_trainer_destroy": ([P], I),
+        "ctf_trainer_step": ([P, ctypes.c_int64, P], I),
+        "ctf_trainer_steps_done": ([P], ctypes.c_int64),
+        "ctf_trainer_gradients": ([P, P, I, P, P, P], I),
+        "ctf_trainer_get_params": ([P, P], I),
+        "ctf_trainer_set_params": ([P, P], I),
+        "ctf_trainer_export": ([P, I, P], I),
+        "ctf_trainer_save": ([P, ctypes.c_char_p], I),
+        "ctf_trainer_load": ([P, ctypes.c_char_p, P], I),
+        "ctf_texture_compare": ([P, P, P, P, P], I),
     }
     for name, (argtypes, restype) in table.items():
         if hasattr(lib, name):
@@ -279,3 +290,114 @@ def ctf_mlp_decode(tex, xy, n, out_rgba, stream=None):
 
 def ctf_sync_check(stream=None):
     _check(load().ctf_sync_check(_stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# Training
+# ---------------------------------------------------------------------------
+class ctf_train_desc(ctypes.Structure):
+    _fields_ = [("latent_w", ctypes.c_int * 2), ("latent_h", ctypes.c_int * 2), ("batch", ctypes.c_int),
+                ("total_steps", ctypes.c_int64), ("lr_weights", ctypes.c_float), ("lr_latents", ctypes.c_float),
+                ("lr_final_frac", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class ctf_mlp_arrays(ctypes.Structure):
+    _fields_ = [("latent", ctypes.c_void_p * 2), ("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p),
+                ("w2", ctypes.c_void_p), ("b2", ctypes.c_void_p), ("w3", ctypes.c_void_p),
+                ("b3", ctypes.c_void_p)]
+
+
+PARAM_NAMES = ("lat0", "lat1", "w1", "b1", "w2", "b2", "w3", "b3")
+
+
+def train_desc(latent_sizes, batch, total_steps, lr_weights=3e-3, lr_latents=3e-2, lr_final_frac=0.1,
+               beta1=0.9, beta2=0.99, eps=1e-10, seed=3):
+    """latent_sizes = ((w0, h0), (w1, h1))."""
+    d = ctf_train_desc()
+    for g in range(2):
+        d.latent_w[g], d.latent_h[g] = int(latent_sizes[g][0]), int(latent_sizes[g][1])
+    d.batch, d.total_steps = int(batch), int(total_steps)
+    d.lr_weights, d.lr_latents, d.lr_final_frac = lr_weights, lr_latents, lr_final_frac
+    d.beta1, d.beta2, d.eps, d.seed = beta1, beta2, eps, int(seed) % 2**64
+    return d
+
+
+def _param_arrays(desc, dtype="float32"):
+    import numpy as np
+    shapes = {"lat0": (desc.latent_h[0], desc.latent_w[0], 8), "lat1": (desc.latent_h[1], desc.latent_w[1], 8),
+              "w1": (64, 16), "b1": (64,), "w2": (64, 64), "b2": (64,), "w3": (4, 64), "b3": (4,)}
+    return {k: np.zeros(v, dtype) for k, v in shapes.items()}
+
+
+def _arrays_struct(d):
+    a = ctf_mlp_arrays()
+    a.latent[0], a.latent[1] = d["lat0"].ctypes.data, d["lat1"].ctypes.data
+    a.w1, a.b1, a.w2, a.b2, a.w3, a.b3 = (d[k].ctypes.data for k in ("w1", "b1", "w2", "b2", "w3", "b3"))
+    return a
+
+
+def ctf_trainer_create(exact_tex, desc):
+    out = ctypes.c_void_p()
+    _check(load().ctf_trainer_create(exact_tex, ctypes.byref(desc), ctypes.byref(out)))
+    return out
+
+
+def ctf_trainer_destroy(tr):
+    _check(load().ctf_trainer_destroy(tr))
+
+
+def ctf_trainer_step(tr, steps, stream=None):
+    _check(load().ctf_trainer_step(tr, int(steps), _stream(stream)))
+
+
+def ctf_trainer_steps_done(tr):
+    return int(load().ctf_trainer_steps_done(tr))
+
+
+def ctf_trainer_gradients(tr, desc, xy, n, stream=None):
+    """(loss, dict of float32 gradient arrays) for device int32 texels xy [n,2]."""
+    g = _param_arrays(desc)
+    loss = ctypes.c_double()
+    a = _arrays_struct(g)
+    _check(load().ctf_trainer_gradients(tr, _ptr(xy), int(n), ctypes.byref(loss), ctypes.byref(a),
+                                        _stream(stream)))
+    return loss.value, g
+
+
+def ctf_trainer_get_params(tr, desc):
+    p = _param_arrays(desc)
+    a = _arrays_struct(p)
+    _check(load().ctf_trainer_get_params(tr, ctypes.byref(a)))
+    return p
+
+
+def ctf_trainer_set_params(tr, params):
+    import numpy as np
+    p = {k: np.ascontiguousarray(v, dtype=np.float32) for k, v in params.items()}
+    a = _arrays_struct(p)
+    _check(load().ctf_trainer_set_params(tr, ctypes.byref(a)))
+
+
+def ctf_trainer_export(tr, mode):
+    out = ctypes.c_void_p()
+    _check(load().ctf_trainer_export(tr, int(mode), ctypes.byref(out)))
+    return out
+
+
+def ctf_trainer_save(tr, path):
+    _check(load().ctf_trainer_save(tr, path.encode()))
+
+
+def ctf_trainer_load(exact_tex, path):
+    out = ctypes.c_void_p()
+    _check(load().ctf_trainer_load(exact_tex, path.encode(), ctypes.byref(out)))
+    return out
+
+
+def ctf_texture_compare(exact_tex, learned_tex, stream=None):
+    """(mse over RGB, max abs channel error) of a learned texture vs the exact one."""
+    mse, mx = ctypes.c_double(), ctypes.c_double()
+    _check(load().ctf_texture_compare(exact_tex, learned_tex, ctypes.byref(mse), ctypes.byref(mx),
+                                      _stream(stream)))
+    return mse.value, mx.value

@@ -1,0 +1,172 @@
+"""GPU training of the learned decode: gradients against the FP64 oracle's
+backward pass, what training gains, deterministic checkpoint/resume, and the
+FP8 export against the FP64 oracle."""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_17770_gb300 import _ctf, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2506_17770_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _decoded(blocks, Wt, Ht, xs, ys):
+    return np.stack([oracle.decode_rgba8(blocks, Wt, Ht, int(x), int(y)) for x, y in zip(xs, ys)]) / 255.0
+
+
+def test_gradients_match_fp64_oracle():
+    Wt = Ht = 64
+    blocks = synth.random_blocks(Wt, Ht, seed=21)
+    tex = _ctf.ctf_texture_create(Wt, Ht, blocks)
+    desc = _ctf.train_desc(((16, 16), (8, 8)), batch=1024, total_steps=10)
+    tr = _ctf.ctf_trainer_create(tex, desc)
+    try:
+        g = np.random.default_rng(7)
+        params = {"lat0": g.normal(0, 0.7, (16, 16, 8)), "lat1": g.normal(0, 0.7, (8, 8, 8)),
+                  "w1": g.normal(0, 0.4, (64, 16)), "b1": g.normal(0, 0.1, 64),
+                  "w2": g.normal(0, 0.18, (64, 64)), "b2": g.normal(0, 0.1, 64),
+                  "w3": g.normal(0, 0.15, (4, 64)), "b3": g.normal(0.5, 0.1, 4)}
+        params = {k: v.astype(np.float32) for k, v in params.items()}
+        _ctf.ctf_trainer_set_params(tr, params)
+        back = _ctf.ctf_trainer_get_params(tr, desc)
+        for k in params:
+            np.testing.assert_array_equal(back[k], params[k])
+        n = 700  # more than one CTA (512 texels) and a ragged tail
+        xs, ys = g.integers(0, Wt, n), g.integers(0, Ht, n)
+        xy = torch.from_numpy(np.stack([xs, ys], -1).astype(np.int32)).cuda()
+        loss, grads = _ctf.ctf_trainer_gradients(tr, desc, xy, n)
+        mlp = oracle.MLP((params["lat0"], params["lat1"]), params["w1"], params["b1"], params["w2"],
+                         params["b2"], params["w3"], params["b3"], saturate=False)
+        ref_loss, ref = oracle.mlp_loss_grad(mlp, Wt, Ht, xs, ys, _decoded(blocks, Wt, Ht, xs, ys))
+        assert loss == pytest.approx(ref_loss, rel=2e-5)
+        for k in _ctf.PARAM_NAMES:
+            scale = np.abs(ref[k]).max()
+            assert scale > 0, k
+            err = np.abs(grads[k] - ref[k]).max()
+            assert err <= 2e-4 * scale + 1e-9, (k, err, scale)
+    finally:
+        _ctf.ctf_trainer_destroy(tr)
+        _ctf.ctf_texture_destroy(tex)
+
+
+@pytest.fixture(scope="module")
+def procedural256():
+    rgba = synth.procedural_rgba8(256, seed=1)
+    blocks = synth.encode_blocks(rgba)
+    tex = _ctf.ctf_texture_create(256, 256, blocks)
+    yield tex, blocks
+    _ctf.ctf_texture_destroy(tex)
+
+
+def _psnr(mse):
+    return -10.0 * math.log10(max(mse, 1e-30))
+
+
+def test_training_gains_over_the_untrained_network(procedural256):
+    """What the trained network gains: PSNR of the learned decode against the
+    exact decode before and after training, both quantised to FP16."""
+    tex, _ = procedural256
+    desc = _ctf.train_desc(((64, 64), (32, 32)), batch=32768, total_steps=300)
+    tr = _ctf.ctf_trainer_create(tex, desc)
+    try:
+        before = _ctf.ctf_trainer_export(tr, _ctf.CTF_EVAL_MLP_FP16)
+        mse0, _ = _ctf.ctf_texture_compare(tex, before)
+        _ctf.ctf_texture_destroy(before)
+        _ctf.ctf_trainer_step(tr, 300)
+        after = _ctf.ctf_trainer_export(tr, _ctf.CTF_EVAL_MLP_FP16)
+        mse1, mx1 = _ctf.ctf_texture_compare(tex, after)
+        _ctf.ctf_sync_check()
+        _ctf.ctf_texture_destroy(after)
+        print(f"PSNR untrained {_psnr(mse0):.2f} dB -> trained {_psnr(mse1):.2f} dB (max abs {mx1:.3f})")
+        assert _psnr(mse1) > _psnr(mse0) + 12.0
+        assert _psnr(mse1) > 26.0
+        assert _ctf.ctf_trainer_steps_done(tr) == 300
+    finally:
+        _ctf.ctf_trainer_destroy(tr)
+
+
+def test_checkpoint_resume_is_bit_identical(procedural256):
+    tex, _ = procedural256
+    desc = _ctf.train_desc(((64, 64), (32, 32)), batch=8192, total_steps=20, seed=99)
+    tr = _ctf.ctf_trainer_create(tex, desc)
+    d = tempfile.mkdtemp()
+    path = os.path.join(d, "ckpt.bin")
+    try:
+        _ctf.ctf_trainer_step(tr, 6)
+        _ctf.ctf_trainer_save(tr, path)
+        _ctf.ctf_trainer_step(tr, 6)
+        straight = _ctf.ctf_trainer_get_params(tr, desc)
+        tr2 = _ctf.ctf_trainer_load(tex, path)
+        try:
+            assert _ctf.ctf_trainer_steps_done(tr2) == 6
+            _ctf.ctf_trainer_step(tr2, 6)
+            resumed = _ctf.ctf_trainer_get_params(tr2, desc)
+        finally:
+            _ctf.ctf_trainer_destroy(tr2)
+        for k in straight:
+            assert np.array_equal(straight[k].view(np.uint32), resumed[k].view(np.uint32)), k
+        # a corrupted checkpoint is refused
+        raw = bytearray(open(path, "rb").read())
+        raw[100] ^= 0x40
+        bad = os.path.join(d, "bad.bin")
+        open(bad, "wb").write(bytes(raw))
+        with pytest.raises(_ctf.CtfError) as ei:
+            _ctf.ctf_trainer_load(tex, bad)
+        assert ei.value.status == _ctf.CTF_ERR_CORRUPT
+    finally:
+        _ctf.ctf_trainer_destroy(tr)
+
+
+def test_fp8_export_matches_fp64_oracle(procedural256):
+    """E4M3 activations: relative rounding 2^-4 plus half the subnormal
+    spacing (2^-10 in scaled units) per input, propagated through |W_eff|
+    as for FP16; W_eff = s_o q[o][k] / a_k exactly as stored."""
+    tex, _ = procedural256
+    desc = _ctf.train_desc(((64, 64), (32, 32)), batch=16384, total_steps=60)
+    tr = _ctf.ctf_trainer_create(tex, desc)
+    try:
+        _ctf.ctf_trainer_step(tr, 60)
+        t8 = _ctf.ctf_trainer_export(tr, _ctf.CTF_EVAL_MLP_FP8)
+        st = _ctf.ctf_mlp_export(t8, ((64, 64, 8), (32, 32, 8)))
+        weff = [st["ws0"][:, None] * st["w1"] / st["as0"][None, :],
+                st["ws1"][:, None] * st["w2"] / st["as1"][None, :],
+                st["ws2"][:, None] * st["w3"] / st["as2"][None, :]]
+        weff = [w.astype(np.float64) for w in weff]
+        mlp = oracle.MLP((st["lat0"], st["lat1"]), weff[0], st["b1"], weff[1], st["b2"], weff[2], st["b3"])
+        g = np.random.default_rng(3)
+        n = 2000
+        xs, ys = g.integers(0, 256, n), g.integers(0, 256, n)
+        d_xy = torch.from_numpy(np.stack([xs, ys], -1).astype(np.int32)).cuda()
+        out = torch.empty((n, 4), device="cuda")
+        _ctf.ctf_mlp_decode(t8, d_xy, n, out)
+        _ctf.ctf_sync_check()
+        got = out.cpu().numpy()
+        ref = oracle.mlp_decode(mlp, 256, 256, xs, ys)
+        F = np.stack([oracle.mlp_features(mlp, 256, 256, int(x), int(y)) for x, y in zip(xs, ys)])
+        h1 = np.maximum(F @ weff[0].T + st["b1"], 0)
+        h2 = np.maximum(h1 @ weff[1].T + st["b2"], 0)
+        u = 2.0 ** -4
+        e_f = u * np.abs(F) + 2.0 ** -10 * st["as0"]
+        e_h1 = u * h1 + 2.0 ** -10 * st["as1"] + e_f @ np.abs(weff[0]).T
+        e_h2 = u * h2 + 2.0 ** -10 * st["as2"] + e_h1 @ np.abs(weff[1]).T
+        tol = 2.0 * (e_h2 @ np.abs(weff[2]).T) + 1e-5
+        err = np.abs(got - ref)
+        assert np.all(err <= tol), (err.max(), (err / tol).max())
+        _ctf.ctf_texture_destroy(t8)
+    finally:
+        _ctf.ctf_trainer_destroy(tr)
