@@ -298,6 +298,55 @@ int ctf_trainer_load(ctf_texture exact_src, const char *path, ctf_trainer *out);
  * Synchronous. */
 int ctf_texture_compare(ctf_texture exact_ref, ctf_texture learned, double *mse_rgb, double *max_abs, void *stream);
 
+/* Batched filtering: many views, each with its own texture (block or
+ * learned), size, magnification and buffers, in one persistent launch.
+ * Work items are 16 warp tiles of a block view or 4 warp tiles of a learned
+ * view; persistent CTAs of 128 threads take items_per_fetch items at a time
+ * from an atomic counter until none are left.  Every view is filtered
+ * exactly as ctf_filter would filter it with the same options. */
+typedef struct {
+    ctf_texture tex;            /* block or learned-decode texture */
+    const float *uv, *jac;      /* device, [height][width][2] and [4] */
+    const uint8_t *coverage;    /* device or NULL */
+    int width, height;          /* [0, 32768] */
+    int view_id;                /* third word of the STF counter */
+    float *out_rgba;            /* device [height][width][4] */
+    uint8_t *out_evals;         /* device [height][width] or NULL */
+} ctf_view;
+
+/* Launch shape of a batch; NULL means the defaults in brackets.
+ *   filter           tile shape, budget, mask_dim, edge_remap (as ctf_filter)
+ *   items_per_fetch  items taken per atomic fetch, 1..64              [4]
+ *   ctas_per_sm      persistent CTAs per SM, 1..4                      [4] */
+typedef struct {
+    ctf_filter_opts filter;
+    int items_per_fetch;
+    int ctas_per_sm;
+} ctf_batch_opts;
+
+/* Filter nviews (1..4096) views in one launch (asynchronous unless stats is
+ * given, in which case the counters are summed over all views). */
+int ctf_filter_batch(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t seed, const ctf_batch_opts *opts,
+                     ctf_stats *stats, void *stream);
+
+/* The same batch captured once into a CUDA graph (counter reset + the
+ * persistent launch) and replayed with ctf_batch_graph_launch.  The views'
+ * buffers are baked in: they must stay valid and at the same addresses. */
+typedef struct ctf_batch_graph_s *ctf_batch_graph;
+int ctf_batch_graph_create(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t seed,
+                           const ctf_batch_opts *opts, ctf_batch_graph *out);
+int ctf_batch_graph_launch(ctf_batch_graph g, void *stream);
+int ctf_batch_graph_destroy(ctf_batch_graph g);
+
+/* Time every warp tile (8x4, 4x8, 16x2) x items_per_fetch (1, 2, 4, 8) x
+ * ctas_per_sm (2, 4) on these views (best of 3 runs each, CUDA events on the
+ * stream) and return the fastest in *best (budget, mask_dim and edge_remap
+ * from *base, or the defaults).  Note that the warp tile changes which
+ * warps succeed, hence the texel choices: every tile shape is a valid
+ * filtering, and results are reproducible for a fixed shape. */
+int ctf_batch_autotune(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t seed, const ctf_batch_opts *base,
+                       ctf_batch_opts *best, double *best_ms, void *stream);
+
 /* ctf_filter_host for callers that cannot let the library allocate device
  * memory.  The paper has no counterpart: this is a deployment variant.
  * ctf_filter_host stages the host arrays in device buffers that the library

@@ -114,6 +114,11 @@ def _bind_optional(lib):
         "ctf_trainer_save": ([P, ctypes.c_char_p], I),
         "ctf_trainer_load": ([P, ctypes.c_char_p, P], I),
         "ctf_texture_compare": ([P, P, P, P, P], I),
+        "ctf_filter_batch": ([P, I, I, U64, P, P, P], I),
+        "ctf_batch_graph_create": ([P, I, I, U64, P, P], I),
+        "ctf_batch_graph_launch": ([P, P], I),
+        "ctf_batch_graph_destroy": ([P], I),
+        "ctf_batch_autotune": ([P, I, I, U64, P, P, P, P], I),
     }
     for name, (argtypes, restype) in table.items():
         if hasattr(lib, name):
@@ -401,3 +406,74 @@ def ctf_texture_compare(exact_tex, learned_tex, stream=None):
     _check(load().ctf_texture_compare(exact_tex, learned_tex, ctypes.byref(mse), ctypes.byref(mx),
                                       _stream(stream)))
     return mse.value, mx.value
+
+
+# ---------------------------------------------------------------------------
+# Batched views
+# ---------------------------------------------------------------------------
+class ctf_view(ctypes.Structure):
+    _fields_ = [("tex", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("jac", ctypes.c_void_p),
+                ("coverage", ctypes.c_void_p), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("view_id", ctypes.c_int), ("out_rgba", ctypes.c_void_p), ("out_evals", ctypes.c_void_p)]
+
+
+class ctf_batch_opts(ctypes.Structure):
+    _fields_ = [("filter", ctf_filter_opts), ("items_per_fetch", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+    def as_dict(self):
+        f = self.filter
+        return {"tile_w": f.tile_w, "tile_h": f.tile_h, "budget": f.budget, "mask_dim": f.mask_dim,
+                "edge_remap": f.edge_remap, "items_per_fetch": self.items_per_fetch,
+                "ctas_per_sm": self.ctas_per_sm}
+
+
+def batch_opts(tile_w=8, tile_h=4, budget=32, mask_dim=16, edge_remap=1, items_per_fetch=4, ctas_per_sm=4):
+    o = ctf_batch_opts()
+    o.filter = ctf_filter_opts(tile_w, tile_h, budget, mask_dim, edge_remap)
+    o.items_per_fetch, o.ctas_per_sm = items_per_fetch, ctas_per_sm
+    return o
+
+
+def views_array(views):
+    """views: list of dicts with tex, uv, jac, coverage, width, height, view_id, out_rgba, out_evals."""
+    arr = (ctf_view * len(views))()
+    for i, v in enumerate(views):
+        arr[i] = ctf_view(v["tex"].value if hasattr(v["tex"], "value") else v["tex"], _ptr(v["uv"]), _ptr(v["jac"]),
+                          _ptr(v.get("coverage")), int(v["width"]), int(v["height"]), int(v.get("view_id", i)),
+                          _ptr(v["out_rgba"]), _ptr(v.get("out_evals")))
+    return arr
+
+
+def ctf_filter_batch(views, alg, seed, opts=None, stats=False, stream=None):
+    arr = views if isinstance(views, ctypes.Array) else views_array(views)
+    st = ctf_stats() if stats else None
+    _check(load().ctf_filter_batch(arr, len(arr), _alg(alg), int(seed) % 2**64,
+                                   ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.byref(st) if st is not None else None, _stream(stream)))
+    return st.as_dict() if st is not None else None
+
+
+def ctf_batch_graph_create(views, alg, seed, opts=None):
+    arr = views if isinstance(views, ctypes.Array) else views_array(views)
+    out = ctypes.c_void_p()
+    _check(load().ctf_batch_graph_create(arr, len(arr), _alg(alg), int(seed) % 2**64,
+                                         ctypes.byref(opts) if opts is not None else None, ctypes.byref(out)))
+    return out
+
+
+def ctf_batch_graph_launch(g, stream=None):
+    _check(load().ctf_batch_graph_launch(g, _stream(stream)))
+
+
+def ctf_batch_graph_destroy(g):
+    _check(load().ctf_batch_graph_destroy(g))
+
+
+def ctf_batch_autotune(views, alg, seed, base=None, stream=None):
+    arr = views if isinstance(views, ctypes.Array) else views_array(views)
+    best = ctf_batch_opts()
+    ms = ctypes.c_double()
+    _check(load().ctf_batch_autotune(arr, len(arr), _alg(alg), int(seed) % 2**64,
+                                     ctypes.byref(base) if base is not None else None, ctypes.byref(best),
+                                     ctypes.byref(ms), _stream(stream)))
+    return best, ms.value

@@ -35,292 +35,10 @@
 #include "ctf_mlp.cuh"
 #include "ctf_select.cuh"
 #include "tc_ops.cuh"
+#include "ctf_mlp_chain.cuh"
 
 namespace ctf {
 namespace {
-
-constexpr int kRows = 128;
-constexpr int kTmemCols = 128;
-constexpr uint32_t kMaxTries = 1u << 24;  // bounded mbarrier polls (about a second)
-
-// Dynamic shared memory of one CTA (offsets in bytes).
-constexpr int kSmImg = 0;
-constexpr int kSmX = 14080;              // A operand of layer 1: 128 x 32 B
-constexpr int kSmH = kSmX + 4096;        // A operand of layers 2 and 3: 128 x 128 B
-constexpr int kSmBar = kSmH + 16384;     // mbarrier (8 B)
-constexpr int kSmTmem = kSmBar + 8;      // TMEM base address (4 B)
-constexpr int kSmList = kSmBar + 64;     // List Merge tables (4 x ListTable)
-constexpr int kSmBytes = kSmList + 4 * (int)sizeof(ListTable);
-// Reserve enough shared memory that at most 4 CTAs share an SM: 4 x 128 TMEM
-// columns fill the SM's 512.
-constexpr int kSmRequest = 48 * 1024;
-static_assert(kSmBytes <= kSmRequest, "shared memory layout");
-
-struct Chain {
-    unsigned char *sm;
-    uint32_t tmem;
-    uint64_t *bar;
-    uint32_t phase;
-};
-
-// Features of texel (x, y) (inside the texture) in FP32.
-__device__ __forceinline__ void texel_features(const MlpDevice &m, int x, int y, float f[kMlpIn]) {
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        const float gx = __fsub_rn(__fmul_rn(__fadd_rn((float)x, 0.5f), m.sx[g]), 0.5f);
-        const float gy = __fsub_rn(__fmul_rn(__fadd_rn((float)y, 0.5f), m.sy[g]), 0.5f);
-        const float fx0 = floorf(gx), fy0 = floorf(gy);
-        const float fx = __fsub_rn(gx, fx0), fy = __fsub_rn(gy, fy0);
-        const int x0 = (int)fx0, y0 = (int)fy0;
-        const int xa = min(max(x0, 0), m.gw[g] - 1), xb = min(max(x0 + 1, 0), m.gw[g] - 1);
-        const int ya = min(max(y0, 0), m.gh[g] - 1), yb = min(max(y0 + 1, 0), m.gh[g] - 1);
-        const uint4 *L = reinterpret_cast<const uint4 *>(m.lat[g]);
-        const uint4 q00 = __ldg(L + (size_t)ya * m.gw[g] + xa);
-        const uint4 q10 = __ldg(L + (size_t)ya * m.gw[g] + xb);
-        const uint4 q01 = __ldg(L + (size_t)yb * m.gw[g] + xa);
-        const uint4 q11 = __ldg(L + (size_t)yb * m.gw[g] + xb);
-        const float ofx = __fsub_rn(1.f, fx), ofy = __fsub_rn(1.f, fy);
-        const float w00 = __fmul_rn(ofx, ofy), w10 = __fmul_rn(fx, ofy), w01 = __fmul_rn(ofx, fy),
-                    w11 = __fmul_rn(fx, fy);
-        const __half2 *h00 = reinterpret_cast<const __half2 *>(&q00);
-        const __half2 *h10 = reinterpret_cast<const __half2 *>(&q10);
-        const __half2 *h01 = reinterpret_cast<const __half2 *>(&q01);
-        const __half2 *h11 = reinterpret_cast<const __half2 *>(&q11);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float2 a = __half22float2(h00[c]), b = __half22float2(h10[c]);
-            const float2 cc = __half22float2(h01[c]), d = __half22float2(h11[c]);
-            f[g * 8 + 2 * c] = __fmaf_rn(w11, d.x, __fmaf_rn(w01, cc.x, __fmaf_rn(w10, b.x, __fmul_rn(w00, a.x))));
-            f[g * 8 + 2 * c + 1] =
-                __fmaf_rn(w11, d.y, __fmaf_rn(w01, cc.y, __fmaf_rn(w10, b.y, __fmul_rn(w00, a.y))));
-        }
-    }
-}
-
-__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
-    const __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&h);
-}
-
-// E4M3 pair: bytes of a (low) and b (high), round to nearest, saturating.
-__device__ __forceinline__ uint16_t pack_e4m3x2(float a, float b) {
-    const __nv_fp8x2_storage_t v = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-    return (uint16_t)v;
-}
-
-// Row `row` of the layer-1 A operand from 16 features.
-__device__ __forceinline__ void store_x_row(unsigned char *sm, int row, const float f[kMlpIn], bool fp8,
-                                            const float *inv_a) {
-    unsigned char *X = sm + kSmX;
-    if (!fp8) {
-        uint4 c0 = make_uint4(pack_half2(f[0], f[1]), pack_half2(f[2], f[3]), pack_half2(f[4], f[5]),
-                              pack_half2(f[6], f[7]));
-        uint4 c1 = make_uint4(pack_half2(f[8], f[9]), pack_half2(f[10], f[11]), pack_half2(f[12], f[13]),
-                              pack_half2(f[14], f[15]));
-        *reinterpret_cast<uint4 *>(X + core_offset(row, 0, 16, 2)) = c0;
-        *reinterpret_cast<uint4 *>(X + core_offset(row, 8, 16, 2)) = c1;
-    } else {
-        // K padded to 32: features 0..15 in the first 16-byte chunk, zeros after
-        uint32_t w[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint16_t lo =
-                pack_e4m3x2(__fmul_rn(f[4 * i], inv_a[4 * i]), __fmul_rn(f[4 * i + 1], inv_a[4 * i + 1]));
-            const uint16_t hi =
-                pack_e4m3x2(__fmul_rn(f[4 * i + 2], inv_a[4 * i + 2]), __fmul_rn(f[4 * i + 3], inv_a[4 * i + 3]));
-            w[i] = (uint32_t)lo | ((uint32_t)hi << 16);
-        }
-        *reinterpret_cast<uint4 *>(X + core_offset(row, 0, 32, 1)) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4 *>(X + core_offset(row, 16, 32, 1)) = make_uint4(0u, 0u, 0u, 0u);
-    }
-}
-
-__device__ __forceinline__ void store_zero_x_row(unsigned char *sm, int row) {
-    unsigned char *X = sm + kSmX;
-    *reinterpret_cast<uint4 *>(X + (row / 8) * 256 + (row % 8) * 16) = make_uint4(0u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4 *>(X + (row / 8) * 256 + 128 + (row % 8) * 16) = make_uint4(0u, 0u, 0u, 0u);
-}
-
-// Hidden epilogue: TMEM columns [col, col+64) of this thread's row -> bias,
-// ReLU -> next layer's A operand (FP16, or E4M3 after multiplying by the
-// inverse activation scales of the next layer's inputs).
-__device__ __forceinline__ void hidden_epilogue(unsigned char *sm, uint32_t taddr, const float *bias,
-                                                const float *oscale, const float *inv_a, bool fp8, int row) {
-    float d[64];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) tc::tmem_ld16(taddr + 16 * q, d + 16 * q);
-    tc::tmem_wait_ld();
-    unsigned char *H = sm + kSmH;
-    if (!fp8) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            uint32_t w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int k = 8 * c + 2 * i;
-                const float a = fmaxf(__fadd_rn(d[k], bias[k]), 0.f);
-                const float b = fmaxf(__fadd_rn(d[k + 1], bias[k + 1]), 0.f);
-                w[i] = pack_half2(a, b);
-            }
-            *reinterpret_cast<uint4 *>(H + core_offset(row, 8 * c, 64, 2)) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            uint32_t w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                float v[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int k = 16 * c + 4 * i + e;
-                    const float h = fmaxf(__fmaf_rn(d[k], oscale[k], bias[k]), 0.f);
-                    v[e] = __fmul_rn(h, inv_a[k]);
-                }
-                w[i] = (uint32_t)pack_e4m3x2(v[0], v[1]) | ((uint32_t)pack_e4m3x2(v[2], v[3]) << 16);
-            }
-            *reinterpret_cast<uint4 *>(H + core_offset(row, 16 * c, 64, 1)) = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-    }
-}
-
-// The three layers for the 128 rows whose layer-1 operand is in place.
-// Every thread of the CTA calls it; returns false (for every thread alike)
-// if an MMA did not complete within the wait bound.
-__device__ __forceinline__ bool mlp_chain(Chain &ch, bool fp8, float4 &out, int *err) {
-    const int tid = threadIdx.x, warp = tid >> 5;
-    unsigned char *sm = ch.sm;
-    const float *b1 = reinterpret_cast<const float *>(sm + kImgB1);
-    const float *b2 = reinterpret_cast<const float *>(sm + kImgB2);
-    const float *b3 = reinterpret_cast<const float *>(sm + kImgB3);
-    const float *s1 = reinterpret_cast<const float *>(sm + kImgS1);
-    const float *s2 = reinterpret_cast<const float *>(sm + kImgS2);
-    const float *s3 = reinterpret_cast<const float *>(sm + kImgS3);
-    const float *a2 = reinterpret_cast<const float *>(sm + kImgA2);
-    const float *a3 = reinterpret_cast<const float *>(sm + kImgA3);
-    const uint32_t lane_base = ch.tmem + ((uint32_t)(32 * warp) << 16);
-    const uint32_t sX = tc::smem_addr(sm + kSmX), sH = tc::smem_addr(sm + kSmH);
-    const uint32_t sW1 = tc::smem_addr(sm + kImgW1), sW2 = tc::smem_addr(sm + kImgW2),
-                   sW3 = tc::smem_addr(sm + kImgW3);
-    // K-major no-swizzle descriptors; one MMA covers K = 16 (FP16) or 32 (E4M3)
-    const uint32_t esz = fp8 ? 1u : 2u;
-    const uint32_t kstep_bytes = 256;  // two 16-byte core-matrix columns = 32 bytes of K per row group
-    const uint32_t sboX = fp8 ? 256u : 256u;   // K = 32 B per row either way
-    const uint32_t sboH = fp8 ? 512u : 1024u;  // 64 elements per row
-    const int nk_h = fp8 ? 2 : 4;              // MMAs over K = 64
-    const uint32_t id64 = fp8 ? tc::idesc_e4m3(128, 64) : tc::idesc_f16(128, 64);
-    const uint32_t id16 = fp8 ? tc::idesc_e4m3(128, 16) : tc::idesc_f16(128, 16);
-    (void)esz;
-
-    bool timed_out = false;
-    // ---- layer 1: D[0..64) = X * W1^T
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-        tc::fence_after_sync();
-        const uint64_t a = tc::smem_desc(sX, 128, sboX), b = tc::smem_desc(sW1, 128, sboX);
-        if (fp8) tc::mma_e4m3(ch.tmem, a, b, id64, false);
-        else tc::mma_f16(ch.tmem, a, b, id64, false);
-        tc::commit(ch.bar);
-    }
-    timed_out |= !tc::mbar_wait(ch.bar, ch.phase, kMaxTries);
-    ch.phase ^= 1u;
-    tc::fence_after_sync();
-    hidden_epilogue(sm, lane_base + 0, b1, s1, a2, fp8, tid);
-    // ---- layer 2: D[64..128) = H1 * W2^T
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    if (__syncthreads_or(timed_out)) {
-        if (tid == 0) atomicExch(err, CTF_ERR_TIMEOUT);
-        return false;
-    }
-    if (tid == 0) {
-        tc::fence_after_sync();
-        for (int j = 0; j < nk_h; ++j) {
-            const uint64_t a = tc::smem_desc(sH + j * kstep_bytes, 128, sboH);
-            const uint64_t b = tc::smem_desc(sW2 + j * kstep_bytes, 128, sboH);
-            if (fp8) tc::mma_e4m3(ch.tmem + 64, a, b, id64, j > 0);
-            else tc::mma_f16(ch.tmem + 64, a, b, id64, j > 0);
-        }
-        tc::commit(ch.bar);
-    }
-    timed_out |= !tc::mbar_wait(ch.bar, ch.phase, kMaxTries);
-    ch.phase ^= 1u;
-    tc::fence_after_sync();
-    // the layer-2 MMAs have read H1, so H2 may overwrite it
-    hidden_epilogue(sm, lane_base + 64, b2, s2, a3, fp8, tid);
-    // ---- layer 3: D[0..16) = H2 * W3^T
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    if (__syncthreads_or(timed_out)) {
-        if (tid == 0) atomicExch(err, CTF_ERR_TIMEOUT);
-        return false;
-    }
-    if (tid == 0) {
-        tc::fence_after_sync();
-        for (int j = 0; j < nk_h; ++j) {
-            const uint64_t a = tc::smem_desc(sH + j * kstep_bytes, 128, sboH);
-            const uint64_t b = tc::smem_desc(sW3 + j * kstep_bytes, 128, sboH);
-            if (fp8) tc::mma_e4m3(ch.tmem, a, b, id16, j > 0);
-            else tc::mma_f16(ch.tmem, a, b, id16, j > 0);
-        }
-        tc::commit(ch.bar);
-    }
-    timed_out |= !tc::mbar_wait(ch.bar, ch.phase, kMaxTries);
-    ch.phase ^= 1u;
-    tc::fence_after_sync();
-    float d[16];
-    tc::tmem_ld16(lane_base + 0, d);
-    tc::tmem_wait_ld();
-    float o[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const float v = fp8 ? __fmaf_rn(d[c], s3[c], b3[c]) : __fadd_rn(d[c], b3[c]);
-        o[c] = fminf(fmaxf(v, 0.f), 1.f);
-    }
-    out = make_float4(o[0], o[1], o[2], o[3]);
-    tc::fence_before_sync();
-    if (__syncthreads_or(timed_out)) {
-        if (tid == 0) atomicExch(err, CTF_ERR_TIMEOUT);
-        return false;
-    }
-    return true;
-}
-
-// CTA set-up shared by both kernels: operand image into shared memory,
-// mbarrier, 128 TMEM columns.
-__device__ __forceinline__ void chain_setup(Chain &ch, unsigned char *sm, const MlpDevice &m) {
-    const uint4 *src = m.img;
-    uint4 *dst = reinterpret_cast<uint4 *>(sm + kSmImg);
-    for (int i = threadIdx.x; i < kImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kSmBar);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kSmTmem);
-    if (threadIdx.x == 0) {
-        tc::mbar_init(bar, 1);
-        tc::fence_mbar_init();
-    }
-    if ((threadIdx.x >> 5) == 0) {
-        tc::tmem_alloc(tslot, kTmemCols);
-        tc::tmem_relinquish();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    ch.sm = sm;
-    ch.bar = bar;
-    ch.tmem = *tslot;
-    ch.phase = 0;
-}
-
-__device__ __forceinline__ void chain_teardown(const Chain &ch) {
-    tc::fence_before_sync();
-    __syncthreads();
-    if ((threadIdx.x >> 5) == 0) {
-        tc::fence_after_sync();
-        tc::tmem_dealloc(ch.tmem, kTmemCols);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Decode an explicit list of texels.
@@ -355,7 +73,6 @@ __global__ void __launch_bounds__(kRows) mlp_decode_kernel(const MlpDevice m, in
 // ---------------------------------------------------------------------------
 template <int ALG, int TW, int MD>
 __global__ void __launch_bounds__(kRows) mlp_filter_kernel(const ExactParams p, const MlpDevice m, int *err) {
-    constexpr int TH = 32 / TW;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned long long block_stats[kNumStats];
     Chain ch;
@@ -369,133 +86,14 @@ __global__ void __launch_bounds__(kRows) mlp_filter_kernel(const ExactParams p, 
     }
     if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
     __syncthreads();
-    const int tx = lane % TW, ty = lane / TW;
     const uint32_t lt = lanemask_lt();
-    const float fW = (float)p.Wt, fH = (float)p.Ht;
     Counters cnt;
 #pragma unroll
     for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
     const long long n_iter = (p.n_tiles + 3) / 4;
     bool ok = true;
     for (long long it = blockIdx.x; it < n_iter && ok; it += gridDim.x) {
-        const long long tile = it * 4 + warp;
-        const bool valid = tile < p.n_tiles;
-        const int bx = valid ? (int)(tile % p.tiles_x) : 0, by = valid ? (int)(tile / p.tiles_x) : 0;
-        const int px = bx * TW + tx, py = by * TH + ty;
-        const bool inside = valid && px < p.W && py < p.H;
-        const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
-        PixelSetup ps;
-        float2 uv = make_float2(0.f, 0.f);
-        float4 jac = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool covered = inside;
-        if (inside) {
-            uv = __ldcs(p.uv + idx);
-            if (ALG >= ALG_LIST) jac = __ldcs(p.jac + idx);
-            if (p.cov) covered = __ldcs(p.cov + idx) != 0;
-        }
-        ps.active = covered;
-        setup_coords(uv, fW, fH, ps);
-
-        float4 result = make_float4(0.f, 0.f, 0.f, 0.f);
-        uint8_t count = 0;
-        if (ALG == ALG_4TAP) {
-            const uint32_t A = __ballot_sync(FULL, ps.active);
-            if (valid) {
-                cnt.v[kStatTilesTotal] += 1;
-                if (A == 0) {
-                    cnt.v[kStatTilesEmpty] += 1;
-                } else {
-                    cnt.v[kStatPixelsActive] += __popc(A);
-                    cnt.v[kStatTilesDirect] += 1;
-                    cnt.v[kStatTexelEvals] += 4 * __popc(A);
-                }
-            }
-            float4 tap[4];
-#pragma unroll 1
-            for (int k = 0; k < 4; ++k) {
-                if (ps.active) {
-                    const int x = min(max(ps.ulx + (k & 1), 0), p.Wt - 1);
-                    const int y = min(max(ps.uly + (k >> 1), 0), p.Ht - 1);
-                    float f[kMlpIn];
-                    texel_features(m, x, y, f);
-                    store_x_row(sm, threadIdx.x, f, m.fp8, inv_a1);
-                } else {
-                    store_zero_x_row(sm, threadIdx.x);
-                }
-                ok = mlp_chain(ch, m.fp8, tap[k], err);
-                if (!ok) break;
-            }
-            if (!ok) break;
-            if (ps.active) {
-                float w[4];
-                bilinear_weights(ps.s, ps.t, w);
-                float r = 0.f, g = 0.f, b = 0.f, a = 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    r = __fmaf_rn(w[k], tap[k].x, r);
-                    g = __fmaf_rn(w[k], tap[k].y, g);
-                    b = __fmaf_rn(w[k], tap[k].z, b);
-                    a = __fmaf_rn(w[k], tap[k].w, a);
-                }
-                result = make_float4(r, g, b, a);
-                count = 4;
-            }
-        } else {
-            Selection sel;
-            if (valid) {
-                sel = select_tile<ALG, MD>(p, ps, jac, px, py, lane, lt, T, cnt);
-            } else {
-                sel.path = PATH_EMPTY;
-                sel.produce = false;
-                sel.count = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) sel.src[k] = lane;
-            }
-            // step 2: the lane's texel goes into the lane's own row
-            if (sel.produce) {
-                const int x = min(max(sel.tx, 0), p.Wt - 1), y = min(max(sel.ty, 0), p.Ht - 1);
-                float f[kMlpIn];
-                texel_features(m, x, y, f);
-                store_x_row(sm, threadIdx.x, f, m.fp8, inv_a1);
-            } else {
-                store_zero_x_row(sm, threadIdx.x);
-            }
-            float4 val;
-            ok = mlp_chain(ch, m.fp8, val, err);
-            if (!ok) break;
-            if (sel.path == PATH_SUCCESS) {
-                // step 3: gather the 2x2 taps from the producing lanes
-                float4 tap[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    tap[k].x = __shfl_sync(FULL, val.x, sel.src[k]);
-                    tap[k].y = __shfl_sync(FULL, val.y, sel.src[k]);
-                    tap[k].z = __shfl_sync(FULL, val.z, sel.src[k]);
-                    tap[k].w = __shfl_sync(FULL, val.w, sel.src[k]);
-                }
-                if (ps.active) {
-                    float w[4];
-                    bilinear_weights(ps.s, ps.t, w);
-                    float r = 0.f, g = 0.f, b = 0.f, a = 0.f;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        r = __fmaf_rn(w[k], tap[k].x, r);
-                        g = __fmaf_rn(w[k], tap[k].y, g);
-                        b = __fmaf_rn(w[k], tap[k].z, b);
-                        a = __fmaf_rn(w[k], tap[k].w, a);
-                    }
-                    result = make_float4(r, g, b, a);
-                    count = sel.count;
-                }
-            } else if (ps.active) {
-                result = val;
-                count = 1;
-            }
-        }
-        if (inside) {
-            __stcs(p.out + idx, result);
-            if (p.evals) p.evals[idx] = count;
-        }
+        ok = mlp_warp_tile<ALG, TW, MD>(p, m, ch, it * 4 + warp, lane, lt, T, cnt, inv_a1, err);
     }
     if (p.stats) {
         if (lane == 0) {
