@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -50,6 +51,9 @@ def parse_args():
     ap.add_argument("--workload", choices=["frame1080", "frame2160", "plane128"], default="frame1080")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline only (for profiling)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-decode workload")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-views workload")
+    ap.add_argument("--train-steps", type=int, default=256, help="training steps of 262144 texels (learned)")
     return ap.parse_args()
 
 
@@ -90,6 +94,14 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def measured_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured burst bf16"
+    except Exception:
+        return 1900.0, "fallback"
 
 
 def kernel_source_hash():
@@ -182,6 +194,186 @@ def run_cpu_oracle(sc, blocks, Wt, Ht, alg, opts, seconds: float, max_frames: in
         if el >= seconds or frames >= max_frames:
             break
     return frames, el, ev_total
+
+
+def _timed_views(launch, steps, warmup, flush, stream):
+    """Sum of per-launch CUDA-event times (ms) with L2 flushed before each."""
+    import torch
+    for _ in range(warmup):
+        if flush is not None:
+            flush.zero_()
+        launch()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        if flush is not None:
+            flush.zero_()
+        a.record(stream)
+        launch()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def bench_learned(args, dev, stream, flush, peaks):
+    """Learned texel decode: a 4096^2 procedural texture (6 octaves of
+    gradient noise + checker edges), block-encoded, learned by the library's
+    trainer into two latent grids (1024^2, 512^2, 8 ch) and a 16-64-64-4 MLP
+    from 256 x 262144 = 64M texels of its exact decode; then a 3840x2160 view
+    with magnification log-uniform in [1, 16] filtered with the learned
+    decode (FP16 and FP8) by per-pixel 4-tap and the collaborative
+    algorithms."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2506_17770_gb300 import _ctf, synth
+    res = {}
+    t0 = time.perf_counter()
+    rgba = synth.procedural_rgba8(4096, device=dev)
+    blocks = synth.encode_blocks(rgba)
+    res["input_gen_s"] = time.perf_counter() - t0
+    exact = _ctf.ctf_texture_create(4096, 4096, blocks)
+    steps = args.train_steps
+    desc = _ctf.train_desc(((1024, 1024), (512, 512)), batch=262144, total_steps=steps, lr_weights=3e-3,
+                           lr_latents=3e-2, seed=3)
+    tr = _ctf.ctf_trainer_create(exact, desc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _ctf.ctf_trainer_step(tr, steps, stream=stream)
+    _ctf.ctf_sync_check(stream)
+    train_s = time.perf_counter() - t0
+    res["training"] = {"steps": steps, "texels": steps * 262144, "seconds": train_s,
+                       "texels_per_s": steps * 262144 / train_s}
+    texs = {"fp16": _ctf.ctf_trainer_export(tr, _ctf.CTF_EVAL_MLP_FP16),
+            "fp8": _ctf.ctf_trainer_export(tr, _ctf.CTF_EVAL_MLP_FP8)}
+    for k, t in texs.items():
+        mse, mx = _ctf.ctf_texture_compare(exact, t, stream=stream)
+        res[f"{k}_texels_vs_exact"] = {"psnr_db": -10 * math.log10(max(mse, 1e-30)), "max_abs": mx}
+    sc = synth.perspective_view(3840, 2160, 4096, 4096, 1.0, 16.0, seed=2)
+    W, H = sc.W, sc.H
+    npix = W * H
+    uv = torch.from_numpy(sc.uv).to(dev)
+    jac = torch.from_numpy(sc.jac).to(dev)
+    cov = torch.from_numpy(sc.coverage).to(dev)
+    out = torch.empty((H, W, 4), device=dev)
+    ev = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    ref_exact = torch.empty((H, W, 4), device=dev)
+    opts11 = {"mask_dim": 11}
+    _ctf.ctf_filter(exact, uv, jac, cov, W, H, 0, "4tap", 0, None, ref_exact, ev, stream=stream)
+    k = max(3, min(args.steps, 20))
+    runs = {}
+    for tname in ("fp16", "fp8"):
+        tex = texs[tname]
+        for alg in ("4tap", "mask", "box", "list_merge"):
+            if tname == "fp8" and alg in ("box", "list_merge"):
+                continue
+            o = opts11 if alg == "mask" else None
+            ms = _timed_views(lambda: _ctf.ctf_filter(tex, uv, jac, cov, W, H, 0, alg, 0, o, out, ev,
+                                                     stream=stream), k, 2, flush, stream)
+            st = _ctf.ctf_filter(tex, uv, jac, cov, W, H, 0, alg, 0, o, out, ev, stats=True, stream=stream)
+            _ctf.ctf_sync_check(stream)
+            mse = torch.mean((out[..., :3] - ref_exact[..., :3]) ** 2).item()
+            t = ms / k * 1e-3
+            flops = st["texel_evals"] * 10752
+            peak = peaks["bf16"] * (2.0 if tname == "fp8" else 1.0)
+            runs[f"{tname}_{alg}"] = {
+                "pixels_per_s": npix / t, "ms_per_view": t * 1e3,
+                "evals_per_pixel": st["texel_evals"] / max(1, st["pixels_active"]),
+                "texel_evals_per_s": st["texel_evals"] / t,
+                "psnr_vs_exact_4tap_db": -10 * math.log10(max(mse, 1e-30)),
+                "tensor": {"achieved_tflops": flops / t / 1e12, "peak_tflops": peak,
+                           "frac": flops / t / 1e12 / peak,
+                           "peak_kind": peaks["bf16_kind"] + (" x2 (nominal fp8/bf16 ratio)" if tname == "fp8" else "")},
+                "tiles_success": st["tiles_success"], "tiles_fallback_budget": st["tiles_fallback_budget"],
+                "tiles_fallback_minified": st["tiles_fallback_minified"]}
+    for tname in ("fp16", "fp8"):
+        a, b = runs.get(f"{tname}_mask"), runs.get(f"{tname}_4tap")
+        if a and b:
+            runs[f"{tname}_mask_vs_4tap"] = a["pixels_per_s"] / b["pixels_per_s"]
+    ms = _timed_views(lambda: _ctf.ctf_filter(exact, uv, jac, cov, W, H, 0, "mask", 0, opts11, out, ev,
+                                             stream=stream), k, 2, flush, stream)
+    runs["exact_mask"] = {"pixels_per_s": npix / (ms / k * 1e-3), "ms_per_view": ms / k}
+    res["filter_3840x2160"] = runs
+    # FP64 oracle on a band of 16 rows of the same view (its own frame on both sides)
+    band = slice(1000, 1016)
+    buv, bjac, bcov = (np.ascontiguousarray(a[band]) for a in (sc.uv, sc.jac, sc.coverage))
+    d_buv, d_bjac, d_bcov = (torch.from_numpy(a).to(dev) for a in (buv, bjac, bcov))
+    bout = torch.empty((16, W, 4), device=dev)
+    bev = torch.empty((16, W), dtype=torch.uint8, device=dev)
+    orc = {}
+    for tname in ("fp16", "fp8"):
+        st_ = _ctf.ctf_mlp_export(texs[tname], ((1024, 1024, 8), (512, 512, 8)))
+        if tname == "fp16":
+            w = [st_["w1"], st_["w2"], st_["w3"]]
+        else:
+            w = [st_["ws0"][:, None] * st_["w1"] / st_["as0"][None, :],
+                 st_["ws1"][:, None] * st_["w2"] / st_["as1"][None, :],
+                 st_["ws2"][:, None] * st_["w3"] / st_["as2"][None, :]]
+        mlp = oracle.MLP((st_["lat0"], st_["lat1"]), w[0].astype(np.float64), st_["b1"], w[1].astype(np.float64),
+                         st_["b2"], w[2].astype(np.float64), st_["b3"])
+        _ctf.ctf_filter(texs[tname], d_buv, d_bjac, d_bcov, W, 16, 0, "mask", 0, opts11, bout, bev, stream=stream)
+        _ctf.ctf_sync_check(stream)
+        t0 = time.perf_counter()
+        ref, ref_ev, _ = oracle.filter_frame_learned_f64(mlp, 4096, 4096, buv, bjac, bcov, alg=oracle.ALG_MASK,
+                                                         mask_dim=11)
+        el = time.perf_counter() - t0
+        g = bout.cpu().numpy().astype(np.float64)
+        err = np.abs(g - ref)
+        mse = float(np.mean(err[..., :3] ** 2))
+        orc[tname] = {"rows": "1000..1015 of 2160", "pixels": 16 * W, "max_abs": float(err.max()),
+                      "psnr_db": -10 * math.log10(max(mse, 1e-30)),
+                      "counts_equal": bool(np.array_equal(bev.cpu().numpy(), ref_ev)), "oracle_s": el}
+    res["vs_fp64_oracle_mask11"] = orc
+    res["_textures"] = (exact, texs, blocks)
+    _ctf.ctf_trainer_destroy(tr)
+    return res
+
+
+def bench_batch(args, dev, stream, learned_tex, block_tex):
+    """64 views, sizes uniform in [256, 3840] x [256, 2160], each a tilted
+    plane with its own magnification range inside [0.25, 64], textures
+    alternating a 2048^2 block texture and the learned 4096^2 FP16 texture;
+    one autotuned persistent launch replayed from a CUDA graph against 64
+    sequential ctf_filter calls."""
+    import torch
+    from paper_2506_17770_gb300 import _ctf, synth
+    t0 = time.perf_counter()
+    tex_sizes = ((2048, 2048), (4096, 4096)) if learned_tex is not None else ((2048, 2048),)
+    raw = synth.uneven_views(64, textures=tex_sizes)
+    gen_s = time.perf_counter() - t0
+    views = []
+    npix = 0
+    for i, (sc, ti) in enumerate(raw):
+        tex = block_tex if ti == 0 else learned_tex
+        views.append({"tex": tex, "uv": torch.from_numpy(sc.uv).to(dev), "jac": torch.from_numpy(sc.jac).to(dev),
+                      "coverage": torch.from_numpy(sc.coverage).to(dev), "width": sc.W, "height": sc.H,
+                      "view_id": i, "out_rgba": torch.empty((sc.H, sc.W, 4), device=dev),
+                      "out_evals": torch.empty((sc.H, sc.W), dtype=torch.uint8, device=dev)})
+        npix += sc.W * sc.H
+    alg = "mask"
+    best, tune_ms = _ctf.ctf_batch_autotune(views, alg, 0, _ctf.batch_opts(mask_dim=11), stream=stream)
+    g = _ctf.ctf_batch_graph_create(views, alg, 0, best)
+    k = max(3, min(args.steps, 10))
+    ms_graph = _timed_views(lambda: _ctf.ctf_batch_graph_launch(g, stream=stream), k, 2, None, stream)
+    fo = {"tile_w": best.filter.tile_w, "tile_h": best.filter.tile_h, "mask_dim": 11}
+
+    def sequential():
+        for v in views:
+            _ctf.ctf_filter(v["tex"], v["uv"], v["jac"], v["coverage"], v["width"], v["height"], v["view_id"], alg, 0,
+                            fo, v["out_rgba"], v["out_evals"], stream=stream)
+
+    ms_seq = _timed_views(sequential, k, 2, None, stream)
+    st = _ctf.ctf_filter_batch(views, alg, 0, best, stats=True, stream=stream)
+    _ctf.ctf_sync_check(stream)
+    _ctf.ctf_batch_graph_destroy(g)
+    tg, ts = ms_graph / k * 1e-3, ms_seq / k * 1e-3
+    return {"views": len(views), "pixels": npix, "input_gen_s": gen_s,
+            "textures": "2048^2 block / 4096^2 learned FP16 alternating" if learned_tex is not None else "2048^2 block",
+            "algorithm": "mask11+stf", "autotuned": best.as_dict(), "autotune_best_ms": tune_ms,
+            "graph_pixels_per_s": npix / tg, "graph_ms": tg * 1e3,
+            "sequential_pixels_per_s": npix / ts, "sequential_ms": ts * 1e3, "graph_vs_sequential": ts / tg,
+            "evals_per_pixel": st["texel_evals"] / max(1, st["pixels_active"]),
+            "l2": "not flushed: 64 views hold several GB, far above L2"}
 
 
 def dist_setup():
@@ -334,6 +526,17 @@ def ours_arm(args):
     d2h = npix * (16 + 1)
 
     peak, peak_kind = measured_peaks()
+    learned = None
+    batch = None
+    if not args.no_extras and not args.no_learned:
+        learned = bench_learned(args, dev, stream, flush, {"bf16": measured_bf16()[0], "bf16_kind": measured_bf16()[1]})
+    if not args.no_extras and not args.no_batch:
+        ltex = learned["_textures"][1]["fp16"] if learned else None
+        batch = bench_batch(args, dev, stream, ltex, tex)
+    if learned:
+        exact_l, texs_l, _ = learned.pop("_textures")
+        for t in list(texs_l.values()) + [exact_l]:
+            _ctf.ctf_texture_destroy(t)
     abytes = algorithmic_bytes(alg, npix, tex_bytes, cov is not None)
     achieved = abytes / (ms_per_step * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload, "mask11")
@@ -363,6 +566,8 @@ def ours_arm(args):
             "cpu_baseline": cpu,
             "e2e": {"value": npix / e2e_s, "unit": "pixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "entry_point": "ctf_filter_host"},
+            "learned": learned,
+            "batch": batch,
             "gpu_launches": args.steps,
             "clocks": clk,
             "wall_s_timed_region": wall}

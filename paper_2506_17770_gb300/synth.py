@@ -81,12 +81,57 @@ def gradient_noise(n: int, freq: int, g: np.random.Generator) -> np.ndarray:
     return (nx0 + uy * (nx1 - nx0)).astype(np.float32)
 
 
-def procedural_rgba8(n: int, seed: int = SEED_TEXTURE, octaves: int = 6, base_freq: int = 8) -> np.ndarray:
+def _gradient_noise_torch(n: int, freq: int, g: np.random.Generator, device):
+    """gradient_noise evaluated with torch on `device` (same lattice draws)."""
+    import torch
+    ang = g.uniform(0, 2 * np.pi, (freq, freq))
+    gx = torch.from_numpy(np.cos(ang).astype(np.float32)).to(device)
+    gy = torch.from_numpy(np.sin(ang).astype(np.float32)).to(device)
+    coords = (torch.arange(n, dtype=torch.float32, device=device) + 0.5) * (freq / n)
+    i0 = torch.floor(coords).long()
+    f = coords - i0
+    i1 = (i0 + 1) % freq
+    i0 = i0 % freq
+    fx, fy = f[None, :], f[:, None]
+    ux, uy = _fade(fx), _fade(fy)
+
+    def corner(iy, ix, ox, oy):
+        return gx[iy[:, None], ix[None, :]] * (fx - ox) + gy[iy[:, None], ix[None, :]] * (fy - oy)
+
+    n00 = corner(i0, i0, 0.0, 0.0)
+    n10 = corner(i0, i1, 1.0, 0.0)
+    n01 = corner(i1, i0, 0.0, 1.0)
+    n11 = corner(i1, i1, 1.0, 1.0)
+    nx0 = n00 + ux * (n10 - n00)
+    nx1 = n01 + ux * (n11 - n01)
+    return nx0 + uy * (nx1 - nx0)
+
+
+def procedural_rgba8(n: int, seed: int = SEED_TEXTURE, octaves: int = 6, base_freq: int = 8,
+                     device=None) -> np.ndarray:
     """n x n RGBA8 target: per channel 6 octaves of gradient noise plus a
-    checker pattern with sharp edges; alpha 255."""
+    checker pattern with sharp edges; alpha 255.  With `device` (a torch
+    device) the noise is evaluated there; the lattice draws are the same."""
     g = _rng(seed, 29)
-    img = np.zeros((n, n, 4), np.float32)
     checker_cells = 16
+    if device is not None:
+        import torch
+        yy, xx = torch.meshgrid(torch.arange(n, device=device), torch.arange(n, device=device), indexing="ij")
+        checker = (((xx * checker_cells) // n + (yy * checker_cells) // n) % 2).float()
+        out = torch.zeros((n, n, 4), dtype=torch.uint8, device=device)
+        for ch in range(3):
+            acc = torch.zeros((n, n), dtype=torch.float32, device=device)
+            amp, freq = 0.5, base_freq
+            for _ in range(octaves):
+                acc += amp * _gradient_noise_torch(n, min(freq, n), g, device)
+                amp *= 0.5
+                freq *= 2
+            tint = g.uniform(0.15, 0.35)
+            img = (0.5 + 0.8 * acc + tint * (checker - 0.5)).clamp(0.0, 1.0)
+            out[..., ch] = torch.round(img * 255.0).to(torch.uint8)
+        out[..., 3] = 255
+        return out.cpu().numpy()
+    img = np.zeros((n, n, 4), np.float32)
     yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     checker = (((xx * checker_cells) // n + (yy * checker_cells) // n) % 2).astype(np.float32)
     for ch in range(3):
