@@ -299,10 +299,12 @@ int ctf_trainer_load(ctf_texture exact_src, const char *path, ctf_trainer *out);
 int ctf_texture_compare(ctf_texture exact_ref, ctf_texture learned, double *mse_rgb, double *max_abs, void *stream);
 
 /* Batched filtering: many views, each with its own texture (block or
- * learned), size, magnification and buffers, in one persistent launch.
- * Work items are 16 warp tiles of a block view or 4 warp tiles of a learned
- * view; persistent CTAs of 128 threads take items_per_fetch items at a time
- * from an atomic counter until none are left.  Every view is filtered
+ * learned), size, magnification and buffers, in two persistent launches on
+ * the stream, one per kind of texel evaluation (block views first).  Block
+ * views: CTAs of 8 warps, every warp takes items of 32 warp tiles from an
+ * atomic counter.  Learned views: CTAs of 4 warps that keep their tensor
+ * memory for the whole launch take items of 4 warp tiles (one per warp,
+ * sharing an MLP chain), items_per_fetch at a time.  Every view is filtered
  * exactly as ctf_filter would filter it with the same options. */
 typedef struct {
     ctf_texture tex;            /* block or learned-decode texture */
@@ -316,8 +318,9 @@ typedef struct {
 
 /* Launch shape of a batch; NULL means the defaults in brackets.
  *   filter           tile shape, budget, mask_dim, edge_remap (as ctf_filter)
- *   items_per_fetch  items taken per atomic fetch, 1..64              [4]
- *   ctas_per_sm      persistent CTAs per SM, 1..4                      [4] */
+ *   items_per_fetch  learned views: items taken per fetch, 1..64      [4]
+ *   ctas_per_sm      learned views: persistent CTAs per SM, 1..4       [4]
+ * (the block-view launch always fills every SM to its occupancy limit). */
 typedef struct {
     ctf_filter_opts filter;
     int items_per_fetch;
@@ -329,8 +332,8 @@ typedef struct {
 int ctf_filter_batch(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t seed, const ctf_batch_opts *opts,
                      ctf_stats *stats, void *stream);
 
-/* The same batch captured once into a CUDA graph (counter reset + the
- * persistent launch) and replayed with ctf_batch_graph_launch.  The views'
+/* The same batch captured once into a CUDA graph (counter reset and both
+ * persistent launches) and replayed with ctf_batch_graph_launch.  The views'
  * buffers are baked in: they must stay valid and at the same addresses. */
 typedef struct ctf_batch_graph_s *ctf_batch_graph;
 int ctf_batch_graph_create(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t seed,

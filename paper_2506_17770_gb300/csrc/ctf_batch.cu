@@ -1,16 +1,16 @@
-// ctf_batch.cu -- many views of uneven size and magnification in one
-// persistent launch, optionally captured into a CUDA graph, with an
-// autotuner over the launch shape.
+// ctf_batch.cu -- many views of uneven size and magnification in two
+// persistent launches (one per kind of texel evaluation), optionally captured
+// together into one CUDA graph, with an autotuner over the launch shape.
 //
-// Work is cut into items: 4 warp tiles of one view for a learned-decode view
-// (one tile per warp, the 4 warps share an MLP chain), 16 warp tiles for a
-// block view (4 consecutive tiles per warp, the next one's inputs prefetched).
-// A prefix over the views' item counts maps a global item number to its view.
-// Persistent CTAs of 128 threads take `items_per_fetch` items at a time from
-// an atomic counter (a plain fetch-and-add: no thread ever waits on another
-// CTA) until the items run out.  Every CTA allocates its 128 TMEM columns up
-// front so that any item can use the tensor cores; the shared-memory request
-// keeps at most 4 CTAs on an SM, so the 512 columns always suffice.
+// Block views: persistent CTAs of 8 warps, like the per-view exact kernel;
+// every warp takes items of 32 consecutive warp tiles of one view from an
+// atomic counter (lane 0 fetches the next item while the current one runs)
+// and walks them with the next tile's inputs prefetched.  Learned views: persistent CTAs of 4
+// warps that hold 128 TMEM columns for the whole launch; the CTA takes items
+// of 4 warp tiles (one per warp, sharing an MLP chain), `items_per_fetch` at
+// a time.  A prefix over each kind's per-view item counts maps an item to its
+// view; the prefixes of up to 1024 views are cached in shared memory.
+// Fetching is a plain fetch-and-add: no thread ever waits on another CTA.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -34,20 +34,25 @@
 namespace ctf {
 namespace {
 
-constexpr int kBlockTilesPerWarp = 4;
+constexpr int kBlockWarps = 8;         // warps per CTA of the block-view kernel
+constexpr int kBlockItemTiles = 32;    // warp tiles per block-view item (one warp)
 constexpr int kMaxViews = 4096;
+constexpr int kSmViews = 1024;         // item prefixes cached in shared memory up to this many views
 
-struct BatchViewDev {
+struct __align__(16) BatchViewDev {
     ExactParams p;
     MlpDevice m;
     int learned;
-    long long items;
 };
+static_assert(sizeof(BatchViewDev) % 16 == 0, "copied in 16-byte pieces");
+static_assert(sizeof(ExactParams) % 16 == 0 && sizeof(ExactParams) <= 32 * 16, "copied in 16-byte pieces");
 
+// One kind of views: their indices in the view table and item prefix.
 struct BatchParams {
     const BatchViewDev *views;
-    const long long *item_begin;  // nviews + 1 prefix
-    int nviews;
+    const int *index;             // views of this kind
+    const long long *item_begin;  // nkind + 1 prefix
+    int nkind;
     long long total_items;
     int items_per_fetch;
     unsigned long long *counter;
@@ -55,55 +60,127 @@ struct BatchParams {
     int *err;
 };
 
-__device__ __forceinline__ int find_view(const long long *begin, int nviews, long long item) {
+// Last view whose first item is <= item (views with no items are skipped
+// because the next view starts at the same item).
+__device__ __forceinline__ int find_view(const long long *begin, const int *sbegin, int nviews, long long item) {
     int lo = 0, hi = nviews - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(begin + mid) <= item) lo = mid;
+        const long long b = sbegin ? (long long)sbegin[mid] : __ldg(begin + mid);
+        if (b <= item) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
+// ---------------------------------------------------------------------------
+// Block views: each warp on its own.
+// ---------------------------------------------------------------------------
 template <int ALG, int TW, int MD>
-__global__ void __launch_bounds__(kRows) batch_kernel(const BatchParams b) {
+__global__ void __launch_bounds__(kBlockWarps * 32) batch_block_kernel(const BatchParams b) {
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
-    extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ float lut[256];
     __shared__ unsigned long long block_stats[kNumStats];
-    __shared__ long long s_item;
-    // The operand image of the learned views is loaded per item (views may
-    // use different networks); chain_setup only needs some image to start.
-    Chain ch;
-    const MlpDevice m0 = b.views[0].m;
-    if (m0.img) {
-        chain_setup(ch, sm, m0);
-    } else {
-        // no learned view in this batch: still allocate TMEM so that the code
-        // path is the same; the image copy is skipped
-        MlpDevice none = m0;
-        none.img = nullptr;
-        uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kSmBar);
-        uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kSmTmem);
-        if (threadIdx.x == 0) {
-            tc::mbar_init(bar, 1);
-            tc::fence_mbar_init();
-        }
-        if ((threadIdx.x >> 5) == 0) {
-            tc::tmem_alloc(tslot, kTmemCols);
-            tc::tmem_relinquish();
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        ch.sm = sm;
-        ch.bar = bar;
-        ch.tmem = *tslot;
-        ch.phase = 0;
-        (void)none;
-    }
+    __shared__ int s_begin[kSmViews];
+    __shared__ __align__(16) ExactParams s_params[kBlockWarps];  // each warp's current view
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = __fdiv_rn((float)i, 255.0f);
+    if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
+    const bool cached = b.nkind <= kSmViews && b.total_items < 0x7fffffffLL;
+    if (cached)
+        for (int i = threadIdx.x; i < b.nkind; i += blockDim.x) s_begin[i] = (int)__ldg(b.item_begin + i);
+    const int *sb = cached ? s_begin : nullptr;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ListTable *T = ALG == ALG_LIST ? reinterpret_cast<ListTable *>(dyn_smem) + warp : nullptr;
+    if (ALG == ALG_LIST) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) T->keys[lane * 8 + s] = kEmpty;
+    }
+    __syncthreads();
+    const int tx = lane % TW, ty = lane / TW;
+    const uint32_t lt = lanemask_lt();
+    Counters cnt;
+#pragma unroll
+    for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
+
+    // the next item is fetched while the current one is filtered
+    int cur_k = -1;
+    long long next = 0;
+    if (lane == 0) next = (long long)atomicAdd(b.counter, 1ull);
+    while (true) {
+        const long long item = __shfl_sync(FULL, next, 0);
+        if (item >= b.total_items) break;
+        if (lane == 0) next = (long long)atomicAdd(b.counter, 1ull);
+        const int k = find_view(b.item_begin, sb, b.nkind, item);
+        if (k != cur_k) {
+            // the view's parameters into this warp's shared-memory slot
+            __syncwarp();
+            const uint4 *src = reinterpret_cast<const uint4 *>(&b.views[__ldg(b.index + k)].p);
+            uint4 *dst = reinterpret_cast<uint4 *>(&s_params[warp]);
+            if (lane < (int)(sizeof(ExactParams) / 16)) dst[lane] = __ldg(src + lane);
+            __syncwarp();
+            cur_k = k;
+        }
+        const ExactParams &p = s_params[warp];
+        const long long first = (item - (sb ? (long long)sb[k] : __ldg(b.item_begin + k))) * kBlockItemTiles;
+        const long long last = min(first + kBlockItemTiles, (long long)p.n_tiles);
+        // walk the item's tiles, the next tile's inputs in flight meanwhile
+        long long tile = first;
+        int bx = (int)(tile % p.tiles_x), by = (int)(tile / p.tiles_x);
+        int px = bx * TW + tx, py = by * TH + ty;
+        bool inside = px < p.W && py < p.H;
+        uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
+        Inputs cur = load_inputs<kJac>(p, inside, idx);
+        while (tile < last) {
+            const long long nt = tile + 1;
+            int nbx = bx + 1, nby = by;
+            if (nbx >= p.tiles_x) {
+                nbx = 0;
+                ++nby;
+            }
+            const int npx = nbx * TW + tx, npy = nby * TH + ty;
+            const bool ninside = nt < last && npx < p.W && npy < p.H;
+            const uint32_t nidx = ninside ? (uint32_t)npy * (uint32_t)p.W + (uint32_t)npx : 0u;
+            const Inputs nxt = load_inputs<kJac>(p, ninside, nidx);
+            filter_tile<ALG, TW, MD>(p, cur, px, py, inside, idx, lane, lt, lut, T, cnt);
+            tile = nt;
+            bx = nbx;
+            by = nby;
+            px = npx;
+            py = npy;
+            inside = ninside;
+            idx = nidx;
+            cur = nxt;
+        }
+    }
+    if (b.stats) {
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < kNumStats; ++i)
+                if (cnt.v[i]) atomicAdd(&block_stats[i], (unsigned long long)cnt.v[i]);
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumStats && block_stats[threadIdx.x]) atomicAdd(b.stats + threadIdx.x, block_stats[threadIdx.x]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Learned views: the 4 warps of a CTA share an MLP chain.
+// ---------------------------------------------------------------------------
+template <int ALG, int TW, int MD>
+__global__ void __launch_bounds__(kRows) batch_mlp_kernel(const BatchParams b) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ unsigned long long block_stats[kNumStats];
+    __shared__ long long s_item;
+    __shared__ int s_begin[kSmViews];
+    __shared__ __align__(16) BatchViewDev s_view;  // the current item's view
+    __shared__ int s_view_k;
+    // the first view's network goes in now; a view with another network
+    // reloads the operand image when its first item comes up
+    Chain ch;
+    const MlpDevice m0 = b.views[__ldg(b.index)].m;
+    chain_setup(ch, sm, m0);
     if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ListTable *T = reinterpret_cast<ListTable *>(sm + kSmList) + warp;
@@ -113,11 +190,15 @@ __global__ void __launch_bounds__(kRows) batch_kernel(const BatchParams b) {
     }
     const float *inv_a1 = reinterpret_cast<const float *>(sm + kImgA1);
     const uint32_t lt = lanemask_lt();
-    const int tx = lane % TW, ty = lane / TW;
     Counters cnt;
 #pragma unroll
     for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
-    const unsigned char *loaded_img = m0.img ? reinterpret_cast<const unsigned char *>(m0.img) : nullptr;
+    const unsigned char *loaded_img = reinterpret_cast<const unsigned char *>(m0.img);
+    const bool cached = b.nkind <= kSmViews && b.total_items < 0x7fffffffLL;
+    if (cached)
+        for (int i = threadIdx.x; i < b.nkind; i += blockDim.x) s_begin[i] = (int)__ldg(b.item_begin + i);
+    const int *sb = cached ? s_begin : nullptr;
+    if (threadIdx.x == 0) s_view_k = -1;
     __syncthreads();
 
     bool ok = true;
@@ -130,35 +211,29 @@ __global__ void __launch_bounds__(kRows) batch_kernel(const BatchParams b) {
         for (int k = 0; k < b.items_per_fetch && ok; ++k) {
             const long long item = first + k;
             if (item >= b.total_items) break;
-            const int v = find_view(b.item_begin, b.nviews, item);
-            const BatchViewDev &V = b.views[v];
-            const long long local = item - __ldg(b.item_begin + v);
-            if (V.learned) {
-                // this view's network into shared memory if it is not there yet
-                const unsigned char *img = reinterpret_cast<const unsigned char *>(V.m.img);
-                if (img != loaded_img) {
-                    tc::fence_before_sync();
-                    __syncthreads();
-                    uint4 *dst = reinterpret_cast<uint4 *>(sm + kSmImg);
-                    for (int i = threadIdx.x; i < kImgBytes / 16; i += blockDim.x)
-                        dst[i] = __ldg(reinterpret_cast<const uint4 *>(img) + i);
-                    loaded_img = img;
-                    __syncthreads();
-                }
-                ok = mlp_warp_tile<ALG, TW, MD>(V.p, V.m, ch, local * 4 + warp, lane, lt, T, cnt, inv_a1, b.err);
-            } else {
-                const ExactParams &p = V.p;
-                for (int r = 0; r < kBlockTilesPerWarp; ++r) {
-                    const long long tile = (local * 4 + warp) * kBlockTilesPerWarp + r;
-                    if (tile >= p.n_tiles) break;
-                    const int bx = (int)(tile % p.tiles_x), by = (int)(tile / p.tiles_x);
-                    const int px = bx * TW + tx, py = by * TH + ty;
-                    const bool inside = px < p.W && py < p.H;
-                    const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
-                    const Inputs in = load_inputs<kJac>(p, inside, idx);
-                    filter_tile<ALG, TW, MD>(p, in, px, py, inside, idx, lane, lt, lut, T, cnt);
-                }
+            const int v = find_view(b.item_begin, sb, b.nkind, item);
+            if (v != s_view_k) {
+                // parameters of the new view into shared memory (CTA-uniform branch)
+                __syncthreads();
+                const uint4 *src = reinterpret_cast<const uint4 *>(b.views + __ldg(b.index + v));
+                uint4 *dst = reinterpret_cast<uint4 *>(&s_view);
+                for (int i = threadIdx.x; i < (int)(sizeof(BatchViewDev) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+                if (threadIdx.x == 0) s_view_k = v;
+                __syncthreads();
             }
+            const BatchViewDev &V = s_view;
+            const long long local = item - (sb ? (long long)sb[v] : __ldg(b.item_begin + v));
+            const unsigned char *img = reinterpret_cast<const unsigned char *>(V.m.img);
+            if (img != loaded_img) {
+                tc::fence_before_sync();
+                __syncthreads();
+                uint4 *dst = reinterpret_cast<uint4 *>(sm + kSmImg);
+                for (int i = threadIdx.x; i < kImgBytes / 16; i += blockDim.x)
+                    dst[i] = __ldg(reinterpret_cast<const uint4 *>(img) + i);
+                loaded_img = img;
+                __syncthreads();
+            }
+            ok = mlp_warp_tile<ALG, TW, MD>(V.p, V.m, ch, local * 4 + warp, lane, lt, T, cnt, inv_a1, b.err);
         }
     }
     if (b.stats && lane == 0) {
@@ -173,32 +248,38 @@ __global__ void __launch_bounds__(kRows) batch_kernel(const BatchParams b) {
 
 using BatchFn = void (*)(const BatchParams);
 
-template <int ALG, int TW>
+template <bool kMlp, int ALG, int TW, int MD>
+BatchFn kernel_of() {
+    if constexpr (kMlp) return batch_mlp_kernel<ALG, TW, MD>;
+    else return batch_block_kernel<ALG, TW, MD>;
+}
+
+template <bool kMlp, int ALG, int TW>
 BatchFn pick_mask(int md) {
     if constexpr (ALG == ALG_MASK) {
-        return md == 11 ? batch_kernel<ALG, TW, 11> : batch_kernel<ALG, TW, 16>;
+        return md == 11 ? kernel_of<kMlp, ALG, TW, 11>() : kernel_of<kMlp, ALG, TW, 16>();
     } else {
-        return batch_kernel<ALG, TW, 16>;
+        return kernel_of<kMlp, ALG, TW, 16>();
     }
 }
 
-template <int TW>
+template <bool kMlp, int TW>
 BatchFn pick_alg(int alg, int md) {
     switch (alg) {
-    case ALG_4TAP: return pick_mask<ALG_4TAP, TW>(md);
-    case ALG_STF: return pick_mask<ALG_STF, TW>(md);
-    case ALG_LIST: return pick_mask<ALG_LIST, TW>(md);
-    case ALG_BOX: return pick_mask<ALG_BOX, TW>(md);
-    case ALG_MASK: return pick_mask<ALG_MASK, TW>(md);
+    case ALG_4TAP: return pick_mask<kMlp, ALG_4TAP, TW>(md);
+    case ALG_STF: return pick_mask<kMlp, ALG_STF, TW>(md);
+    case ALG_LIST: return pick_mask<kMlp, ALG_LIST, TW>(md);
+    case ALG_BOX: return pick_mask<kMlp, ALG_BOX, TW>(md);
+    case ALG_MASK: return pick_mask<kMlp, ALG_MASK, TW>(md);
     default: return nullptr;
     }
 }
 
-BatchFn pick(int alg, int tile_w, int md) {
+BatchFn pick(bool mlp, int alg, int tile_w, int md) {
     switch (tile_w) {
-    case 8: return pick_alg<8>(alg, md);
-    case 4: return pick_alg<4>(alg, md);
-    case 16: return pick_alg<16>(alg, md);
+    case 8: return mlp ? pick_alg<true, 8>(alg, md) : pick_alg<false, 8>(alg, md);
+    case 4: return mlp ? pick_alg<true, 4>(alg, md) : pick_alg<false, 4>(alg, md);
+    case 16: return mlp ? pick_alg<true, 16>(alg, md) : pick_alg<false, 16>(alg, md);
     default: return nullptr;
     }
 }
@@ -245,20 +326,19 @@ int resolve(const ctf_batch_opts *o, ResolvedBatch *r) {
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-// Host-side plan of a batch: the device view table and item prefix.
+// Host-side plan of a batch: the device view table and, per kind, the view
+// indices and item prefix.
 struct Plan {
     std::vector<BatchViewDev> views;
-    std::vector<long long> begin;
-    long long total_items = 0;
+    std::vector<int> index[2];           // [0] block views, [1] learned views
+    std::vector<long long> begin[2];
+    long long items[2] = {0, 0};
 };
 
 int make_plan(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t seed, const ResolvedBatch &r, Plan *plan) {
     if (!views || nviews < 1 || nviews > kMaxViews) return report(CTF_ERR_ARG, "nviews %d outside [1, %d]", nviews, kMaxViews);
     if ((int)alg < CTF_ALG_4TAP || (int)alg > CTF_ALG_MASK) return report(CTF_ERR_ARG, "unknown algorithm %d", (int)alg);
     plan->views.resize(nviews);
-    plan->begin.resize(nviews + 1);
-    long long acc = 0;
-    const void *img0 = nullptr;
     for (int i = 0; i < nviews; ++i) {
         const ctf_view &v = views[i];
         if (!v.tex) return report(CTF_ERR_ARG, "view %d has no texture", i);
@@ -291,38 +371,38 @@ int make_plan(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t see
         p.evals = v.out_evals;
         p.stats = nullptr;
         d.learned = v.tex->mode != CTF_EVAL_BLOCK;
-        if (d.learned) {
-            d.m = mlp_device_view(v.tex);
-            if (!img0) img0 = v.tex->img;
-        }
-        const long long per_item = d.learned ? 4 : 4 * kBlockTilesPerWarp;
-        d.items = (p.n_tiles + per_item - 1) / per_item;
-        plan->begin[i] = acc;
-        acc += d.items;
+        if (d.learned) d.m = mlp_device_view(v.tex);
+        const int kind = d.learned ? 1 : 0;
+        const long long per_item = d.learned ? 4 : kBlockItemTiles;
+        plan->index[kind].push_back(i);
+        plan->begin[kind].push_back(plan->items[kind]);
+        plan->items[kind] += (p.n_tiles + per_item - 1) / per_item;
     }
-    plan->begin[nviews] = acc;
-    plan->total_items = acc;
-    // view 0's image doubles as the first one a CTA loads
-    if (img0 && !plan->views[0].learned) plan->views[0].m.img = static_cast<const uint4 *>(img0);
+    for (int k = 0; k < 2; ++k) plan->begin[k].push_back(plan->items[k]);
     return CTF_OK;
 }
 
-// Device copy of a plan plus its work counter (owned by the caller).
+// Device copy of a plan plus its two work counters (owned by the caller).
 struct DevPlan {
     void *buf = nullptr;
     size_t bytes = 0;
     BatchViewDev *views = nullptr;
-    long long *begin = nullptr;
-    unsigned long long *counter = nullptr;
+    int *index[2] = {nullptr, nullptr};
+    long long *begin[2] = {nullptr, nullptr};
+    unsigned long long *counter = nullptr;  // [2] counters, then kNumStats stats words
 };
 
-size_t plan_bytes(int nviews) {
-    return ((sizeof(BatchViewDev) * nviews + 255) & ~(size_t)255) + ((8 * (size_t)(nviews + 1) + 255) & ~(size_t)255) + 256;
-}
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 cudaError_t upload_plan(const Plan &plan, DevPlan *dp, cudaStream_t s) {
     const int n = (int)plan.views.size();
-    const size_t need = plan_bytes(n);
+    const size_t vb = up256(sizeof(BatchViewDev) * n);
+    size_t ib[2], bb[2];
+    for (int k = 0; k < 2; ++k) {
+        ib[k] = up256(4 * (plan.index[k].size() + 1));
+        bb[k] = up256(8 * plan.begin[k].size());
+    }
+    const size_t need = vb + ib[0] + ib[1] + bb[0] + bb[1] + 256;
     if (dp->bytes < need) {
         if (dp->buf) {
             cudaStreamSynchronize(s);
@@ -335,39 +415,67 @@ cudaError_t upload_plan(const Plan &plan, DevPlan *dp, cudaStream_t s) {
         dp->bytes = need;
     }
     char *base = static_cast<char *>(dp->buf);
-    const size_t vb = (sizeof(BatchViewDev) * n + 255) & ~(size_t)255;
-    const size_t bb = (8 * (size_t)(n + 1) + 255) & ~(size_t)255;
     dp->views = reinterpret_cast<BatchViewDev *>(base);
-    dp->begin = reinterpret_cast<long long *>(base + vb);
-    dp->counter = reinterpret_cast<unsigned long long *>(base + vb + bb);
+    base += vb;
+    for (int k = 0; k < 2; ++k) {
+        dp->index[k] = reinterpret_cast<int *>(base);
+        base += ib[k];
+        dp->begin[k] = reinterpret_cast<long long *>(base);
+        base += bb[k];
+    }
+    dp->counter = reinterpret_cast<unsigned long long *>(base);
     cudaError_t e = cudaMemcpyAsync(dp->views, plan.views.data(), sizeof(BatchViewDev) * n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dp->begin, plan.begin.data(), 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        if (!plan.index[k].empty())
+            e = cudaMemcpyAsync(dp->index[k], plan.index[k].data(), 4 * plan.index[k].size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dp->begin[k], plan.begin[k].data(), 8 * plan.begin[k].size(), cudaMemcpyHostToDevice, s);
+    }
     return e;
 }
 
+// Counter reset, then the block-view kernel, then the learned-view kernel,
+// all on stream s (so a capture of s records the whole batch).
 cudaError_t launch_plan(const Plan &plan, const DevPlan &dp, int alg, const ResolvedBatch &r,
                         unsigned long long *stats, int *err, cudaStream_t s) {
-    BatchFn fn = pick(alg, r.tile_w, r.mask_dim);
-    if (!fn) return cudaErrorInvalidValue;
-    cudaError_t e = prepare_batch(fn);
+    cudaError_t e = cudaMemsetAsync(dp.counter, 0, 16, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(dp.counter, 0, 8, s);
-    if (e != cudaSuccess) return e;
-    if (plan.total_items == 0) return cudaSuccess;
-    BatchParams b;
-    b.views = dp.views;
-    b.item_begin = dp.begin;
-    b.nviews = (int)plan.views.size();
-    b.total_items = plan.total_items;
-    b.items_per_fetch = r.items_per_fetch;
-    b.counter = dp.counter;
-    b.stats = stats;
-    b.err = err;
-    long long grid = (long long)device_sm_count() * r.ctas_per_sm;
-    const long long useful = (plan.total_items + r.items_per_fetch - 1) / r.items_per_fetch;
-    if (grid > useful) grid = useful;
-    fn<<<(int)grid, kRows, kSmRequest, s>>>(b);
-    return cudaGetLastError();
+    for (int k = 0; k < 2; ++k) {
+        if (plan.items[k] == 0) continue;
+        BatchFn fn = pick(k == 1, alg, r.tile_w, r.mask_dim);
+        if (!fn) return cudaErrorInvalidValue;
+        BatchParams b;
+        b.views = dp.views;
+        b.index = dp.index[k];
+        b.item_begin = dp.begin[k];
+        b.nkind = (int)plan.index[k].size();
+        b.total_items = plan.items[k];
+        b.items_per_fetch = r.items_per_fetch;
+        b.counter = dp.counter + k;
+        b.stats = stats;
+        b.err = err;
+        if (k == 1) {
+            e = prepare_batch(fn);
+            if (e != cudaSuccess) return e;
+            long long grid = (long long)device_sm_count() * r.ctas_per_sm;
+            const long long useful = (plan.items[k] + r.items_per_fetch - 1) / r.items_per_fetch;
+            if (grid > useful) grid = useful;
+            fn<<<(int)grid, kRows, kSmRequest, s>>>(b);
+        } else {
+            const size_t smem = alg == ALG_LIST ? sizeof(ListTable) * kBlockWarps : 0;
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlockWarps * 32, smem) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            long long grid = (long long)device_sm_count() * per_sm;
+            const long long useful = (plan.items[k] + kBlockWarps - 1) / kBlockWarps;
+            if (grid > useful) grid = useful;
+            fn<<<(int)grid, kBlockWarps * 32, smem, s>>>(b);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 DevPlan g_plan[64];
@@ -407,10 +515,10 @@ int ctf_filter_batch(const ctf_view *views, int nviews, ctf_algorithm alg, uint6
     cudaError_t e = upload_plan(plan, &dp, s);
     if (e != cudaSuccess) return report_cuda(e, "batch plan upload");
     if (stats) {
-        // counters right after the work counter in the plan buffer
-        e = cudaMemsetAsync(dp.counter + 1, 0, 8 * kNumStats, s);
+        // stats words right after the two work counters in the plan buffer
+        e = cudaMemsetAsync(dp.counter + 2, 0, 8 * kNumStats, s);
         if (e != cudaSuccess) return report_cuda(e, "clearing stats");
-        dstats = dp.counter + 1;
+        dstats = dp.counter + 2;
     }
     e = launch_plan(plan, dp, (int)alg, r, dstats, err, s);
     if (e != cudaSuccess) return report_cuda(e, "batch launch");
@@ -447,7 +555,7 @@ int ctf_batch_graph_create(const ctf_view *views, int nviews, ctf_algorithm alg,
     if (e == cudaSuccess) e = upload_plan(plan, &g->plan, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     // the kernel attribute must be set before capture
-    if (e == cudaSuccess) e = prepare_batch(pick((int)alg, r.tile_w, r.mask_dim));
+    if (e == cudaSuccess && plan.items[1]) e = prepare_batch(pick(true, (int)alg, r.tile_w, r.mask_dim));
     if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t le = launch_plan(plan, g->plan, (int)alg, r, nullptr, err, s);

@@ -38,7 +38,7 @@ enum StatIndex {
     kNumStats
 };
 
-struct ExactParams {
+struct __align__(16) ExactParams {
     const uint2 *blocks;  // (Wt/4)*(Ht/4) blocks
     int Wt, Ht, nbx;
     const float2 *uv;

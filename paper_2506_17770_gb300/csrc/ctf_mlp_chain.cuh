@@ -270,7 +270,8 @@ __device__ __forceinline__ bool mlp_chain(Chain &ch, bool fp8, float4 &out, int 
 __device__ __forceinline__ void chain_setup(Chain &ch, unsigned char *sm, const MlpDevice &m) {
     const uint4 *src = m.img;
     uint4 *dst = reinterpret_cast<uint4 *>(sm + kSmImg);
-    for (int i = threadIdx.x; i < kImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    if (src)
+        for (int i = threadIdx.x; i < kImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kSmBar);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kSmTmem);
     if (threadIdx.x == 0) {
