@@ -80,12 +80,13 @@ template <int ALG, int TW, int MD>
 __global__ void __launch_bounds__(kBlockWarps * 32) batch_block_kernel(const BatchParams b) {
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
-    __shared__ float lut[256];
+    __shared__ DecodeTables tabs;
+    __shared__ int rank_slots[kBlockWarps][32];
     __shared__ unsigned long long block_stats[kNumStats];
     __shared__ int s_begin[kSmViews];
     __shared__ __align__(16) ExactParams s_params[kBlockWarps];  // each warp's current view
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = __fdiv_rn((float)i, 255.0f);
+    build_decode_tables(&tabs);
     if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
     const bool cached = b.nkind <= kSmViews && b.total_items < 0x7fffffffLL;
     if (cached)
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32) batch_block_kernel(const Bat
             const bool ninside = nt < last && npx < p.W && npy < p.H;
             const uint32_t nidx = ninside ? (uint32_t)npy * (uint32_t)p.W + (uint32_t)npx : 0u;
             const Inputs nxt = load_inputs<kJac>(p, ninside, nidx);
-            filter_tile<ALG, TW, MD>(p, cur, px, py, inside, idx, lane, lt, lut, T, cnt);
+            filter_tile<ALG, TW, MD, true>(p, cur, px, py, inside, idx, lane, lt, &tabs, T, rank_slots[warp], cnt);
             tile = nt;
             bx = nbx;
             by = nby;

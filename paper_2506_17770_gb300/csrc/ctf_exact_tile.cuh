@@ -38,8 +38,49 @@ __device__ __forceinline__ void store_pixel(const ExactParams &p, uint32_t idx, 
     if (p.evals) p.evals[idx] = count;
 }
 
-__device__ __forceinline__ float3 to_float3(uint32_t rgba8, const float *lut) {
-    return make_float3(lut[rgba8 & 0xffu], lut[(rgba8 >> 8) & 0xffu], lut[(rgba8 >> 16) & 0xffu]);
+// Decode tables, built in shared memory by every CTA: the two endpoints of a
+// block expand to 8-bit channels laid out in 10-bit fields (r bits 0-9, g
+// 10-19, b 20-29) by two lookups each, so that the palette entries 2 and 3,
+// (2a+b+1)/3 with (a, b) = (c0, c1) or (c1, c0), come out of one integer
+// expression for all three channels, and `val` turns a field into the
+// channel value: val[v] = v/255 for v < 256, val[256 + s] = floor(s/3)/255
+// for s < 768 (both correctly rounded, IEEE division).
+struct DecodeTables {
+    uint32_t rg[2048];  // c >> 5 = (r5 << 6) | g6  ->  r8 | g8 << 10
+    uint32_t b[32];     // c & 31 = b5              ->  b8 << 20
+    float val[1024];
+};
+
+__device__ __forceinline__ void build_decode_tables(DecodeTables *t) {
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) {
+        const uint32_t r5 = (uint32_t)i >> 6, g6 = (uint32_t)i & 63u;
+        t->rg[i] = ((r5 << 3) | (r5 >> 2)) | (((g6 << 2) | (g6 >> 4)) << 10);
+    }
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) t->b[i] = (((uint32_t)i << 3) | ((uint32_t)i >> 2)) << 20;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x)
+        t->val[i] = i < 256 ? __fdiv_rn((float)i, 255.0f) : __fdiv_rn((float)((i - 256) / 3), 255.0f);
+}
+
+// RGB of texel (x, y) of a block (alpha is 1): palette c0, c1,
+// (2c0+c1+1)/3, (c0+2c1+1)/3, 2-bit index at bits 2*(4*(y&3)+(x&3)).
+__device__ __forceinline__ float3 decode_texel_f(uint2 blk, int x, int y, const DecodeTables *T) {
+    const uint32_t sel = (blk.y >> ((((uint32_t)y & 3u) << 3) | (((uint32_t)x & 3u) << 1))) & 3u;
+    const uint32_t c0 = blk.x & 0xffffu, c1 = blk.x >> 16;
+    const uint32_t e0 = T->rg[c0 >> 5] | T->b[c0 & 31u];
+    const uint32_t e1 = T->rg[c1 >> 5] | T->b[c1 & 31u];
+    const bool odd = (sel & 1u) != 0, mid = (sel & 2u) != 0;
+    const uint32_t a = odd ? e1 : e0, b = odd ? e0 : e1;
+    const uint32_t v = mid ? (2u * a + b + 0x100401u) : a;  // every field < 768
+    const float *base = T->val + (mid ? 256 : 0);
+    return make_float3(base[v & 0x3ffu], base[(v >> 10) & 0x3ffu], base[v >> 20]);
+}
+
+// Clamp-to-edge fetch and decode of texel (x, y).
+__device__ __forceinline__ float3 fetch_decode(const ExactParams &p, int x, int y, const DecodeTables *T) {
+    x = min(max(x, 0), p.Wt - 1);
+    y = min(max(y, 0), p.Ht - 1);
+    const uint2 blk = __ldg(p.blocks + (uint32_t)(y >> 2) * (uint32_t)p.nbx + (uint32_t)(x >> 2));
+    return decode_texel_f(blk, x, y, T);
 }
 
 // acc = fma(w_k, p_k, acc) from 0, k = 0..3; alpha of every block texel is 1.
@@ -55,31 +96,33 @@ __device__ __forceinline__ float4 filter4(const float w[4], const float3 t[4]) {
     return make_float4(r, g, b, a);
 }
 
-template <int ALG, int TW, int MD>
+template <int ALG, int TW, int MD, bool kStats>
 __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &in, int px, int py, bool inside,
-                                            uint32_t idx, int lane, uint32_t lt, const float *lut, ListTable *T,
-                                            Counters &cnt) {
+                                            uint32_t idx, int lane, uint32_t lt, const DecodeTables *tabs,
+                                            ListTable *T, int *ranks, Counters &cnt) {
     PixelSetup ps;
     ps.active = in.covered;
     setup_coords(in.uv, (float)p.Wt, (float)p.Ht, ps);
 
     if (ALG == ALG_4TAP) {
         // ---------------- per-pixel 4-tap ----------------
-        const uint32_t A = __ballot_sync(FULL, ps.active);
-        cnt.v[kStatTilesTotal] += 1;
-        if (A == 0) {
-            cnt.v[kStatTilesEmpty] += 1;
-        } else {
-            const int nactive = __popc(A);
-            cnt.v[kStatPixelsActive] += nactive;
-            cnt.v[kStatTilesDirect] += 1;
-            cnt.v[kStatTexelEvals] += 4 * nactive;
+        if (kStats) {
+            const uint32_t A = __ballot_sync(FULL, ps.active);
+            cnt.v[kStatTilesTotal] += 1;
+            if (A == 0) {
+                cnt.v[kStatTilesEmpty] += 1;
+            } else {
+                const int nactive = __popc(A);
+                cnt.v[kStatPixelsActive] += nactive;
+                cnt.v[kStatTilesDirect] += 1;
+                cnt.v[kStatTexelEvals] += 4 * nactive;
+            }
         }
         if (ps.active) {
             float3 t[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                t[k] = to_float3(fetch_block_texel(p.blocks, p.nbx, p.Wt, p.Ht, ps.ulx + (k & 1), ps.uly + (k >> 1)), lut);
+                t[k] = fetch_decode(p, ps.ulx + (k & 1), ps.uly + (k >> 1), tabs);
             float w[4];
             bilinear_weights(ps.s, ps.t, w);
             store_pixel(p, idx, filter4(w, t), 4);
@@ -89,10 +132,10 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
         return;
     }
 
-    const Selection sel = select_tile<ALG, MD>(p, ps, in.jac, px, py, lane, lt, T, cnt);
+    const Selection sel = select_tile<ALG, MD, kStats>(p, ps, in.jac, px, py, lane, lt, T, ranks, cnt);
     // step 2: exact decode of the lane's texel (clamped to the texture)
     float3 val = make_float3(0.f, 0.f, 0.f);
-    if (sel.produce) val = to_float3(fetch_block_texel(p.blocks, p.nbx, p.Wt, p.Ht, sel.tx, sel.ty), lut);
+    if (sel.produce) val = fetch_decode(p, sel.tx, sel.ty, tabs);
     if (sel.path == PATH_SUCCESS) {
         // step 3: gather the 2x2 taps from their producers and filter
         float3 t[4];

@@ -35,15 +35,16 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
-template <int ALG, int TW, int MD>
+template <int ALG, int TW, int MD, bool kStats>
 __global__ void __launch_bounds__(kThreads) exact_filter_kernel(const ExactParams p) {
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
-    __shared__ float lut[256];
+    __shared__ DecodeTables tabs;
+    __shared__ int rank_slots[kWarps][32];
     __shared__ unsigned long long block_stats[kNumStats];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
 
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = __fdiv_rn((float)i, 255.0f);
+    build_decode_tables(&tabs);
     if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ListTable *T = ALG == ALG_LIST ? reinterpret_cast<ListTable *>(dyn_smem) + warp : nullptr;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) exact_filter_kernel(const ExactParam
         const uint32_t nidx = ninside ? (uint32_t)npy * (uint32_t)p.W + (uint32_t)npx : 0u;
         const Inputs nxt = load_inputs<kJac>(p, ninside, nidx);
 
-        filter_tile<ALG, TW, MD>(p, cur, px, py, inside, idx, lane, lt, lut, T, cnt);
+        filter_tile<ALG, TW, MD, kStats>(p, cur, px, py, inside, idx, lane, lt, &tabs, T, rank_slots[warp], cnt);
 
         tile = ntile;
         bx = nbx;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) exact_filter_kernel(const ExactParam
         cur = nxt;
     }
 
-    if (p.stats) {
+    if (kStats) {
         if (lane == 0) {
 #pragma unroll
             for (int i = 0; i < kNumStats; ++i)
@@ -110,23 +111,23 @@ __global__ void __launch_bounds__(kThreads) exact_filter_kernel(const ExactParam
 
 using KernelFn = void (*)(const ExactParams);
 
-template <int ALG, int TW>
+template <int ALG, int TW, bool kStats>
 KernelFn pick_mask(int md) {
     if constexpr (ALG == ALG_MASK) {
-        return md == 11 ? exact_filter_kernel<ALG, TW, 11> : exact_filter_kernel<ALG, TW, 16>;
+        return md == 11 ? exact_filter_kernel<ALG, TW, 11, kStats> : exact_filter_kernel<ALG, TW, 16, kStats>;
     } else {
-        return exact_filter_kernel<ALG, TW, 16>;
+        return exact_filter_kernel<ALG, TW, 16, kStats>;
     }
 }
 
-template <int TW>
+template <int TW, bool kStats>
 KernelFn pick_alg(int alg, int md) {
     switch (alg) {
-    case ALG_4TAP: return pick_mask<ALG_4TAP, TW>(md);
-    case ALG_STF: return pick_mask<ALG_STF, TW>(md);
-    case ALG_LIST: return pick_mask<ALG_LIST, TW>(md);
-    case ALG_BOX: return pick_mask<ALG_BOX, TW>(md);
-    case ALG_MASK: return pick_mask<ALG_MASK, TW>(md);
+    case ALG_4TAP: return pick_mask<ALG_4TAP, TW, kStats>(md);
+    case ALG_STF: return pick_mask<ALG_STF, TW, kStats>(md);
+    case ALG_LIST: return pick_mask<ALG_LIST, TW, kStats>(md);
+    case ALG_BOX: return pick_mask<ALG_BOX, TW, kStats>(md);
+    case ALG_MASK: return pick_mask<ALG_MASK, TW, kStats>(md);
     default: return nullptr;
     }
 }
@@ -148,10 +149,11 @@ int device_sm_count() {
 
 cudaError_t launch_exact_filter(const ExactParams &p, int alg, int tile_w, int mask_dim, cudaStream_t stream) {
     KernelFn fn = nullptr;
+    const bool st = p.stats != nullptr;
     switch (tile_w) {
-    case 8: fn = pick_alg<8>(alg, mask_dim); break;
-    case 4: fn = pick_alg<4>(alg, mask_dim); break;
-    case 16: fn = pick_alg<16>(alg, mask_dim); break;
+    case 8: fn = st ? pick_alg<8, true>(alg, mask_dim) : pick_alg<8, false>(alg, mask_dim); break;
+    case 4: fn = st ? pick_alg<4, true>(alg, mask_dim) : pick_alg<4, false>(alg, mask_dim); break;
+    case 16: fn = st ? pick_alg<16, true>(alg, mask_dim) : pick_alg<16, false>(alg, mask_dim); break;
     default: return cudaErrorInvalidValue;
     }
     if (!fn) return cudaErrorInvalidValue;

@@ -27,7 +27,8 @@ constexpr int kSmH = kSmX + 4096;        // A operand of layers 2 and 3: 128 x 1
 constexpr int kSmBar = kSmH + 16384;     // mbarrier (8 B)
 constexpr int kSmTmem = kSmBar + 8;      // TMEM base address (4 B)
 constexpr int kSmList = kSmBar + 64;     // List Merge tables (4 x ListTable)
-constexpr int kSmBytes = kSmList + 4 * (int)sizeof(ListTable);
+constexpr int kSmRanks = kSmList + 4 * (int)sizeof(ListTable);  // Mask rank slots (4 x 32 ints)
+constexpr int kSmBytes = kSmRanks + 4 * 32 * 4;
 // Reserve enough shared memory that at most 4 CTAs share an SM: 4 x 128 TMEM
 // columns fill the SM's 512.
 constexpr int kSmRequest = 48 * 1024;
@@ -378,7 +379,8 @@ __device__ __forceinline__ bool mlp_warp_tile(const ExactParams &p, const MlpDev
     } else {
         Selection sel;
         if (valid) {
-            sel = select_tile<ALG, MD>(p, ps, jac, px, py, lane, lt, T, cnt);
+            sel = select_tile<ALG, MD, true>(p, ps, jac, px, py, lane, lt, T,
+                                          reinterpret_cast<int *>(sm + kSmRanks) + 32 * (threadIdx.x >> 5), cnt);
         } else {
             sel.path = PATH_EMPTY;
             sel.produce = false;

@@ -78,21 +78,6 @@ __device__ __forceinline__ int mask_rank(const uint32_t Bw[NW], const int pre[NW
     return base + __popc(word & ((1u << (q & 31)) - 1u));
 }
 
-// h(i, B): position of the i-th set bit of B (i < popcount(B)).
-template <int NW>
-__device__ __forceinline__ int mask_select(const uint32_t Bw[NW], const int pre[NW], int i) {
-    uint32_t word = Bw[0];
-    int base = 0, wsel = 0;
-#pragma unroll
-    for (int w = 1; w < NW; ++w) {
-        const bool ge = i >= pre[w];
-        word = ge ? Bw[w] : word;
-        base = ge ? pre[w] : base;
-        wsel = ge ? w : wsel;
-    }
-    return 32 * wsel + (int)__fns(word, 0, i - base + 1);
-}
-
 // Outcome of step 1 for one lane.
 struct Selection {
     int path;        // PATH_*
@@ -106,9 +91,11 @@ struct Selection {
 
 // Step 1 for the collaborative algorithms (ALG >= ALG_LIST) and the STF
 // algorithm.  `ps` holds the lane's setup (ps.active already decided).
-template <int ALG, int MD>
+// `ranks` is a per-warp array of 32 ints in shared memory (Mask Sampling
+// passes texel coordinates through it); counters are kept when kStats.
+template <int ALG, int MD, bool kStats>
 __device__ __forceinline__ Selection select_tile(const ExactParams &p, const PixelSetup &ps, const float4 jac,
-                                                 int px, int py, int lane, uint32_t lt, ListTable *T,
+                                                 int px, int py, int lane, uint32_t lt, ListTable *T, int *ranks,
                                                  Counters &cnt) {
     constexpr int NW = (MD * MD + 31) / 32;
     const float fW = (float)p.Wt, fH = (float)p.Ht;
@@ -120,15 +107,15 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
     sel.count = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) sel.src[k] = lane;
-    cnt.v[kStatTilesTotal] += 1;
+    if (kStats) cnt.v[kStatTilesTotal] += 1;
     if (sel.A == 0) {
         sel.path = PATH_EMPTY;
-        cnt.v[kStatTilesEmpty] += 1;
+        if (kStats) cnt.v[kStatTilesEmpty] += 1;
         return sel;
     }
     const uint32_t A = sel.A;
     const int nactive = __popc(A);
-    cnt.v[kStatPixelsActive] += nactive;
+    if (kStats) cnt.v[kStatPixelsActive] += nactive;
 
     bool mini = false, fits = false;
     int n = 0, minx = 0, miny = 0, bw = 0, mcls = 0;
@@ -241,13 +228,13 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
         // one-tap STF: every active lane evaluates its own stochastic texel
         if (ALG >= ALG_LIST) {
             sel.path = mini ? PATH_FALLBACK_MINIFIED : PATH_FALLBACK_BUDGET;
-            cnt.v[kStatTilesFallbackMinified] += mini ? 1 : 0;
-            cnt.v[kStatTilesFallbackBudget] += mini ? 0 : 1;
+            if (kStats) cnt.v[kStatTilesFallbackMinified] += mini ? 1 : 0;
+            if (kStats) cnt.v[kStatTilesFallbackBudget] += mini ? 0 : 1;
         } else {
             sel.path = PATH_DIRECT;
-            cnt.v[kStatTilesDirect] += 1;
+            if (kStats) cnt.v[kStatTilesDirect] += 1;
         }
-        cnt.v[kStatTexelEvals] += nactive;
+        if (kStats) cnt.v[kStatTexelEvals] += nactive;
         if (ps.active) {
             int dx, dy;
             stf_offset(px, py, p.view, p.k0, p.k1, ps.s, ps.t, dx, dy);
@@ -259,40 +246,11 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
     } else {
         sel.path = PATH_SUCCESS;
         sel.n = n;
-        cnt.v[kStatTilesSuccess] += 1;
-        cnt.v[kStatTexelEvals] += n;
-        // step 2: texel i is evaluated by lane h(i, A)
+        if (kStats) cnt.v[kStatTilesSuccess] += 1;
+        if (kStats) cnt.v[kStatTexelEvals] += n;
         const bool full = A == FULL;
         const int my_i = (full || !p.edge_remap) ? lane : (((A >> lane) & 1u) ? __popc(A & lt) : 32);
-        if (my_i < n) {
-            int x, y;
-            if (ALG == ALG_BOX) {
-                const int q = div_small(my_i, bw);
-                x = minx + (my_i - q * bw);
-                y = miny + q;
-            } else if (ALG == ALG_MASK) {
-                int t;
-                if (mcls == 1) {
-                    t = (int)__fns(Bw[0], 0, my_i + 1);
-                } else if (mcls == 2) {
-                    t = my_i < pre[1] ? (int)__fns(Bw[0], 0, my_i + 1) : 32 + (int)__fns(Bw[1], 0, my_i - pre[1] + 1);
-                } else {
-                    t = mask_select<NW>(Bw, pre, my_i);
-                }
-                const int q = div_small(t, bw);
-                x = minx + (t - q * bw);
-                y = miny + q;
-            } else {
-                const unsigned long long key = T->list[my_i];
-                x = minx + (int)(uint32_t)key;
-                y = miny + (int)(uint32_t)(key >> 32);
-            }
-            sel.produce = true;
-            sel.tx = x;
-            sel.ty = y;
-            sel.count = 1;
-        }
-        // step 3 (indices): where each of the 4 taps was produced
+        // step 3 (indices): where each of the 4 taps is produced
         int j[4];
         const int dx0 = ps.ulx - minx, dy0 = ps.uly - miny;
         if (ALG == ALG_BOX) {
@@ -315,6 +273,16 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
             }
             j[1] = j[0] + 1;
             j[3] = j[2] + 1;
+            // Each set bit's rank is known to the lanes that need it, so the
+            // texel of rank i (the i-th set bit, h(i, B)) reaches its producer
+            // through the warp's rank slots: no bit search is needed.
+            if (ps.active) {
+                ranks[j[0]] = (dy0 << 16) | dx0;
+                ranks[j[1]] = (dy0 << 16) | (dx0 + 1);
+                ranks[j[2]] = ((dy0 + 1) << 16) | dx0;
+                ranks[j[3]] = ((dy0 + 1) << 16) | (dx0 + 1);
+            }
+            __syncwarp();
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -335,6 +303,28 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                 }
             }
         }
+        // step 2: texel i is evaluated by lane h(i, A)
+        if (my_i < n) {
+            int x, y;
+            if (ALG == ALG_BOX) {
+                const int q = div_small(my_i, bw);
+                x = minx + (my_i - q * bw);
+                y = miny + q;
+            } else if (ALG == ALG_MASK) {
+                const int v = ranks[my_i];
+                x = minx + (v & 0xffff);
+                y = miny + (v >> 16);
+            } else {
+                const unsigned long long key = T->list[my_i];
+                x = minx + (int)(uint32_t)key;
+                y = miny + (int)(uint32_t)(key >> 32);
+            }
+            sel.produce = true;
+            sel.tx = x;
+            sel.ty = y;
+            sel.count = 1;
+        }
+        if (ALG == ALG_MASK) __syncwarp();  // rank slots free for the next tile
         if (!full && p.edge_remap) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) j[k] = nth_set_lane(A, j[k]);
