@@ -100,8 +100,8 @@ __device__ __forceinline__ void setup_coords(float2 uv, float fW, float fH, Pixe
     float fx = floorf(xf), fy = floorf(yf);
     p.ulx = ok ? (int)fx : 0;
     p.uly = ok ? (int)fy : 0;
-    p.s = ok ? __fsub_rn(xf, fx) : 0.f;
-    p.t = ok ? __fsub_rn(yf, fy) : 0.f;
+    p.s = __fsub_rn(xf, fx);  // read for active pixels only
+    p.t = __fsub_rn(yf, fy);
     p.active = p.active && ok;
 }
 

@@ -33,6 +33,18 @@ __device__ __forceinline__ Inputs load_inputs(const ExactParams &p, bool inside,
     return in;
 }
 
+// Unpredicated variant: every lane loads, lanes outside the frame at pixel 0
+// (any valid index), and their inputs count as uncovered.
+template <bool kJac>
+__device__ __forceinline__ Inputs load_inputs_any(const ExactParams &p, bool inside, uint32_t idx) {
+    Inputs in;
+    const uint32_t i = inside ? idx : 0u;
+    in.uv = __ldcs(p.uv + i);
+    in.jac = kJac ? __ldcs(p.jac + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    in.covered = inside && (p.cov == nullptr || __ldcs(p.cov + i) != 0);
+    return in;
+}
+
 __device__ __forceinline__ void store_pixel(const ExactParams &p, uint32_t idx, float4 v, uint8_t count) {
     __stcs(p.out + idx, v);
     if (p.evals) p.evals[idx] = count;
@@ -44,7 +56,8 @@ __device__ __forceinline__ void store_pixel(const ExactParams &p, uint32_t idx, 
 // (2a+b+1)/3 with (a, b) = (c0, c1) or (c1, c0), come out of one integer
 // expression for all three channels, and `val` turns a field into the
 // channel value: val[v] = v/255 for v < 256, val[256 + s] = floor(s/3)/255
-// for s < 768 (both correctly rounded, IEEE division).
+// for s < 768 (both correctly rounded, IEEE division); the interpolated
+// entries carry the offset 256 in every field of the sum.
 struct DecodeTables {
     uint32_t rg[2048];  // c >> 5 = (r5 << 6) | g6  ->  r8 | g8 << 10
     uint32_t b[32];     // c & 31 = b5              ->  b8 << 20
@@ -70,9 +83,9 @@ __device__ __forceinline__ float3 decode_texel_f(uint2 blk, int x, int y, const 
     const uint32_t e1 = T->rg[c1 >> 5] | T->b[c1 & 31u];
     const bool odd = (sel & 1u) != 0, mid = (sel & 2u) != 0;
     const uint32_t a = odd ? e1 : e0, b = odd ? e0 : e1;
-    const uint32_t v = mid ? (2u * a + b + 0x100401u) : a;  // every field < 768
-    const float *base = T->val + (mid ? 256 : 0);
-    return make_float3(base[v & 0x3ffu], base[(v >> 10) & 0x3ffu], base[v >> 20]);
+    // per field 2a + b + 1 + 256 <= 1022: no carry between the fields
+    const uint32_t v = mid ? (2u * a + b + 0x10140501u) : a;
+    return make_float3(T->val[v & 0x3ffu], T->val[(v >> 10) & 0x3ffu], T->val[v >> 20]);
 }
 
 // Clamp-to-edge fetch and decode of texel (x, y).
@@ -103,6 +116,10 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
     PixelSetup ps;
     ps.active = in.covered;
     setup_coords(in.uv, (float)p.Wt, (float)p.Ht, ps);
+    // Every path ends in one store per pixel: RGBA 0 and count 0 unless the
+    // pixel is active.
+    float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t count = 0;
 
     if (ALG == ALG_4TAP) {
         // ---------------- per-pixel 4-tap ----------------
@@ -118,45 +135,44 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
                 cnt.v[kStatTexelEvals] += 4 * nactive;
             }
         }
-        if (ps.active) {
-            float3 t[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                t[k] = fetch_decode(p, ps.ulx + (k & 1), ps.uly + (k >> 1), tabs);
-            float w[4];
-            bilinear_weights(ps.s, ps.t, w);
-            store_pixel(p, idx, filter4(w, t), 4);
-        } else if (inside) {
-            store_pixel(p, idx, make_float4(0.f, 0.f, 0.f, 0.f), 0);
-        }
-        return;
-    }
-
-    const Selection sel = select_tile<ALG, MD, kStats>(p, ps, in.jac, px, py, lane, lt, T, ranks, cnt);
-    // step 2: exact decode of the lane's texel (clamped to the texture)
-    float3 val = make_float3(0.f, 0.f, 0.f);
-    if (sel.produce) val = fetch_decode(p, sel.tx, sel.ty, tabs);
-    if (sel.path == PATH_SUCCESS) {
-        // step 3: gather the 2x2 taps from their producers and filter
+        // inactive lanes decode too (their own clamped texels): the warp
+        // stays converged and the values are dropped
         float3 t[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            t[k].x = __shfl_sync(FULL, val.x, sel.src[k]);
-            t[k].y = __shfl_sync(FULL, val.y, sel.src[k]);
-            t[k].z = __shfl_sync(FULL, val.z, sel.src[k]);
-        }
+        for (int k = 0; k < 4; ++k) t[k] = fetch_decode(p, ps.ulx + (k & 1), ps.uly + (k >> 1), tabs);
         if (ps.active) {
             float w[4];
             bilinear_weights(ps.s, ps.t, w);
-            store_pixel(p, idx, filter4(w, t), sel.count);
-        } else if (inside) {
-            store_pixel(p, idx, make_float4(0.f, 0.f, 0.f, 0.f), 0);
+            res = filter4(w, t);
+            count = 4;
         }
-    } else if (ps.active) {
-        store_pixel(p, idx, make_float4(val.x, val.y, val.z, 1.0f), 1);
-    } else if (inside) {
-        store_pixel(p, idx, make_float4(0.f, 0.f, 0.f, 0.f), 0);
+    } else {
+        const Selection sel = select_tile<ALG, MD, kStats>(p, ps, in.jac, px, py, lane, lt, T, ranks, cnt);
+        // step 2: exact decode of the lane's texel (clamped to the texture);
+        // lanes that produce nothing decode their own upper-left texel, which
+        // the warp reads anyway, and drop it
+        const float3 val = fetch_decode(p, sel.tx, sel.ty, tabs);
+        if (sel.path == PATH_SUCCESS) {
+            // step 3: gather the 2x2 taps from their producers and filter
+            float3 t[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                t[k].x = __shfl_sync(FULL, val.x, sel.src[k]);
+                t[k].y = __shfl_sync(FULL, val.y, sel.src[k]);
+                t[k].z = __shfl_sync(FULL, val.z, sel.src[k]);
+            }
+            if (ps.active) {
+                float w[4];
+                bilinear_weights(ps.s, ps.t, w);
+                res = filter4(w, t);
+                count = sel.count;
+            }
+        } else if (ps.active) {
+            res = make_float4(val.x, val.y, val.z, 1.0f);
+            count = 1;
+        }
     }
+    if (inside) store_pixel(p, idx, res, (uint8_t)count);
 }
 
 }  // namespace

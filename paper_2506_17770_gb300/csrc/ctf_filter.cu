@@ -35,8 +35,15 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
+// The collaborative kernels are issue-bound: five CTAs (40 warps) per SM
+// hide more latency than the registers a looser cap would buy.
+template <int ALG>
+constexpr int min_blocks() {
+    return ALG >= ALG_LIST ? 5 : 1;
+}
+
 template <int ALG, int TW, int MD, bool kStats>
-__global__ void __launch_bounds__(kThreads) exact_filter_kernel(const ExactParams p) {
+__global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kernel(const ExactParams p) {
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
     __shared__ DecodeTables tabs;
@@ -61,38 +68,40 @@ __global__ void __launch_bounds__(kThreads) exact_filter_kernel(const ExactParam
     for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
 
     // Warp-uniform tile walk: tile -> (bx, by) once, then advanced by the
-    // grid stride without dividing again.
+    // grid stride without dividing again.  A pixel's index is the tile's
+    // first pixel plus a per-lane offset, and the lane is inside the frame
+    // while bx < lim_x and by < lim_y (per-lane bounds).  Lanes outside
+    // read pixel 0, which exists whenever there is a tile, and drop it.
+    const uint32_t W = (uint32_t)p.W, H = (uint32_t)p.H;
     const uint32_t ntiles = (uint32_t)p.n_tiles, tiles_x = (uint32_t)p.tiles_x;
+    const uint32_t lim_x = (W - (uint32_t)tx + TW - 1) / TW, lim_y = (H - (uint32_t)ty + TH - 1) / TH;
+    const uint32_t lane_off = (uint32_t)ty * W + (uint32_t)tx;
     const uint32_t stride = gridDim.x * kWarps;
     const uint32_t sbx = stride % tiles_x, sby = stride / tiles_x;
-    uint32_t tile = blockIdx.x * kWarps + warp;
-    uint32_t bx = tile % tiles_x, by = tile / tiles_x;
+    const uint32_t tile0 = blockIdx.x * kWarps + warp;
+    const uint32_t n_mine = tile0 < ntiles ? (ntiles - 1u - tile0) / stride + 1u : 0u;
+    uint32_t bx = tile0 % tiles_x, by = tile0 / tiles_x;
 
-    int px = (int)(bx * TW) + tx, py = (int)(by * TH) + ty;
-    bool inside = tile < ntiles && px < p.W && py < p.H;
-    uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
-    Inputs cur = load_inputs<kJac>(p, inside, idx);
+    bool inside = n_mine > 0 && bx < lim_x && by < lim_y;
+    uint32_t idx = by * (TH * W) + bx * TW + lane_off;
+    Inputs cur = load_inputs_any<kJac>(p, inside, idx);
 
-    while (tile < ntiles) {
+    for (uint32_t i = 0; i < n_mine; ++i) {
         // prefetch the next tile of this warp
         uint32_t nbx = bx + sbx, nby = by + sby;
         if (nbx >= tiles_x) {
             nbx -= tiles_x;
             ++nby;
         }
-        const uint32_t ntile = tile + stride;
-        const int npx = (int)(nbx * TW) + tx, npy = (int)(nby * TH) + ty;
-        const bool ninside = ntile < ntiles && npx < p.W && npy < p.H;
-        const uint32_t nidx = ninside ? (uint32_t)npy * (uint32_t)p.W + (uint32_t)npx : 0u;
-        const Inputs nxt = load_inputs<kJac>(p, ninside, nidx);
+        const bool ninside = i + 1u < n_mine && nbx < lim_x && nby < lim_y;
+        const uint32_t nidx = nby * (TH * W) + nbx * TW + lane_off;
+        const Inputs nxt = load_inputs_any<kJac>(p, ninside, nidx);
 
-        filter_tile<ALG, TW, MD, kStats>(p, cur, px, py, inside, idx, lane, lt, &tabs, T, rank_slots[warp], cnt);
+        filter_tile<ALG, TW, MD, kStats>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
+                                         &tabs, T, rank_slots[warp], cnt);
 
-        tile = ntile;
         bx = nbx;
         by = nby;
-        px = npx;
-        py = npy;
         inside = ninside;
         idx = nidx;
         cur = nxt;

@@ -103,10 +103,9 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
     sel.A = __ballot_sync(FULL, ps.active);
     sel.n = 0;
     sel.produce = false;
-    sel.tx = sel.ty = 0;
-    sel.count = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) sel.src[k] = lane;
+    sel.tx = ps.ulx;  // lanes that produce nothing keep their own upper-left texel
+    sel.ty = ps.uly;
+    sel.count = 0;  // sel.src is set on the success path only
     if (kStats) cnt.v[kStatTilesTotal] += 1;
     if (sel.A == 0) {
         sel.path = PATH_EMPTY;
@@ -119,20 +118,15 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
 
     bool mini = false, fits = false;
     int n = 0, minx = 0, miny = 0, bw = 0, mcls = 0;
-    uint32_t Bw[NW];
+    uint32_t Bw[NW];  // mask words and their prefix popcounts, set (and read) per size class
     int pre[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        Bw[w] = 0;
-        pre[w] = 0;
-    }
     if (ALG >= ALG_LIST) {
         mini = __any_sync(FULL, ps.active && is_minified(jac, fW, fH));
         if (!mini) {
             minx = __reduce_min_sync(FULL, ps.active ? ps.ulx : INT_MAX);
             miny = __reduce_min_sync(FULL, ps.active ? ps.uly : INT_MAX);
-            const int maxx = __reduce_max_sync(FULL, ps.active ? ps.ulx + 1 : INT_MIN);
-            const int maxy = __reduce_max_sync(FULL, ps.active ? ps.uly + 1 : INT_MIN);
+            const int maxx = __reduce_max_sync(FULL, ps.active ? ps.ulx : INT_MIN) + 1;
+            const int maxy = __reduce_max_sync(FULL, ps.active ? ps.uly : INT_MIN) + 1;
             bw = maxx - minx + 1;
             const int bh = maxy - miny + 1;
             if (ALG == ALG_BOX) {
@@ -249,88 +243,104 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
         if (kStats) cnt.v[kStatTilesSuccess] += 1;
         if (kStats) cnt.v[kStatTexelEvals] += n;
         const bool full = A == FULL;
+        // Evaluation counts follow the paper's assignment of texel i to lane
+        // h(i, A) (edge remapping) or to lane i, whichever lane of the warp
+        // does the arithmetic.
         const int my_i = (full || !p.edge_remap) ? lane : (((A >> lane) & 1u) ? __popc(A & lt) : 32);
-        // step 3 (indices): where each of the 4 taps is produced
-        int j[4];
+        sel.count = my_i < n ? 1 : 0;
         const int dx0 = ps.ulx - minx, dy0 = ps.uly - miny;
-        if (ALG == ALG_BOX) {
-            j[0] = dx0 + dy0 * bw;
-            j[1] = j[0] + 1;
-            j[2] = j[0] + bw;
-            j[3] = j[2] + 1;
-        } else if (ALG == ALG_MASK) {
-            const int t00 = dy0 * bw + dx0, t01 = t00 + bw;
-            if (mcls == 1) {
-                j[0] = __popc(Bw[0] & ((1u << t00) - 1u));
-                j[2] = __popc(Bw[0] & ((1u << t01) - 1u));
-            } else if (mcls == 2) {
-                const unsigned long long B = ((unsigned long long)Bw[1] << 32) | Bw[0];
-                j[0] = __popcll(B & ((1ull << t00) - 1ull));
-                j[2] = __popcll(B & ((1ull << t01) - 1ull));
-            } else {
-                j[0] = mask_rank<NW>(Bw, pre, t00);
-                j[2] = mask_rank<NW>(Bw, pre, t01);
+        const int t00 = dy0 * bw + dx0, t01 = t00 + bw;  // box positions of taps (0,0) and (0,1)
+        int j[4];  // lanes that hold taps k = (k%2, k/2)
+        if (ALG == ALG_BOX || (ALG == ALG_MASK && mcls == 1)) {
+            // A box of at most 32 texels: lane L evaluates box position L
+            // when it is in the set, so each tap is read from the lane of its
+            // box position and no compaction is needed.  The texels, hence
+            // every output, are those of the paper's lane assignment.
+            j[0] = t00;
+            j[1] = t00 + 1;
+            j[2] = t01;
+            j[3] = t01 + 1;
+            const bool in_set = ALG == ALG_BOX ? lane < n : ((Bw[0] >> lane) & 1u) != 0;
+            if (in_set) {
+                const int q = div_small(lane, bw);
+                sel.produce = true;
+                sel.tx = minx + (lane - q * bw);
+                sel.ty = miny + q;
             }
-            j[1] = j[0] + 1;
-            j[3] = j[2] + 1;
-            // Each set bit's rank is known to the lanes that need it, so the
-            // texel of rank i (the i-th set bit, h(i, B)) reaches its producer
-            // through the warp's rank slots: no bit search is needed.
-            if (ps.active) {
-                ranks[j[0]] = (dy0 << 16) | dx0;
-                ranks[j[1]] = (dy0 << 16) | (dx0 + 1);
-                ranks[j[2]] = ((dy0 + 1) << 16) | dx0;
-                ranks[j[3]] = ((dy0 + 1) << 16) | (dx0 + 1);
-            }
-            __syncwarp();
         } else {
+            // Larger masks and List Merge: texel i is evaluated by lane
+            // h(i, A); each tap is read from the lane of its rank.
+            if (ALG == ALG_MASK) {
+                if (mcls == 2) {
+                    const unsigned long long B = ((unsigned long long)Bw[1] << 32) | Bw[0];
+                    j[0] = __popcll(B & ((1ull << t00) - 1ull));
+                    j[2] = __popcll(B & ((1ull << t01) - 1ull));
+                } else {
+                    j[0] = mask_rank<NW>(Bw, pre, t00);
+                    j[2] = mask_rank<NW>(Bw, pre, t01);
+                }
+                j[1] = j[0] + 1;
+                j[3] = j[2] + 1;
+                // The texel of rank i (the i-th set bit, h(i, B)) reaches its
+                // producer through the warp's rank slots, so no bit search is
+                // needed.  Up to 64 bits, lane L stands for bit positions L
+                // and L + 32, and the rank of a set bit is a masked popcount;
+                // larger masks are filled by the pixels, each at the ranks of
+                // its taps.
+                if (mcls == 2) {
+                    if ((Bw[0] >> lane) & 1u) ranks[__popc(Bw[0] & lt)] = lane;
+                    if ((Bw[1] >> lane) & 1u) ranks[pre[1] + __popc(Bw[1] & lt)] = lane + 32;
+                } else if (ps.active) {
+                    ranks[j[0]] = t00;
+                    ranks[j[1]] = t00 + 1;
+                    ranks[j[2]] = t01;
+                    ranks[j[3]] = t01 + 1;
+                }
+                __syncwarp();
+            } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                j[k] = 0;
-                if (ps.active) {
-                    const unsigned long long key =
-                        ((unsigned long long)(uint32_t)(dy0 + (k >> 1)) << 32) | (uint32_t)(dx0 + (k & 1));
-                    unsigned h = hash_key(key) & 255u;
-                    for (int probe = 0; probe < 256; ++probe) {
-                        const unsigned long long kk = T->keys[h];
-                        if (kk == key) {
-                            j[k] = T->index[h];
-                            break;
+                for (int k = 0; k < 4; ++k) {
+                    j[k] = 0;
+                    if (ps.active) {
+                        const unsigned long long key =
+                            ((unsigned long long)(uint32_t)(dy0 + (k >> 1)) << 32) | (uint32_t)(dx0 + (k & 1));
+                        unsigned h = hash_key(key) & 255u;
+                        for (int probe = 0; probe < 256; ++probe) {
+                            const unsigned long long kk = T->keys[h];
+                            if (kk == key) {
+                                j[k] = T->index[h];
+                                break;
+                            }
+                            if (kk == kEmpty) break;
+                            h = (h + 1) & 255u;
                         }
-                        if (kk == kEmpty) break;
-                        h = (h + 1) & 255u;
                     }
                 }
             }
-        }
-        // step 2: texel i is evaluated by lane h(i, A)
-        if (my_i < n) {
-            int x, y;
-            if (ALG == ALG_BOX) {
-                const int q = div_small(my_i, bw);
-                x = minx + (my_i - q * bw);
-                y = miny + q;
-            } else if (ALG == ALG_MASK) {
-                const int v = ranks[my_i];
-                x = minx + (v & 0xffff);
-                y = miny + (v >> 16);
-            } else {
-                const unsigned long long key = T->list[my_i];
-                x = minx + (int)(uint32_t)key;
-                y = miny + (int)(uint32_t)(key >> 32);
+            if (my_i < n) {
+                int x, y;
+                if (ALG == ALG_MASK) {
+                    const int t = ranks[my_i];  // bit position dy * bw + dx
+                    const int q = div_small(t, bw);
+                    x = minx + (t - q * bw);
+                    y = miny + q;
+                } else {
+                    const unsigned long long key = T->list[my_i];
+                    x = minx + (int)(uint32_t)key;
+                    y = miny + (int)(uint32_t)(key >> 32);
+                }
+                sel.produce = true;
+                sel.tx = x;
+                sel.ty = y;
             }
-            sel.produce = true;
-            sel.tx = x;
-            sel.ty = y;
-            sel.count = 1;
-        }
-        if (ALG == ALG_MASK) __syncwarp();  // rank slots free for the next tile
-        if (!full && p.edge_remap) {
+            if (ALG == ALG_MASK) __syncwarp();  // rank slots free for the next tile
+            if (!full && p.edge_remap) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) j[k] = nth_set_lane(A, j[k]);
+                for (int k = 0; k < 4; ++k) j[k] = nth_set_lane(A, j[k]);
+            }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sel.src[k] = j[k] & 31;
+        for (int k = 0; k < 4; ++k) sel.src[k] = j[k];
     }
     if (ALG == ALG_LIST) {
         __syncwarp();
