@@ -94,50 +94,36 @@ struct PixelSetup {
 constexpr float kCoordLimit = 4194304.0f;  // 2^22
 
 __device__ __forceinline__ void setup_coords(float2 uv, float fW, float fH, PixelSetup &p) {
-    float xf = __fsub_rn(__fmul_rn(uv.x, fW), 0.5f);
-    float yf = __fsub_rn(__fmul_rn(uv.y, fH), 0.5f);
-    bool ok = fabsf(xf) < kCoordLimit && fabsf(yf) < kCoordLimit;  // false for NaN
-    float fx = floorf(xf), fy = floorf(yf);
+    // x - 0.5 is x + (-0.5) in IEEE arithmetic; the packed operations round
+    // each component like their scalar forms
+    const float2 xy = __fadd2_rn(__fmul2_rn(uv, make_float2(fW, fH)), make_float2(-0.5f, -0.5f));
+    bool ok = fabsf(xy.x) < kCoordLimit && fabsf(xy.y) < kCoordLimit;  // false for NaN
+    float fx = floorf(xy.x), fy = floorf(xy.y);
     p.ulx = ok ? (int)fx : 0;
     p.uly = ok ? (int)fy : 0;
-    p.s = __fsub_rn(xf, fx);  // read for active pixels only
-    p.t = __fsub_rn(yf, fy);
+    const float2 st = __fadd2_rn(xy, make_float2(-fx, -fy));  // read for active pixels only
+    p.s = st.x;
+    p.t = st.y;
     p.active = p.active && ok;
 }
 
 __device__ __forceinline__ bool is_minified(float4 j, float fW, float fH) {
-    float a = __fmul_rn(j.x, fW), b = __fmul_rn(j.y, fH);
-    float c = __fmul_rn(j.z, fW), d = __fmul_rn(j.w, fH);
-    float rx = __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b));
-    float ry = __fadd_rn(__fmul_rn(c, c), __fmul_rn(d, d));
+    const float2 ab = __fmul2_rn(make_float2(j.x, j.y), make_float2(fW, fH));
+    const float2 cd = __fmul2_rn(make_float2(j.z, j.w), make_float2(fW, fH));
+    const float2 ab2 = __fmul2_rn(ab, ab), cd2 = __fmul2_rn(cd, cd);
+    const float rx = __fadd_rn(ab2.x, ab2.y), ry = __fadd_rn(cd2.x, cd2.y);
     return !(rx <= 1.0f && ry <= 1.0f);
 }
 
-// Bilinear weights of taps k = (k%2, k/2).
+// Bilinear weights of taps k = (k%2, k/2): (1-s)(1-t), s(1-t), (1-s)t, st.
 __device__ __forceinline__ void bilinear_weights(float s, float t, float w[4]) {
-    float os = __fsub_rn(1.0f, s), ot = __fsub_rn(1.0f, t);
-    w[0] = __fmul_rn(os, ot);
-    w[1] = __fmul_rn(s, ot);
-    w[2] = __fmul_rn(os, t);
-    w[3] = __fmul_rn(s, t);
-}
-
-// acc = 0; acc = fma(w_k, p_k, acc) for k = 0..3, per channel; alpha of
-// every block texel is 1.0.
-__device__ __forceinline__ float4 filter_rgba8(const float w[4], const uint32_t p[4], const float *lut) {
-    float r = 0.f, g = 0.f, b = 0.f, a = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        r = __fmaf_rn(w[k], lut[p[k] & 0xffu], r);
-        g = __fmaf_rn(w[k], lut[(p[k] >> 8) & 0xffu], g);
-        b = __fmaf_rn(w[k], lut[(p[k] >> 16) & 0xffu], b);
-        a = __fmaf_rn(w[k], 1.0f, a);
-    }
-    return make_float4(r, g, b, a);
-}
-
-__device__ __forceinline__ float4 rgba8_to_float(uint32_t p, const float *lut) {
-    return make_float4(lut[p & 0xffu], lut[(p >> 8) & 0xffu], lut[(p >> 16) & 0xffu], 1.0f);
+    const float2 o = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-s, -t));
+    const float2 w01 = __fmul2_rn(make_float2(o.x, s), make_float2(o.y, o.y));
+    const float2 w23 = __fmul2_rn(make_float2(o.x, s), make_float2(t, t));
+    w[0] = w01.x;
+    w[1] = w01.y;
+    w[2] = w23.x;
+    w[3] = w23.y;
 }
 
 // h(i, A) for a 32-bit lane mask: lane of the i-th set bit.

@@ -96,17 +96,18 @@ __device__ __forceinline__ float3 fetch_decode(const ExactParams &p, int x, int 
     return decode_texel_f(blk, x, y, T);
 }
 
-// acc = fma(w_k, p_k, acc) from 0, k = 0..3; alpha of every block texel is 1.
+// acc = fma(w_k, p_k, acc) from 0, k = 0..3; alpha of every block texel is
+// 1.  The channels run in pairs (r, g) and (b, a) through packed FMAs that
+// round each component like fmaf.
 __device__ __forceinline__ float4 filter4(const float w[4], const float3 t[4]) {
-    float r = 0.f, g = 0.f, b = 0.f, a = 0.f;
+    float2 rg = make_float2(0.f, 0.f), ba = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        r = __fmaf_rn(w[k], t[k].x, r);
-        g = __fmaf_rn(w[k], t[k].y, g);
-        b = __fmaf_rn(w[k], t[k].z, b);
-        a = __fmaf_rn(w[k], 1.0f, a);
+        const float2 wk = make_float2(w[k], w[k]);
+        rg = __ffma2_rn(wk, make_float2(t[k].x, t[k].y), rg);
+        ba = __ffma2_rn(wk, make_float2(t[k].z, 1.0f), ba);
     }
-    return make_float4(r, g, b, a);
+    return make_float4(rg.x, rg.y, ba.x, ba.y);
 }
 
 template <int ALG, int TW, int MD, bool kStats>
