@@ -64,13 +64,18 @@ __device__ __forceinline__ void texel_features(const MlpDevice &m, int x, int y,
         const __half2 *h10 = reinterpret_cast<const __half2 *>(&q10);
         const __half2 *h01 = reinterpret_cast<const __half2 *>(&q01);
         const __half2 *h11 = reinterpret_cast<const __half2 *>(&q11);
+        // channels 2c and 2c+1 together: packed multiply and FMAs round each
+        // component like their scalar forms
+        const float2 v00 = make_float2(w00, w00), v10 = make_float2(w10, w10), v01 = make_float2(w01, w01),
+                     v11 = make_float2(w11, w11);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const float2 a = __half22float2(h00[c]), b = __half22float2(h10[c]);
-            const float2 cc = __half22float2(h01[c]), d = __half22float2(h11[c]);
-            f[g * 8 + 2 * c] = __fmaf_rn(w11, d.x, __fmaf_rn(w01, cc.x, __fmaf_rn(w10, b.x, __fmul_rn(w00, a.x))));
-            f[g * 8 + 2 * c + 1] =
-                __fmaf_rn(w11, d.y, __fmaf_rn(w01, cc.y, __fmaf_rn(w10, b.y, __fmul_rn(w00, a.y))));
+            float2 acc = __fmul2_rn(v00, __half22float2(h00[c]));
+            acc = __ffma2_rn(v10, __half22float2(h10[c]), acc);
+            acc = __ffma2_rn(v01, __half22float2(h01[c]), acc);
+            acc = __ffma2_rn(v11, __half22float2(h11[c]), acc);
+            f[g * 8 + 2 * c] = acc.x;
+            f[g * 8 + 2 * c + 1] = acc.y;
         }
     }
 }
@@ -78,6 +83,20 @@ __device__ __forceinline__ void texel_features(const MlpDevice &m, int x, int y,
 __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
     const __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// relu(a), relu(b) as FP16 (a in the low half), round to nearest.
+__device__ __forceinline__ uint32_t relu_half2(float a, float b) {
+    uint32_t r;
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+
+// relu(a), relu(b) as E4M3 (a in the low byte), round to nearest, saturating.
+__device__ __forceinline__ uint16_t relu_e4m3x2(float a, float b) {
+    uint16_t r;
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(b), "f"(a));
+    return r;
 }
 
 // E4M3 pair: bytes of a (low) and b (high), round to nearest, saturating.
@@ -129,6 +148,10 @@ __device__ __forceinline__ void hidden_epilogue(unsigned char *sm, uint32_t tadd
     for (int q = 0; q < 4; ++q) tc::tmem_ld16(taddr + 16 * q, d + 16 * q);
     tc::tmem_wait_ld();
     unsigned char *H = sm + kSmH;
+    // Bias and scale in packed pairs; the ReLU is applied by the conversion
+    // (the rounding of a negative value is not positive, and the positive
+    // scales do not change signs).
+    const float2 *b2 = reinterpret_cast<const float2 *>(bias);
     if (!fp8) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -136,26 +159,25 @@ __device__ __forceinline__ void hidden_epilogue(unsigned char *sm, uint32_t tadd
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int k = 8 * c + 2 * i;
-                const float a = fmaxf(__fadd_rn(d[k], bias[k]), 0.f);
-                const float b = fmaxf(__fadd_rn(d[k + 1], bias[k + 1]), 0.f);
-                w[i] = pack_half2(a, b);
+                const float2 t = __fadd2_rn(make_float2(d[k], d[k + 1]), b2[k / 2]);
+                w[i] = relu_half2(t.x, t.y);
             }
             *reinterpret_cast<uint4 *>(H + core_offset(row, 8 * c, 64, 2)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     } else {
+        const float2 *o2 = reinterpret_cast<const float2 *>(oscale);
+        const float2 *i2 = reinterpret_cast<const float2 *>(inv_a);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             uint32_t w[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                float v[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int k = 16 * c + 4 * i + e;
-                    const float h = fmaxf(__fmaf_rn(d[k], oscale[k], bias[k]), 0.f);
-                    v[e] = __fmul_rn(h, inv_a[k]);
-                }
-                w[i] = (uint32_t)pack_e4m3x2(v[0], v[1]) | ((uint32_t)pack_e4m3x2(v[2], v[3]) << 16);
+                const int k = 16 * c + 4 * i;
+                float2 t0 = __ffma2_rn(make_float2(d[k], d[k + 1]), o2[k / 2], b2[k / 2]);
+                float2 t1 = __ffma2_rn(make_float2(d[k + 2], d[k + 3]), o2[k / 2 + 1], b2[k / 2 + 1]);
+                t0 = __fmul2_rn(t0, i2[k / 2]);
+                t1 = __fmul2_rn(t1, i2[k / 2 + 1]);
+                w[i] = (uint32_t)relu_e4m3x2(t0.x, t0.y) | ((uint32_t)relu_e4m3x2(t1.x, t1.y) << 16);
             }
             *reinterpret_cast<uint4 *>(H + core_offset(row, 16 * c, 64, 1)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
