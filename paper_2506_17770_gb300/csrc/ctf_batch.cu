@@ -5,11 +5,13 @@
 // Block views: persistent CTAs of 8 warps, like the per-view exact kernel;
 // every warp takes items of 32 consecutive warp tiles of one view from an
 // atomic counter (lane 0 fetches the next item while the current one runs)
-// and walks them with the next tile's inputs prefetched.  Learned views: persistent CTAs of 4
-// warps that hold 128 TMEM columns for the whole launch; the CTA takes items
-// of 4 warp tiles (one per warp, sharing an MLP chain), `items_per_fetch` at
-// a time.  A prefix over each kind's per-view item counts maps an item to its
-// view; the prefixes of up to 1024 views are cached in shared memory.
+// and walks them with the next tile's inputs prefetched.  Learned views:
+// persistent CTAs of 4 warps that hold 128 TMEM columns for the whole launch;
+// the CTA takes items of 8 warp tiles (two per warp, their texel lists packed
+// into shared MLP chains; 4 tiles, one per warp, for per-pixel 4-tap),
+// `items_per_fetch` at a time.  A prefix over each kind's per-view item
+// counts maps an item to its view; the prefixes of up to 1024 block views
+// (256 learned views) are cached in shared memory.
 // Fetching is a plain fetch-and-add: no thread ever waits on another CTA.
 #include <algorithm>
 #include <cstdint>
@@ -38,6 +40,7 @@ constexpr int kBlockWarps = 8;         // warps per CTA of the block-view kernel
 constexpr int kBlockItemTiles = 32;    // warp tiles per block-view item (one warp)
 constexpr int kMaxViews = 4096;
 constexpr int kSmViews = 1024;         // item prefixes cached in shared memory up to this many views
+constexpr int kSmViewsMlp = 256;       // the same for the learned kernel (4 CTAs of it share an SM)
 
 struct __align__(16) BatchViewDev {
     ExactParams p;
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(kRows) batch_mlp_kernel(const BatchParams b) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned long long block_stats[kNumStats];
     __shared__ long long s_item;
-    __shared__ int s_begin[kSmViews];
+    __shared__ int s_begin[kSmViewsMlp];
     __shared__ __align__(16) BatchViewDev s_view;  // the current item's view
     __shared__ int s_view_k;
     // the first view's network goes in now; a view with another network
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(kRows) batch_mlp_kernel(const BatchParams b) {
 #pragma unroll
     for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
     const unsigned char *loaded_img = reinterpret_cast<const unsigned char *>(m0.img);
-    const bool cached = b.nkind <= kSmViews && b.total_items < 0x7fffffffLL;
+    const bool cached = b.nkind <= kSmViewsMlp && b.total_items < 0x7fffffffLL;
     if (cached)
         for (int i = threadIdx.x; i < b.nkind; i += blockDim.x) s_begin[i] = (int)__ldg(b.item_begin + i);
     const int *sb = cached ? s_begin : nullptr;
@@ -234,7 +237,10 @@ __global__ void __launch_bounds__(kRows) batch_mlp_kernel(const BatchParams b) {
                 loaded_img = img;
                 __syncthreads();
             }
-            ok = mlp_warp_tile<ALG, TW, MD>(V.p, V.m, ch, local * 4 + warp, lane, lt, T, cnt, inv_a1, b.err);
+            if (ALG == ALG_4TAP)
+                ok = mlp_warp_tile<ALG, TW, MD>(V.p, V.m, ch, local * 4 + warp, lane, lt, T, cnt, inv_a1, b.err);
+            else
+                ok = mlp_group<ALG, TW, MD>(V.p, V.m, ch, local * kGroupTiles, lane, lt, T, cnt, inv_a1, b.err);
         }
     }
     if (b.stats && lane == 0) {
@@ -374,7 +380,7 @@ int make_plan(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t see
         d.learned = v.tex->mode != CTF_EVAL_BLOCK;
         if (d.learned) d.m = mlp_device_view(v.tex);
         const int kind = d.learned ? 1 : 0;
-        const long long per_item = d.learned ? 4 : kBlockItemTiles;
+        const long long per_item = d.learned ? mlp_group_tiles((int)alg) : kBlockItemTiles;
         plan->index[kind].push_back(i);
         plan->begin[kind].push_back(plan->items[kind]);
         plan->items[kind] += (p.n_tiles + per_item - 1) / per_item;

@@ -90,10 +90,12 @@ __global__ void __launch_bounds__(kRows) mlp_filter_kernel(const ExactParams p, 
     Counters cnt;
 #pragma unroll
     for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
-    const long long n_iter = (p.n_tiles + 3) / 4;
+    constexpr int kTiles = mlp_group_tiles(ALG);
+    const long long n_iter = (p.n_tiles + kTiles - 1) / kTiles;
     bool ok = true;
     for (long long it = blockIdx.x; it < n_iter && ok; it += gridDim.x) {
-        ok = mlp_warp_tile<ALG, TW, MD>(p, m, ch, it * 4 + warp, lane, lt, T, cnt, inv_a1, err);
+        if (ALG == ALG_4TAP) ok = mlp_warp_tile<ALG, TW, MD>(p, m, ch, it * kTiles + warp, lane, lt, T, cnt, inv_a1, err);
+        else ok = mlp_group<ALG, TW, MD>(p, m, ch, it * kTiles, lane, lt, T, cnt, inv_a1, err);
     }
     if (p.stats) {
         if (lane == 0) {
@@ -171,7 +173,7 @@ cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg,
     if (p.n_tiles == 0) return cudaSuccess;
     cudaError_t e = prepare(fn);
     if (e != cudaSuccess) return e;
-    const long long iters = (p.n_tiles + 3) / 4;
+    const long long iters = (p.n_tiles + mlp_group_tiles(alg) - 1) / mlp_group_tiles(alg);
     const long long cap = (long long)device_sm_count() * 4;
     const int grid = (int)(iters < cap ? iters : cap);
     fn<<<grid, kRows, kSmRequest, stream>>>(p, m, err);

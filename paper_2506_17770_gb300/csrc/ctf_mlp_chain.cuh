@@ -28,11 +28,27 @@ constexpr int kSmBar = kSmH + 16384;     // mbarrier (8 B)
 constexpr int kSmTmem = kSmBar + 8;      // TMEM base address (4 B)
 constexpr int kSmList = kSmBar + 64;     // List Merge tables (4 x ListTable)
 constexpr int kSmRanks = kSmList + 4 * (int)sizeof(ListTable);  // Mask rank slots (4 x 32 ints)
-constexpr int kSmBytes = kSmRanks + 4 * 32 * 4;
+// Packed groups of 8 tiles (collaborative algorithms and STF): per pixel the
+// fractions (s, t) and a packed word, the texel value of every list row, the
+// texels per tile; the texel lists themselves sit in the X buffer until the
+// first chain overwrites it.
+constexpr int kGroupTiles = 8;
+constexpr int kSmPixST = kSmRanks + 4 * 32 * 4;       // 256 x float2
+constexpr int kSmPixInfo = kSmPixST + 256 * 8;        // 256 x uint32
+constexpr int kSmOut = kSmPixInfo + 256 * 4;          // 256 rows x float4
+constexpr int kSmCount = kSmOut + 256 * 16;           // 8 x int
+constexpr int kSmTexList = kSmX;                      // 8 tiles x 32 x int2 (2 KB, inside X)
+constexpr int kSmBytes = kSmCount + kGroupTiles * 4;
 // Reserve enough shared memory that at most 4 CTAs share an SM: 4 x 128 TMEM
-// columns fill the SM's 512.
-constexpr int kSmRequest = 48 * 1024;
+// columns fill the SM's 512 (5 x 54 KB exceed the SM's 228 KB).
+constexpr int kSmRequest = 54 * 1024;
 static_assert(kSmBytes <= kSmRequest, "shared memory layout");
+static_assert(5 * kSmRequest > 228 * 1024, "more than 4 CTAs per SM would overcommit TMEM");
+
+// Tiles per CTA iteration of the learned filter: per-pixel 4-tap fills the
+// 128 rows with one tile per warp and tap, the other algorithms pack the
+// texel lists of two tiles per warp into as few 128-row chains as they need.
+__host__ __device__ constexpr int mlp_group_tiles(int alg) { return alg == 0 ? 4 : kGroupTiles; }
 
 struct Chain {
     unsigned char *sm;
@@ -456,6 +472,172 @@ __device__ __forceinline__ bool mlp_warp_tile(const ExactParams &p, const MlpDev
         if (p.evals) p.evals[idx] = count;
     }
         return true;
+}
+
+// One iteration of the learned-decode filter for the collaborative
+// algorithms and STF.  The CTA's 4 warps run step 1 on two pixel tiles each
+// (slots g = warp and g = 4 + warp of the group of 8 tiles from `first`); the
+// texel lists of the 8 tiles are packed into consecutive rows in slot order
+// and decoded by as few 128-row chains as they fill (none for an empty
+// group), and every pixel then gathers its taps from the rows.  Which thread
+// computes a texel does not change its value: the rows of an MMA are
+// independent.  Returns false (for every thread alike) if a chain gave up.
+template <int ALG, int TW, int MD>
+__device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice &m, Chain &ch, long long first,
+                                          int lane, uint32_t lt, ListTable *T, Counters &cnt, const float *inv_a1,
+                                          int *err) {
+    constexpr int TH = 32 / TW;
+    unsigned char *sm = ch.sm;
+    const int warp = threadIdx.x >> 5, tx = lane % TW, ty = lane / TW;
+    const float fW = (float)p.Wt, fH = (float)p.Ht;
+    float2 *pix_st = reinterpret_cast<float2 *>(sm + kSmPixST);
+    uint32_t *pix_info = reinterpret_cast<uint32_t *>(sm + kSmPixInfo);
+    int2 *texlist = reinterpret_cast<int2 *>(sm + kSmTexList);
+    float4 *outrow = reinterpret_cast<float4 *>(sm + kSmOut);
+    int *count = reinterpret_cast<int *>(sm + kSmCount);
+    int *ranks = reinterpret_cast<int *>(sm + kSmRanks) + 32 * warp;
+
+    // ---- step 1 on the warp's two tiles; the texel list of slot g goes to
+    // texlist[32 g + rank], and each pixel keeps (s, t) and a packed word:
+    // bits 0-19 the list indices of its 4 taps (success) or of its own texel
+    // (bits 0-4, fallback), 20-22 its count, 23 active, 24 inside, 25 success.
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const int g = 4 * h + warp;
+        const long long tile = first + g;
+        const bool valid = tile < p.n_tiles;
+        const int bx = valid ? (int)(tile % p.tiles_x) : 0, by = valid ? (int)(tile / p.tiles_x) : 0;
+        const int px = bx * TW + tx, py = by * TH + ty;
+        const bool inside = valid && px < p.W && py < p.H;
+        const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
+        float2 uv = make_float2(0.f, 0.f);
+        float4 jac = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool covered = inside;
+        if (inside) {
+            uv = __ldcs(p.uv + idx);
+            if (ALG >= ALG_LIST) jac = __ldcs(p.jac + idx);
+            if (p.cov) covered = __ldcs(p.cov + idx) != 0;
+        }
+        PixelSetup ps;
+        ps.active = covered;
+        setup_coords(uv, fW, fH, ps);
+        Selection sel;
+        if (valid) {
+            sel = select_tile<ALG, MD, true>(p, ps, jac, px, py, lane, lt, T, ranks, cnt);
+        } else {
+            sel.path = PATH_EMPTY;
+            sel.A = 0;
+            sel.produce = false;
+            sel.count = 0;
+            sel.my_rank = 0;
+        }
+        if (sel.produce)
+            texlist[32 * g + sel.my_rank] =
+                make_int2(min(max(sel.tx, 0), p.Wt - 1), min(max(sel.ty, 0), p.Ht - 1));
+        const bool succ = sel.path == PATH_SUCCESS;
+        if (lane == 0) count[g] = succ ? sel.n : __popc(sel.A);
+        // (inactive pixels carry arbitrary tap indices: masked to their fields)
+        uint32_t info = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) info |= ((uint32_t)sel.rk[k] & 31u) << (5 * k);
+        info = succ ? info : ((uint32_t)sel.my_rank & 31u);
+        info |= ((uint32_t)sel.count << 20) | (ps.active ? 1u << 23 : 0u) | (inside ? 1u << 24 : 0u) |
+                (succ ? 1u << 25 : 0u);
+        pix_st[32 * g + lane] = make_float2(ps.s, ps.t);
+        pix_info[32 * g + lane] = info;
+    }
+    __syncthreads();
+
+    // ---- rows: slot g owns [base_g, base_g + count[g]).  Every thread
+    // reads the texels of its rows (threadIdx.x and 128 + threadIdx.x) before
+    // the first chain overwrites the X buffer that holds the lists.
+    int cnts[kGroupTiles];
+#pragma unroll
+    for (int g = 0; g < kGroupTiles; ++g) cnts[g] = count[g];
+    int R = 0, my_base[2] = {0, 0};
+    int2 xy[2] = {make_int2(0, 0), make_int2(0, 0)};
+    {
+        int start[kGroupTiles];
+#pragma unroll
+        for (int g = 0; g < kGroupTiles; ++g) {
+            start[g] = R;
+            if (g == warp) my_base[0] = R;
+            if (g == 4 + warp) my_base[1] = R;
+            R += cnts[g];
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int row = kRows * c + (int)threadIdx.x;
+            if (row < R) {
+                int g = 0, b = 0;
+#pragma unroll
+                for (int k = 1; k < kGroupTiles; ++k) {
+                    if (row >= start[k]) {
+                        g = k;
+                        b = start[k];
+                    }
+                }
+                xy[c] = texlist[32 * g + (row - b)];
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- the chains (CTA-uniform count: 0, 1 or 2)
+    const int passes = (R + kRows - 1) / kRows;
+#pragma unroll 1
+    for (int c = 0; c < passes; ++c) {
+        const int row = kRows * c + (int)threadIdx.x;
+        if (row < R) {
+            const int2 t = c == 0 ? xy[0] : xy[1];
+            float f[kMlpIn];
+            texel_features(m, t.x, t.y, f);
+            store_x_row(sm, threadIdx.x, f, m.fp8, inv_a1);
+        } else {
+            store_zero_x_row(sm, threadIdx.x);
+        }
+        float4 v;
+        if (!mlp_chain(ch, m.fp8, v, err)) return false;
+        outrow[row] = v;
+    }
+    __syncthreads();
+
+    // ---- step 3: gather from the rows, filter, store
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const int g = 4 * h + warp;
+        const uint32_t info = pix_info[32 * g + lane];
+        if (!((info >> 24) & 1u)) continue;  // outside the frame (or no tile)
+        const long long tile = first + g;
+        const int bx = (int)(tile % p.tiles_x), by = (int)(tile / p.tiles_x);
+        const uint32_t idx = (uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx);
+        const int b = h == 0 ? my_base[0] : my_base[1];
+        float4 result = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint8_t cv = 0;
+        if ((info >> 23) & 1u) {
+            if ((info >> 25) & 1u) {
+                const float2 st = pix_st[32 * g + lane];
+                float w[4];
+                bilinear_weights(st.x, st.y, w);
+                float2 rg = make_float2(0.f, 0.f), ba = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float4 t = outrow[b + (int)((info >> (5 * k)) & 31u)];
+                    const float2 wk = make_float2(w[k], w[k]);
+                    rg = __ffma2_rn(wk, make_float2(t.x, t.y), rg);
+                    ba = __ffma2_rn(wk, make_float2(t.z, t.w), ba);
+                }
+                result = make_float4(rg.x, rg.y, ba.x, ba.y);
+                cv = (uint8_t)((info >> 20) & 7u);
+            } else {
+                result = outrow[b + (int)(info & 31u)];
+                cv = 1;
+            }
+        }
+        __stcs(p.out + idx, result);
+        if (p.evals) p.evals[idx] = cv;
+    }
+    return true;
 }
 
 }  // namespace

@@ -86,6 +86,8 @@ struct Selection {
     bool produce;    // this lane evaluates a texel
     int tx, ty;      // that texel (unclamped)
     int src[4];      // success path: lane holding tap k = (k%2, k/2)
+    int rk[4];       // success path: index of tap k in the warp's texel list
+    int my_rank;     // index of this lane's texel in that list (when produce)
     uint8_t count;   // texel evaluations of this lane
 };
 
@@ -105,7 +107,8 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
     sel.produce = false;
     sel.tx = ps.ulx;  // lanes that produce nothing keep their own upper-left texel
     sel.ty = ps.uly;
-    sel.count = 0;  // sel.src is set on the success path only
+    sel.count = 0;  // sel.src and sel.rk are set on the success path only
+    sel.my_rank = 0;
     if (kStats) cnt.v[kStatTilesTotal] += 1;
     if (sel.A == 0) {
         sel.path = PATH_EMPTY;
@@ -233,6 +236,7 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
             int dx, dy;
             stf_offset(px, py, p.view, p.k0, p.k1, ps.s, ps.t, dx, dy);
             sel.produce = true;
+            sel.my_rank = __popc(A & lt);  // producers are the active lanes
             sel.tx = ps.ulx + dx;
             sel.ty = ps.uly + dy;
             sel.count = 1;
@@ -261,6 +265,18 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
             j[2] = t01;
             j[3] = t01 + 1;
             const bool in_set = ALG == ALG_BOX ? lane < n : ((Bw[0] >> lane) & 1u) != 0;
+            // the texel list in rank order (what the learned decode packs)
+            if (ALG == ALG_BOX) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) sel.rk[k] = j[k];
+                sel.my_rank = lane;
+            } else {
+                sel.rk[0] = __popc(Bw[0] & ((1u << t00) - 1u));
+                sel.rk[1] = sel.rk[0] + 1;
+                sel.rk[2] = __popc(Bw[0] & ((1u << t01) - 1u));
+                sel.rk[3] = sel.rk[2] + 1;
+                sel.my_rank = __popc(Bw[0] & lt);
+            }
             if (in_set) {
                 const int q = div_small(lane, bw);
                 sel.produce = true;
@@ -334,6 +350,9 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                 sel.ty = y;
             }
             if (ALG == ALG_MASK) __syncwarp();  // rank slots free for the next tile
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sel.rk[k] = j[k];
+            sel.my_rank = my_i;
             if (!full && p.edge_remap) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) j[k] = nth_set_lane(A, j[k]);
