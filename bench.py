@@ -343,16 +343,24 @@ def bench_learned(args, dev, stream, flush, peaks):
 
 
 def bench_batch(args, dev, stream, learned_tex, block_tex):
-    """64 views, sizes uniform in [256, 3840] x [256, 2160], each a tilted
-    plane with its own magnification range inside [0.25, 64], textures
-    alternating a 2048^2 block texture and the learned 4096^2 FP16 texture;
-    one autotuned persistent launch replayed from a CUDA graph against 64
-    sequential ctf_filter calls."""
+    """Two view sets, each a list of tilted planes with their own
+    magnification range inside [0.25, 64] and textures alternating a 2048^2
+    block texture and the learned 4096^2 FP16 texture: 64 views of sizes
+    uniform in [256, 3840] x [256, 2160], and 256 small views of sizes
+    uniform in [64, 512]^2.  Each set: one autotuned persistent launch per
+    kind replayed from a CUDA graph against sequential ctf_filter calls."""
+    out = _bench_batch_set(args, dev, stream, learned_tex, block_tex, 64, {})
+    out["small_views"] = _bench_batch_set(args, dev, stream, learned_tex, block_tex, 256,
+                                          {"min_w": 64, "min_h": 64, "max_w": 512, "max_h": 512})
+    return out
+
+
+def _bench_batch_set(args, dev, stream, learned_tex, block_tex, n_views, sizes):
     import torch
     from paper_2506_17770_gb300 import _ctf, synth
     t0 = time.perf_counter()
     tex_sizes = ((2048, 2048), (4096, 4096)) if learned_tex is not None else ((2048, 2048),)
-    raw = synth.uneven_views(64, textures=tex_sizes)
+    raw = synth.uneven_views(n_views, textures=tex_sizes, **sizes)
     gen_s = time.perf_counter() - t0
     views = []
     npix = 0
@@ -380,13 +388,34 @@ def bench_batch(args, dev, stream, learned_tex, block_tex):
     _ctf.ctf_sync_check(stream)
     _ctf.ctf_batch_graph_destroy(g)
     tg, ts = ms_graph / k * 1e-3, ms_seq / k * 1e-3
-    return {"views": len(views), "pixels": npix, "input_gen_s": gen_s,
+
+    # each kind of texel evaluation on its own (same configuration)
+    kinds = {}
+    for name, sub in (("block_views", [v for v in views if v["tex"] is block_tex]),
+                      ("learned_views", [v for v in views if v["tex"] is not block_tex])):
+        if not sub:
+            continue
+        gs = _ctf.ctf_batch_graph_create(sub, alg, 0, best)
+        ms_g = _timed_views(lambda: _ctf.ctf_batch_graph_launch(gs, stream=stream), k, 2, None, stream)
+        _ctf.ctf_batch_graph_destroy(gs)
+
+        def seq_sub(sub=sub):
+            for v in sub:
+                _ctf.ctf_filter(v["tex"], v["uv"], v["jac"], v["coverage"], v["width"], v["height"], v["view_id"],
+                                alg, 0, fo, v["out_rgba"], v["out_evals"], stream=stream)
+
+        ms_s = _timed_views(seq_sub, k, 2, None, stream)
+        px = sum(v["width"] * v["height"] for v in sub)
+        kinds[name] = {"views": len(sub), "pixels": px, "graph_ms": ms_g / k, "sequential_ms": ms_s / k,
+                       "graph_vs_sequential": ms_s / ms_g}
+    return {"views": len(views), "sizes": sizes or {"min_w": 256, "min_h": 256, "max_w": 3840, "max_h": 2160},
+            "pixels": npix, "input_gen_s": gen_s,
             "textures": "2048^2 block / 4096^2 learned FP16 alternating" if learned_tex is not None else "2048^2 block",
             "algorithm": "mask11+stf", "autotuned": best.as_dict(), "autotune_best_ms": tune_ms,
             "graph_pixels_per_s": npix / tg, "graph_ms": tg * 1e3,
             "sequential_pixels_per_s": npix / ts, "sequential_ms": ts * 1e3, "graph_vs_sequential": ts / tg,
-            "evals_per_pixel": st["texel_evals"] / max(1, st["pixels_active"]),
-            "l2": "not flushed: 64 views hold several GB, far above L2"}
+            "evals_per_pixel": st["texel_evals"] / max(1, st["pixels_active"]), "by_kind": kinds,
+            "l2": f"not flushed: {npix * 42 / 1e6:.0f} MB of pixel I/O per pass, above the 129 MB L2"}
 
 
 def dist_setup():

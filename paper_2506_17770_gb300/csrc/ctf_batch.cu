@@ -79,8 +79,15 @@ __device__ __forceinline__ int find_view(const long long *begin, const int *sbeg
 // ---------------------------------------------------------------------------
 // Block views: each warp on its own.
 // ---------------------------------------------------------------------------
+// The view bookkeeping costs registers: four CTAs per SM, not five as for the
+// per-view kernels (at five the collaborative kernels spill).
+template <int ALG>
+constexpr int batch_min_blocks() {
+    return ALG >= ALG_LIST ? 4 : 1;
+}
+
 template <int ALG, int TW, int MD>
-__global__ void __launch_bounds__(kBlockWarps * 32) batch_block_kernel(const BatchParams b) {
+__global__ void __launch_bounds__(kBlockWarps * 32, batch_min_blocks<ALG>()) batch_block_kernel(const BatchParams b) {
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
     __shared__ DecodeTables tabs;
@@ -129,30 +136,30 @@ __global__ void __launch_bounds__(kBlockWarps * 32) batch_block_kernel(const Bat
         const ExactParams &p = s_params[warp];
         const long long first = (item - (sb ? (long long)sb[k] : __ldg(b.item_begin + k))) * kBlockItemTiles;
         const long long last = min(first + kBlockItemTiles, (long long)p.n_tiles);
-        // walk the item's tiles, the next tile's inputs in flight meanwhile
-        long long tile = first;
-        int bx = (int)(tile % p.tiles_x), by = (int)(tile / p.tiles_x);
-        int px = bx * TW + tx, py = by * TH + ty;
-        bool inside = px < p.W && py < p.H;
-        uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
-        Inputs cur = load_inputs<kJac>(p, inside, idx);
-        while (tile < last) {
-            const long long nt = tile + 1;
-            int nbx = bx + 1, nby = by;
-            if (nbx >= p.tiles_x) {
+        // walk the item's tiles, the next tile's inputs in flight meanwhile;
+        // a pixel's index is the tile's first pixel plus a per-lane offset,
+        // and the lane is inside the frame while bx < lim_x and by < lim_y
+        const uint32_t W = (uint32_t)p.W, H = (uint32_t)p.H, tiles_x = (uint32_t)p.tiles_x;
+        const uint32_t lim_x = (W - (uint32_t)tx + TW - 1) / TW, lim_y = (H - (uint32_t)ty + TH - 1) / TH;
+        const uint32_t lane_off = (uint32_t)ty * W + (uint32_t)tx;
+        const uint32_t n_item = (uint32_t)(last - first);
+        uint32_t bx = (uint32_t)(first % tiles_x), by = (uint32_t)(first / tiles_x);
+        bool inside = n_item > 0 && bx < lim_x && by < lim_y;
+        uint32_t idx = by * (TH * W) + bx * TW + lane_off;
+        Inputs cur = load_inputs_any<kJac>(p, inside, idx);
+        for (uint32_t i = 0; i < n_item; ++i) {
+            uint32_t nbx = bx + 1, nby = by;
+            if (nbx >= tiles_x) {
                 nbx = 0;
                 ++nby;
             }
-            const int npx = nbx * TW + tx, npy = nby * TH + ty;
-            const bool ninside = nt < last && npx < p.W && npy < p.H;
-            const uint32_t nidx = ninside ? (uint32_t)npy * (uint32_t)p.W + (uint32_t)npx : 0u;
-            const Inputs nxt = load_inputs<kJac>(p, ninside, nidx);
-            filter_tile<ALG, TW, MD, true>(p, cur, px, py, inside, idx, lane, lt, &tabs, T, rank_slots[warp], cnt);
-            tile = nt;
+            const bool ninside = i + 1u < n_item && nbx < lim_x && nby < lim_y;
+            const uint32_t nidx = nby * (TH * W) + nbx * TW + lane_off;
+            const Inputs nxt = load_inputs_any<kJac>(p, ninside, nidx);
+            filter_tile<ALG, TW, MD, true>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
+                                           &tabs, T, rank_slots[warp], cnt);
             bx = nbx;
             by = nby;
-            px = npx;
-            py = npy;
             inside = ninside;
             idx = nidx;
             cur = nxt;
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32) batch_block_kernel(const Bat
 // Learned views: the 4 warps of a CTA share an MLP chain.
 // ---------------------------------------------------------------------------
 template <int ALG, int TW, int MD>
-__global__ void __launch_bounds__(kRows) batch_mlp_kernel(const BatchParams b) {
+__global__ void __launch_bounds__(kRows, 4) batch_mlp_kernel(const BatchParams b) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned long long block_stats[kNumStats];
     __shared__ long long s_item;

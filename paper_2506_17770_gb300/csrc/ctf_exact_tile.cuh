@@ -110,6 +110,14 @@ __device__ __forceinline__ float4 filter4(const float w[4], const float3 t[4]) {
     return make_float4(rg.x, rg.y, ba.x, ba.y);
 }
 
+// CTAs of 8 warps per SM that the exact kernels ask the compiler to fit:
+// the collaborative kernels are issue-bound, and five CTAs (40 warps) hide
+// more latency than the registers a looser cap would buy.
+template <int ALG>
+constexpr int min_blocks() {
+    return ALG >= ALG_LIST ? 5 : 1;
+}
+
 template <int ALG, int TW, int MD, bool kStats>
 __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &in, int px, int py, bool inside,
                                             uint32_t idx, int lane, uint32_t lt, const DecodeTables *tabs,

@@ -35,13 +35,6 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
-// The collaborative kernels are issue-bound: five CTAs (40 warps) per SM
-// hide more latency than the registers a looser cap would buy.
-template <int ALG>
-constexpr int min_blocks() {
-    return ALG >= ALG_LIST ? 5 : 1;
-}
-
 template <int ALG, int TW, int MD, bool kStats>
 __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kernel(const ExactParams p) {
     constexpr int TH = 32 / TW;
