@@ -108,12 +108,21 @@ typedef struct {
  *   edge_remap      1: producer of texel i is the i-th active lane h(i,A)
  *                   (supplemental Sec. 2), success needs n <= popcount(A);
  *                   0: lane i produces texel i and lanes 0..n-1 must be
- *                   active                                        [1] */
+ *                   active                                        [1]
+ *   group_dedup     learned textures, algorithms other than 4TAP: the
+ *                   texels a CTA's group of 8 consecutive warp tiles
+ *                   (tile index order) produces are evaluated once per
+ *                   distinct (clamped) texel instead of once per warp, the
+ *                   shared-memory extension of Sec. 3 that Sec. 6 proposes;
+ *                   outputs and out_evals are unchanged, ctf_stats
+ *                   texel_evals_unique counts the evaluations done.  0 or 1
+ *                                                                 [0] */
 typedef struct {
     int tile_w, tile_h;
     int budget;
     int mask_dim;
     int edge_remap;
+    int group_dedup;
 } ctf_filter_opts;
 
 /* Per-call counters (filled only when a stats pointer is given). */
@@ -126,6 +135,8 @@ typedef struct {
     int64_t tiles_fallback_minified; /* collaborative tiles with a minified pixel -> STF */
     int64_t pixels_active;
     int64_t texel_evals;             /* sum of out_evals */
+    int64_t texel_evals_unique;      /* texel evaluations done: texel_evals,
+                                        less the repeats group_dedup removed */
 } ctf_stats;
 
 /* Library and device information. */

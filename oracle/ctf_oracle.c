@@ -338,12 +338,14 @@ typedef struct {
 
 /* Output for one active lane on the STF path: its own STF texel, count 1. */
 static void stf_lane(const texel_source *src, const pixel_setup *p, int view, uint64_t seed, int fp64,
-                     float *out, double *outd, uint8_t *evals, size_t idx)
+                     float *out, double *outd, uint8_t *evals, size_t idx, int *tx, int *ty)
 {
     int dx, dy;
     oracle_stf_offset(p->px, p->py, view, seed, p->s, p->t, &dx, &dy);
     float vf[4];
     double vd[4];
+    *tx = p->ulx + dx;
+    *ty = p->uly + dy;
     fetch_texel(src, p->ulx + dx, p->uly + dy, vf, vd);
     for (int ch = 0; ch < 4; ++ch) {
         if (out) out[4 * idx + ch] = fp64 ? (float)vd[ch] : vf[ch];
@@ -367,6 +369,31 @@ static int list_find(const texel_list *L, int x, int y)
 }
 
 /*
+ * Distinct texels evaluated by a group of consecutive tiles, after clamping
+ * to the texture (a group of 8 tiles evaluates at most 8 x 32 texels).  This
+ * is the count of the shared-memory extension Sec. 6 proposes, in which a
+ * group of warps evaluates each texel once.
+ */
+typedef struct {
+    int n;
+    int x[256], y[256];
+} group_set;
+
+static void group_note(group_set *G, const texel_source *src, int x, int y)
+{
+    int xc = x < 0 ? 0 : (x > src->Wt - 1 ? src->Wt - 1 : x);
+    int yc = y < 0 ? 0 : (y > src->Ht - 1 ? src->Ht - 1 : y);
+    for (int i = 0; i < G->n; ++i)
+        if (G->x[i] == xc && G->y[i] == yc)
+            return;
+    if (G->n < 256) {
+        G->x[G->n] = xc;
+        G->y[G->n] = yc;
+        G->n++;
+    }
+}
+
+/*
  * oracle_filter_ex: filter one frame.
  *   src            texel source (exact blocks or learned)
  *   uv   [H][W][2] float, jac [H][W][4] float = (du/dx, dv/dx, du/dy, dv/dy)
@@ -374,14 +401,24 @@ static int list_find(const texel_list *L, int x, int y)
  *   out  [H][W][4] float (FP32 result; may be NULL), outd [H][W][4] double (may be NULL)
  *   evals[H][W] uint8 per-pixel texel evaluations
  *   tile_path / tile_n: per tile outcome code and texel-set size (may be NULL)
+ *   group_tiles    0, or the size of the tile groups (consecutive tile
+ *                  indices, at most 8) whose distinct evaluated texels
+ *                  stats[8] counts; 4TAP is never grouped
+ *   stats[9]       tiles_total, tiles_empty, tiles_direct, tiles_success,
+ *                  tiles_fallback_budget, tiles_fallback_minified,
+ *                  pixels_active, texel_evals (sum of evals), and the
+ *                  grouped distinct-texel count (texel_evals if ungrouped)
  * Returns 0 on success, -1 on bad arguments.
  */
 static int oracle_filter_ex(const texel_source *src, const float *uv, const float *jac, const uint8_t *cov,
                             int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h,
-                            int budget, int mask_dim, int edge_remap, int fp64, float *out, double *outd,
-                            uint8_t *evals, int32_t *tile_path, int32_t *tile_n, int64_t *stats_out)
+                            int budget, int mask_dim, int edge_remap, int group_tiles, int fp64, float *out,
+                            double *outd, uint8_t *evals, int32_t *tile_path, int32_t *tile_n,
+                            int64_t *stats_out)
 {
     if (W < 0 || H < 0 || tile_w <= 0 || tile_h <= 0 || tile_w * tile_h != 32)
+        return -1;
+    if (group_tiles < 0 || group_tiles > 8)
         return -1;
     if (alg < 0 || alg > 4 || budget < 1 || budget > 32)
         return -1;
@@ -390,9 +427,21 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
     oracle_stats st;
     memset(&st, 0, sizeof(st));
     int tiles_x = (W + tile_w - 1) / tile_w, tiles_y = (H + tile_h - 1) / tile_h;
+    /* groups of group_tiles consecutive tiles (tile index order); 4TAP is
+       never grouped */
+    const int grouped = group_tiles > 0 && alg != ALG_4TAP;
+    group_set G;
+    G.n = 0;
+    int cur_group = 0;
+    int64_t unique = 0;
     for (int by = 0; by < tiles_y; ++by) {
         for (int bx = 0; bx < tiles_x; ++bx) {
             int tile_id = by * tiles_x + bx;
+            if (grouped && tile_id / group_tiles != cur_group) {
+                unique += G.n;
+                G.n = 0;
+                cur_group = tile_id / group_tiles;
+            }
             pixel_setup lane[32];
             uint32_t A = 0;
             int any_minified = 0;
@@ -430,7 +479,9 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                     const pixel_setup *p = &lane[l];
                     size_t idx = (size_t)p->py * W + p->px;
                     if (alg == ALG_STF) {
-                        stf_lane(src, p, view, seed, fp64, out, outd, evals, idx);
+                        int tx, ty;
+                        stf_lane(src, p, view, seed, fp64, out, outd, evals, idx, &tx, &ty);
+                        group_note(&G, src, tx, ty);
                     } else {
                         float w[4], pv[4][4], o[4];
                         double pd[4][4], od[4];
@@ -554,7 +605,9 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                 for (int l = 0; l < 32; ++l) {
                     if (!lane[l].active) continue;
                     size_t idx = (size_t)lane[l].py * W + lane[l].px;
-                    stf_lane(src, &lane[l], view, seed, fp64, out, outd, evals, idx);
+                    int tx, ty;
+                    stf_lane(src, &lane[l], view, seed, fp64, out, outd, evals, idx, &tx, &ty);
+                    group_note(&G, src, tx, ty);
                 }
                 continue;
             }
@@ -568,6 +621,7 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                 size_t idx = (size_t)p->py * W + p->px;
                 fetch_texel(src, L.x[i], L.y[i], valf[i], vald[i]);
                 evals[idx] = 1;
+                group_note(&G, src, L.x[i], L.y[i]);
             }
             /* Step 3: every active lane gathers its four taps and filters. */
             for (int l = 0; l < 32; ++l) {
@@ -600,6 +654,7 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
         for (int x = 0; x < W; ++x)
             tot += evals[(size_t)y * W + x];
     st.texel_evals = tot;
+    unique += G.n;
     if (stats_out) {
         stats_out[0] = st.tiles_total;
         stats_out[1] = st.tiles_empty;
@@ -609,6 +664,7 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
         stats_out[5] = st.tiles_fallback_minified;
         stats_out[6] = st.pixels_active;
         stats_out[7] = st.texel_evals;
+        stats_out[8] = grouped ? unique : st.texel_evals;
     }
     return 0;
 }
@@ -616,25 +672,26 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
 /* Exact block decode, FP32 arithmetic with the rounding described above. */
 int oracle_filter(const uint8_t *blocks, int Wt, int Ht, const float *uv, const float *jac, const uint8_t *cov,
                   int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h, int budget,
-                  int mask_dim, int edge_remap, float *out, uint8_t *evals, int32_t *tile_path,
-                  int32_t *tile_n, int64_t *stats)
+                  int mask_dim, int edge_remap, int group_tiles, float *out, uint8_t *evals,
+                  int32_t *tile_path, int32_t *tile_n, int64_t *stats)
 {
     if (Wt <= 0 || Ht <= 0 || Wt % 4 || Ht % 4 || !blocks)
         return -1;
     texel_source src = {0, Wt, Ht, blocks, NULL};
     return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
-                            edge_remap, 0, out, NULL, evals, tile_path, tile_n, stats);
+                            edge_remap, group_tiles, 0, out, NULL, evals, tile_path, tile_n, stats);
 }
 
 /* Learned decode: texel values from the FP64 MLP, filter in double. */
 int oracle_filter_learned_f64(const void *mlp, int Wt, int Ht, const float *uv, const float *jac,
                               const uint8_t *cov, int W, int H, int view, int alg, uint64_t seed, int tile_w,
-                              int tile_h, int budget, int mask_dim, int edge_remap, double *outd,
-                              uint8_t *evals, int32_t *tile_path, int32_t *tile_n, int64_t *stats)
+                              int tile_h, int budget, int mask_dim, int edge_remap, int group_tiles,
+                              double *outd, uint8_t *evals, int32_t *tile_path, int32_t *tile_n,
+                              int64_t *stats)
 {
     if (Wt <= 0 || Ht <= 0 || !mlp)
         return -1;
     texel_source src = {1, Wt, Ht, NULL, mlp};
     return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
-                            edge_remap, 1, NULL, outd, evals, tile_path, tile_n, stats);
+                            edge_remap, group_tiles, 1, NULL, outd, evals, tile_path, tile_n, stats);
 }

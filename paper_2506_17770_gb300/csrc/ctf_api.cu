@@ -92,7 +92,7 @@ int scratch_stage(size_t bytes, void **out) {
 }
 
 struct ResolvedOpts {
-    int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1;
+    int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1, group_dedup = 0;
 };
 
 int resolve_opts(const ctf_filter_opts *o, ResolvedOpts *r) {
@@ -103,9 +103,11 @@ int resolve_opts(const ctf_filter_opts *o, ResolvedOpts *r) {
     r->budget = o->budget;
     r->mask_dim = o->mask_dim;
     r->edge_remap = o->edge_remap;
+    r->group_dedup = o->group_dedup;
     const bool shape_ok = (r->tile_w == 8 && r->tile_h == 4) || (r->tile_w == 4 && r->tile_h == 8) ||
                           (r->tile_w == 16 && r->tile_h == 2);
     if (!shape_ok) return fail(CTF_ERR_ARG, "tile %dx%d not one of 8x4, 4x8, 16x2", r->tile_w, r->tile_h);
+    if (r->group_dedup != 0 && r->group_dedup != 1) return fail(CTF_ERR_ARG, "group_dedup must be 0 or 1");
     if (r->budget < 1 || r->budget > 32) return fail(CTF_ERR_ARG, "budget %d outside [1, 32]", r->budget);
     if (r->mask_dim != 16 && r->mask_dim != 11) return fail(CTF_ERR_ARG, "mask_dim %d not 16 or 11", r->mask_dim);
     if (r->edge_remap != 0 && r->edge_remap != 1) return fail(CTF_ERR_ARG, "edge_remap must be 0 or 1");
@@ -155,6 +157,7 @@ int run_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t
     p.k1 = (uint32_t)(seed >> 32);
     p.budget = ro.budget;
     p.edge_remap = ro.edge_remap;
+    p.group_dedup = ro.group_dedup;
     p.out = reinterpret_cast<float4 *>(out);
     p.evals = evals;
     p.stats = dstats;
@@ -184,6 +187,7 @@ int read_stats(unsigned long long *dstats, ctf_stats *stats, cudaStream_t stream
     stats->tiles_fallback_minified = (int64_t)h[ctf::kStatTilesFallbackMinified];
     stats->pixels_active = (int64_t)h[ctf::kStatPixelsActive];
     stats->texel_evals = (int64_t)h[ctf::kStatTexelEvals];
+    stats->texel_evals_unique = (int64_t)h[ctf::kStatTexelEvalsUnique];
     return CTF_OK;
 }
 

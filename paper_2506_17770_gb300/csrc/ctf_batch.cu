@@ -312,7 +312,7 @@ cudaError_t prepare_batch(BatchFn fn) {
 }
 
 struct ResolvedBatch {
-    int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1;
+    int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1, group_dedup = 0;
     int items_per_fetch = 4, ctas_per_sm = 4;
 };
 
@@ -324,6 +324,7 @@ int resolve(const ctf_batch_opts *o, ResolvedBatch *r) {
     r->budget = o->filter.budget;
     r->mask_dim = o->filter.mask_dim;
     r->edge_remap = o->filter.edge_remap;
+    r->group_dedup = o->filter.group_dedup;
     r->items_per_fetch = o->items_per_fetch;
     r->ctas_per_sm = o->ctas_per_sm;
     const bool shape_ok = (r->tile_w == 8 && r->tile_h == 4) || (r->tile_w == 4 && r->tile_h == 8) ||
@@ -332,6 +333,7 @@ int resolve(const ctf_batch_opts *o, ResolvedBatch *r) {
     if (r->budget < 1 || r->budget > 32) return report(CTF_ERR_ARG, "budget %d outside [1, 32]", r->budget);
     if (r->mask_dim != 16 && r->mask_dim != 11) return report(CTF_ERR_ARG, "mask_dim %d not 16 or 11", r->mask_dim);
     if (r->edge_remap != 0 && r->edge_remap != 1) return report(CTF_ERR_ARG, "edge_remap must be 0 or 1");
+    if (r->group_dedup != 0 && r->group_dedup != 1) return report(CTF_ERR_ARG, "group_dedup must be 0 or 1");
     if (r->items_per_fetch < 1 || r->items_per_fetch > 64)
         return report(CTF_ERR_ARG, "items_per_fetch %d outside [1, 64]", r->items_per_fetch);
     if (r->ctas_per_sm < 1 || r->ctas_per_sm > 4) return report(CTF_ERR_ARG, "ctas_per_sm %d outside [1, 4]", r->ctas_per_sm);
@@ -381,6 +383,7 @@ int make_plan(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t see
         p.k1 = (uint32_t)(seed >> 32);
         p.budget = r.budget;
         p.edge_remap = r.edge_remap;
+        p.group_dedup = r.group_dedup;
         p.out = reinterpret_cast<float4 *>(v.out_rgba);
         p.evals = v.out_evals;
         p.stats = nullptr;
@@ -623,6 +626,7 @@ int ctf_batch_autotune(const ctf_view *views, int nviews, ctf_algorithm alg, uin
         b0.filter.budget = 32;
         b0.filter.mask_dim = 16;
         b0.filter.edge_remap = 1;
+        b0.filter.group_dedup = 0;
         b0.items_per_fetch = 4;
         b0.ctas_per_sm = 4;
     }

@@ -142,6 +142,7 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
                 cnt.v[kStatPixelsActive] += nactive;
                 cnt.v[kStatTilesDirect] += 1;
                 cnt.v[kStatTexelEvals] += 4 * nactive;
+                cnt.v[kStatTexelEvalsUnique] += 4 * nactive;
             }
         }
         // inactive lanes decode too (their own clamped texels): the warp

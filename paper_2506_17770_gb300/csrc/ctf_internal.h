@@ -35,6 +35,7 @@ enum StatIndex {
     kStatTilesFallbackMinified,
     kStatPixelsActive,
     kStatTexelEvals,
+    kStatTexelEvalsUnique,
     kNumStats
 };
 
@@ -51,6 +52,7 @@ struct __align__(16) ExactParams {
     uint32_t k0, k1;      // STF key
     int budget;
     int edge_remap;
+    int group_dedup;      // learned decode: one evaluation per distinct texel of a tile group
     float4 *out;
     uint8_t *evals;       // nullable
     unsigned long long *stats;  // kNumStats counters or nullptr

@@ -37,8 +37,14 @@ constexpr int kSmPixST = kSmRanks + 4 * 32 * 4;       // 256 x float2
 constexpr int kSmPixInfo = kSmPixST + 256 * 8;        // 256 x uint32
 constexpr int kSmOut = kSmPixInfo + 256 * 4;          // 256 rows x float4
 constexpr int kSmCount = kSmOut + 256 * 16;           // 8 x int
+constexpr int kSmRowMap = kSmCount + kGroupTiles * 4;  // 256 x u8: list entry -> row (group_dedup)
+constexpr int kSmNUnique = kSmRowMap + 256;           // int
 constexpr int kSmTexList = kSmX;                      // 8 tiles x 32 x int2 (2 KB, inside X)
-constexpr int kSmBytes = kSmCount + kGroupTiles * 4;
+// group_dedup: a 512-slot hash table of texels and their rows, inside H
+// (free between the chains of two groups)
+constexpr int kSmHashKey = kSmH;                      // 512 x u64
+constexpr int kSmHashRow = kSmH + 512 * 8;            // 512 x u8
+constexpr int kSmBytes = kSmNUnique + 16;
 // Reserve enough shared memory that at most 4 CTAs share an SM: 4 x 128 TMEM
 // columns fill the SM's 512 (5 x 54 KB exceed the SM's 228 KB).
 constexpr int kSmRequest = 54 * 1024;
@@ -382,6 +388,7 @@ __device__ __forceinline__ bool mlp_warp_tile(const ExactParams &p, const MlpDev
                 cnt.v[kStatPixelsActive] += __popc(A);
                 cnt.v[kStatTilesDirect] += 1;
                 cnt.v[kStatTexelEvals] += 4 * __popc(A);
+                cnt.v[kStatTexelEvalsUnique] += 4 * __popc(A);
             }
         }
         float4 tap[4];
@@ -523,7 +530,7 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
         setup_coords(uv, fW, fH, ps);
         Selection sel;
         if (valid) {
-            sel = select_tile<ALG, MD, true>(p, ps, jac, px, py, lane, lt, T, ranks, cnt);
+            sel = select_tile<ALG, MD, true, false>(p, ps, jac, px, py, lane, lt, T, ranks, cnt);
         } else {
             sel.path = PATH_EMPTY;
             sel.A = 0;
@@ -548,15 +555,73 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
     }
     __syncthreads();
 
-    // ---- rows: slot g owns [base_g, base_g + count[g]).  Every thread
-    // reads the texels of its rows (threadIdx.x and 128 + threadIdx.x) before
-    // the first chain overwrites the X buffer that holds the lists.
+    // ---- rows.  Without group_dedup slot g owns rows [base_g, base_g +
+    // count[g]) in slot order.  With it, the distinct texels of the group
+    // get rows in the order their first lists entries win a shared hash
+    // table, and rowmap sends every list entry to its texel's row.  Every
+    // thread then reads the texels of its rows (threadIdx.x and 128 +
+    // threadIdx.x) before the first chain overwrites the X buffer that holds
+    // the lists.
     int cnts[kGroupTiles];
 #pragma unroll
     for (int g = 0; g < kGroupTiles; ++g) cnts[g] = count[g];
     int R = 0, my_base[2] = {0, 0};
     int2 xy[2] = {make_int2(0, 0), make_int2(0, 0)};
-    {
+    unsigned char *rowmap = sm + kSmRowMap;
+    if (p.group_dedup) {  // CTA-uniform
+        unsigned long long *hkey = reinterpret_cast<unsigned long long *>(sm + kSmHashKey);
+        unsigned char *hrow = sm + kSmHashRow;
+        int *nuniq = reinterpret_cast<int *>(sm + kSmNUnique);
+        for (int i = threadIdx.x; i < 512; i += kRows) hkey[i] = ~0ull;
+        if (threadIdx.x == 0) *nuniq = 0;
+        __syncthreads();
+        int slot[2] = {0, 0};
+        bool has[2] = {false, false}, won[2] = {false, false};
+        int2 t2[2] = {make_int2(0, 0), make_int2(0, 0)};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int e = (int)threadIdx.x + kRows * c, g = e >> 5;
+            int n_g = cnts[0];
+#pragma unroll
+            for (int k = 1; k < kGroupTiles; ++k) n_g = g == k ? cnts[k] : n_g;
+            if ((e & 31) < n_g) {
+                has[c] = true;
+                t2[c] = texlist[e];
+                const unsigned long long key = ((unsigned long long)(uint32_t)t2[c].y << 32) | (uint32_t)t2[c].x;
+                unsigned h = (((uint32_t)t2[c].x * 0x9E3779B1u) ^ ((uint32_t)t2[c].y * 0x85EBCA77u)) >> 23;
+                // at most 256 keys in 512 slots: the probe always ends
+                for (int probe = 0; probe < 512; ++probe) {
+                    const unsigned long long old = atomicCAS(&hkey[h], ~0ull, key);
+                    if (old == ~0ull || old == key) {
+                        won[c] = old == ~0ull;
+                        slot[c] = (int)h;
+                        break;
+                    }
+                    h = (h + 1) & 511u;
+                }
+            }
+        }
+        __syncthreads();
+        int2 *uxy = texlist;  // the lists have been read: the distinct texels reuse the space
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (won[c]) {
+                const int row = atomicAdd(nuniq, 1);
+                hrow[slot[c]] = (unsigned char)row;
+                uxy[row] = t2[c];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            if (has[c]) rowmap[threadIdx.x + kRows * c] = hrow[slot[c]];
+        R = *nuniq;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int row = kRows * c + (int)threadIdx.x;
+            if (row < R) xy[c] = uxy[row];
+        }
+    } else {
         int start[kGroupTiles];
 #pragma unroll
         for (int g = 0; g < kGroupTiles; ++g) {
@@ -581,6 +646,7 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
             }
         }
     }
+    if (threadIdx.x == 0) cnt.v[kStatTexelEvalsUnique] += R;
     __syncthreads();
 
     // ---- the chains (CTA-uniform count: 0, 1 or 2)
@@ -612,6 +678,9 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
         const int bx = (int)(tile % p.tiles_x), by = (int)(tile / p.tiles_x);
         const uint32_t idx = (uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx);
         const int b = h == 0 ? my_base[0] : my_base[1];
+        const bool dedup = p.group_dedup != 0;
+        // row of list entry i of this tile
+        auto row_of = [&](uint32_t i) { return dedup ? (int)rowmap[32 * g + (int)i] : b + (int)i; };
         float4 result = make_float4(0.f, 0.f, 0.f, 0.f);
         uint8_t cv = 0;
         if ((info >> 23) & 1u) {
@@ -622,7 +691,7 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
                 float2 rg = make_float2(0.f, 0.f), ba = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float4 t = outrow[b + (int)((info >> (5 * k)) & 31u)];
+                    const float4 t = outrow[row_of((info >> (5 * k)) & 31u)];
                     const float2 wk = make_float2(w[k], w[k]);
                     rg = __ffma2_rn(wk, make_float2(t.x, t.y), rg);
                     ba = __ffma2_rn(wk, make_float2(t.z, t.w), ba);
@@ -630,7 +699,7 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
                 result = make_float4(rg.x, rg.y, ba.x, ba.y);
                 cv = (uint8_t)((info >> 20) & 7u);
             } else {
-                result = outrow[b + (int)(info & 31u)];
+                result = outrow[row_of(info & 31u)];
                 cv = 1;
             }
         }

@@ -95,7 +95,7 @@ struct Selection {
 // algorithm.  `ps` holds the lane's setup (ps.active already decided).
 // `ranks` is a per-warp array of 32 ints in shared memory (Mask Sampling
 // passes texel coordinates through it); counters are kept when kStats.
-template <int ALG, int MD, bool kStats>
+template <int ALG, int MD, bool kStats, bool kUnique = true>
 __device__ __forceinline__ Selection select_tile(const ExactParams &p, const PixelSetup &ps, const float4 jac,
                                                  int px, int py, int lane, uint32_t lt, ListTable *T, int *ranks,
                                                  Counters &cnt) {
@@ -232,6 +232,7 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
             if (kStats) cnt.v[kStatTilesDirect] += 1;
         }
         if (kStats) cnt.v[kStatTexelEvals] += nactive;
+        if (kStats && kUnique) cnt.v[kStatTexelEvalsUnique] += nactive;
         if (ps.active) {
             int dx, dy;
             stf_offset(px, py, p.view, p.k0, p.k1, ps.s, ps.t, dx, dy);
@@ -246,6 +247,7 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
         sel.n = n;
         if (kStats) cnt.v[kStatTilesSuccess] += 1;
         if (kStats) cnt.v[kStatTexelEvals] += n;
+        if (kStats && kUnique) cnt.v[kStatTexelEvalsUnique] += n;
         const bool full = A == FULL;
         // Evaluation counts follow the paper's assignment of texel i to lane
         // h(i, A) (edge remapping) or to lane i, whichever lane of the warp

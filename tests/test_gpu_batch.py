@@ -157,3 +157,20 @@ def test_autotune_picks_a_consistent_configuration(textures):
         ref, ref_ev, _ = _single(v, "box", 1, fopts)
         H, W = v["height"], v["width"]
         assert np.array_equal(v["out_rgba"].cpu().numpy()[:H, :W].view(np.uint32), ref[:H, :W].view(np.uint32))
+
+
+def test_batch_group_dedup_equals_per_view_calls(textures):
+    views = _make_views(textures, n=7, seed=19)
+    o = _ctf.batch_opts(tile_w=8, tile_h=4, mask_dim=11, items_per_fetch=2, ctas_per_sm=4, group_dedup=1)
+    fopts = {"tile_w": 8, "tile_h": 4, "mask_dim": 11, "group_dedup": 1}
+    st = _ctf.ctf_filter_batch(views, "mask", 5, o, stats=True)
+    _ctf.ctf_sync_check()
+    singles = []
+    for v in views:
+        ref, ref_ev, ref_st = _single(v, "mask", 5, fopts)
+        singles.append(ref_st)
+        H, W = v["height"], v["width"]
+        assert np.array_equal(v["out_rgba"].cpu().numpy()[:H, :W].view(np.uint32), ref[:H, :W].view(np.uint32))
+        assert np.array_equal(v["out_evals"].cpu().numpy()[:H, :W], ref_ev[:H, :W])
+    assert st == _sum_stats(singles)
+    assert st["texel_evals_unique"] < st["texel_evals"]

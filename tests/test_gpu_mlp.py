@@ -200,3 +200,32 @@ def test_learned_success_equals_learned_4tap_bitwise(tex64):
         assert st["tiles_success"] == st["tiles_total"]
         assert np.array_equal(out.view(np.uint32), ref.view(np.uint32)), alg
         assert st["texel_evals"] < 0.75 * st["pixels_active"]
+
+
+@pytest.mark.parametrize("alg", ["stf", "list_merge", "box", "mask"])
+@pytest.mark.parametrize("W,H,seed", [(128, 64, 11), (37, 21, 12)])
+def test_group_dedup_changes_only_the_evaluation_count(tex64, alg, W, H, seed):
+    """group_dedup evaluates each distinct texel of a group of 8 tiles once:
+    the image (bitwise) and the per-pixel counts stay those of the per-warp
+    method, and texel_evals_unique equals the oracle's grouped count."""
+    uv, jac, cov = _scene(W, H, seed)
+    out0, ev0, st0 = gpu_filter(tex64, uv, jac, cov, alg, {"mask_dim": 11})
+    out1, ev1, st1 = gpu_filter(tex64, uv, jac, cov, alg, {"mask_dim": 11, "group_dedup": 1})
+    assert np.array_equal(out1.view(np.uint32), out0.view(np.uint32))
+    np.testing.assert_array_equal(ev1, ev0)
+    ref_st = oracle.filter_frame_learned_f64(tex64.mlp, 64, 64, uv, jac, cov, alg=ALGS[alg], seed=0, mask_dim=11,
+                                             group_tiles=8)[2]
+    assert st1 == ref_st
+    assert st1["texel_evals_unique"] <= st0["texel_evals_unique"] == st0["texel_evals"]
+
+
+def test_group_dedup_on_a_magnified_plane(tex64):
+    sc = synth.magnified_plane(256, 128, 64, 64, scale=0.25)
+    out0, _, st0 = gpu_filter(tex64, sc.uv, sc.jac, None, "box")
+    out1, _, st1 = gpu_filter(tex64, sc.uv, sc.jac, None, "box", {"group_dedup": 1})
+    assert np.array_equal(out1.view(np.uint32), out0.view(np.uint32))
+    ref_st = oracle.filter_frame_learned_f64(tex64.mlp, 64, 64, sc.uv, sc.jac, None, alg=ALGS["box"], seed=0,
+                                             group_tiles=8)[2]
+    assert st1 == ref_st
+    # neighbouring 8x4 tiles share the texels along their common edges
+    assert st1["texel_evals_unique"] < 0.8 * st1["texel_evals"]

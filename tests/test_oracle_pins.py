@@ -223,6 +223,47 @@ def test_set_sizes_and_nested_success(oracle_lib):
     assert sl.sum() > sm.sum() >= sb.sum() > 0 or sl.sum() >= sm.sum() > sb.sum() > 0
 
 
+def test_group_distinct_texels_brute_force(oracle_lib):
+    """Groups of 8 consecutive tiles evaluating each distinct clamped texel
+    once (the shared-memory extension of Sec. 6): on a magnified plane every
+    Box tile succeeds and evaluates its whole bounding box, so the grouped
+    count is the size of the union of the clamped boxes, which numpy computes
+    here from the FP32 texel coordinates.  The plane starts 3 texels left of
+    the texture, so clamping merges texels too."""
+    o = oracle_lib
+    Wt = Ht = 64
+    blocks = synth.random_blocks(Wt, Ht, seed=17)
+    sc = synth.magnified_plane(96, 40, Wt, Ht, scale=0.25, seed=5)
+    uv = sc.uv.copy()
+    uv[..., 0] -= np.float32(3.0 / Wt)
+    cov = np.ones((40, 96), np.uint8)
+    _, ev, st, tp, _ = o.filter_frame(blocks, Wt, Ht, uv, sc.jac, cov, alg=o.ALG_BOX, group_tiles=8,
+                                      want_tiles=True)
+    assert np.all(tp == o.PATH_SUCCESS)
+    xf = uv[..., 0] * np.float32(Wt) - np.float32(0.5)
+    yf = uv[..., 1] * np.float32(Ht) - np.float32(0.5)
+    ulx, uly = np.floor(xf).astype(int), np.floor(yf).astype(int)
+    tiles_x, tiles_y = 96 // 8, 40 // 4
+    groups = {}
+    for ty in range(tiles_y):
+        for tx in range(tiles_x):
+            sl = (slice(ty * 4, ty * 4 + 4), slice(tx * 8, tx * 8 + 8))
+            x0, x1 = ulx[sl].min(), ulx[sl].max() + 1
+            y0, y1 = uly[sl].min(), uly[sl].max() + 1
+            texels = {(min(max(x, 0), Wt - 1), min(max(y, 0), Ht - 1))
+                      for x in range(x0, x1 + 1) for y in range(y0, y1 + 1)}
+            groups.setdefault((ty * tiles_x + tx) // 8, set()).update(texels)
+    assert st["texel_evals_unique"] == sum(len(g) for g in groups.values())
+    assert st["texel_evals_unique"] < st["texel_evals"] == int(ev.sum())
+    # one tile per group: only the clamping merges texels; no grouping: the per-warp count
+    st1 = o.filter_frame(blocks, Wt, Ht, uv, sc.jac, cov, alg=o.ALG_BOX, group_tiles=1)[2]
+    st0 = o.filter_frame(blocks, Wt, Ht, uv, sc.jac, cov, alg=o.ALG_BOX)[2]
+    assert st["texel_evals_unique"] < st1["texel_evals_unique"] < st0["texel_evals_unique"] == st0["texel_evals"]
+    # Mask produces a subset of each box: never more distinct texels
+    stm = o.filter_frame(blocks, Wt, Ht, uv, sc.jac, cov, alg=o.ALG_MASK, group_tiles=8)[2]
+    assert stm["texel_evals_unique"] <= st["texel_evals_unique"]
+
+
 def test_mask11_equals_mask16_when_bbox_fits(oracle_lib):
     o = oracle_lib
     blocks = synth.random_blocks(64, 64, seed=14)
