@@ -277,21 +277,24 @@ def bench_learned(args, dev, stream, flush, peaks):
     runs = {}
     for tname in ("fp16", "fp8"):
         tex = texs[tname]
-        for alg in ("4tap", "mask", "box", "list_merge"):
-            if tname == "fp8" and alg in ("box", "list_merge"):
+        for name in ("4tap", "mask", "mask_group_dedup", "box", "list_merge"):
+            if tname == "fp8" and name in ("box", "list_merge"):
                 continue
-            o = opts11 if alg == "mask" else None
+            alg = "mask" if name.startswith("mask") else name
+            o = opts11 if name == "mask" else ({"mask_dim": 11, "group_dedup": 1} if name == "mask_group_dedup"
+                                              else None)
             ms = _timed_views(lambda: _ctf.ctf_filter(tex, uv, jac, cov, W, H, 0, alg, 0, o, out, ev,
                                                      stream=stream), k, 2, flush, stream)
             st = _ctf.ctf_filter(tex, uv, jac, cov, W, H, 0, alg, 0, o, out, ev, stats=True, stream=stream)
             _ctf.ctf_sync_check(stream)
             mse = torch.mean((out[..., :3] - ref_exact[..., :3]) ** 2).item()
             t = ms / k * 1e-3
-            flops = st["texel_evals"] * 10752
+            flops = st["texel_evals_unique"] * 10752  # evaluations done
             peak = peaks["bf16"] * (2.0 if tname == "fp8" else 1.0)
-            runs[f"{tname}_{alg}"] = {
+            runs[f"{tname}_{name}"] = {
                 "pixels_per_s": npix / t, "ms_per_view": t * 1e3,
                 "evals_per_pixel": st["texel_evals"] / max(1, st["pixels_active"]),
+                "evaluations_done_per_pixel": st["texel_evals_unique"] / max(1, st["pixels_active"]),
                 "texel_evals_per_s": st["texel_evals"] / t,
                 "psnr_vs_exact_4tap_db": -10 * math.log10(max(mse, 1e-30)),
                 "tensor": {"achieved_tflops": flops / t / 1e12, "peak_tflops": peak,
