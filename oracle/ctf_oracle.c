@@ -394,6 +394,175 @@ static void group_note(group_set *G, const texel_source *src, int x, int y)
 }
 
 /*
+ * Eq. 2 with the wave of 32 lanes replaced by the na active lanes: the
+ * source lane (index among the active lanes) whose footprint remaining lane
+ * c (n <= c < na) draws from, l = round((na-1)(c-n) / (na-1-n)) rounded half
+ * up, and l = 0 when a single lane remains (na-1 = n, where the equation
+ * reads 0/0).  Returns -1 for arguments outside that range.
+ */
+int oracle_cplus_source(int na, int n, int c)
+{
+    if (na < 1 || na > 32 || n < 0 || n >= na || c < n || c >= na)
+        return -1;
+    const int den = na - 1 - n;
+    return den == 0 ? 0 : (2 * (na - 1) * (c - n) + den) / (2 * den);
+}
+
+/*
+ * Fallbacks C and C+ (Sec. 3.4, "New Fallback Methods") for a magnified tile
+ * whose texel set does not fit the budget.  mode 1 = C, 2 = C+.
+ *
+ * Every active lane draws its one-tap STF texel.  C: every active lane
+ * produces its STF texel.  C+: the distinct STF texels U (in the order of
+ * the first active lane that draws each; the order changes no output) are
+ * produced by the first |U| = n active lanes, and each remaining active lane
+ * c (index among the active lanes, n <= c < na) takes the footprint of
+ * active lane l = round_half_up((na-1)(c-n)/(na-1-n)) (l = 0 when na-1 = n;
+ * eq. 2 with 32 replaced by the number of active lanes na) and produces one
+ * of its taps with nonzero weight outside U, chosen with probability
+ * proportional to the weights by xi2 = (r2 >> 8) 2^-24, the third word of
+ * the lane's own STF draw; a lane whose source has no such tap produces
+ * nothing.  Then every active pixel filters with the N distinct texels of
+ * its footprint that have nonzero weight and were produced (eq. 1):
+ *   N = all nonzero-weight taps: the 4-tap filter (zero-weight taps add
+ *       nothing to it), i.e. exact bilinear;
+ *   N = 1: that texel;
+ *   else: c = fma(1 - S_w, S_p / N, S_wp) per channel, with S_wp the fma
+ *       chain of w_k p_k, S_w the sum of w_k and S_p the sum of p_k over the
+ *       produced taps in tap order (FP32; FP64 mode in double).
+ * Counts: 1 per producing lane.
+ */
+static void fallback_c(const texel_source *src, const pixel_setup *lane, uint32_t A, int mode, int view,
+                       uint64_t seed, int fp64, int W, float *out, double *outd, uint8_t *evals, group_set *G)
+{
+    int act[32], na = 0;
+    for (int l = 0; l < 32; ++l)
+        if ((A >> l) & 1u) act[na++] = l;
+    int sx[32], sy[32];
+    float xi2[32];
+    for (int i = 0; i < na; ++i) {
+        const pixel_setup *p = &lane[act[i]];
+        uint32_t ctr[4] = {(uint32_t)p->px, (uint32_t)p->py, (uint32_t)view, 0u};
+        uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+        uint32_t r[4];
+        oracle_philox4x32_10(ctr, key, r);
+        float xi0 = (float)(r[0] >> 8) * 0x1p-24f, xi1 = (float)(r[1] >> 8) * 0x1p-24f;
+        xi2[i] = (float)(r[2] >> 8) * 0x1p-24f;
+        sx[i] = p->ulx + (xi0 < p->s ? 1 : 0);
+        sy[i] = p->uly + (xi1 < p->t ? 1 : 0);
+    }
+    /* produced texels: coordinates and values (a texel may appear twice) */
+    int pn = 0, qx[32], qy[32];
+    float qv[32][4];
+    double qd[32][4];
+#define PRODUCE(l_, x_, y_)                                                   \
+    do {                                                                      \
+        qx[pn] = (x_);                                                        \
+        qy[pn] = (y_);                                                        \
+        fetch_texel(src, qx[pn], qy[pn], qv[pn], qd[pn]);                     \
+        group_note(G, src, qx[pn], qy[pn]);                                   \
+        evals[(size_t)lane[l_].py * W + lane[l_].px] = 1;                     \
+        pn++;                                                                 \
+    } while (0)
+    if (mode == 1) {
+        for (int i = 0; i < na; ++i) PRODUCE(act[i], sx[i], sy[i]);
+    } else {
+        int ux[32], uy[32], n = 0;
+        for (int i = 0; i < na; ++i) {
+            int seen = 0;
+            for (int j = 0; j < n; ++j) seen |= ux[j] == sx[i] && uy[j] == sy[i];
+            if (!seen) {
+                ux[n] = sx[i];
+                uy[n] = sy[i];
+                n++;
+            }
+        }
+        for (int i = 0; i < n; ++i) PRODUCE(act[i], ux[i], uy[i]);
+        for (int c = n; c < na; ++c) {
+            const int l = oracle_cplus_source(na, n, c);
+            const pixel_setup *q = &lane[act[l]];
+            float w[4];
+            bilinear_weights(q->s, q->t, w);
+            int cand[4], nc = 0;
+            for (int k = 0; k < 4; ++k) {
+                if (!(w[k] > 0.0f)) continue;
+                int tx = q->ulx + k % 2, ty = q->uly + k / 2, inu = 0;
+                for (int j = 0; j < n; ++j) inu |= ux[j] == tx && uy[j] == ty;
+                if (!inu) cand[nc++] = k;
+            }
+            if (nc == 0) continue;
+            float wc = 0.0f;
+            for (int j = 0; j < nc; ++j) wc = wc + w[cand[j]];
+            const float tsel = xi2[c] * wc;
+            int pick = cand[nc - 1];
+            float run = 0.0f;
+            for (int j = 0; j < nc; ++j) {
+                run = run + w[cand[j]];
+                if (tsel < run) {
+                    pick = cand[j];
+                    break;
+                }
+            }
+            PRODUCE(act[c], q->ulx + pick % 2, q->uly + pick / 2);
+        }
+    }
+#undef PRODUCE
+    /* eq. 1 for every active pixel */
+    for (int i = 0; i < na; ++i) {
+        const pixel_setup *p = &lane[act[i]];
+        size_t idx = (size_t)p->py * W + p->px;
+        float w[4];
+        bilinear_weights(p->s, p->t, w);
+        int nz = 0, N = 0, at[4];
+        for (int k = 0; k < 4; ++k) {
+            at[k] = -1;
+            if (!(w[k] > 0.0f)) continue;
+            nz++;
+            for (int j = 0; j < pn; ++j)
+                if (qx[j] == p->ulx + k % 2 && qy[j] == p->uly + k / 2) {
+                    at[k] = j;
+                    break;
+                }
+            if (at[k] >= 0) N++;
+        }
+        for (int ch = 0; ch < 4; ++ch) {
+            float o;
+            double od;
+            if (N == 1) {
+                int j = -1;
+                for (int k = 0; k < 4; ++k)
+                    if (at[k] >= 0) j = at[k];
+                o = qv[j][ch];
+                od = qd[j][ch];
+            } else if (!fp64) {
+                float swp = 0.0f, sw = 0.0f, sp = 0.0f;
+                for (int k = 0; k < 4; ++k) {
+                    if (at[k] < 0) continue;
+                    swp = fmaf(w[k], qv[at[k]][ch], swp);
+                    sw = sw + w[k];
+                    sp = sp + qv[at[k]][ch];
+                }
+                o = N == nz ? swp : fmaf(1.0f - sw, sp / (float)N, swp);
+                od = (double)o;
+            } else {
+                double swp = 0.0, sw = 0.0, sp = 0.0;
+                for (int k = 0; k < 4; ++k) {
+                    if (at[k] < 0) continue;
+                    swp += (double)w[k] * qd[at[k]][ch];
+                    sw += (double)w[k];
+                    sp += qd[at[k]][ch];
+                }
+                od = N == nz ? swp : swp + (1.0 - sw) * sp / (double)N;
+                o = (float)od;
+            }
+            if (out) out[4 * idx + ch] = o;
+            if (outd) outd[4 * idx + ch] = od;
+        }
+    }
+}
+
+
+/*
  * oracle_filter_ex: filter one frame.
  *   src            texel source (exact blocks or learned)
  *   uv   [H][W][2] float, jac [H][W][4] float = (du/dx, dv/dx, du/dy, dv/dy)
@@ -401,6 +570,8 @@ static void group_note(group_set *G, const texel_source *src, int x, int y)
  *   out  [H][W][4] float (FP32 result; may be NULL), outd [H][W][4] double (may be NULL)
  *   evals[H][W] uint8 per-pixel texel evaluations
  *   tile_path / tile_n: per tile outcome code and texel-set size (may be NULL)
+ *   fallback       0: over-budget tiles take one-tap STF; 1: fallback C;
+ *                  2: fallback C+ (Sec. 3.4); minified tiles always STF
  *   group_tiles    0, or the size of the tile groups (consecutive tile
  *                  indices, at most 8) whose distinct evaluated texels
  *                  stats[8] counts; 4TAP is never grouped
@@ -412,10 +583,12 @@ static void group_note(group_set *G, const texel_source *src, int x, int y)
  */
 static int oracle_filter_ex(const texel_source *src, const float *uv, const float *jac, const uint8_t *cov,
                             int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h,
-                            int budget, int mask_dim, int edge_remap, int group_tiles, int fp64, float *out,
-                            double *outd, uint8_t *evals, int32_t *tile_path, int32_t *tile_n,
+                            int budget, int mask_dim, int edge_remap, int group_tiles, int fallback, int fp64,
+                            float *out, double *outd, uint8_t *evals, int32_t *tile_path, int32_t *tile_n,
                             int64_t *stats_out)
 {
+    if (fallback < 0 || fallback > 2)
+        return -1;
     if (W < 0 || H < 0 || tile_w <= 0 || tile_h <= 0 || tile_w * tile_h != 32)
         return -1;
     if (group_tiles < 0 || group_tiles > 8)
@@ -602,6 +775,10 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
             if (!fits) {
                 if (path == PATH_FALLBACK_MINIFIED) st.tiles_fallback_minified++;
                 else st.tiles_fallback_budget++;
+                if (path == PATH_FALLBACK_BUDGET && fallback) {
+                    fallback_c(src, lane, A, fallback, view, seed, fp64, W, out, outd, evals, &G);
+                    continue;
+                }
                 for (int l = 0; l < 32; ++l) {
                     if (!lane[l].active) continue;
                     size_t idx = (size_t)lane[l].py * W + lane[l].px;
@@ -672,26 +849,26 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
 /* Exact block decode, FP32 arithmetic with the rounding described above. */
 int oracle_filter(const uint8_t *blocks, int Wt, int Ht, const float *uv, const float *jac, const uint8_t *cov,
                   int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h, int budget,
-                  int mask_dim, int edge_remap, int group_tiles, float *out, uint8_t *evals,
+                  int mask_dim, int edge_remap, int group_tiles, int fallback, float *out, uint8_t *evals,
                   int32_t *tile_path, int32_t *tile_n, int64_t *stats)
 {
     if (Wt <= 0 || Ht <= 0 || Wt % 4 || Ht % 4 || !blocks)
         return -1;
     texel_source src = {0, Wt, Ht, blocks, NULL};
     return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
-                            edge_remap, group_tiles, 0, out, NULL, evals, tile_path, tile_n, stats);
+                            edge_remap, group_tiles, fallback, 0, out, NULL, evals, tile_path, tile_n, stats);
 }
 
 /* Learned decode: texel values from the FP64 MLP, filter in double. */
 int oracle_filter_learned_f64(const void *mlp, int Wt, int Ht, const float *uv, const float *jac,
                               const uint8_t *cov, int W, int H, int view, int alg, uint64_t seed, int tile_w,
                               int tile_h, int budget, int mask_dim, int edge_remap, int group_tiles,
-                              double *outd, uint8_t *evals, int32_t *tile_path, int32_t *tile_n,
+                              int fallback, double *outd, uint8_t *evals, int32_t *tile_path, int32_t *tile_n,
                               int64_t *stats)
 {
     if (Wt <= 0 || Ht <= 0 || !mlp)
         return -1;
     texel_source src = {1, Wt, Ht, NULL, mlp};
     return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
-                            edge_remap, group_tiles, 1, NULL, outd, evals, tile_path, tile_n, stats);
+                            edge_remap, group_tiles, fallback, 1, NULL, outd, evals, tile_path, tile_n, stats);
 }

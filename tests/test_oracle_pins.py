@@ -264,6 +264,138 @@ def test_group_distinct_texels_brute_force(oracle_lib):
     assert stm["texel_evals_unique"] <= st["texel_evals_unique"]
 
 
+# ---------------------------------------------------------------------------
+# Fallbacks C and C+ (Sec. 3.4)
+# ---------------------------------------------------------------------------
+def test_cplus_lane_mapping_eq2(oracle_lib):
+    """Eq. 2 with 32 lanes: l = round(31 (c - n) / (31 - n)), computed here in
+    exact rationals with halves rounded up; the text's properties: lanes 0
+    and 31 are sources whenever two or more lanes remain, a single remaining
+    lane maps to 0, and the sources never decrease with c."""
+    from fractions import Fraction
+    o = oracle_lib
+    for n in range(32):
+        prev = -1
+        for c in range(n, 32):
+            got = o.cplus_source(32, n, c)
+            if n == 31:
+                assert got == 0
+                continue
+            x = Fraction(31 * (c - n), 31 - n)
+            assert got == int(x + Fraction(1, 2)), (n, c)
+            assert got >= prev
+            prev = got
+        if 32 - n >= 2:
+            assert o.cplus_source(32, n, n) == 0 and o.cplus_source(32, n, 31) == 31
+    assert o.cplus_source(32, 5, 4) == -1 and o.cplus_source(33, 0, 0) == -1
+
+
+def _fallback_tiles(o, blocks, uv, jac, cov, fallback, alg=None):
+    alg = o.ALG_BOX if alg is None else alg
+    return o.filter_frame(blocks, 64, 64, uv, jac, cov, alg=alg, seed=9, fallback=fallback, want_tiles=True)
+
+
+def _tile_lanes(uv, cov, tx, ty):
+    """Active lanes of an 8x4 tile with their FP32 setup (texel units)."""
+    lanes = []
+    for l in range(32):
+        px, py = tx * 8 + l % 8, ty * 4 + l // 8
+        if not cov[py, px]:
+            continue
+        xf = np.float32(uv[py, px, 0]) * np.float32(64) - np.float32(0.5)
+        yf = np.float32(uv[py, px, 1]) * np.float32(64) - np.float32(0.5)
+        ulx, uly = int(np.floor(xf)), int(np.floor(yf))
+        s_, t_ = np.float32(xf - np.float32(ulx)), np.float32(yf - np.float32(uly))
+        os_, ot_ = np.float32(1) - s_, np.float32(1) - t_
+        w = [os_ * ot_, s_ * ot_, os_ * t_, s_ * t_]
+        lanes.append((l, px, py, ulx, uly, float(s_), float(t_), w))
+    return lanes
+
+
+def test_fallback_c_is_eq1_in_exact_arithmetic(oracle_lib):
+    """Fallback C: every active lane produces its STF texel (the pinned Philox
+    draw); each pixel then blends the distinct produced texels of its
+    footprint with nonzero weight by eq. 1, evaluated here in exact rationals
+    from the pinned block decode: sum w p + (1 - sum w) mean(p), or exact
+    bilinear when all of them are present, or the single texel."""
+    from fractions import Fraction
+    o = oracle_lib
+    blocks = synth.random_blocks(64, 64, seed=13)
+    uv, jac, cov = _scene_mix(seed=9)
+    out, ev, st, tp, _ = _fallback_tiles(o, blocks, uv, jac, cov, o.FALLBACK_C)
+    ref_stf = _fallback_tiles(o, blocks, uv, jac, cov, o.FALLBACK_STF)[0]
+    bil = o.filter_frame(blocks, 64, 64, uv, jac, cov, alg=o.ALG_4TAP)[0]
+    tiles_x = 96 // 8
+    cases = {"all": 0, "one": 0, "blend": 0}
+    for tid in np.nonzero(tp == o.PATH_FALLBACK_BUDGET)[0]:
+        ty, tx = divmod(int(tid), tiles_x)
+        lanes = _tile_lanes(uv, cov, tx, ty)
+        produced = set()
+        for (l, px, py, ulx, uly, s_, t_, w) in lanes:
+            dx, dy = o.stf_offset(px, py, 0, 9, s_, t_)
+            produced.add((ulx + dx, uly + dy))
+            assert ev[py, px] == 1
+        for (l, px, py, ulx, uly, s_, t_, w) in lanes:
+            taps = [(ulx + k % 2, uly + k // 2) for k in range(4)]
+            nz = [k for k in range(4) if w[k] > 0]
+            pres = [k for k in nz if taps[k] in produced]
+            vals = {k: [Fraction(int(v), 255) for v in o.decode_rgba8(blocks, 64, 64, *taps[k])] for k in pres}
+            if len(pres) == len(nz):
+                cases["all"] += 1
+                assert np.array_equal(out[py, px].view(np.uint32), bil[py, px].view(np.uint32))
+                continue
+            if len(pres) == 1:
+                cases["one"] += 1
+                assert np.array_equal(out[py, px].view(np.uint32), ref_stf[py, px].view(np.uint32))
+                continue
+            cases["blend"] += 1
+            sw = sum(Fraction(float(w[k])) for k in pres)
+            for ch in range(4):
+                sp = sum(vals[k][ch] for k in pres)
+                exact = sum(Fraction(float(w[k])) * vals[k][ch] for k in pres) + (1 - sw) * sp / len(pres)
+                assert abs(float(exact) - float(out[py, px, ch])) <= 4e-7 * max(1.0, abs(float(exact))), (tid, l, ch)
+    assert min(cases.values()) > 10, cases
+
+
+def test_fallback_cplus_invariants(oracle_lib):
+    """Fallback C+: the distinct STF texels are produced by the first n
+    active lanes and the other lanes add texels outside that set, so every
+    pixel sees at least the texels of fallback C: where C is exact bilinear
+    so is C+.  Quality improves as Sec. 3.4 states: mean absolute error
+    against bilinear over the fallback tiles, C+ < C < one-tap STF."""
+    o = oracle_lib
+    blocks = synth.random_blocks(64, 64, seed=13)
+    uv, jac, cov = _scene_mix(seed=9)
+    bil = o.filter_frame(blocks, 64, 64, uv, jac, cov, alg=o.ALG_4TAP)[0]
+    res = {f: _fallback_tiles(o, blocks, uv, jac, cov, f) for f in (o.FALLBACK_STF, o.FALLBACK_C, o.FALLBACK_CPLUS)}
+    outp, evp, stp, tpp, _ = res[o.FALLBACK_CPLUS]
+    outc = res[o.FALLBACK_C][0]
+    tiles_x = 96 // 8
+    mask = np.zeros(cov.shape, bool)
+    for tid in np.nonzero(tpp == o.PATH_FALLBACK_BUDGET)[0]:
+        ty, tx = divmod(int(tid), tiles_x)
+        lanes = _tile_lanes(uv, cov, tx, ty)
+        stf = []
+        for (l, px, py, ulx, uly, s_, t_, w) in lanes:
+            dx, dy = o.stf_offset(px, py, 0, 9, s_, t_)
+            stf.append((ulx + dx, uly + dy))
+            mask[py, px] = True
+        n = len(set(stf))
+        counts = [int(evp[py, px]) for (l, px, py, *_r) in lanes]
+        assert counts[:n] == [1] * n and all(c in (0, 1) for c in counts[n:])
+        for (l, px, py, ulx, uly, s_, t_, w) in lanes:
+            taps = [(ulx + k % 2, uly + k // 2) for k in range(4)]
+            if all(taps[k] in set(stf) for k in range(4) if w[k] > 0):
+                # C has every texel of this footprint, hence so has C+: both exact bilinear
+                assert np.array_equal(outc[py, px].view(np.uint32), bil[py, px].view(np.uint32))
+                assert np.array_equal(outp[py, px].view(np.uint32), bil[py, px].view(np.uint32))
+    assert mask.sum() > 100
+    err = {f: float(np.abs(r[0][mask] - bil[mask]).mean()) for f, r in res.items()}
+    assert err[o.FALLBACK_CPLUS] < err[o.FALLBACK_C] < err[o.FALLBACK_STF], err
+    # outside the fallback tiles nothing changes
+    np.testing.assert_array_equal(outp[~mask], res[o.FALLBACK_STF][0][~mask])
+
+
 def test_mask11_equals_mask16_when_bbox_fits(oracle_lib):
     o = oracle_lib
     blocks = synth.random_blocks(64, 64, seed=14)
