@@ -116,13 +116,22 @@ typedef struct {
  *                   shared-memory extension of Sec. 3 that Sec. 6 proposes;
  *                   outputs and out_evals are unchanged, ctf_stats
  *                   texel_evals_unique counts the evaluations done.  0 or 1
- *                                                                 [0] */
+ *                                                                 [0]
+ *   fallback        magnified tiles over budget: 0 one-tap STF, 1 fallback
+ *                   C, 2 fallback C+ (Sec. 3.4: every active lane draws its
+ *                   STF texel; C produces them, C+ produces the distinct
+ *                   ones and spends the other lanes on further texels of
+ *                   the footprints (eq. 2); each pixel blends the produced
+ *                   texels of its footprint by eq. 1).  Minified tiles take
+ *                   one-tap STF.  Block textures only (CTF_ERR_UNSUPPORTED
+ *                   for learned ones)                             [0] */
 typedef struct {
     int tile_w, tile_h;
     int budget;
     int mask_dim;
     int edge_remap;
     int group_dedup;
+    int fallback;
 } ctf_filter_opts;
 
 /* Per-call counters (filled only when a stats pointer is given). */

@@ -86,12 +86,13 @@ constexpr int batch_min_blocks() {
     return ALG >= ALG_LIST ? 4 : 1;
 }
 
-template <int ALG, int TW, int MD>
+template <int ALG, int TW, int MD, bool kFb>
 __global__ void __launch_bounds__(kBlockWarps * 32, batch_min_blocks<ALG>()) batch_block_kernel(const BatchParams b) {
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
     __shared__ DecodeTables tabs;
     __shared__ int rank_slots[kBlockWarps][32];
+    __shared__ unsigned long long fb_keys[kBlockWarps][32];  // fallback C / C+ texel keys
     __shared__ unsigned long long block_stats[kNumStats];
     __shared__ int s_begin[kSmViews];
     __shared__ __align__(16) ExactParams s_params[kBlockWarps];  // each warp's current view
@@ -156,8 +157,8 @@ __global__ void __launch_bounds__(kBlockWarps * 32, batch_min_blocks<ALG>()) bat
             const bool ninside = i + 1u < n_item && nbx < lim_x && nby < lim_y;
             const uint32_t nidx = nby * (TH * W) + nbx * TW + lane_off;
             const Inputs nxt = load_inputs_any<kJac>(p, ninside, nidx);
-            filter_tile<ALG, TW, MD, true>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
-                                           &tabs, T, rank_slots[warp], cnt);
+            filter_tile<ALG, TW, MD, true, kFb>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
+                                           &tabs, T, rank_slots[warp], fb_keys[warp], cnt);
             bx = nbx;
             by = nby;
             inside = ninside;
@@ -262,38 +263,45 @@ __global__ void __launch_bounds__(kRows, 4) batch_mlp_kernel(const BatchParams b
 
 using BatchFn = void (*)(const BatchParams);
 
+// Learned views never take fallbacks C / C+ (the plan refuses them); block
+// views of the collaborative algorithms have a variant that does.
 template <bool kMlp, int ALG, int TW, int MD>
-BatchFn kernel_of() {
-    if constexpr (kMlp) return batch_mlp_kernel<ALG, TW, MD>;
-    else return batch_block_kernel<ALG, TW, MD>;
+BatchFn kernel_of(bool fb) {
+    if constexpr (kMlp) {
+        return batch_mlp_kernel<ALG, TW, MD>;
+    } else if constexpr (ALG >= ALG_LIST) {
+        return fb ? batch_block_kernel<ALG, TW, MD, true> : batch_block_kernel<ALG, TW, MD, false>;
+    } else {
+        return batch_block_kernel<ALG, TW, MD, false>;
+    }
 }
 
 template <bool kMlp, int ALG, int TW>
-BatchFn pick_mask(int md) {
+BatchFn pick_mask(int md, bool fb) {
     if constexpr (ALG == ALG_MASK) {
-        return md == 11 ? kernel_of<kMlp, ALG, TW, 11>() : kernel_of<kMlp, ALG, TW, 16>();
+        return md == 11 ? kernel_of<kMlp, ALG, TW, 11>(fb) : kernel_of<kMlp, ALG, TW, 16>(fb);
     } else {
-        return kernel_of<kMlp, ALG, TW, 16>();
+        return kernel_of<kMlp, ALG, TW, 16>(fb);
     }
 }
 
 template <bool kMlp, int TW>
-BatchFn pick_alg(int alg, int md) {
+BatchFn pick_alg(int alg, int md, bool fb) {
     switch (alg) {
-    case ALG_4TAP: return pick_mask<kMlp, ALG_4TAP, TW>(md);
-    case ALG_STF: return pick_mask<kMlp, ALG_STF, TW>(md);
-    case ALG_LIST: return pick_mask<kMlp, ALG_LIST, TW>(md);
-    case ALG_BOX: return pick_mask<kMlp, ALG_BOX, TW>(md);
-    case ALG_MASK: return pick_mask<kMlp, ALG_MASK, TW>(md);
+    case ALG_4TAP: return pick_mask<kMlp, ALG_4TAP, TW>(md, fb);
+    case ALG_STF: return pick_mask<kMlp, ALG_STF, TW>(md, fb);
+    case ALG_LIST: return pick_mask<kMlp, ALG_LIST, TW>(md, fb);
+    case ALG_BOX: return pick_mask<kMlp, ALG_BOX, TW>(md, fb);
+    case ALG_MASK: return pick_mask<kMlp, ALG_MASK, TW>(md, fb);
     default: return nullptr;
     }
 }
 
-BatchFn pick(bool mlp, int alg, int tile_w, int md) {
+BatchFn pick(bool mlp, int alg, int tile_w, int md, bool fb) {
     switch (tile_w) {
-    case 8: return mlp ? pick_alg<true, 8>(alg, md) : pick_alg<false, 8>(alg, md);
-    case 4: return mlp ? pick_alg<true, 4>(alg, md) : pick_alg<false, 4>(alg, md);
-    case 16: return mlp ? pick_alg<true, 16>(alg, md) : pick_alg<false, 16>(alg, md);
+    case 8: return mlp ? pick_alg<true, 8>(alg, md, fb) : pick_alg<false, 8>(alg, md, fb);
+    case 4: return mlp ? pick_alg<true, 4>(alg, md, fb) : pick_alg<false, 4>(alg, md, fb);
+    case 16: return mlp ? pick_alg<true, 16>(alg, md, fb) : pick_alg<false, 16>(alg, md, fb);
     default: return nullptr;
     }
 }
@@ -312,7 +320,7 @@ cudaError_t prepare_batch(BatchFn fn) {
 }
 
 struct ResolvedBatch {
-    int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1, group_dedup = 0;
+    int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1, group_dedup = 0, fallback = 0;
     int items_per_fetch = 4, ctas_per_sm = 4;
 };
 
@@ -325,6 +333,7 @@ int resolve(const ctf_batch_opts *o, ResolvedBatch *r) {
     r->mask_dim = o->filter.mask_dim;
     r->edge_remap = o->filter.edge_remap;
     r->group_dedup = o->filter.group_dedup;
+    r->fallback = o->filter.fallback;
     r->items_per_fetch = o->items_per_fetch;
     r->ctas_per_sm = o->ctas_per_sm;
     const bool shape_ok = (r->tile_w == 8 && r->tile_h == 4) || (r->tile_w == 4 && r->tile_h == 8) ||
@@ -334,6 +343,7 @@ int resolve(const ctf_batch_opts *o, ResolvedBatch *r) {
     if (r->mask_dim != 16 && r->mask_dim != 11) return report(CTF_ERR_ARG, "mask_dim %d not 16 or 11", r->mask_dim);
     if (r->edge_remap != 0 && r->edge_remap != 1) return report(CTF_ERR_ARG, "edge_remap must be 0 or 1");
     if (r->group_dedup != 0 && r->group_dedup != 1) return report(CTF_ERR_ARG, "group_dedup must be 0 or 1");
+    if (r->fallback < 0 || r->fallback > 2) return report(CTF_ERR_ARG, "fallback %d not 0, 1 or 2", r->fallback);
     if (r->items_per_fetch < 1 || r->items_per_fetch > 64)
         return report(CTF_ERR_ARG, "items_per_fetch %d outside [1, 64]", r->items_per_fetch);
     if (r->ctas_per_sm < 1 || r->ctas_per_sm > 4) return report(CTF_ERR_ARG, "ctas_per_sm %d outside [1, 4]", r->ctas_per_sm);
@@ -384,10 +394,13 @@ int make_plan(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t see
         p.budget = r.budget;
         p.edge_remap = r.edge_remap;
         p.group_dedup = r.group_dedup;
+        p.fallback = r.fallback;
         p.out = reinterpret_cast<float4 *>(v.out_rgba);
         p.evals = v.out_evals;
         p.stats = nullptr;
         d.learned = v.tex->mode != CTF_EVAL_BLOCK;
+        if (d.learned && r.fallback)
+            return report(CTF_ERR_UNSUPPORTED, "view %d: fallbacks C and C+ are built for block textures only", i);
         if (d.learned) d.m = mlp_device_view(v.tex);
         const int kind = d.learned ? 1 : 0;
         const long long per_item = d.learned ? mlp_group_tiles((int)alg) : kBlockItemTiles;
@@ -459,7 +472,7 @@ cudaError_t launch_plan(const Plan &plan, const DevPlan &dp, int alg, const Reso
     if (e != cudaSuccess) return e;
     for (int k = 0; k < 2; ++k) {
         if (plan.items[k] == 0) continue;
-        BatchFn fn = pick(k == 1, alg, r.tile_w, r.mask_dim);
+        BatchFn fn = pick(k == 1, alg, r.tile_w, r.mask_dim, r.fallback != 0);
         if (!fn) return cudaErrorInvalidValue;
         BatchParams b;
         b.views = dp.views;
@@ -572,7 +585,7 @@ int ctf_batch_graph_create(const ctf_view *views, int nviews, ctf_algorithm alg,
     if (e == cudaSuccess) e = upload_plan(plan, &g->plan, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     // the kernel attribute must be set before capture
-    if (e == cudaSuccess && plan.items[1]) e = prepare_batch(pick(true, (int)alg, r.tile_w, r.mask_dim));
+    if (e == cudaSuccess && plan.items[1]) e = prepare_batch(pick(true, (int)alg, r.tile_w, r.mask_dim, false));
     if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t le = launch_plan(plan, g->plan, (int)alg, r, nullptr, err, s);
@@ -627,6 +640,7 @@ int ctf_batch_autotune(const ctf_view *views, int nviews, ctf_algorithm alg, uin
         b0.filter.mask_dim = 16;
         b0.filter.edge_remap = 1;
         b0.filter.group_dedup = 0;
+        b0.filter.fallback = 0;
         b0.items_per_fetch = 4;
         b0.ctas_per_sm = 4;
     }

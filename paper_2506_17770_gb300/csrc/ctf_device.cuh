@@ -42,6 +42,18 @@ __device__ __forceinline__ void stf_offset(int px, int py, int view, uint32_t k0
     dy = xi1 < t ? 1 : 0;
 }
 
+// The same draw with the third word of the Philox output as xi2 (fallback
+// C+ picks its extra texel with it).
+__device__ __forceinline__ void stf_draw(int px, int py, int view, uint32_t k0, uint32_t k1, float s, float t, int &dx,
+                                         int &dy, float &xi2) {
+    uint4 r = philox4x32_10(make_uint4((uint32_t)px, (uint32_t)py, (uint32_t)view, 0u), k0, k1);
+    float xi0 = __fmul_rn((float)(r.x >> 8), 5.9604644775390625e-08f);  // 2^-24
+    float xi1 = __fmul_rn((float)(r.y >> 8), 5.9604644775390625e-08f);
+    xi2 = __fmul_rn((float)(r.z >> 8), 5.9604644775390625e-08f);
+    dx = xi0 < s ? 1 : 0;
+    dy = xi1 < t ? 1 : 0;
+}
+
 // ---------------------------------------------------------------------------
 // Block decode.  Texture = (Wt/4) x (Ht/4) blocks of 8 bytes read as one
 // uint2: .x = c0 | c1 << 16, .y = 2-bit indices.  Returns RGBA8 packed

@@ -110,6 +110,193 @@ __device__ __forceinline__ float4 filter4(const float w[4], const float3 t[4]) {
     return make_float4(rg.x, rg.y, ba.x, ba.y);
 }
 
+// ---------------------------------------------------------------------------
+// Fallbacks C and C+ (Sec. 3.4) for a magnified tile whose texel set does
+// not fit the budget; mode 1 = C, 2 = C+.  Every active lane draws its
+// one-tap STF texel.  C: every active lane produces it.  C+: the distinct
+// STF texels are produced by the first n active lanes (in the order of the
+// lowest lane that draws each), and remaining active lane c (index among the
+// active lanes) takes the footprint of active lane
+// l = round_half_up((na-1)(c-n)/(na-1-n)) (l = 0 when na-1 = n: eq. 2 with
+// the na active lanes for the 32) and produces one of its nonzero-weight
+// taps outside that set, drawn by weight with the third word of its own STF
+// draw (nothing if there is none).  Every active pixel then blends the
+// produced texels of its footprint that have nonzero weight by eq. 1:
+// exact bilinear when all are present, the texel itself when one is, else
+// fma(1 - S_w, S_p / N, S_wp) per channel (tap order, FP32 RN).
+// `keys` is a per-warp array of 32 64-bit words in shared memory.
+// Warp-collective; kept out of line so that it does not weigh on the
+// registers of the common path.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long texel_key(int x, int y) {
+    return ((unsigned long long)(uint32_t)y << 32) | (uint32_t)x;
+}
+
+struct FallbackOut {
+    float4 res;
+    uint32_t count;
+};
+
+// The block fields and the STF key are passed by value: a kernel parameter
+// handed by reference to an out-of-line function would be copied to local
+// memory for the whole kernel.
+struct FallbackArgs {
+    const uint2 *blocks;
+    int Wt, Ht, nbx;
+    int view;
+    uint32_t k0, k1;
+    int mode;
+};
+
+__device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ulx, int uly, float s, float t,
+                                                   bool active, int px, int py, uint32_t A, int lane, uint32_t lt,
+                                                   const DecodeTables *tabs, unsigned long long *keys) {
+    // no texel: x = INT_MIN is never a texel coordinate (|x| < 2^22 + 2)
+    constexpr unsigned long long kNone = 0x8000000080000000ull;
+    const int na = __popc(A);
+    const int ai = __popc(A & lt);
+    int dx = 0, dy = 0;
+    float xi2 = 0.f;
+    if (active) stf_draw(px, py, fa.view, fa.k0, fa.k1, s, t, dx, dy, xi2);
+    const int sx = ulx + dx, sy = uly + dy;
+    int qx = sx, qy = sy;  // the texel this lane produces
+    bool produce = active;
+    if (fa.mode == 2) {
+        // distinct STF texels: the lowest active lane of each group leads
+        const unsigned long long skey = active ? texel_key(sx, sy) : texel_key(INT_MIN, lane);  // distinct when inactive
+        const uint32_t grp = __match_any_sync(FULL, skey);
+        const uint32_t L = __ballot_sync(FULL, active && (__ffs(grp) - 1) == lane);
+        const int n = __popc(L);
+        keys[lane] = active ? skey : kNone;
+        __syncwarp();
+        const int lead = nth_set_lane(L, active && ai < n ? ai : 0);
+        const int ux = __shfl_sync(FULL, sx, lead), uy = __shfl_sync(FULL, sy, lead);
+        // remaining lanes: the footprint of source lane h(l, A)
+        const bool extra = active && ai >= n;
+        int l = 0;
+        if (extra) {
+            const int den = na - 1 - n;
+            l = den == 0 ? 0 : (2 * (na - 1) * (ai - n) + den) / (2 * den);
+        }
+        const int src = nth_set_lane(A, l);
+        const int sux = __shfl_sync(FULL, ulx, src), suy = __shfl_sync(FULL, uly, src);
+        const float ss = __shfl_sync(FULL, s, src), st = __shfl_sync(FULL, t, src);
+        if (!extra) {
+            qx = ux;
+            qy = uy;
+            produce = active;
+        } else {
+            float w[4];
+            bilinear_weights(ss, st, w);
+            bool cand[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned long long tk = texel_key(sux + (k & 1), suy + (k >> 1));
+                bool in_set = false;
+#pragma unroll 8
+                for (int j = 0; j < 32; ++j) in_set |= keys[j] == tk;
+                cand[k] = w[k] > 0.f && !in_set;
+            }
+            float wc = 0.f;
+            int last = -1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (cand[k]) {
+                    wc = __fadd_rn(wc, w[k]);
+                    last = k;
+                }
+            }
+            produce = last >= 0;
+            if (produce) {
+                const float tsel = __fmul_rn(xi2, wc);
+                float run = 0.f;
+                int pick = last;
+                bool done = false;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (cand[k] && !done) {
+                        run = __fadd_rn(run, w[k]);
+                        if (tsel < run) {
+                            pick = k;
+                            done = true;
+                        }
+                    }
+                }
+                qx = sux + (pick & 1);
+                qy = suy + (pick >> 1);
+            }
+        }
+        __syncwarp();
+    }
+    // produce; every lane decodes (non-producers their own clamped texel)
+    float3 val;
+    {
+        const int x = min(max(produce ? qx : ulx, 0), fa.Wt - 1), y = min(max(produce ? qy : uly, 0), fa.Ht - 1);
+        const uint2 blk = __ldg(fa.blocks + (uint32_t)(y >> 2) * (uint32_t)fa.nbx + (uint32_t)(x >> 2));
+        val = decode_texel_f(blk, x, y, tabs);
+    }
+    keys[lane] = produce ? texel_key(qx, qy) : kNone;
+    __syncwarp();
+    // eq. 1: the produced texels of the pixel's footprint with nonzero weight
+    float w[4];
+    bilinear_weights(s, t, w);
+    int srcl[4];
+    bool pres[4];
+    int nz = 0, N = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned long long tk = texel_key(ulx + (k & 1), uly + (k >> 1));
+        int found = -1;
+#pragma unroll 8
+        for (int j = 31; j >= 0; --j) found = keys[j] == tk ? j : found;
+        pres[k] = active && w[k] > 0.f && found >= 0;
+        srcl[k] = found >= 0 ? found : lane;
+        nz += w[k] > 0.f ? 1 : 0;
+        N += pres[k] ? 1 : 0;
+    }
+    float3 tv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        tv[k].x = __shfl_sync(FULL, val.x, srcl[k]);
+        tv[k].y = __shfl_sync(FULL, val.y, srcl[k]);
+        tv[k].z = __shfl_sync(FULL, val.z, srcl[k]);
+    }
+    __syncwarp();  // keys free for the next tile
+    FallbackOut o;
+    o.res = make_float4(0.f, 0.f, 0.f, 0.f);
+    o.count = produce ? 1u : 0u;
+    if (!active) return o;
+    if (N == 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (pres[k]) o.res = make_float4(tv[k].x, tv[k].y, tv[k].z, 1.0f);
+        return o;
+    }
+    float4 swp = make_float4(0.f, 0.f, 0.f, 0.f), sp = make_float4(0.f, 0.f, 0.f, 0.f);
+    float sw = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (!pres[k]) continue;
+        swp.x = __fmaf_rn(w[k], tv[k].x, swp.x);
+        swp.y = __fmaf_rn(w[k], tv[k].y, swp.y);
+        swp.z = __fmaf_rn(w[k], tv[k].z, swp.z);
+        swp.w = __fmaf_rn(w[k], 1.0f, swp.w);
+        sw = __fadd_rn(sw, w[k]);
+        sp.x = __fadd_rn(sp.x, tv[k].x);
+        sp.y = __fadd_rn(sp.y, tv[k].y);
+        sp.z = __fadd_rn(sp.z, tv[k].z);
+        sp.w = __fadd_rn(sp.w, 1.0f);
+    }
+    if (N == nz) {
+        o.res = swp;
+        return o;
+    }
+    const float r = __fsub_rn(1.0f, sw), fn = (float)N;
+    o.res = make_float4(__fmaf_rn(r, __fdiv_rn(sp.x, fn), swp.x), __fmaf_rn(r, __fdiv_rn(sp.y, fn), swp.y),
+                        __fmaf_rn(r, __fdiv_rn(sp.z, fn), swp.z), __fmaf_rn(r, __fdiv_rn(sp.w, fn), swp.w));
+    return o;
+}
+
 // CTAs of 8 warps per SM that the exact kernels ask the compiler to fit:
 // the collaborative kernels are issue-bound, and five CTAs (40 warps) hide
 // more latency than the registers a looser cap would buy.
@@ -118,10 +305,12 @@ constexpr int min_blocks() {
     return ALG >= ALG_LIST ? 5 : 1;
 }
 
-template <int ALG, int TW, int MD, bool kStats>
+// kFallback: the kernel variant that runs fallbacks C / C+ (p.fallback != 0);
+// the other variant carries no code for them.
+template <int ALG, int TW, int MD, bool kStats, bool kFallback = false>
 __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &in, int px, int py, bool inside,
                                             uint32_t idx, int lane, uint32_t lt, const DecodeTables *tabs,
-                                            ListTable *T, int *ranks, Counters &cnt) {
+                                            ListTable *T, int *ranks, unsigned long long *fbkeys, Counters &cnt) {
     PixelSetup ps;
     ps.active = in.covered;
     setup_coords(in.uv, (float)p.Wt, (float)p.Ht, ps);
@@ -158,6 +347,27 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
         }
     } else {
         const Selection sel = select_tile<ALG, MD, kStats>(p, ps, in.jac, px, py, lane, lt, T, ranks, cnt);
+        if (kFallback && ALG >= ALG_LIST && sel.path == PATH_FALLBACK_BUDGET) {
+            // fallback C or C+ in place of one-tap STF
+            FallbackArgs fa;
+            fa.blocks = p.blocks;
+            fa.Wt = p.Wt;
+            fa.Ht = p.Ht;
+            fa.nbx = p.nbx;
+            fa.view = p.view;
+            fa.k0 = p.k0;
+            fa.k1 = p.k1;
+            fa.mode = p.fallback;
+            const FallbackOut fo =
+                fallback_blend(fa, ps.ulx, ps.uly, ps.s, ps.t, ps.active, px, py, sel.A, lane, lt, tabs, fbkeys);
+            if (kStats) {  // select_tile counted one evaluation per active lane
+                const int d = __popc(__ballot_sync(FULL, fo.count != 0)) - __popc(sel.A);
+                cnt.v[kStatTexelEvals] += d;
+                cnt.v[kStatTexelEvalsUnique] += d;
+            }
+            if (inside) store_pixel(p, idx, fo.res, (uint8_t)fo.count);
+            return;
+        }
         // step 2: exact decode of the lane's texel (clamped to the texture);
         // lanes that produce nothing decode their own upper-left texel, which
         // the warp reads anyway, and drop it

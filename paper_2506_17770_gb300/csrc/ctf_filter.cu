@@ -35,12 +35,13 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
-template <int ALG, int TW, int MD, bool kStats>
+template <int ALG, int TW, int MD, bool kStats, bool kFb>
 __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kernel(const ExactParams p) {
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
     __shared__ DecodeTables tabs;
     __shared__ int rank_slots[kWarps][32];
+    __shared__ unsigned long long fb_keys[kWarps][32];  // fallback C / C+ texel keys
     __shared__ unsigned long long block_stats[kNumStats];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
 
@@ -90,8 +91,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kern
         const uint32_t nidx = nby * (TH * W) + nbx * TW + lane_off;
         const Inputs nxt = load_inputs_any<kJac>(p, ninside, nidx);
 
-        filter_tile<ALG, TW, MD, kStats>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
-                                         &tabs, T, rank_slots[warp], cnt);
+        filter_tile<ALG, TW, MD, kStats, kFb>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
+                                         &tabs, T, rank_slots[warp], fb_keys[warp], cnt);
 
         bx = nbx;
         by = nby;
@@ -113,23 +114,33 @@ __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kern
 
 using KernelFn = void (*)(const ExactParams);
 
-template <int ALG, int TW, bool kStats>
-KernelFn pick_mask(int md) {
-    if constexpr (ALG == ALG_MASK) {
-        return md == 11 ? exact_filter_kernel<ALG, TW, 11, kStats> : exact_filter_kernel<ALG, TW, 16, kStats>;
+// The collaborative algorithms have a second variant for fallbacks C / C+.
+template <int ALG, int TW, int MD, bool kStats>
+KernelFn pick_fb(bool fb) {
+    if constexpr (ALG >= ALG_LIST) {
+        return fb ? exact_filter_kernel<ALG, TW, MD, kStats, true> : exact_filter_kernel<ALG, TW, MD, kStats, false>;
     } else {
-        return exact_filter_kernel<ALG, TW, 16, kStats>;
+        return exact_filter_kernel<ALG, TW, MD, kStats, false>;
+    }
+}
+
+template <int ALG, int TW, bool kStats>
+KernelFn pick_mask(int md, bool fb) {
+    if constexpr (ALG == ALG_MASK) {
+        return md == 11 ? pick_fb<ALG, TW, 11, kStats>(fb) : pick_fb<ALG, TW, 16, kStats>(fb);
+    } else {
+        return pick_fb<ALG, TW, 16, kStats>(fb);
     }
 }
 
 template <int TW, bool kStats>
-KernelFn pick_alg(int alg, int md) {
+KernelFn pick_alg(int alg, int md, bool fb) {
     switch (alg) {
-    case ALG_4TAP: return pick_mask<ALG_4TAP, TW, kStats>(md);
-    case ALG_STF: return pick_mask<ALG_STF, TW, kStats>(md);
-    case ALG_LIST: return pick_mask<ALG_LIST, TW, kStats>(md);
-    case ALG_BOX: return pick_mask<ALG_BOX, TW, kStats>(md);
-    case ALG_MASK: return pick_mask<ALG_MASK, TW, kStats>(md);
+    case ALG_4TAP: return pick_mask<ALG_4TAP, TW, kStats>(md, fb);
+    case ALG_STF: return pick_mask<ALG_STF, TW, kStats>(md, fb);
+    case ALG_LIST: return pick_mask<ALG_LIST, TW, kStats>(md, fb);
+    case ALG_BOX: return pick_mask<ALG_BOX, TW, kStats>(md, fb);
+    case ALG_MASK: return pick_mask<ALG_MASK, TW, kStats>(md, fb);
     default: return nullptr;
     }
 }
@@ -151,11 +162,11 @@ int device_sm_count() {
 
 cudaError_t launch_exact_filter(const ExactParams &p, int alg, int tile_w, int mask_dim, cudaStream_t stream) {
     KernelFn fn = nullptr;
-    const bool st = p.stats != nullptr;
+    const bool st = p.stats != nullptr, fb = p.fallback != 0;
     switch (tile_w) {
-    case 8: fn = st ? pick_alg<8, true>(alg, mask_dim) : pick_alg<8, false>(alg, mask_dim); break;
-    case 4: fn = st ? pick_alg<4, true>(alg, mask_dim) : pick_alg<4, false>(alg, mask_dim); break;
-    case 16: fn = st ? pick_alg<16, true>(alg, mask_dim) : pick_alg<16, false>(alg, mask_dim); break;
+    case 8: fn = st ? pick_alg<8, true>(alg, mask_dim, fb) : pick_alg<8, false>(alg, mask_dim, fb); break;
+    case 4: fn = st ? pick_alg<4, true>(alg, mask_dim, fb) : pick_alg<4, false>(alg, mask_dim, fb); break;
+    case 16: fn = st ? pick_alg<16, true>(alg, mask_dim, fb) : pick_alg<16, false>(alg, mask_dim, fb); break;
     default: return cudaErrorInvalidValue;
     }
     if (!fn) return cudaErrorInvalidValue;

@@ -53,6 +53,7 @@ struct __align__(16) ExactParams {
     int budget;
     int edge_remap;
     int group_dedup;      // learned decode: one evaluation per distinct texel of a tile group
+    int fallback;         // over-budget tiles: 0 one-tap STF, 1 fallback C, 2 fallback C+
     float4 *out;
     uint8_t *evals;       // nullable
     unsigned long long *stats;  // kNumStats counters or nullptr

@@ -174,3 +174,23 @@ def test_batch_group_dedup_equals_per_view_calls(textures):
         assert np.array_equal(v["out_evals"].cpu().numpy()[:H, :W], ref_ev[:H, :W])
     assert st == _sum_stats(singles)
     assert st["texel_evals_unique"] < st["texel_evals"]
+
+
+def test_batch_fallback_cplus_equals_per_view_calls(textures):
+    views = [v for v in _make_views(textures, n=9, seed=23) if v["kind"] == "block"]
+    o = _ctf.batch_opts(tile_w=8, tile_h=4, mask_dim=11, items_per_fetch=2, ctas_per_sm=4, fallback=2)
+    fopts = {"tile_w": 8, "tile_h": 4, "mask_dim": 11, "fallback": 2}
+    st = _ctf.ctf_filter_batch(views, "mask", 5, o, stats=True)
+    _ctf.ctf_sync_check()
+    singles = []
+    for v in views:
+        ref, ref_ev, ref_st = _single(v, "mask", 5, fopts)
+        singles.append(ref_st)
+        H, W = v["height"], v["width"]
+        assert np.array_equal(v["out_rgba"].cpu().numpy()[:H, :W].view(np.uint32), ref[:H, :W].view(np.uint32))
+        assert np.array_equal(v["out_evals"].cpu().numpy()[:H, :W], ref_ev[:H, :W])
+    assert st == _sum_stats(singles)
+    # a learned view refuses the C / C+ fallbacks
+    lv = [v for v in _make_views(textures, n=4, seed=23) if v["kind"] != "block"][:1]
+    with pytest.raises(_ctf.CtfError):
+        _ctf.ctf_filter_batch(lv, "mask", 5, o)

@@ -186,6 +186,26 @@ def test_ragged_mixed(mixed, W, H, alg):
                       cpu_filter(mixed, uv, jac, cov, alg, seed=77, opts=opts))
 
 
+@pytest.mark.parametrize("fallback", [1, 2])
+@pytest.mark.parametrize("alg", ["box", "mask", "list_merge"])
+def test_fallback_c_and_cplus(frame, mixed, alg, fallback):
+    """Fallbacks C (1) and C+ (2) of Sec. 3.4 in place of one-tap STF on the
+    over-budget tiles: the full view, and ragged frames with coverage holes,
+    clamped edges and the option sets of the ragged test."""
+    tex, sc = frame
+    for opts in ({"fallback": fallback}, {"fallback": fallback, "mask_dim": 11, "tile_w": 4, "tile_h": 8}):
+        g = gpu_filter(tex, sc.uv, sc.jac, sc.coverage, alg, seed=31, opts=opts)
+        assert_parity(g, cpu_filter(tex, sc.uv, sc.jac, sc.coverage, alg, seed=31, opts=opts))
+        assert g[2]["tiles_fallback_budget"] > 0
+    for W, H in ((133, 77), (17, 3), (250, 131)):
+        uv, jac, cov = _mixed_scene(W, H, seed=W * 1000 + H)
+        for opts in ({"fallback": fallback}, {"fallback": fallback, "edge_remap": 0},
+                     {"fallback": fallback, "budget": 9, "mask_dim": 11},
+                     {"fallback": fallback, "tile_w": 16, "tile_h": 2, "budget": 20}):
+            assert_parity(gpu_filter(mixed, uv, jac, cov, alg, seed=77, opts=opts),
+                          cpu_filter(mixed, uv, jac, cov, alg, seed=77, opts=opts))
+
+
 def test_empty_and_uncovered(mixed):
     uv, jac, cov = _mixed_scene(40, 20, seed=1)
     z = np.zeros((20, 40), np.uint8)

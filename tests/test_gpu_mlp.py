@@ -229,3 +229,9 @@ def test_group_dedup_on_a_magnified_plane(tex64):
     assert st1 == ref_st
     # neighbouring 8x4 tiles share the texels along their common edges
     assert st1["texel_evals_unique"] < 0.8 * st1["texel_evals"]
+
+
+def test_learned_textures_refuse_fallback_c(tex64):
+    uv, jac, cov = _scene(37, 21, 12)
+    with pytest.raises(_ctf.CtfError):
+        gpu_filter(tex64, uv, jac, cov, "mask", {"fallback": 1})
