@@ -37,7 +37,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "filtered pixels/s and texel evals/pixel, collaborative vs 4-tap on one GB300 at tol"
 HEADLINE = ("mask", {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 11, "edge_remap": 1})
-OTHERS = [("4tap", {}), ("box", {}), ("list_merge", {}), ("mask", {"mask_dim": 16})]
+OTHERS = [("4tap", "4tap", {}), ("box", "box", {}), ("list_merge", "list_merge", {}),
+          ("mask16", "mask", {"mask_dim": 16}),
+          ("mask11_fallback_c", "mask", {"fallback": 1}), ("mask11_fallback_cplus", "mask", {"fallback": 2})]
 ALG_ID = {"4tap": 0, "stf": 1, "list_merge": 2, "box": 3, "mask": 4}
 FALLBACK_HBM_GBS = 6800.0
 
@@ -194,6 +196,13 @@ def run_cpu_oracle(sc, blocks, Wt, Ht, alg, opts, seconds: float, max_frames: in
         if el >= seconds or frames >= max_frames:
             break
     return frames, el, ev_total
+
+
+def _psnr(img, ref):
+    """PSNR of RGB in [0, 1] (alpha excluded), log10."""
+    import torch
+    mse = torch.mean((img[..., :3] - ref[..., :3]) ** 2).item()
+    return -10 * math.log10(max(mse, 1e-30))
 
 
 def _timed_views(launch, steps, warmup, flush, stream):
@@ -543,17 +552,26 @@ def ours_arm(args):
     extras = {}
     if not args.no_extras:
         k = min(args.steps, 1000)
-        for a, o in OTHERS:
+        ref4 = None
+        for key, a, o in [("mask11", HEADLINE[0], {})] + OTHERS:
             oo = dict(HEADLINE[1])
             oo.update(o)
+            if key == "mask11":  # headline image, for the error against 4-tap only
+                stats_of(a, oo)
+                img = out.clone()
+                continue
             ms_a, _ = timed(a, oo, k, 5)
             sa = stats_of(a, oo)
-            key = a if a != "mask" else f"mask{oo['mask_dim']}"
+            if key == "4tap":
+                ref4 = out.clone()
+                extras["mask11"] = {"psnr_vs_4tap_db": _psnr(img, ref4)}
             extras[key] = {"pixels_per_s": npix / (ms_a / k * 1e-3), "ms_per_view": ms_a / k,
                            "evals_per_pixel": sa["texel_evals"] / max(1, sa["pixels_active"]),
                            "tiles_success": sa["tiles_success"], "tiles_fallback_budget": sa["tiles_fallback_budget"],
                            "tiles_fallback_minified": sa["tiles_fallback_minified"],
                            "achieved_gbs": algorithmic_bytes(a, npix, tex_bytes, cov is not None) / (ms_a / k * 1e-3) / 1e9}
+            if ref4 is not None and key != "4tap":
+                extras[key]["psnr_vs_4tap_db"] = _psnr(out, ref4)
     # end-to-end through the host entry point (pinned host buffers)
     h_uv = torch.from_numpy(sc.uv).pin_memory()
     h_jac = torch.from_numpy(sc.jac).pin_memory()
