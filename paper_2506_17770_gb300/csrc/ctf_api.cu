@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -163,6 +164,7 @@ int run_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t
     p.edge_remap = ro.edge_remap;
     p.group_dedup = ro.group_dedup;
     p.fallback = ro.fallback;
+    p.tables = tex->tables;
     p.out = reinterpret_cast<float4 *>(out);
     p.evals = evals;
     p.stats = dstats;
@@ -197,6 +199,44 @@ int read_stats(unsigned long long *dstats, ctf_stats *stats, cudaStream_t stream
 }
 
 }  // namespace
+
+// Decode tables of the exact path, made once per device: rg and b by bit
+// replication of the RGB565 fields, val by IEEE single-precision division
+// (correctly rounded on the host as on the device).
+namespace ctf {
+
+const DecodeTables *device_decode_tables() {
+    static std::mutex mu;
+    static std::map<int, DecodeTables *> made;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = made.find(dev);
+    if (it != made.end()) return it->second;
+    std::vector<DecodeTables> host(1);
+    DecodeTables &t = host[0];
+    for (uint32_t i = 0; i < 2048; ++i) {
+        const uint32_t r5 = i >> 6, g6 = i & 63u;
+        t.rg[i] = ((r5 << 3) | (r5 >> 2)) | (((g6 << 2) | (g6 >> 4)) << 10);
+    }
+    for (uint32_t i = 0; i < 32; ++i) t.b[i] = ((i << 3) | (i >> 2)) << 20;
+    for (int i = 0; i < 1024; ++i) {
+        volatile float num = (float)(i < 256 ? i : (i - 256) / 3);  // no contraction or reassociation
+        t.val[i] = num / 255.0f;
+    }
+    DecodeTables *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(DecodeTables));
+    if (e == cudaSuccess) e = cudaMemcpy(d, &t, sizeof(DecodeTables), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (d) cudaFree(d);
+        report_cuda(e, "decode tables");
+        return nullptr;
+    }
+    made[dev] = d;
+    return d;
+}
+
+}  // namespace ctf
 
 // Error reporting and the per-device error word, shared with the other
 // translation units of the library.
@@ -339,6 +379,12 @@ int ctf_texture_create(const ctf_texture_desc *desc, ctf_texture *out) {
         cudaFree(t->blocks);
         delete t;
         return cuda_fail(e, "copying blocks");
+    }
+    t->tables = ctf::device_decode_tables();
+    if (!t->tables) {
+        cudaFree(t->blocks);
+        delete t;
+        return CTF_ERR_CUDA;
     }
     *out = t;
     return CTF_OK;

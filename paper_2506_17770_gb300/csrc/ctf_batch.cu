@@ -61,6 +61,7 @@ struct BatchParams {
     unsigned long long *counter;
     unsigned long long *stats;
     int *err;
+    const DecodeTables *tables;  // block views: the device's decode tables
 };
 
 // Last view whose first item is <= item (views with no items are skipped
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, batch_min_blocks<ALG>()) bat
     __shared__ int s_begin[kSmViews];
     __shared__ __align__(16) ExactParams s_params[kBlockWarps];  // each warp's current view
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    build_decode_tables(&tabs);
+    load_decode_tables(&tabs, b.tables);
     if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
     const bool cached = b.nkind <= kSmViews && b.total_items < 0x7fffffffLL;
     if (cached)
@@ -398,6 +399,7 @@ int make_plan(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t see
         p.out = reinterpret_cast<float4 *>(v.out_rgba);
         p.evals = v.out_evals;
         p.stats = nullptr;
+        p.tables = v.tex->tables;
         d.learned = v.tex->mode != CTF_EVAL_BLOCK;
         if (d.learned && r.fallback)
             return report(CTF_ERR_UNSUPPORTED, "view %d: fallbacks C and C+ are built for block textures only", i);
@@ -484,6 +486,7 @@ cudaError_t launch_plan(const Plan &plan, const DevPlan &dp, int alg, const Reso
         b.counter = dp.counter + k;
         b.stats = stats;
         b.err = err;
+        b.tables = k == 0 ? plan.views[plan.index[0][0]].p.tables : nullptr;
         if (k == 1) {
             e = prepare_batch(fn);
             if (e != cudaSuccess) return e;

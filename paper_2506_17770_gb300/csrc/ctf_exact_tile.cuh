@@ -50,28 +50,13 @@ __device__ __forceinline__ void store_pixel(const ExactParams &p, uint32_t idx, 
     if (p.evals) p.evals[idx] = count;
 }
 
-// Decode tables, built in shared memory by every CTA: the two endpoints of a
-// block expand to 8-bit channels laid out in 10-bit fields (r bits 0-9, g
-// 10-19, b 20-29) by two lookups each, so that the palette entries 2 and 3,
-// (2a+b+1)/3 with (a, b) = (c0, c1) or (c1, c0), come out of one integer
-// expression for all three channels, and `val` turns a field into the
-// channel value: val[v] = v/255 for v < 256, val[256 + s] = floor(s/3)/255
-// for s < 768 (both correctly rounded, IEEE division); the interpolated
-// entries carry the offset 256 in every field of the sum.
-struct DecodeTables {
-    uint32_t rg[2048];  // c >> 5 = (r5 << 6) | g6  ->  r8 | g8 << 10
-    uint32_t b[32];     // c & 31 = b5              ->  b8 << 20
-    float val[1024];
-};
-
-__device__ __forceinline__ void build_decode_tables(DecodeTables *t) {
-    for (int i = threadIdx.x; i < 2048; i += blockDim.x) {
-        const uint32_t r5 = (uint32_t)i >> 6, g6 = (uint32_t)i & 63u;
-        t->rg[i] = ((r5 << 3) | (r5 >> 2)) | (((g6 << 2) | (g6 >> 4)) << 10);
-    }
-    for (int i = threadIdx.x; i < 32; i += blockDim.x) t->b[i] = (((uint32_t)i << 3) | ((uint32_t)i >> 2)) << 20;
-    for (int i = threadIdx.x; i < 1024; i += blockDim.x)
-        t->val[i] = i < 256 ? __fdiv_rn((float)i, 255.0f) : __fdiv_rn((float)((i - 256) / 3), 255.0f);
+// The decode tables (DecodeTables, ctf_internal.h) into this CTA's shared
+// memory, 16 bytes per thread and step; the interpolated palette entries
+// carry the offset 256 in every field of the sum.
+__device__ __forceinline__ void load_decode_tables(DecodeTables *t, const DecodeTables *g) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(g);
+    uint4 *dst = reinterpret_cast<uint4 *>(t);
+    for (int i = threadIdx.x; i < (int)(sizeof(DecodeTables) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
 // RGB of texel (x, y) of a block (alpha is 1): palette c0, c1,

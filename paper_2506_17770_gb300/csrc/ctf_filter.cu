@@ -45,7 +45,6 @@ __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kern
     __shared__ unsigned long long block_stats[kNumStats];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
 
-    build_decode_tables(&tabs);
     if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ListTable *T = ALG == ALG_LIST ? reinterpret_cast<ListTable *>(dyn_smem) + warp : nullptr;
@@ -53,7 +52,6 @@ __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kern
 #pragma unroll
         for (int s = 0; s < 8; ++s) T->keys[lane * 8 + s] = kEmpty;
     }
-    __syncthreads();
 
     const int tx = lane % TW, ty = lane / TW;
     const uint32_t lt = lanemask_lt();
@@ -79,6 +77,9 @@ __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kern
     bool inside = n_mine > 0 && bx < lim_x && by < lim_y;
     uint32_t idx = by * (TH * W) + bx * TW + lane_off;
     Inputs cur = load_inputs_any<kJac>(p, inside, idx);
+    // the decode tables come in while the first tile's inputs are in flight
+    load_decode_tables(&tabs, p.tables);
+    __syncthreads();
 
     for (uint32_t i = 0; i < n_mine; ++i) {
         // prefetch the next tile of this warp

@@ -9,12 +9,30 @@
 #include "../../include/ctf.h"
 #include "ctf_mlp.cuh"
 
+namespace ctf {
+// Decode tables of the exact block decode, one copy per device in global
+// memory (made on the host, ctf_api.cu) and copied into shared memory by
+// every CTA: the two endpoints of a block expand to 8-bit channels laid out
+// in 10-bit fields (r bits 0-9, g 10-19, b 20-29) by two lookups each, so
+// that the palette entries 2 and 3, (2a+b+1)/3 with (a, b) = (c0, c1) or
+// (c1, c0), come out of one integer expression for all three channels, and
+// `val` turns a field into the channel value: val[v] = v/255 for v < 256,
+// val[256 + s] = floor(s/3)/255 for s < 768 (both correctly rounded).
+struct DecodeTables {
+    uint32_t rg[2048];  // c >> 5 = (r5 << 6) | g6  ->  r8 | g8 << 10
+    uint32_t b[32];     // c & 31 = b5              ->  b8 << 20
+    float val[1024];
+};
+static_assert(sizeof(DecodeTables) % 16 == 0, "copied in 16-byte pieces");
+}  // namespace ctf
+
 // Texture object behind the opaque ctf_texture handle.
 struct ctf_texture_s {
     int width = 0, height = 0;
     ctf_eval_mode mode = CTF_EVAL_BLOCK;
     int device = 0;
     void *blocks = nullptr;  // BLOCK: device copy of the blocks
+    const ctf::DecodeTables *tables = nullptr;  // BLOCK: the device's decode tables (shared, not owned)
     // learned decode
     __half *lat[2] = {nullptr, nullptr};  // device latent grids [gh][gw][8]
     int gw[2] = {0, 0}, gh[2] = {0, 0};
@@ -54,6 +72,7 @@ struct __align__(16) ExactParams {
     int edge_remap;
     int group_dedup;      // learned decode: one evaluation per distinct texel of a tile group
     int fallback;         // over-budget tiles: 0 one-tap STF, 1 fallback C, 2 fallback C+
+    const DecodeTables *tables;  // block decode tables in global memory (block textures)
     float4 *out;
     uint8_t *evals;       // nullable
     unsigned long long *stats;  // kNumStats counters or nullptr
@@ -65,6 +84,10 @@ cudaError_t launch_exact_filter(const ExactParams &p, int alg, int tile_w, int m
 
 // Number of SMs of the current device (cached).
 int device_sm_count();
+
+// The current device's decode tables (made once per device; nullptr and a
+// recorded error if that failed).
+const DecodeTables *device_decode_tables();
 
 // Learned decode (ctf_mlp.cu).
 cudaError_t launch_mlp_decode(const MlpDevice &m, int Wt, int Ht, const int2 *xy, int n, float4 *out, int *err,
