@@ -570,6 +570,8 @@ static void fallback_c(const texel_source *src, const pixel_setup *lane, uint32_
  *   out  [H][W][4] float (FP32 result; may be NULL), outd [H][W][4] double (may be NULL)
  *   evals[H][W] uint8 per-pixel texel evaluations
  *   tile_path / tile_n: per tile outcome code and texel-set size (may be NULL)
+ *   tpl            texels a lane may produce, 1 or 2 (Sec. 5: "more than
+ *                  one texel per lane"); budget up to 32 * tpl
  *   fallback       0: over-budget tiles take one-tap STF; 1: fallback C;
  *                  2: fallback C+ (Sec. 3.4); minified tiles always STF
  *   group_tiles    0, or the size of the tile groups (consecutive tile
@@ -583,17 +585,19 @@ static void fallback_c(const texel_source *src, const pixel_setup *lane, uint32_
  */
 static int oracle_filter_ex(const texel_source *src, const float *uv, const float *jac, const uint8_t *cov,
                             int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h,
-                            int budget, int mask_dim, int edge_remap, int group_tiles, int fallback, int fp64,
-                            float *out, double *outd, uint8_t *evals, int32_t *tile_path, int32_t *tile_n,
-                            int64_t *stats_out)
+                            int budget, int mask_dim, int edge_remap, int group_tiles, int fallback, int tpl,
+                            int fp64, float *out, double *outd, uint8_t *evals, int32_t *tile_path,
+                            int32_t *tile_n, int64_t *stats_out)
 {
+    if (tpl != 1 && tpl != 2)
+        return -1;
     if (fallback < 0 || fallback > 2)
         return -1;
     if (W < 0 || H < 0 || tile_w <= 0 || tile_h <= 0 || tile_w * tile_h != 32)
         return -1;
     if (group_tiles < 0 || group_tiles > 8)
         return -1;
-    if (alg < 0 || alg > 4 || budget < 1 || budget > 32)
+    if (alg < 0 || alg > 4 || budget < 1 || budget > 32 * tpl)
         return -1;
     if (alg == ALG_MASK && mask_dim != 16 && mask_dim != 11)
         return -1;
@@ -756,14 +760,17 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                     if (nset > budget)
                         fits = 0;
                 }
-                /* Enough lanes to produce n texels?  With edge remapping any n
-                 * active lanes do (producer of texel i is lane h(i, A));
-                 * without it, lanes 0..n-1 must all be active. */
+                /* Enough lanes to produce n texels, tpl each?  With edge
+                 * remapping any ceil(n / tpl) active lanes do (producer of
+                 * texel i is lane h(i mod na, A), in round i div na); without
+                 * it, lanes 0..min(n, 32)-1 must all be active (producer of
+                 * texel i is lane i mod 32). */
                 if (fits) {
                     if (edge_remap) {
-                        if (L.n > nactive) fits = 0;
+                        if (L.n > tpl * nactive) fits = 0;
                     } else {
-                        uint32_t need = L.n >= 32 ? 0xffffffffu : ((1u << L.n) - 1u);
+                        int lanes = L.n < 32 ? L.n : 32;
+                        uint32_t need = lanes >= 32 ? 0xffffffffu : ((1u << lanes) - 1u);
                         if ((A & need) != need) fits = 0;
                     }
                 }
@@ -789,15 +796,16 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                 continue;
             }
             st.tiles_success++;
-            /* Step 2: texel i is produced once, by lane h(i, A) (or lane i). */
+            /* Step 2: texel i is produced once, by lane h(i mod na, A) (or lane
+             * i mod 32); a lane produces up to tpl texels. */
             float valf[128][4];
             double vald[128][4];
             for (int i = 0; i < L.n; ++i) {
-                int producer = edge_remap ? oracle_h(&A, 1, i) : i;
+                int producer = edge_remap ? oracle_h(&A, 1, i % nactive) : i % 32;
                 const pixel_setup *p = &lane[producer];
                 size_t idx = (size_t)p->py * W + p->px;
                 fetch_texel(src, L.x[i], L.y[i], valf[i], vald[i]);
-                evals[idx] = 1;
+                evals[idx]++;
                 group_note(&G, src, L.x[i], L.y[i]);
             }
             /* Step 3: every active lane gathers its four taps and filters. */
@@ -849,26 +857,28 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
 /* Exact block decode, FP32 arithmetic with the rounding described above. */
 int oracle_filter(const uint8_t *blocks, int Wt, int Ht, const float *uv, const float *jac, const uint8_t *cov,
                   int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h, int budget,
-                  int mask_dim, int edge_remap, int group_tiles, int fallback, float *out, uint8_t *evals,
-                  int32_t *tile_path, int32_t *tile_n, int64_t *stats)
+                  int mask_dim, int edge_remap, int group_tiles, int fallback, int tpl, float *out,
+                  uint8_t *evals, int32_t *tile_path, int32_t *tile_n, int64_t *stats)
 {
     if (Wt <= 0 || Ht <= 0 || Wt % 4 || Ht % 4 || !blocks)
         return -1;
     texel_source src = {0, Wt, Ht, blocks, NULL};
     return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
-                            edge_remap, group_tiles, fallback, 0, out, NULL, evals, tile_path, tile_n, stats);
+                            edge_remap, group_tiles, fallback, tpl, 0, out, NULL, evals, tile_path, tile_n,
+                            stats);
 }
 
 /* Learned decode: texel values from the FP64 MLP, filter in double. */
 int oracle_filter_learned_f64(const void *mlp, int Wt, int Ht, const float *uv, const float *jac,
                               const uint8_t *cov, int W, int H, int view, int alg, uint64_t seed, int tile_w,
                               int tile_h, int budget, int mask_dim, int edge_remap, int group_tiles,
-                              int fallback, double *outd, uint8_t *evals, int32_t *tile_path, int32_t *tile_n,
-                              int64_t *stats)
+                              int fallback, int tpl, double *outd, uint8_t *evals, int32_t *tile_path,
+                              int32_t *tile_n, int64_t *stats)
 {
     if (Wt <= 0 || Ht <= 0 || !mlp)
         return -1;
     texel_source src = {1, Wt, Ht, NULL, mlp};
     return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
-                            edge_remap, group_tiles, fallback, 1, NULL, outd, evals, tile_path, tile_n, stats);
+                            edge_remap, group_tiles, fallback, tpl, 1, NULL, outd, evals, tile_path, tile_n,
+                            stats);
 }

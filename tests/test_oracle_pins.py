@@ -465,6 +465,37 @@ def test_fig4_thresholds_and_max_unique(oracle_lib):
     assert int(tn.max()) == max_unique
 
 
+def test_two_texels_per_lane_always_succeed_at_unit_magnification(oracle_lib):
+    """Sec. 5: an 8x4 wave needs at most 54 distinct texels at magnification
+    1, so two texel evaluations per lane always succeed once every pixel is
+    magnified.  With texels_per_lane 2 and budget 64, List Merge and the
+    16x16 mask succeed on every rotation and phase just above magnification
+    1, the outputs equal per-pixel bilinear bitwise, and the counts follow
+    the round-robin assignment: active lane a produces texels a and a + 32."""
+    o = oracle_lib
+    degrees = np.arange(0, 91, 3.0)
+    sc = synth.rotated_quad_tiles(1.001, degrees, 60)
+    blocks = synth.random_blocks(4096, 4096, seed=16)
+    ref = o.filter_frame(blocks, 4096, 4096, sc.uv, sc.jac, None, alg=o.ALG_4TAP)[0]
+    for alg, md in ((o.ALG_LIST_MERGE, 16), (o.ALG_MASK, 16)):
+        out1, ev1, st1, tp1, tn1 = o.filter_frame(blocks, 4096, 4096, sc.uv, sc.jac, None, alg=alg, mask_dim=md,
+                                                  want_tiles=True)
+        assert np.any(tp1 == o.PATH_FALLBACK_BUDGET)  # one texel per lane is not enough here
+        out, ev, st, tp, tn = o.filter_frame(blocks, 4096, 4096, sc.uv, sc.jac, None, alg=alg, mask_dim=md,
+                                             budget=64, texels_per_lane=2, want_tiles=True)
+        assert np.all(tp == o.PATH_SUCCESS) and tn.max() > 32
+        assert np.array_equal(out.view(np.uint32), ref.view(np.uint32))
+        for tid in range(tp.size):
+            n = int(tn[tid])
+            cnt = ev[tid * 4:tid * 4 + 4].ravel()
+            expect = np.array([(a < n) + (a + 32 < n) for a in range(32)], np.uint8)
+            np.testing.assert_array_equal(cnt, expect)
+        # tiles that one texel per lane already handled are unchanged
+        same = tp1 == o.PATH_SUCCESS
+        rows = np.repeat(same, 4)
+        np.testing.assert_array_equal(ev[rows], ev1[rows])
+
+
 # ---------------------------------------------------------------------------
 # One-tap STF: unbiased for bilinear (Sec. 3.4 opening; Pharr et al. 2024)
 # ---------------------------------------------------------------------------
