@@ -103,7 +103,8 @@ typedef struct {
 /* Filter options; NULL means the defaults in brackets.
  *   tile_w, tile_h  warp pixel tile, 8x4, 4x8 or 16x2            [8 x 4]
  *   budget          texels one warp may produce, 1..32 (one per lane,
- *                   Sec. 3 "at most one texel evaluation per lane") [32]
+ *                   Sec. 3 "at most one texel evaluation per lane"), up to
+ *                   64 with two texels per lane                 [32]
  *   mask_dim        Mask Sampling mask side, 16 or 11 (Sec. 3.3)  [16]
  *   edge_remap      1: producer of texel i is the i-th active lane h(i,A)
  *                   (supplemental Sec. 2), success needs n <= popcount(A);
@@ -124,7 +125,15 @@ typedef struct {
  *                   the footprints (eq. 2); each pixel blends the produced
  *                   texels of its footprint by eq. 1).  Minified tiles take
  *                   one-tap STF.  Block textures only (CTF_ERR_UNSUPPORTED
- *                   for learned ones)                             [0] */
+ *                   for learned ones)                             [0]
+ *   texels_per_lane 0 or 1: one texel evaluation per lane; 2: up to two
+ *                   (Sec. 5: at magnification 1 an 8x4 wave needs at most
+ *                   54 texels, so two per lane always succeed once every
+ *                   pixel is magnified).  Texel i is evaluated for lane
+ *                   h(i mod na, A) (or lane i mod 32 without edge
+ *                   remapping), whose count becomes 2 when it has two;
+ *                   success needs n <= 2 popcount(A).  Block textures only
+ *                   (CTF_ERR_UNSUPPORTED for learned ones)        [1] */
 typedef struct {
     int tile_w, tile_h;
     int budget;
@@ -132,6 +141,7 @@ typedef struct {
     int edge_remap;
     int group_dedup;
     int fallback;
+    int texels_per_lane;
 } ctf_filter_opts;
 
 /* Per-call counters (filled only when a stats pointer is given). */

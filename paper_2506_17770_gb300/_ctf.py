@@ -36,7 +36,7 @@ class ctf_texture_desc(ctypes.Structure):
 class ctf_filter_opts(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("budget", ctypes.c_int),
                 ("mask_dim", ctypes.c_int), ("edge_remap", ctypes.c_int), ("group_dedup", ctypes.c_int),
-                ("fallback", ctypes.c_int)]
+                ("fallback", ctypes.c_int), ("texels_per_lane", ctypes.c_int)]
 
 
 class ctf_stats(ctypes.Structure):
@@ -162,7 +162,8 @@ def _stream(stream):
 def _opts(opts):
     if opts is None or isinstance(opts, ctf_filter_opts):
         return opts
-    d = {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 16, "edge_remap": 1, "group_dedup": 0, "fallback": 0}
+    d = {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 16, "edge_remap": 1, "group_dedup": 0, "fallback": 0,
+         "texels_per_lane": 1}
     d.update(opts)
     return ctf_filter_opts(**d)
 
@@ -425,14 +426,15 @@ class ctf_batch_opts(ctypes.Structure):
         f = self.filter
         return {"tile_w": f.tile_w, "tile_h": f.tile_h, "budget": f.budget, "mask_dim": f.mask_dim,
                 "edge_remap": f.edge_remap, "group_dedup": f.group_dedup, "fallback": f.fallback,
+                "texels_per_lane": f.texels_per_lane,
                 "items_per_fetch": self.items_per_fetch,
                 "ctas_per_sm": self.ctas_per_sm}
 
 
 def batch_opts(tile_w=8, tile_h=4, budget=32, mask_dim=16, edge_remap=1, items_per_fetch=4, ctas_per_sm=4,
-               group_dedup=0, fallback=0):
+               group_dedup=0, fallback=0, texels_per_lane=1):
     o = ctf_batch_opts()
-    o.filter = ctf_filter_opts(tile_w, tile_h, budget, mask_dim, edge_remap, group_dedup, fallback)
+    o.filter = ctf_filter_opts(tile_w, tile_h, budget, mask_dim, edge_remap, group_dedup, fallback, texels_per_lane)
     o.items_per_fetch, o.ctas_per_sm = items_per_fetch, ctas_per_sm
     return o
 

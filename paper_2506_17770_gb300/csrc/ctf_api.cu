@@ -94,6 +94,7 @@ int scratch_stage(size_t bytes, void **out) {
 
 struct ResolvedOpts {
     int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1, group_dedup = 0, fallback = 0;
+    int tpl = 1;
 };
 
 int resolve_opts(const ctf_filter_opts *o, ResolvedOpts *r) {
@@ -106,12 +107,15 @@ int resolve_opts(const ctf_filter_opts *o, ResolvedOpts *r) {
     r->edge_remap = o->edge_remap;
     r->group_dedup = o->group_dedup;
     r->fallback = o->fallback;
+    r->tpl = o->texels_per_lane == 0 ? 1 : o->texels_per_lane;
     const bool shape_ok = (r->tile_w == 8 && r->tile_h == 4) || (r->tile_w == 4 && r->tile_h == 8) ||
                           (r->tile_w == 16 && r->tile_h == 2);
     if (!shape_ok) return fail(CTF_ERR_ARG, "tile %dx%d not one of 8x4, 4x8, 16x2", r->tile_w, r->tile_h);
     if (r->group_dedup != 0 && r->group_dedup != 1) return fail(CTF_ERR_ARG, "group_dedup must be 0 or 1");
     if (r->fallback < 0 || r->fallback > 2) return fail(CTF_ERR_ARG, "fallback %d not 0 (STF), 1 (C) or 2 (C+)", r->fallback);
-    if (r->budget < 1 || r->budget > 32) return fail(CTF_ERR_ARG, "budget %d outside [1, 32]", r->budget);
+    if (r->tpl != 1 && r->tpl != 2) return fail(CTF_ERR_ARG, "texels_per_lane %d not 0, 1 or 2", r->tpl);
+    if (r->budget < 1 || r->budget > 32 * r->tpl)
+        return fail(CTF_ERR_ARG, "budget %d outside [1, %d]", r->budget, 32 * r->tpl);
     if (r->mask_dim != 16 && r->mask_dim != 11) return fail(CTF_ERR_ARG, "mask_dim %d not 16 or 11", r->mask_dim);
     if (r->edge_remap != 0 && r->edge_remap != 1) return fail(CTF_ERR_ARG, "edge_remap must be 0 or 1");
     return CTF_OK;
@@ -131,8 +135,8 @@ int validate_filter_args(ctf_texture tex, const float *uv, const float *jac, int
     if ((int)alg < CTF_ALG_4TAP || (int)alg > CTF_ALG_MASK) return fail(CTF_ERR_ARG, "unknown algorithm %d", (int)alg);
     rc = resolve_opts(opts, ro);
     if (rc) return rc;
-    if (ro->fallback != 0 && tex->mode != CTF_EVAL_BLOCK)
-        return fail(CTF_ERR_UNSUPPORTED, "fallbacks C and C+ are built for block textures only");
+    if ((ro->fallback != 0 || ro->tpl != 1) && tex->mode != CTF_EVAL_BLOCK)
+        return fail(CTF_ERR_UNSUPPORTED, "fallbacks C and C+ and two texels per lane are built for block textures only");
     if ((size_t)width * (size_t)height == 0) return CTF_OK;
     if (!uv || !jac || !out) return fail(CTF_ERR_ARG, "uv, jac and out_rgba must not be NULL");
     if (!aligned(uv, 8)) return fail(CTF_ERR_ALIGN, "uv must be 8-byte aligned");
@@ -164,6 +168,7 @@ int run_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t
     p.edge_remap = ro.edge_remap;
     p.group_dedup = ro.group_dedup;
     p.fallback = ro.fallback;
+    p.tpl = ro.tpl;
     p.tables = tex->tables;
     p.out = reinterpret_cast<float4 *>(out);
     p.evals = evals;

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, batch_min_blocks<ALG>()) bat
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
     __shared__ DecodeTables tabs;
-    __shared__ int rank_slots[kBlockWarps][32];
+    __shared__ int rank_slots[kBlockWarps][64];
     __shared__ unsigned long long fb_keys[kBlockWarps][32];  // fallback C / C+ texel keys
     __shared__ unsigned long long block_stats[kNumStats];
     __shared__ int s_begin[kSmViews];
@@ -322,6 +322,7 @@ cudaError_t prepare_batch(BatchFn fn) {
 
 struct ResolvedBatch {
     int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1, group_dedup = 0, fallback = 0;
+    int tpl = 1;
     int items_per_fetch = 4, ctas_per_sm = 4;
 };
 
@@ -335,12 +336,15 @@ int resolve(const ctf_batch_opts *o, ResolvedBatch *r) {
     r->edge_remap = o->filter.edge_remap;
     r->group_dedup = o->filter.group_dedup;
     r->fallback = o->filter.fallback;
+    r->tpl = o->filter.texels_per_lane == 0 ? 1 : o->filter.texels_per_lane;
     r->items_per_fetch = o->items_per_fetch;
     r->ctas_per_sm = o->ctas_per_sm;
     const bool shape_ok = (r->tile_w == 8 && r->tile_h == 4) || (r->tile_w == 4 && r->tile_h == 8) ||
                           (r->tile_w == 16 && r->tile_h == 2);
     if (!shape_ok) return report(CTF_ERR_ARG, "tile %dx%d not one of 8x4, 4x8, 16x2", r->tile_w, r->tile_h);
-    if (r->budget < 1 || r->budget > 32) return report(CTF_ERR_ARG, "budget %d outside [1, 32]", r->budget);
+    if (r->tpl != 1 && r->tpl != 2) return report(CTF_ERR_ARG, "texels_per_lane %d not 0, 1 or 2", r->tpl);
+    if (r->budget < 1 || r->budget > 32 * r->tpl)
+        return report(CTF_ERR_ARG, "budget %d outside [1, %d]", r->budget, 32 * r->tpl);
     if (r->mask_dim != 16 && r->mask_dim != 11) return report(CTF_ERR_ARG, "mask_dim %d not 16 or 11", r->mask_dim);
     if (r->edge_remap != 0 && r->edge_remap != 1) return report(CTF_ERR_ARG, "edge_remap must be 0 or 1");
     if (r->group_dedup != 0 && r->group_dedup != 1) return report(CTF_ERR_ARG, "group_dedup must be 0 or 1");
@@ -396,13 +400,15 @@ int make_plan(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t see
         p.edge_remap = r.edge_remap;
         p.group_dedup = r.group_dedup;
         p.fallback = r.fallback;
+        p.tpl = r.tpl;
         p.out = reinterpret_cast<float4 *>(v.out_rgba);
         p.evals = v.out_evals;
         p.stats = nullptr;
         p.tables = v.tex->tables;
         d.learned = v.tex->mode != CTF_EVAL_BLOCK;
-        if (d.learned && r.fallback)
-            return report(CTF_ERR_UNSUPPORTED, "view %d: fallbacks C and C+ are built for block textures only", i);
+        if (d.learned && (r.fallback || r.tpl != 1))
+            return report(CTF_ERR_UNSUPPORTED,
+                          "view %d: fallbacks C and C+ and two texels per lane are built for block textures only", i);
         if (d.learned) d.m = mlp_device_view(v.tex);
         const int kind = d.learned ? 1 : 0;
         const long long per_item = d.learned ? mlp_group_tiles((int)alg) : kBlockItemTiles;
@@ -474,7 +480,7 @@ cudaError_t launch_plan(const Plan &plan, const DevPlan &dp, int alg, const Reso
     if (e != cudaSuccess) return e;
     for (int k = 0; k < 2; ++k) {
         if (plan.items[k] == 0) continue;
-        BatchFn fn = pick(k == 1, alg, r.tile_w, r.mask_dim, r.fallback != 0);
+        BatchFn fn = pick(k == 1, alg, r.tile_w, r.mask_dim, r.fallback != 0 || r.tpl == 2);
         if (!fn) return cudaErrorInvalidValue;
         BatchParams b;
         b.views = dp.views;
@@ -644,6 +650,7 @@ int ctf_batch_autotune(const ctf_view *views, int nviews, ctf_algorithm alg, uin
         b0.filter.edge_remap = 1;
         b0.filter.group_dedup = 0;
         b0.filter.fallback = 0;
+        b0.filter.texels_per_lane = 1;
         b0.items_per_fetch = 4;
         b0.ctas_per_sm = 4;
     }

@@ -290,9 +290,10 @@ constexpr int min_blocks() {
     return ALG >= ALG_LIST ? 5 : 1;
 }
 
-// kFallback: the kernel variant that runs fallbacks C / C+ (p.fallback != 0);
-// the other variant carries no code for them.
-template <int ALG, int TW, int MD, bool kStats, bool kFallback = false>
+// kExt: the kernel variant for the optional extensions, fallbacks C / C+
+// (p.fallback != 0) and two texels per lane (p.tpl == 2); the other variant
+// carries no code for them.
+template <int ALG, int TW, int MD, bool kStats, bool kExt = false>
 __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &in, int px, int py, bool inside,
                                             uint32_t idx, int lane, uint32_t lt, const DecodeTables *tabs,
                                             ListTable *T, int *ranks, unsigned long long *fbkeys, Counters &cnt) {
@@ -331,8 +332,8 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
             count = 4;
         }
     } else {
-        const Selection sel = select_tile<ALG, MD, kStats>(p, ps, in.jac, px, py, lane, lt, T, ranks, cnt);
-        if (kFallback && ALG >= ALG_LIST && sel.path == PATH_FALLBACK_BUDGET) {
+        const Selection sel = select_tile<ALG, MD, kStats, true, kExt>(p, ps, in.jac, px, py, lane, lt, T, ranks, cnt);
+        if (kExt && ALG >= ALG_LIST && p.fallback != 0 && sel.path == PATH_FALLBACK_BUDGET) {
             // fallback C or C+ in place of one-tap STF
             FallbackArgs fa;
             fa.blocks = p.blocks;
@@ -357,14 +358,30 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
         // lanes that produce nothing decode their own upper-left texel, which
         // the warp reads anyway, and drop it
         const float3 val = fetch_decode(p, sel.tx, sel.ty, tabs);
+        const bool two = kExt && ALG >= ALG_LIST && p.tpl == 2;
         if (sel.path == PATH_SUCCESS) {
             // step 3: gather the 2x2 taps from their producers and filter
             float3 t[4];
+            if (two) {
+                // second texels (non-producers decode their own texel again)
+                const float3 val2 = fetch_decode(p, sel.produce2 ? sel.tx2 : sel.tx, sel.produce2 ? sel.ty2 : sel.ty,
+                                                 tabs);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                t[k].x = __shfl_sync(FULL, val.x, sel.src[k]);
-                t[k].y = __shfl_sync(FULL, val.y, sel.src[k]);
-                t[k].z = __shfl_sync(FULL, val.z, sel.src[k]);
+                for (int k = 0; k < 4; ++k) {
+                    const int l = sel.src[k] & 31;
+                    const bool r = sel.src[k] >= 32;
+                    const float ax = __shfl_sync(FULL, val.x, l), bx = __shfl_sync(FULL, val2.x, l);
+                    const float ay = __shfl_sync(FULL, val.y, l), by = __shfl_sync(FULL, val2.y, l);
+                    const float az = __shfl_sync(FULL, val.z, l), bz = __shfl_sync(FULL, val2.z, l);
+                    t[k] = make_float3(r ? bx : ax, r ? by : ay, r ? bz : az);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    t[k].x = __shfl_sync(FULL, val.x, sel.src[k]);
+                    t[k].y = __shfl_sync(FULL, val.y, sel.src[k]);
+                    t[k].z = __shfl_sync(FULL, val.z, sel.src[k]);
+                }
             }
             if (ps.active) {
                 float w[4];

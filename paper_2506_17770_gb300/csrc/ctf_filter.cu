@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kern
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
     __shared__ DecodeTables tabs;
-    __shared__ int rank_slots[kWarps][32];
+    __shared__ int rank_slots[kWarps][64];
     __shared__ unsigned long long fb_keys[kWarps][32];  // fallback C / C+ texel keys
     __shared__ unsigned long long block_stats[kNumStats];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kern
 
 using KernelFn = void (*)(const ExactParams);
 
-// The collaborative algorithms have a second variant for fallbacks C / C+.
+// The collaborative algorithms have a second variant for the optional
+// extensions (fallbacks C / C+, two texels per lane).
 template <int ALG, int TW, int MD, bool kStats>
 KernelFn pick_fb(bool fb) {
     if constexpr (ALG >= ALG_LIST) {
@@ -163,7 +164,7 @@ int device_sm_count() {
 
 cudaError_t launch_exact_filter(const ExactParams &p, int alg, int tile_w, int mask_dim, cudaStream_t stream) {
     KernelFn fn = nullptr;
-    const bool st = p.stats != nullptr, fb = p.fallback != 0;
+    const bool st = p.stats != nullptr, fb = p.fallback != 0 || p.tpl == 2;
     switch (tile_w) {
     case 8: fn = st ? pick_alg<8, true>(alg, mask_dim, fb) : pick_alg<8, false>(alg, mask_dim, fb); break;
     case 4: fn = st ? pick_alg<4, true>(alg, mask_dim, fb) : pick_alg<4, false>(alg, mask_dim, fb); break;

@@ -72,6 +72,7 @@ struct __align__(16) ExactParams {
     int edge_remap;
     int group_dedup;      // learned decode: one evaluation per distinct texel of a tile group
     int fallback;         // over-budget tiles: 0 one-tap STF, 1 fallback C, 2 fallback C+
+    int tpl;              // texels a lane may evaluate: 1, or 2 (budget up to 64)
     const DecodeTables *tables;  // block decode tables in global memory (block textures)
     float4 *out;
     uint8_t *evals;       // nullable

@@ -22,7 +22,7 @@ enum { PATH_EMPTY = 0, PATH_SUCCESS = 1, PATH_FALLBACK_BUDGET = 2, PATH_FALLBACK
 struct ListTable {
     unsigned long long keys[256];
     unsigned char index[256];
-    unsigned long long list[32];
+    unsigned long long list[64];
 };
 constexpr unsigned long long kEmpty = ~0ull;
 
@@ -85,7 +85,10 @@ struct Selection {
     int n;           // texels the warp evaluates (success path)
     bool produce;    // this lane evaluates a texel
     int tx, ty;      // that texel (unclamped)
-    int src[4];      // success path: lane holding tap k = (k%2, k/2)
+    int src[4];      // success path: lane holding tap k = (k%2, k/2); with two
+                     // texels per lane, lane + 32 * round
+    bool produce2;   // two texels per lane: this lane evaluates a second texel
+    int tx2, ty2;    // that texel (unclamped)
     int rk[4];       // success path: index of tap k in the warp's texel list
     int my_rank;     // index of this lane's texel in that list (when produce)
     uint8_t count;   // texel evaluations of this lane
@@ -95,7 +98,9 @@ struct Selection {
 // algorithm.  `ps` holds the lane's setup (ps.active already decided).
 // `ranks` is a per-warp array of 32 ints in shared memory (Mask Sampling
 // passes texel coordinates through it); counters are kept when kStats.
-template <int ALG, int MD, bool kStats, bool kUnique = true>
+// kTwo: the variant that may evaluate two texels per lane (p.tpl == 2); the
+// other carries no code for it.
+template <int ALG, int MD, bool kStats, bool kUnique = true, bool kTwo = false>
 __device__ __forceinline__ Selection select_tile(const ExactParams &p, const PixelSetup &ps, const float4 jac,
                                                  int px, int py, int lane, uint32_t lt, ListTable *T, int *ranks,
                                                  Counters &cnt) {
@@ -109,6 +114,8 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
     sel.ty = ps.uly;
     sel.count = 0;  // sel.src and sel.rk are set on the success path only
     sel.my_rank = 0;
+    sel.produce2 = false;
+    sel.tx2 = sel.ty2 = 0;
     if (kStats) cnt.v[kStatTilesTotal] += 1;
     if (sel.A == 0) {
         sel.path = PATH_EMPTY;
@@ -198,7 +205,7 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                     if (inserted) {
                         const int index = base + __popc(newm & lt);
                         T->index[slot] = (unsigned char)index;
-                        if (index < 32) T->list[index] = key;
+                        if (index < 64) T->list[index] = key;
                     }
                     base += __popc(newm);
                     __syncwarp();
@@ -211,8 +218,9 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                 fits = !over;
             }
             if (fits) {
+                const int tpl = kTwo ? p.tpl : 1;
                 if (p.edge_remap) {
-                    fits = n <= nactive;
+                    fits = n <= tpl * nactive;
                 } else {
                     const uint32_t need = n >= 32 ? FULL : ((1u << n) - 1u);
                     fits = (A & need) == need;
@@ -257,6 +265,105 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
         const int dx0 = ps.ulx - minx, dy0 = ps.uly - miny;
         const int t00 = dy0 * bw + dx0, t01 = t00 + bw;  // box positions of taps (0,0) and (0,1)
         int j[4];  // lanes that hold taps k = (k%2, k/2)
+        if (kTwo && p.tpl == 2) {
+            // Up to two texels per lane (Sec. 5).  The counts follow the
+            // paper's assignment extended round-robin: texel i by active
+            // lane i mod na (edge remapping) or lane i mod 32, so lane a
+            // counts [a < n] + [a + na < n].  The arithmetic: index i (a box
+            // position, or a rank for the larger masks and List Merge) is
+            // evaluated by lane i mod 32 in round i div 32, and each tap is
+            // read from that lane and round.
+            const int na = p.edge_remap ? nactive : 32;
+            const int a = p.edge_remap ? (((A >> lane) & 1u) ? __popc(A & lt) : 64) : lane;
+            sel.count = (uint8_t)((a < n ? 1 : 0) + (a + na < n ? 1 : 0));
+            int pos0 = -1, pos1 = -1;  // box positions of this lane's texels (direct)
+            if (ALG == ALG_BOX || (ALG == ALG_MASK && mcls <= 2)) {
+                // a box of at most 64 texels: positions lane and lane + 32
+                j[0] = t00;
+                j[1] = t00 + 1;
+                j[2] = t01;
+                j[3] = t01 + 1;
+                if (ALG == ALG_BOX) {
+                    pos0 = lane < n ? lane : -1;
+                    pos1 = lane + 32 < n ? lane + 32 : -1;
+                } else {
+                    pos0 = ((Bw[0] >> lane) & 1u) ? lane : -1;
+                    pos1 = (mcls == 2 && ((Bw[1] >> lane) & 1u)) ? lane + 32 : -1;
+                }
+            } else if (ALG == ALG_MASK) {
+                // ranks: the pixels file the box position of each tap's rank
+                j[0] = mask_rank<NW>(Bw, pre, t00);
+                j[2] = mask_rank<NW>(Bw, pre, t01);
+                j[1] = j[0] + 1;
+                j[3] = j[2] + 1;
+                if (ps.active) {
+                    ranks[j[0]] = t00;
+                    ranks[j[1]] = t00 + 1;
+                    ranks[j[2]] = t01;
+                    ranks[j[3]] = t01 + 1;
+                }
+                __syncwarp();
+                pos0 = lane < n ? ranks[lane] : -1;
+                pos1 = lane + 32 < n ? ranks[lane + 32] : -1;
+                __syncwarp();
+            } else {  // List Merge: list indices of the taps, list order
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    j[k] = 0;
+                    if (ps.active) {
+                        const unsigned long long key =
+                            ((unsigned long long)(uint32_t)(dy0 + (k >> 1)) << 32) | (uint32_t)(dx0 + (k & 1));
+                        unsigned h = hash_key(key) & 255u;
+                        for (int probe = 0; probe < 256; ++probe) {
+                            const unsigned long long kk = T->keys[h];
+                            if (kk == key) {
+                                j[k] = T->index[h];
+                                break;
+                            }
+                            if (kk == kEmpty) break;
+                            h = (h + 1) & 255u;
+                        }
+                    }
+                }
+                if (lane < n) {
+                    const unsigned long long key = T->list[lane];
+                    sel.produce = true;
+                    sel.tx = minx + (int)(uint32_t)key;
+                    sel.ty = miny + (int)(uint32_t)(key >> 32);
+                }
+                if (lane + 32 < n) {
+                    const unsigned long long key = T->list[lane + 32];
+                    sel.produce2 = true;
+                    sel.tx2 = minx + (int)(uint32_t)key;
+                    sel.ty2 = miny + (int)(uint32_t)(key >> 32);
+                }
+            }
+            if (ALG != ALG_LIST) {
+                // box position -> texel (bw <= 16 for the masks: div_small
+                // holds; a Box row may be wider)
+                if (pos0 >= 0) {
+                    const int q = ALG == ALG_BOX ? pos0 / bw : div_small(pos0, bw);
+                    sel.produce = true;
+                    sel.tx = minx + (pos0 - q * bw);
+                    sel.ty = miny + q;
+                }
+                if (pos1 >= 0) {
+                    const int q = ALG == ALG_BOX ? pos1 / bw : div_small(pos1, bw);
+                    sel.produce2 = true;
+                    sel.tx2 = minx + (pos1 - q * bw);
+                    sel.ty2 = miny + q;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sel.src[k] = j[k];
+            if (ALG == ALG_LIST) {
+                __syncwarp();
+#pragma unroll
+                for (int s = 0; s < 8; ++s) T->keys[lane * 8 + s] = kEmpty;
+                __syncwarp();
+            }
+            return sel;
+        }
         if (ALG == ALG_BOX || (ALG == ALG_MASK && mcls == 1)) {
             // A box of at most 32 texels: lane L evaluates box position L
             // when it is in the set, so each tap is read from the lane of its

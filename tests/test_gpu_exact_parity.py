@@ -206,6 +206,36 @@ def test_fallback_c_and_cplus(frame, mixed, alg, fallback):
                           cpu_filter(mixed, uv, jac, cov, alg, seed=77, opts=opts))
 
 
+@pytest.mark.parametrize("alg", ["box", "mask", "list_merge"])
+def test_two_texels_per_lane(frame, mixed, alg):
+    """Up to two texels per lane (budget up to 64), alone and with fallback
+    C+, on the full view, on ragged frames with the option sets of the
+    ragged test, and on rotated head-on quads just above magnification 1,
+    where every 8x4 wave succeeds (Sec. 5)."""
+    tex, sc = frame
+    for opts in ({"texels_per_lane": 2, "budget": 64}, {"texels_per_lane": 2, "budget": 64, "mask_dim": 11},
+                 {"texels_per_lane": 2, "budget": 40, "fallback": 2}):
+        g = gpu_filter(tex, sc.uv, sc.jac, sc.coverage, alg, seed=3, opts=opts)
+        assert_parity(g, cpu_filter(tex, sc.uv, sc.jac, sc.coverage, alg, seed=3, opts=opts))
+    for W, H in ((133, 77), (17, 3), (250, 131)):
+        uv, jac, cov = _mixed_scene(W, H, seed=W * 1000 + H)
+        for opts in ({"texels_per_lane": 2, "budget": 64}, {"texels_per_lane": 2, "budget": 64, "edge_remap": 0},
+                     {"texels_per_lane": 2, "budget": 48, "mask_dim": 11},
+                     {"texels_per_lane": 2, "budget": 64, "tile_w": 16, "tile_h": 2, "fallback": 1}):
+            assert_parity(gpu_filter(mixed, uv, jac, cov, alg, seed=77, opts=opts),
+                          cpu_filter(mixed, uv, jac, cov, alg, seed=77, opts=opts))
+    q = synth.rotated_quad_tiles(1.001, np.arange(0, 91, 3.0), 40)
+    qt = Tex(synth.random_blocks(4096, 4096, seed=16), 4096, 4096)
+    try:
+        opts = {"texels_per_lane": 2, "budget": 64}
+        g = gpu_filter(qt, q.uv, q.jac, None, alg, opts=opts)
+        assert_parity(g, cpu_filter(qt, q.uv, q.jac, None, alg, opts=opts))
+        if alg != "box":
+            assert g[2]["tiles_success"] == g[2]["tiles_total"]
+    finally:
+        qt.close()
+
+
 def test_empty_and_uncovered(mixed):
     uv, jac, cov = _mixed_scene(40, 20, seed=1)
     z = np.zeros((20, 40), np.uint8)
