@@ -39,7 +39,8 @@ METRIC = "filtered pixels/s and texel evals/pixel, collaborative vs 4-tap on one
 HEADLINE = ("mask", {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 11, "edge_remap": 1})
 OTHERS = [("4tap", "4tap", {}), ("box", "box", {}), ("list_merge", "list_merge", {}),
           ("mask16", "mask", {"mask_dim": 16}),
-          ("mask11_fallback_c", "mask", {"fallback": 1}), ("mask11_fallback_cplus", "mask", {"fallback": 2})]
+          ("mask11_fallback_c", "mask", {"fallback": 1}), ("mask11_fallback_cplus", "mask", {"fallback": 2}),
+          ("mask11_two_texels_per_lane", "mask", {"texels_per_lane": 2, "budget": 64})]
 ALG_ID = {"4tap": 0, "stf": 1, "list_merge": 2, "box": 3, "mask": 4}
 FALLBACK_HBM_GBS = 6800.0
 
