@@ -381,6 +381,8 @@ typedef struct {
 
 static void group_note(group_set *G, const texel_source *src, int x, int y)
 {
+    if (!G)
+        return;
     int xc = x < 0 ? 0 : (x > src->Wt - 1 ? src->Wt - 1 : x);
     int yc = y < 0 ? 0 : (y > src->Ht - 1 ? src->Ht - 1 : y);
     for (int i = 0; i < G->n; ++i)
@@ -658,7 +660,7 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                     if (alg == ALG_STF) {
                         int tx, ty;
                         stf_lane(src, p, view, seed, fp64, out, outd, evals, idx, &tx, &ty);
-                        group_note(&G, src, tx, ty);
+                        group_note(grouped ? &G : NULL, src, tx, ty);
                     } else {
                         float w[4], pv[4][4], o[4];
                         double pd[4][4], od[4];
@@ -783,7 +785,7 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                 if (path == PATH_FALLBACK_MINIFIED) st.tiles_fallback_minified++;
                 else st.tiles_fallback_budget++;
                 if (path == PATH_FALLBACK_BUDGET && fallback) {
-                    fallback_c(src, lane, A, fallback, view, seed, fp64, W, out, outd, evals, &G);
+                    fallback_c(src, lane, A, fallback, view, seed, fp64, W, out, outd, evals, grouped ? &G : NULL);
                     continue;
                 }
                 for (int l = 0; l < 32; ++l) {
@@ -791,7 +793,7 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                     size_t idx = (size_t)lane[l].py * W + lane[l].px;
                     int tx, ty;
                     stf_lane(src, &lane[l], view, seed, fp64, out, outd, evals, idx, &tx, &ty);
-                    group_note(&G, src, tx, ty);
+                    group_note(grouped ? &G : NULL, src, tx, ty);
                 }
                 continue;
             }
@@ -806,7 +808,7 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                 size_t idx = (size_t)p->py * W + p->px;
                 fetch_texel(src, L.x[i], L.y[i], valf[i], vald[i]);
                 evals[idx]++;
-                group_note(&G, src, L.x[i], L.y[i]);
+                group_note(grouped ? &G : NULL, src, L.x[i], L.y[i]);
             }
             /* Step 3: every active lane gathers its four taps and filters. */
             for (int l = 0; l < 32; ++l) {
