@@ -285,26 +285,6 @@ static void bilinear_weights(float s, float t, float w[4])
     w[3] = s * t;
 }
 
-/* Filter of Sec. 3 step 3: acc = 0; acc = fma(w_k, p_k, acc) for k = 0..3.
- * FP32 mode uses fmaf; FP64 mode accumulates in double. */
-static void filter4(const float w[4], float p[4][4], double pd[4][4], int fp64, float out[4], double outd[4])
-{
-    for (int ch = 0; ch < 4; ++ch) {
-        if (!fp64) {
-            float acc = 0.0f;
-            for (int k = 0; k < 4; ++k)
-                acc = fmaf(w[k], p[k][ch], acc);
-            out[ch] = acc;
-            outd[ch] = (double)acc;
-        } else {
-            double acc = 0.0;
-            for (int k = 0; k < 4; ++k)
-                acc += (double)w[k] * pd[k][ch];
-            outd[ch] = acc;
-            out[ch] = (float)acc;
-        }
-    }
-}
 
 /* One-tap STF texel choice: Philox4x32-10 with counter (px, py, view, 0) and
  * key (seed low, seed high); xi = (r >> 8) * 2^-24; the right neighbour is
@@ -323,6 +303,86 @@ void oracle_stf_offset(int px, int py, int view, uint64_t seed, float s, float t
     *dy = xi1 < t ? 1 : 0;
 }
 
+/*
+ * Bicubic filters (Sec. 4.2): the 4x4 texels from one left of and above the
+ * upper-left texel of the bilinear footprint, separable weights w_x(s) w_y(t)
+ * with s, t the same fractions.  Cubic B-spline:
+ *   ((1-f)^3, 3f^3 - 6f^2 + 4, -3f^3 + 3f^2 + 3f + 1, f^3) / 6;
+ * Catmull-Rom (cubic convolution, a = -1/2):
+ *   (2f^2 - f^3 - f, 3f^3 - 5f^2 + 2, -3f^3 + 4f^2 + f, f^3 - f^2) / 2;
+ * each term a single round-to-nearest FP32 operation in the order written.
+ */
+enum { FILTER_BILINEAR = 0, FILTER_BSPLINE = 1, FILTER_CATMULL_ROM = 2 };
+
+static int filter_side(int filter) { return filter == FILTER_BILINEAR ? 2 : 4; }
+
+static void cubic_weights(int filter, float f, float w[4])
+{
+    float f2 = f * f, f3 = f2 * f;
+    if (filter == FILTER_BSPLINE) {
+        float u = 1.0f - f;
+        w[0] = ((u * u) * u) / 6.0f;
+        w[1] = ((3.0f * f3 - 6.0f * f2) + 4.0f) / 6.0f;
+        w[2] = (((-3.0f * f3 + 3.0f * f2) + 3.0f * f) + 1.0f) / 6.0f;
+        w[3] = f3 / 6.0f;
+    } else {
+        w[0] = 0.5f * ((2.0f * f2 - f3) - f);
+        w[1] = 0.5f * ((3.0f * f3 - 5.0f * f2) + 2.0f);
+        w[2] = 0.5f * ((-3.0f * f3 + 4.0f * f2) + f);
+        w[3] = 0.5f * (f3 - f2);
+    }
+}
+
+/* Weights of the F x F taps k = j F + i (tap (ox + i, oy + j)); returns F*F. */
+static int filter_weights(int filter, float s, float t, float *w)
+{
+    if (filter == FILTER_BILINEAR) {
+        bilinear_weights(s, t, w);
+        return 4;
+    }
+    float wx[4], wy[4];
+    cubic_weights(filter, s, wx);
+    cubic_weights(filter, t, wy);
+    for (int j = 0; j < 4; ++j)
+        for (int i = 0; i < 4; ++i)
+            w[4 * j + i] = wx[i] * wy[j];
+    return 16;
+}
+
+/* acc = fma(w_k, p_k, acc) from 0 over the n taps in order (FP32), or the
+ * weighted sum in double. */
+static void filter_n(int n, const float *w, float p[][4], double pd[][4], int fp64, float out[4], double outd[4])
+{
+    for (int ch = 0; ch < 4; ++ch) {
+        if (!fp64) {
+            float acc = 0.0f;
+            for (int k = 0; k < n; ++k)
+                acc = fmaf(w[k], p[k][ch], acc);
+            out[ch] = acc;
+            outd[ch] = (double)acc;
+        } else {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k)
+                acc += (double)w[k] * pd[k][ch];
+            outd[ch] = acc;
+            out[ch] = (float)acc;
+        }
+    }
+}
+
+/* One tap of 4 drawn with probability |w_i| / sum |w| by xi in [0, 1):
+ * cumulative sums c in tap order, the first i with xi * S < c_i.  *g is
+ * S with the sign of w_i. */
+static int pick_tap(const float w[4], float xi, float *g)
+{
+    float a0 = fabsf(w[0]), a1 = fabsf(w[1]), a2 = fabsf(w[2]), a3 = fabsf(w[3]);
+    float c0 = a0, c1 = c0 + a1, c2 = c1 + a2, S = c2 + a3;
+    float tsel = xi * S;
+    int i = tsel < c0 ? 0 : (tsel < c1 ? 1 : (tsel < c2 ? 2 : 3));
+    *g = w[i] < 0.0f ? -S : S;
+    return i;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithms and per-tile outcome codes (shared numbering with the public  */
 /* interface; the numbers are the only thing the two sides agree on).       */
@@ -336,28 +396,57 @@ typedef struct {
     int64_t pixels_active, texel_evals;
 } oracle_stats;
 
-/* Output for one active lane on the STF path: its own STF texel, count 1. */
-static void stf_lane(const texel_source *src, const pixel_setup *p, int view, uint64_t seed, int fp64,
-                     float *out, double *outd, uint8_t *evals, size_t idx, int *tx, int *ty)
+/* Output for one active lane on the STF path: its own STF texel, count 1.
+ * Bilinear: the separable Bernoulli draw.  Bicubic: per axis the tap drawn
+ * with probability |w| / sum |w| (pick_tap, xi0 for x and xi1 for y of the
+ * same Philox draw); the B-spline returns the texel, Catmull-Rom the texel
+ * times sign(w_x) S_x times sign(w_y) S_y (one-sample estimate of the
+ * filter with negative lobes; positivization would need two texels). */
+static void stf_lane(const texel_source *src, const pixel_setup *p, int filter, int view, uint64_t seed,
+                     int fp64, float *out, double *outd, uint8_t *evals, size_t idx, int *tx, int *ty)
 {
-    int dx, dy;
-    oracle_stf_offset(p->px, p->py, view, seed, p->s, p->t, &dx, &dy);
+    float gx = 1.0f, gy = 1.0f;
+    if (filter == FILTER_BILINEAR) {
+        int dx, dy;
+        oracle_stf_offset(p->px, p->py, view, seed, p->s, p->t, &dx, &dy);
+        *tx = p->ulx + dx;
+        *ty = p->uly + dy;
+    } else {
+        uint32_t ctr[4] = {(uint32_t)p->px, (uint32_t)p->py, (uint32_t)view, 0u};
+        uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+        uint32_t r[4];
+        oracle_philox4x32_10(ctr, key, r);
+        float wx[4], wy[4];
+        cubic_weights(filter, p->s, wx);
+        cubic_weights(filter, p->t, wy);
+        int i = pick_tap(wx, (float)(r[0] >> 8) * 0x1p-24f, &gx);
+        int j = pick_tap(wy, (float)(r[1] >> 8) * 0x1p-24f, &gy);
+        *tx = p->ulx - 1 + i;
+        *ty = p->uly - 1 + j;
+    }
     float vf[4];
     double vd[4];
-    *tx = p->ulx + dx;
-    *ty = p->uly + dy;
-    fetch_texel(src, p->ulx + dx, p->uly + dy, vf, vd);
+    fetch_texel(src, *tx, *ty, vf, vd);
+    const int scale = filter == FILTER_CATMULL_ROM;
     for (int ch = 0; ch < 4; ++ch) {
-        if (out) out[4 * idx + ch] = fp64 ? (float)vd[ch] : vf[ch];
-        if (outd) outd[4 * idx + ch] = fp64 ? vd[ch] : (double)vf[ch];
+        float of = fp64 ? (float)vd[ch] : vf[ch];
+        double od = fp64 ? vd[ch] : (double)vf[ch];
+        if (scale) {
+            of = (vf[ch] * gx) * gy;
+            od = fp64 ? (vd[ch] * (double)gx) * (double)gy : (double)of;
+            if (fp64) of = (float)od;
+        }
+        if (out) out[4 * idx + ch] = of;
+        if (outd) outd[4 * idx + ch] = od;
     }
     evals[idx] = 1;
 }
 
-/* Set of unique texel coordinates, kept in insertion order. */
+/* Set of unique texel coordinates, kept in insertion order (a wave's 4x4
+ * footprints hold at most 32 x 16 texels). */
 typedef struct {
     int n;
-    int x[128], y[128];
+    int x[512], y[512];
 } texel_list;
 
 static int list_find(const texel_list *L, int x, int y)
@@ -572,6 +661,9 @@ static void fallback_c(const texel_source *src, const pixel_setup *lane, uint32_
  *   out  [H][W][4] float (FP32 result; may be NULL), outd [H][W][4] double (may be NULL)
  *   evals[H][W] uint8 per-pixel texel evaluations
  *   tile_path / tile_n: per tile outcome code and texel-set size (may be NULL)
+ *   filter         0 bilinear (2x2), 1 cubic B-spline, 2 Catmull-Rom (4x4,
+ *                  Sec. 4.2); the bicubic ones with one texel per lane and
+ *                  the one-tap STF fallback only
  *   tpl            texels a lane may produce, 1 or 2 (Sec. 5: "more than
  *                  one texel per lane"); budget up to 32 * tpl
  *   fallback       0: over-budget tiles take one-tap STF; 1: fallback C;
@@ -588,11 +680,14 @@ static void fallback_c(const texel_source *src, const pixel_setup *lane, uint32_
 static int oracle_filter_ex(const texel_source *src, const float *uv, const float *jac, const uint8_t *cov,
                             int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h,
                             int budget, int mask_dim, int edge_remap, int group_tiles, int fallback, int tpl,
-                            int fp64, float *out, double *outd, uint8_t *evals, int32_t *tile_path,
-                            int32_t *tile_n, int64_t *stats_out)
+                            int filter, int fp64, float *out, double *outd, uint8_t *evals,
+                            int32_t *tile_path, int32_t *tile_n, int64_t *stats_out)
 {
     if (tpl != 1 && tpl != 2)
         return -1;
+    if (filter < 0 || filter > 2 || (filter != FILTER_BILINEAR && (fallback != 0 || tpl != 1)))
+        return -1;
+    const int F = filter_side(filter), off = F == 4 ? 1 : 0;
     if (fallback < 0 || fallback > 2)
         return -1;
     if (W < 0 || H < 0 || tile_w <= 0 || tile_h <= 0 || tile_w * tile_h != 32)
@@ -659,25 +754,25 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                     size_t idx = (size_t)p->py * W + p->px;
                     if (alg == ALG_STF) {
                         int tx, ty;
-                        stf_lane(src, p, view, seed, fp64, out, outd, evals, idx, &tx, &ty);
+                        stf_lane(src, p, filter, view, seed, fp64, out, outd, evals, idx, &tx, &ty);
                         group_note(grouped ? &G : NULL, src, tx, ty);
                     } else {
-                        float w[4], pv[4][4], o[4];
-                        double pd[4][4], od[4];
-                        bilinear_weights(p->s, p->t, w);
-                        for (int k = 0; k < 4; ++k)
-                            fetch_texel(src, p->ulx + k % 2, p->uly + k / 2, pv[k], pd[k]);
-                        filter4(w, pv, pd, fp64, o, od);
+                        float w[16], pv[16][4], o[4];
+                        double pd[16][4], od[4];
+                        const int nt = filter_weights(filter, p->s, p->t, w);
+                        for (int k = 0; k < nt; ++k)
+                            fetch_texel(src, p->ulx - off + k % F, p->uly - off + k / F, pv[k], pd[k]);
+                        filter_n(nt, w, pv, pd, fp64, o, od);
                         for (int ch = 0; ch < 4; ++ch) {
                             if (out) out[4 * idx + ch] = o[ch];
                             if (outd) outd[4 * idx + ch] = od[ch];
                         }
-                        evals[idx] = 4;
+                        evals[idx] = (uint8_t)nt;
                     }
                 }
                 st.tiles_direct++;
                 if (tile_path) tile_path[tile_id] = path;
-                if (tile_n) tile_n[tile_id] = alg == ALG_STF ? nactive : 4 * nactive;
+                if (tile_n) tile_n[tile_id] = alg == ALG_STF ? nactive : F * F * nactive;
                 continue;
             }
 
@@ -695,11 +790,11 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                 int minx = 0, miny = 0, maxx = 0, maxy = 0, first = 1;
                 for (int l = 0; l < 32; ++l) {
                     if (!lane[l].active) continue;
-                    int ux = lane[l].ulx, uy = lane[l].uly;
+                    int ux = lane[l].ulx - off, uy = lane[l].uly - off;
                     if (first || ux < minx) minx = ux;
                     if (first || uy < miny) miny = uy;
-                    if (first || ux + 1 > maxx) maxx = ux + 1;
-                    if (first || uy + 1 > maxy) maxy = uy + 1;
+                    if (first || ux + F - 1 > maxx) maxx = ux + F - 1;
+                    if (first || uy + F - 1 > maxy) maxy = uy + F - 1;
                     first = 0;
                 }
                 int64_t bw = (int64_t)maxx - minx + 1, bh = (int64_t)maxy - miny + 1;
@@ -728,9 +823,9 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                         int nwords = (M * M + 31) / 32;
                         for (int l = 0; l < 32; ++l) {
                             if (!lane[l].active) continue;
-                            int dx = lane[l].ulx - minx, dy = lane[l].uly - miny;
-                            for (int k = 0; k < 4; ++k) {
-                                int tb = (dy + k / 2) * M + (dx + k % 2);
+                            int dx = lane[l].ulx - off - minx, dy = lane[l].uly - off - miny;
+                            for (int k = 0; k < F * F; ++k) {
+                                int tb = (dy + k / F) * M + (dx + k % F);
                                 B[tb / 32] |= 1u << (tb % 32);
                             }
                         }
@@ -749,8 +844,8 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                 } else { /* ALG_LIST_MERGE: the exact set union of all 2x2 lists. */
                     for (int l = 0; l < 32; ++l) {
                         if (!lane[l].active) continue;
-                        for (int k = 0; k < 4; ++k) {
-                            int x = lane[l].ulx + k % 2, y = lane[l].uly + k / 2;
+                        for (int k = 0; k < F * F; ++k) {
+                            int x = lane[l].ulx - off + k % F, y = lane[l].uly - off + k / F;
                             if (list_find(&L, x, y) < 0) {
                                 L.x[L.n] = x;
                                 L.y[L.n] = y;
@@ -792,7 +887,7 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                     if (!lane[l].active) continue;
                     size_t idx = (size_t)lane[l].py * W + lane[l].px;
                     int tx, ty;
-                    stf_lane(src, &lane[l], view, seed, fp64, out, outd, evals, idx, &tx, &ty);
+                    stf_lane(src, &lane[l], filter, view, seed, fp64, out, outd, evals, idx, &tx, &ty);
                     group_note(grouped ? &G : NULL, src, tx, ty);
                 }
                 continue;
@@ -810,16 +905,16 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                 evals[idx]++;
                 group_note(grouped ? &G : NULL, src, L.x[i], L.y[i]);
             }
-            /* Step 3: every active lane gathers its four taps and filters. */
+            /* Step 3: every active lane gathers its F x F taps and filters. */
             for (int l = 0; l < 32; ++l) {
                 if (!lane[l].active) continue;
                 const pixel_setup *p = &lane[l];
                 size_t idx = (size_t)p->py * W + p->px;
-                float w[4], pv[4][4], o[4];
-                double pd[4][4], od[4];
-                bilinear_weights(p->s, p->t, w);
-                for (int k = 0; k < 4; ++k) {
-                    int j = list_find(&L, p->ulx + k % 2, p->uly + k / 2);
+                float w[16], pv[16][4], o[4];
+                double pd[16][4], od[4];
+                const int nt = filter_weights(filter, p->s, p->t, w);
+                for (int k = 0; k < nt; ++k) {
+                    int j = list_find(&L, p->ulx - off + k % F, p->uly - off + k / F);
                     if (j < 0)
                         return -2; /* cannot happen: the set covers every tap */
                     for (int ch = 0; ch < 4; ++ch) {
@@ -827,7 +922,7 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
                         pd[k][ch] = vald[j][ch];
                     }
                 }
-                filter4(w, pv, pd, fp64, o, od);
+                filter_n(nt, w, pv, pd, fp64, o, od);
                 for (int ch = 0; ch < 4; ++ch) {
                     if (out) out[4 * idx + ch] = o[ch];
                     if (outd) outd[4 * idx + ch] = od[ch];
@@ -859,28 +954,28 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
 /* Exact block decode, FP32 arithmetic with the rounding described above. */
 int oracle_filter(const uint8_t *blocks, int Wt, int Ht, const float *uv, const float *jac, const uint8_t *cov,
                   int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h, int budget,
-                  int mask_dim, int edge_remap, int group_tiles, int fallback, int tpl, float *out,
+                  int mask_dim, int edge_remap, int group_tiles, int fallback, int tpl, int filter, float *out,
                   uint8_t *evals, int32_t *tile_path, int32_t *tile_n, int64_t *stats)
 {
     if (Wt <= 0 || Ht <= 0 || Wt % 4 || Ht % 4 || !blocks)
         return -1;
     texel_source src = {0, Wt, Ht, blocks, NULL};
     return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
-                            edge_remap, group_tiles, fallback, tpl, 0, out, NULL, evals, tile_path, tile_n,
-                            stats);
+                            edge_remap, group_tiles, fallback, tpl, filter, 0, out, NULL, evals, tile_path,
+                            tile_n, stats);
 }
 
 /* Learned decode: texel values from the FP64 MLP, filter in double. */
 int oracle_filter_learned_f64(const void *mlp, int Wt, int Ht, const float *uv, const float *jac,
                               const uint8_t *cov, int W, int H, int view, int alg, uint64_t seed, int tile_w,
                               int tile_h, int budget, int mask_dim, int edge_remap, int group_tiles,
-                              int fallback, int tpl, double *outd, uint8_t *evals, int32_t *tile_path,
-                              int32_t *tile_n, int64_t *stats)
+                              int fallback, int tpl, int filter, double *outd, uint8_t *evals,
+                              int32_t *tile_path, int32_t *tile_n, int64_t *stats)
 {
     if (Wt <= 0 || Ht <= 0 || !mlp)
         return -1;
     texel_source src = {1, Wt, Ht, NULL, mlp};
     return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
-                            edge_remap, group_tiles, fallback, tpl, 1, NULL, outd, evals, tile_path, tile_n,
-                            stats);
+                            edge_remap, group_tiles, fallback, tpl, filter, 1, NULL, outd, evals, tile_path,
+                            tile_n, stats);
 }

@@ -128,6 +128,55 @@ def test_4tap_matches_scipy_bilinear(oracle_lib, Wt, Ht):
         np.testing.assert_allclose(out[..., ch], ref, rtol=0, atol=2e-6)
 
 
+def test_bspline_matches_scipy(oracle_lib):
+    """Per-pixel bicubic with the cubic B-spline (Sec. 4.2) is scipy's order-3
+    B-spline applied to the texel samples without prefiltering, clamped to
+    the edge, at the same FP32 texel coordinates."""
+    from scipy.ndimage import map_coordinates
+    o = oracle_lib
+    Wt, Ht = 32, 16
+    blocks = synth.random_blocks(Wt, Ht, seed=12)
+    img = _decoded_image(o, blocks, Wt, Ht)
+    g = np.random.default_rng(4)
+    W, H = 24, 12
+    uv = g.uniform(-0.2, 1.2, (H, W, 2)).astype(np.float32)
+    jac = np.zeros((H, W, 4), np.float32)
+    out, ev, st = o.filter_frame(blocks, Wt, Ht, uv, jac, alg=o.ALG_4TAP, filter=o.FILTER_BSPLINE)
+    assert np.all(ev == 16)
+    xf = (uv[..., 0] * np.float32(Wt)) - np.float32(0.5)
+    yf = (uv[..., 1] * np.float32(Ht)) - np.float32(0.5)
+    for ch in range(4):
+        ref = map_coordinates(img[..., ch], [yf.astype(np.float64).ravel(), xf.astype(np.float64).ravel()],
+                              order=3, mode="nearest", prefilter=False).reshape(H, W)
+        np.testing.assert_allclose(out[..., ch], ref, rtol=0, atol=4e-6)
+
+
+def test_catmull_rom_closed_forms(oracle_lib):
+    """Catmull-Rom interpolates: at texel centres (s = t = 0) the output is
+    the texel itself, bitwise; halfway between centres its weights per axis
+    are (-1, 9, 9, -1) / 16, so the output is that dyadic blend of the 4x4
+    texels (exact rational arithmetic here)."""
+    from fractions import Fraction
+    o = oracle_lib
+    Wt = Ht = 16
+    blocks = synth.random_blocks(Wt, Ht, seed=21)
+    img = _decoded_image(o, blocks, Wt, Ht)
+    xs, ys = np.meshgrid(np.arange(3, 12), np.arange(3, 12))
+    uv = np.stack([(xs + 0.5) / Wt, (ys + 0.5) / Ht], axis=-1).astype(np.float32)
+    jac = np.zeros(uv.shape[:2] + (4,), np.float32)
+    out = o.filter_frame(blocks, Wt, Ht, uv, jac, alg=o.ALG_4TAP, filter=o.FILTER_CATMULL_ROM)[0]
+    assert np.array_equal(out.view(np.uint32), img[ys, xs].astype(np.float32).view(np.uint32))
+    uv = np.stack([(xs + 1.0) / Wt, (ys + 1.0) / Ht], axis=-1).astype(np.float32)
+    out = o.filter_frame(blocks, Wt, Ht, uv, jac, alg=o.ALG_4TAP, filter=o.FILTER_CATMULL_ROM)[0]
+    wv = [Fraction(-1, 16), Fraction(9, 16), Fraction(9, 16), Fraction(-1, 16)]
+    dec = [[[Fraction(int(v), 255) for v in o.decode_rgba8(blocks, Wt, Ht, x, y)] for x in range(Wt)]
+           for y in range(Ht)]
+    for (y, x) in [(3, 3), (5, 8), (10, 11), (7, 4)]:
+        for ch in range(4):
+            exact = sum(wv[i] * wv[j] * dec[y - 1 + j][x - 1 + i][ch] for i in range(4) for j in range(4))
+            assert abs(float(exact) - float(out[y - 3, x - 3, ch])) <= 3e-7, (y, x, ch)
+
+
 def test_4tap_closed_form_at_texel_centres_and_midpoints(oracle_lib):
     """s,t = 0 returns the texel itself; s,t = 1/2 returns the mean of the 2x2."""
     Wt = Ht = 16
@@ -520,6 +569,65 @@ def test_stf_mean_converges_to_bilinear(oracle_lib):
     var = np.maximum(acc2 / S - mean ** 2, 0)
     bound = 4.5 * np.sqrt(var / S) + 2.0 ** -22
     assert np.all(np.abs(mean - ref) <= bound)
+
+
+@pytest.mark.parametrize("flt", ["bspline", "catmull_rom"])
+def test_bicubic_stf_mean_converges(oracle_lib, flt):
+    """One-tap STF for the bicubic filters draws a tap per axis with
+    probability |w| / sum |w|; the B-spline returns the texel and Catmull-Rom
+    the texel times the signed sums, so the mean over seeds converges to the
+    filter, negative lobes included."""
+    o = oracle_lib
+    f = {"bspline": o.FILTER_BSPLINE, "catmull_rom": o.FILTER_CATMULL_ROM}[flt]
+    Wt = Ht = 16
+    blocks = synth.random_blocks(Wt, Ht, seed=19)
+    g = np.random.default_rng(6)
+    W, H = 8, 4
+    uv = g.uniform(0.2, 0.8, (H, W, 2)).astype(np.float32)
+    jac = np.zeros((H, W, 4), np.float32)
+    ref, _, _ = o.filter_frame(blocks, Wt, Ht, uv, jac, alg=o.ALG_4TAP, filter=f)
+    S = 4096
+    acc = np.zeros_like(ref, dtype=np.float64)
+    acc2 = np.zeros_like(acc)
+    for seed in range(S):
+        out, ev, _ = o.filter_frame(blocks, Wt, Ht, uv, jac, alg=o.ALG_STF, filter=f,
+                                    seed=seed * 0x9E3779B97F4A7C15 % 2**64)
+        assert np.all(ev == 1)
+        acc += out
+        acc2 += out.astype(np.float64) ** 2
+    mean = acc / S
+    var = np.maximum(acc2 / S - mean ** 2, 0)
+    assert np.all(np.abs(mean - ref) <= 4.5 * np.sqrt(var / S) + 2.0 ** -20)
+
+
+@pytest.mark.parametrize("flt", ["bspline", "catmull_rom"])
+def test_bicubic_success_reproduces_per_pixel_bitwise(oracle_lib, flt):
+    """Sec. 4.2: the same algorithms serve any discrete filter; a bicubic
+    success tile equals the per-pixel 16-tap filter bitwise, Mask-16 and List
+    Merge agree on n whenever the box fits, and the first n active lanes
+    count 1."""
+    o = oracle_lib
+    f = {"bspline": o.FILTER_BSPLINE, "catmull_rom": o.FILTER_CATMULL_ROM}[flt]
+    blocks = synth.random_blocks(64, 64, seed=13)
+    uv, jac, cov = _scene_mix(seed=4)
+    ref = o.filter_frame(blocks, 64, 64, uv, jac, cov, alg=o.ALG_4TAP, filter=f)[0]
+    res = {}
+    for name, a in (("box", o.ALG_BOX), ("mask", o.ALG_MASK), ("list", o.ALG_LIST_MERGE)):
+        out, ev, st, tp, tn = o.filter_frame(blocks, 64, 64, uv, jac, cov, alg=a, filter=f, want_tiles=True)
+        res[name] = (tp, tn)
+        tiles_x = 96 // 8
+        succ = np.nonzero(tp == o.PATH_SUCCESS)[0]
+        assert succ.size > 10, name
+        for tid in succ:
+            ty, tx = divmod(int(tid), tiles_x)
+            sl = (slice(ty * 4, ty * 4 + 4), slice(tx * 8, tx * 8 + 8))
+            assert np.array_equal(out[sl].view(np.uint32), ref[sl].view(np.uint32))
+            act = cov[sl].ravel() != 0
+            expect = np.zeros(32, np.uint8)
+            expect[np.nonzero(act)[0][:int(tn[tid])]] = 1
+            np.testing.assert_array_equal(ev[sl].ravel(), expect)
+    fit = res["mask"][1] >= 0
+    np.testing.assert_array_equal(res["mask"][1][fit], res["list"][1][fit])
 
 
 def test_stf_choice_frequencies_equal_weights(oracle_lib):
