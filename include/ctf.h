@@ -133,7 +133,15 @@ typedef struct {
  *                   h(i mod na, A) (or lane i mod 32 without edge
  *                   remapping), whose count becomes 2 when it has two;
  *                   success needs n <= 2 popcount(A).  Block textures only
- *                   (CTF_ERR_UNSUPPORTED for learned ones)        [1] */
+ *                   (CTF_ERR_UNSUPPORTED for learned ones)        [1]
+ *   filter          0 bilinear (2x2 footprint); 1 cubic B-spline, 2
+ *                   Catmull-Rom (4x4 footprint, Sec. 4.2: the same
+ *                   algorithms with the footprint, weights and mask bits of
+ *                   the larger filter; one-tap STF draws a tap per axis by
+ *                   |w|, scaled by the signed sums for Catmull-Rom's
+ *                   negative lobes).  The bicubic filters take one texel per
+ *                   lane and the STF fallback, block textures, single views
+ *                   (CTF_ERR_UNSUPPORTED otherwise)            [0] */
 typedef struct {
     int tile_w, tile_h;
     int budget;
@@ -142,6 +150,7 @@ typedef struct {
     int group_dedup;
     int fallback;
     int texels_per_lane;
+    int filter;
 } ctf_filter_opts;
 
 /* Per-call counters (filled only when a stats pointer is given). */

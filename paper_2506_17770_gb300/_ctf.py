@@ -36,7 +36,7 @@ class ctf_texture_desc(ctypes.Structure):
 class ctf_filter_opts(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("budget", ctypes.c_int),
                 ("mask_dim", ctypes.c_int), ("edge_remap", ctypes.c_int), ("group_dedup", ctypes.c_int),
-                ("fallback", ctypes.c_int), ("texels_per_lane", ctypes.c_int)]
+                ("fallback", ctypes.c_int), ("texels_per_lane", ctypes.c_int), ("filter", ctypes.c_int)]
 
 
 class ctf_stats(ctypes.Structure):
@@ -163,7 +163,7 @@ def _opts(opts):
     if opts is None or isinstance(opts, ctf_filter_opts):
         return opts
     d = {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 16, "edge_remap": 1, "group_dedup": 0, "fallback": 0,
-         "texels_per_lane": 1}
+         "texels_per_lane": 1, "filter": 0}
     d.update(opts)
     return ctf_filter_opts(**d)
 

@@ -95,6 +95,7 @@ int scratch_stage(size_t bytes, void **out) {
 struct ResolvedOpts {
     int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1, group_dedup = 0, fallback = 0;
     int tpl = 1;
+    int filter = 0;
 };
 
 int resolve_opts(const ctf_filter_opts *o, ResolvedOpts *r) {
@@ -108,12 +109,16 @@ int resolve_opts(const ctf_filter_opts *o, ResolvedOpts *r) {
     r->group_dedup = o->group_dedup;
     r->fallback = o->fallback;
     r->tpl = o->texels_per_lane == 0 ? 1 : o->texels_per_lane;
+    r->filter = o->filter;
     const bool shape_ok = (r->tile_w == 8 && r->tile_h == 4) || (r->tile_w == 4 && r->tile_h == 8) ||
                           (r->tile_w == 16 && r->tile_h == 2);
     if (!shape_ok) return fail(CTF_ERR_ARG, "tile %dx%d not one of 8x4, 4x8, 16x2", r->tile_w, r->tile_h);
     if (r->group_dedup != 0 && r->group_dedup != 1) return fail(CTF_ERR_ARG, "group_dedup must be 0 or 1");
     if (r->fallback < 0 || r->fallback > 2) return fail(CTF_ERR_ARG, "fallback %d not 0 (STF), 1 (C) or 2 (C+)", r->fallback);
     if (r->tpl != 1 && r->tpl != 2) return fail(CTF_ERR_ARG, "texels_per_lane %d not 0, 1 or 2", r->tpl);
+    if (r->filter < 0 || r->filter > 2) return fail(CTF_ERR_ARG, "filter %d not 0, 1 or 2", r->filter);
+    if (r->filter != 0 && (r->tpl != 1 || r->fallback != 0))
+        return fail(CTF_ERR_UNSUPPORTED, "the bicubic filters take one texel per lane and the STF fallback");
     if (r->budget < 1 || r->budget > 32 * r->tpl)
         return fail(CTF_ERR_ARG, "budget %d outside [1, %d]", r->budget, 32 * r->tpl);
     if (r->mask_dim != 16 && r->mask_dim != 11) return fail(CTF_ERR_ARG, "mask_dim %d not 16 or 11", r->mask_dim);
@@ -135,8 +140,9 @@ int validate_filter_args(ctf_texture tex, const float *uv, const float *jac, int
     if ((int)alg < CTF_ALG_4TAP || (int)alg > CTF_ALG_MASK) return fail(CTF_ERR_ARG, "unknown algorithm %d", (int)alg);
     rc = resolve_opts(opts, ro);
     if (rc) return rc;
-    if ((ro->fallback != 0 || ro->tpl != 1) && tex->mode != CTF_EVAL_BLOCK)
-        return fail(CTF_ERR_UNSUPPORTED, "fallbacks C and C+ and two texels per lane are built for block textures only");
+    if ((ro->fallback != 0 || ro->tpl != 1 || ro->filter != 0) && tex->mode != CTF_EVAL_BLOCK)
+        return fail(CTF_ERR_UNSUPPORTED,
+                    "fallbacks C and C+, two texels per lane and the bicubic filters are built for block textures only");
     if ((size_t)width * (size_t)height == 0) return CTF_OK;
     if (!uv || !jac || !out) return fail(CTF_ERR_ARG, "uv, jac and out_rgba must not be NULL");
     if (!aligned(uv, 8)) return fail(CTF_ERR_ALIGN, "uv must be 8-byte aligned");
@@ -174,7 +180,9 @@ int run_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t
     p.evals = evals;
     p.stats = dstats;
     cudaError_t e;
-    if (tex->mode == CTF_EVAL_BLOCK) {
+    if (tex->mode == CTF_EVAL_BLOCK && ro.filter != 0) {
+        e = ctf::launch_bicubic_filter(p, (int)alg, ro.tile_w, ro.mask_dim, ro.filter, stream);
+    } else if (tex->mode == CTF_EVAL_BLOCK) {
         e = ctf::launch_exact_filter(p, (int)alg, ro.tile_w, ro.mask_dim, stream);
     } else {
         int *err = nullptr;

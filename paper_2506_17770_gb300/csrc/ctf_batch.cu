@@ -337,6 +337,7 @@ int resolve(const ctf_batch_opts *o, ResolvedBatch *r) {
     r->group_dedup = o->filter.group_dedup;
     r->fallback = o->filter.fallback;
     r->tpl = o->filter.texels_per_lane == 0 ? 1 : o->filter.texels_per_lane;
+    if (o->filter.filter != 0) return report(CTF_ERR_UNSUPPORTED, "batches take the bilinear filter only");
     r->items_per_fetch = o->items_per_fetch;
     r->ctas_per_sm = o->ctas_per_sm;
     const bool shape_ok = (r->tile_w == 8 && r->tile_h == 4) || (r->tile_w == 4 && r->tile_h == 8) ||
@@ -651,6 +652,7 @@ int ctf_batch_autotune(const ctf_view *views, int nviews, ctf_algorithm alg, uin
         b0.filter.group_dedup = 0;
         b0.filter.fallback = 0;
         b0.filter.texels_per_lane = 1;
+        b0.filter.filter = 0;
         b0.items_per_fetch = 4;
         b0.ctas_per_sm = 4;
     }

@@ -83,6 +83,11 @@ struct __align__(16) ExactParams {
 // mask_dim in {11, 16}.  Returns cudaSuccess or the launch error.
 cudaError_t launch_exact_filter(const ExactParams &p, int alg, int tile_w, int mask_dim, cudaStream_t stream);
 
+// The same with a bicubic filter: filter 1 = cubic B-spline, 2 = Catmull-Rom
+// (ctf_bicubic.cu).
+cudaError_t launch_bicubic_filter(const ExactParams &p, int alg, int tile_w, int mask_dim, int filter,
+                                  cudaStream_t stream);
+
 // Number of SMs of the current device (cached).
 int device_sm_count();
 

@@ -236,6 +236,26 @@ def test_two_texels_per_lane(frame, mixed, alg):
         qt.close()
 
 
+@pytest.mark.parametrize("flt", [1, 2])
+@pytest.mark.parametrize("alg", list(ALGS))
+def test_bicubic_filters(frame, mixed, alg, flt):
+    """The bicubic filters of Sec. 4.2 (1 cubic B-spline, 2 Catmull-Rom) for
+    every algorithm: the full view, and ragged frames with coverage holes,
+    clamped edges and the option sets of the ragged test."""
+    tex, sc = frame
+    for opts in ({"filter": flt}, {"filter": flt, "mask_dim": 11, "tile_w": 4, "tile_h": 8}):
+        g = gpu_filter(tex, sc.uv, sc.jac, sc.coverage, alg, seed=11, opts=opts)
+        assert_parity(g, cpu_filter(tex, sc.uv, sc.jac, sc.coverage, alg, seed=11, opts=opts))
+        if alg in ("box", "mask", "list_merge"):
+            assert g[2]["tiles_success"] > 0
+    for W, H in ((133, 77), (17, 3), (250, 131)):
+        uv, jac, cov = _mixed_scene(W, H, seed=W * 1000 + H)
+        for opts in ({"filter": flt}, {"filter": flt, "edge_remap": 0}, {"filter": flt, "budget": 20, "mask_dim": 11},
+                     {"filter": flt, "tile_w": 16, "tile_h": 2}):
+            assert_parity(gpu_filter(mixed, uv, jac, cov, alg, seed=77, opts=opts),
+                          cpu_filter(mixed, uv, jac, cov, alg, seed=77, opts=opts))
+
+
 def test_empty_and_uncovered(mixed):
     uv, jac, cov = _mixed_scene(40, 20, seed=1)
     z = np.zeros((20, 40), np.uint8)
