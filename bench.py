@@ -40,7 +40,9 @@ HEADLINE = ("mask", {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 11, "ed
 OTHERS = [("4tap", "4tap", {}), ("box", "box", {}), ("list_merge", "list_merge", {}),
           ("mask16", "mask", {"mask_dim": 16}),
           ("mask11_fallback_c", "mask", {"fallback": 1}), ("mask11_fallback_cplus", "mask", {"fallback": 2}),
-          ("mask11_two_texels_per_lane", "mask", {"texels_per_lane": 2, "budget": 64})]
+          ("mask11_two_texels_per_lane", "mask", {"texels_per_lane": 2, "budget": 64}),
+          ("bspline_16tap", "4tap", {"filter": 1}), ("bspline_mask16", "mask", {"filter": 1, "mask_dim": 16}),
+          ("catmull_rom_16tap", "4tap", {"filter": 2}), ("catmull_rom_mask16", "mask", {"filter": 2, "mask_dim": 16})]
 ALG_ID = {"4tap": 0, "stf": 1, "list_merge": 2, "box": 3, "mask": 4}
 FALLBACK_HBM_GBS = 6800.0
 
@@ -553,7 +555,7 @@ def ours_arm(args):
     extras = {}
     if not args.no_extras:
         k = min(args.steps, 1000)
-        ref4 = None
+        ref4 = ref16 = None
         for key, a, o in [("mask11", HEADLINE[0], {})] + OTHERS:
             oo = dict(HEADLINE[1])
             oo.update(o)
@@ -566,12 +568,16 @@ def ours_arm(args):
             if key == "4tap":
                 ref4 = out.clone()
                 extras["mask11"] = {"psnr_vs_4tap_db": _psnr(img, ref4)}
+            if key.endswith("_16tap"):
+                ref16 = out.clone()
             extras[key] = {"pixels_per_s": npix / (ms_a / k * 1e-3), "ms_per_view": ms_a / k,
                            "evals_per_pixel": sa["texel_evals"] / max(1, sa["pixels_active"]),
                            "tiles_success": sa["tiles_success"], "tiles_fallback_budget": sa["tiles_fallback_budget"],
                            "tiles_fallback_minified": sa["tiles_fallback_minified"],
                            "achieved_gbs": algorithmic_bytes(a, npix, tex_bytes, cov is not None) / (ms_a / k * 1e-3) / 1e9}
-            if ref4 is not None and key != "4tap":
+            if key.endswith("_mask16"):
+                extras[key]["psnr_vs_16tap_db"] = _psnr(out, ref16)
+            elif ref4 is not None and key != "4tap" and not key.endswith("_16tap"):
                 extras[key]["psnr_vs_4tap_db"] = _psnr(out, ref4)
     # end-to-end through the host entry point (pinned host buffers)
     h_uv = torch.from_numpy(sc.uv).pin_memory()
