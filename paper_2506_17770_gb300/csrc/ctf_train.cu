@@ -4,14 +4,15 @@
 // 16 -> 64 -> 64 -> 4 with ReLU) is fitted to the exact decode of a block
 // texture.  FP32 master parameters live in one device buffer:
 //   [w1 1024 | b1 64 | w2 4096 | b2 64 | w3 256 | b3 4 | pad 4 | latent0 | latent1]
-// A step samples a batch of texels with Philox4x32-10, and for every texel
-// one thread runs the forward and backward pass in FP32 (weights in shared
-// memory, per-texel activations in shared-memory rows).  The CTA then sums
-// the weight gradients of its 128 texels in a fixed order, and adds them,
-// like the latent-grid gradient scatter, to 64-bit fixed-point accumulators
-// (integer atomics are order-independent, so a step is deterministic).  An
-// Adam kernel converts the sums back, updates parameters and moments, and
-// clears the accumulators.
+// A step samples a batch of texels with Philox4x32-10.  A CTA of 512 threads
+// takes 128 texels per round and runs the forward and backward pass in FP32
+// as register-tiled products over them (weights and feature-major
+// activations in shared memory).  It sums the weight gradients of its
+// texels in texel order, and adds them, like the latent-grid gradient
+// scatter, to 64-bit fixed-point accumulators (integer atomics are
+// order-independent, so a step is deterministic).  An Adam kernel converts
+// the sums back, updates parameters and moments, and clears the
+// accumulators.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -33,9 +34,11 @@ constexpr int kWeights = 5508;
 constexpr int kOffLat = 5512;
 constexpr double kFix = 17592186044416.0;  // 2^44: gradient fixed point
 constexpr double kLossFix = 4294967296.0;  // 2^32: loss fixed point
-constexpr int kThreads = 128;
-constexpr int kRounds = 4;                 // rounds of 128 texels per CTA
-constexpr int kRow = 68;                   // row length of the per-texel activation rows
+constexpr int kThreads = 128;              // threads of the activation-statistics kernel
+constexpr int kGradThreads = 512;          // threads of the gradient kernel
+constexpr int kT = 128;                    // texels per round of the gradient kernel
+constexpr int kMaxRounds = 4;              // rounds per CTA, at most
+constexpr int kLd = kT + 4;                // row stride of the feature-major activation rows (floats)
 
 struct GradParams {
     const float *params;
@@ -45,6 +48,7 @@ struct GradParams {
     float sx[2], sy[2];
     const int2 *xy;        // explicit texels, or nullptr: Philox sampling
     int n;                 // texels in this call
+    int rounds;            // rounds of kT texels per CTA
     uint32_t step;         // Philox counter word
     uint32_t k0, k1;       // Philox key
     float dscale;          // 2 / batch
@@ -52,97 +56,78 @@ struct GradParams {
     long long *loss;       // fixed-point sum of squared errors
 };
 
-__device__ __forceinline__ long long to_fix(float v) { return __double2ll_rn((double)v * kFix); }
+// v * 2^44 is exact in FP32 (a power-of-two scale), so this rounds the same
+// value as the FP64 product would, without FP64 arithmetic.
+__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * 0x1p44f); }
 
-// Shared memory of the gradient kernel (floats).  Per-texel rows have a
-// stride of 68 floats: 16-byte aligned, and 8 threads reading 16 bytes each
-// from their own rows touch all 32 banks once.
-constexpr int kRowF = 20;                     // features (16 used)
-constexpr int kSmF = 5512;                    // [128][20]
-constexpr int kSmH1 = kSmF + 128 * kRowF;     // [128][68]
-constexpr int kSmH2 = kSmH1 + 128 * kRow;
-constexpr int kSmD1 = kSmH2 + 128 * kRow;
-constexpr int kSmD2 = kSmD1 + 128 * kRow;
-constexpr int kSmDY = kSmD2 + 128 * kRow;     // [128][4]
-constexpr int kSmLoss = kSmDY + 128 * 4;      // [128]
-constexpr int kSmAcc = kSmLoss + 128;         // [44][128] per-thread gradient sums
-constexpr int kNAcc = 44;
-constexpr int kSmFloats = kSmAcc + kNAcc * 128;
+// Shared memory of the gradient kernel (floats).  The weights are held as
+// stored ([out][in]) and transposed; activations are feature-major rows of
+// kLd floats (one column per texel), so that every product below reads
+// 16-byte vectors along a contiguous index.  kLd = 132 puts consecutive rows
+// 4 banks apart.
+constexpr int kSW1 = 0;                    // W1 [64][16]
+constexpr int kSW1t = 1024;                // W1^T [16][64]
+constexpr int kSW2 = 2048;                 // W2 [64][64]
+constexpr int kSW2t = 6144;                // W2^T [64][64]
+constexpr int kSW3 = 10240;                // W3 [4][64]
+constexpr int kSB1 = 10496, kSB2 = 10560, kSB3 = 10624;
+constexpr int kSF = 10628;                 // F^T  [16][kLd]  features
+constexpr int kSH1 = kSF + 16 * kLd;       // H1^T [64][kLd]
+constexpr int kSH2 = kSH1 + 64 * kLd;      // H2^T [64][kLd]
+constexpr int kSD2 = kSH2 + 64 * kLd;      // dH2^T [64][kLd] (masked)
+constexpr int kSD1 = kSD2 + 64 * kLd;      // dH1^T [64][kLd] (masked)
+constexpr int kSDY = kSD1 + 64 * kLd;      // dY^T [4][kLd]
+constexpr int kSDF = kSDY + 4 * kLd;       // dF^T [16][kLd]
+constexpr int kSE = kSDF + 16 * kLd;       // output errors [4][kT]
+constexpr int kSXY = kSE + 4 * kT;         // texel coordinates, int2 [kT]
+constexpr int kSmFloats = kSXY + 2 * kT;
 constexpr size_t kGradSmem = (size_t)kSmFloats * 4;
+static_assert(kSF % 4 == 0 && kSH1 % 4 == 0 && kSD2 % 4 == 0 && kSDY % 4 == 0 && kSE % 4 == 0 && kLd % 4 == 0,
+              "16-byte rows");
+static_assert(kGradSmem <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
-// y = W x + b over own rows: W [OUT][IN] and b in shared memory, x and y
-// rows of this thread; 8 outputs at a time, 4 inputs per step.
-template <int IN, int OUT>
-__device__ __forceinline__ void dense_fwd(const float *W, const float *b, const float *x, float *y) {
-#pragma unroll 1
-    for (int j = 0; j < OUT; j += 8) {
-        float acc[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = b[j + q];
+// acc[i][j] += sum over k < K of A[k][m0 + i] * B[k][n0 + j]: A rows of lda
+// floats (contiguous in m), B rows of kLd floats (contiguous in n), k
+// ascending, one fused multiply-add per term.
+template <int K>
+__device__ __forceinline__ void mm44(const float *A, int lda, const float *B, int m0, int n0, float (&acc)[4][4]) {
 #pragma unroll 4
-        for (int k = 0; k < IN; k += 4) {
-            const float4 xv = ld4(x + k);
+    for (int k = 0; k < K; ++k) {
+        const float4 a = ld4(A + k * lda + m0), b = ld4(B + k * kLd + n0);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float4 w = ld4(W + (j + q) * IN + k);
-                acc[q] = __fmaf_rn(w.x, xv.x, acc[q]);
-                acc[q] = __fmaf_rn(w.y, xv.y, acc[q]);
-                acc[q] = __fmaf_rn(w.z, xv.z, acc[q]);
-                acc[q] = __fmaf_rn(w.w, xv.w, acc[q]);
-            }
-        }
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int q = 0; q < 8; q += 4)
-            st4(y + j + q, make_float4(fmaxf(acc[q], 0.f), fmaxf(acc[q + 1], 0.f), fmaxf(acc[q + 2], 0.f),
-                                       fmaxf(acc[q + 3], 0.f)));
+            for (int j = 0; j < 4; ++j) acc[i][j] = __fmaf_rn(av[i], bv[j], acc[i][j]);
     }
 }
 
-// dx = W^T dy over own rows, masked by (h > 0): W [OUT][IN]; 8 inputs at a
-// time, one output per step.
-template <int IN, int OUT>
-__device__ __forceinline__ void dense_bwd(const float *W, const float *dy, const float *h, float *dx) {
-#pragma unroll 1
-    for (int k = 0; k < IN; k += 8) {
-        float acc[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < OUT; ++j) {
-            const float d = dy[j];
-            const float4 w0 = ld4(W + j * IN + k), w1 = ld4(W + j * IN + k + 4);
-            acc[0] = __fmaf_rn(w0.x, d, acc[0]);
-            acc[1] = __fmaf_rn(w0.y, d, acc[1]);
-            acc[2] = __fmaf_rn(w0.z, d, acc[2]);
-            acc[3] = __fmaf_rn(w0.w, d, acc[3]);
-            acc[4] = __fmaf_rn(w1.x, d, acc[4]);
-            acc[5] = __fmaf_rn(w1.y, d, acc[5]);
-            acc[6] = __fmaf_rn(w1.z, d, acc[6]);
-            acc[7] = __fmaf_rn(w1.w, d, acc[7]);
-        }
-        const float4 h0 = ld4(h + k), h1 = ld4(h + k + 4);
-        st4(dx + k, make_float4(h0.x > 0.f ? acc[0] : 0.f, h0.y > 0.f ? acc[1] : 0.f, h0.z > 0.f ? acc[2] : 0.f,
-                                h0.w > 0.f ? acc[3] : 0.f));
-        st4(dx + k + 4, make_float4(h1.x > 0.f ? acc[4] : 0.f, h1.y > 0.f ? acc[5] : 0.f,
-                                    h1.z > 0.f ? acc[6] : 0.f, h1.w > 0.f ? acc[7] : 0.f));
-    }
+// Block of one thread in a 64 x 128 product: warps tile 4 x 4 blocks of
+// 16 x 32, lanes 4 x 8 blocks of 4 x 4.
+__device__ __forceinline__ void tile_64x128(int tid, int &m0, int &n0) {
+    const int w = tid >> 5, l = tid & 31;
+    m0 = (w & 3) * 16 + (l >> 3) * 4;
+    n0 = (w >> 2) * 32 + (l & 7) * 4;
 }
 
 __device__ __forceinline__ void bilinear_taps(const GradParams &g, int grid, int x, int y, int idx[4], float w[4]) {
-    const float gx = __fsub_rn(__fmul_rn(__fadd_rn((float)x, 0.5f), g.sx[grid]), 0.5f);
-    const float gy = __fsub_rn(__fmul_rn(__fadd_rn((float)y, 0.5f), g.sy[grid]), 0.5f);
+    // grid is 0 or 1; selecting by value keeps the parameter block out of local memory
+    const float sx = grid ? g.sx[1] : g.sx[0], sy = grid ? g.sy[1] : g.sy[0];
+    const int gw = grid ? g.gw[1] : g.gw[0], gh = grid ? g.gh[1] : g.gh[0];
+    const float gx = __fsub_rn(__fmul_rn(__fadd_rn((float)x, 0.5f), sx), 0.5f);
+    const float gy = __fsub_rn(__fmul_rn(__fadd_rn((float)y, 0.5f), sy), 0.5f);
     const float fx0 = floorf(gx), fy0 = floorf(gy);
     const float fx = __fsub_rn(gx, fx0), fy = __fsub_rn(gy, fy0);
     const int x0 = (int)fx0, y0 = (int)fy0;
-    const int xa = min(max(x0, 0), g.gw[grid] - 1), xb = min(max(x0 + 1, 0), g.gw[grid] - 1);
-    const int ya = min(max(y0, 0), g.gh[grid] - 1), yb = min(max(y0 + 1, 0), g.gh[grid] - 1);
-    idx[0] = ya * g.gw[grid] + xa;
-    idx[1] = ya * g.gw[grid] + xb;
-    idx[2] = yb * g.gw[grid] + xa;
-    idx[3] = yb * g.gw[grid] + xb;
+    const int xa = min(max(x0, 0), gw - 1), xb = min(max(x0 + 1, 0), gw - 1);
+    const int ya = min(max(y0, 0), gh - 1), yb = min(max(y0 + 1, 0), gh - 1);
+    idx[0] = ya * gw + xa;
+    idx[1] = ya * gw + xb;
+    idx[2] = yb * gw + xa;
+    idx[3] = yb * gw + xb;
     const float ofx = __fsub_rn(1.f, fx), ofy = __fsub_rn(1.f, fy);
     w[0] = __fmul_rn(ofx, ofy);
     w[1] = __fmul_rn(fx, ofy);
@@ -150,173 +135,270 @@ __device__ __forceinline__ void bilinear_taps(const GradParams &g, int grid, int
     w[3] = __fmul_rn(fx, fy);
 }
 
-__global__ void __launch_bounds__(kThreads) grad_kernel(const GradParams g) {
+// Forward and backward pass of kT texels per round, as products over the
+// round's texels.  Every texel's activations and input-side gradients come
+// out of the same operations in the same order as a per-texel evaluation;
+// the weight gradients are summed over the CTA's texels in texel order.
+__global__ void __launch_bounds__(kGradThreads, 1) grad_kernel(const GradParams g) {
     extern __shared__ __align__(16) float sm[];
     const int tid = threadIdx.x;
-    for (int i = tid; i < kWeights; i += kThreads) sm[i] = g.params[i];
-    static_assert(kSmF % 4 == 0 && kSmH1 % 4 == 0 && kSmD2 % 4 == 0 && kSmDY % 4 == 0, "16-byte rows");
-    float *W1 = sm + kOffW1, *B1 = sm + kOffB1, *W2 = sm + kOffW2, *B2 = sm + kOffB2, *W3 = sm + kOffW3,
-          *B3 = sm + kOffB3;
-    float *F = sm + kSmF, *H1 = sm + kSmH1, *H2 = sm + kSmH2, *D1 = sm + kSmD1, *D2 = sm + kSmD2, *DY = sm + kSmDY,
-          *LS = sm + kSmLoss;
-    const float *lat[2] = {g.params + kOffLat, g.params + kOffLat + (size_t)g.gw[0] * g.gh[0] * 8};
-    long long *glat[2] = {g.grad + kOffLat, g.grad + kOffLat + (size_t)g.gw[0] * g.gh[0] * 8};
-    // reduction ownership: dW2 (j2, i2..i2+31), dW1 (j2, k1..k1+7), dW3 (c3, i3, i3+1)
-    const int j2 = tid >> 1, i2 = (tid & 1) * 32, k1 = (tid & 1) * 8;
-    const int c3 = tid >> 5, i3 = (tid & 31) * 2;
-    // per-thread sums: [0,32) dW2, [32,40) dW1, [40,42) dW3, 42 db1/db2, 43 db3
-    float *ACC = sm + kSmAcc;
-#pragma unroll
-    for (int q = 0; q < kNAcc; ++q) ACC[q * 128 + tid] = 0.f;
-    float loss = 0.f;
+    // transposed copies are read transposed from global (L2) and written in
+    // order, which keeps the shared-memory stores free of bank conflicts
+    for (int i = tid; i < 1024; i += kGradThreads) {
+        sm[kSW1 + i] = g.params[kOffW1 + i];
+        sm[kSW1t + i] = g.params[kOffW1 + (i & 63) * 16 + (i >> 6)];
+    }
+    for (int i = tid; i < 4096; i += kGradThreads) {
+        sm[kSW2 + i] = g.params[kOffW2 + i];
+        sm[kSW2t + i] = g.params[kOffW2 + (i & 63) * 64 + (i >> 6)];
+    }
+    for (int i = tid; i < 256; i += kGradThreads) sm[kSW3 + i] = g.params[kOffW3 + i];
+    if (tid < 64) {
+        sm[kSB1 + tid] = g.params[kOffB1 + tid];
+        sm[kSB2 + tid] = g.params[kOffB2 + tid];
+    }
+    if (tid < 4) sm[kSB3 + tid] = g.params[kOffB3 + tid];
+    const float *W1 = sm + kSW1, *W1t = sm + kSW1t, *W2 = sm + kSW2, *W2t = sm + kSW2t, *W3 = sm + kSW3;
+    const float *B1 = sm + kSB1, *B2 = sm + kSB2, *B3 = sm + kSB3;
+    float *F = sm + kSF, *H1 = sm + kSH1, *H2 = sm + kSH2, *D2 = sm + kSD2, *D1 = sm + kSD1, *DY = sm + kSDY,
+          *DF = sm + kSDF, *E = sm + kSE;
+    int2 *XY = reinterpret_cast<int2 *>(sm + kSXY);
+    const size_t lat1 = (size_t)g.gw[0] * g.gh[0] * 8;  // start of the second grid
+    const int w = tid >> 5, l = tid & 31;
+    int m0, n0;
+    tile_64x128(tid, m0, n0);
+    // persistent weight-gradient sums of this thread:
+    //   dW2 rows m2 + {0, 4}, columns n2 + {0, 8, 16, 24}; dW1 row tid/8,
+    //   columns (tid%8) + {0, 8}; dW3 (tid < 256) row tid/64, column tid%64;
+    //   db2 (tid < 64), db1 (64 <= tid < 128), db3 (128 <= tid < 132)
+    const int m2 = (w & 7) * 8 + (l >> 3), n2 = (w >> 3) * 32 + (l & 7);
+    const int m1 = tid >> 3, n1 = tid & 7;
+    float aW2[2][4] = {}, aW1[2] = {}, aW3 = 0.f, aB = 0.f, loss = 0.f;
     __syncthreads();
 
 #pragma unroll 1
-    for (int r = 0; r < kRounds; ++r) {
-        const int i = (blockIdx.x * kRounds + r) * kThreads + tid;
-        const bool valid = i < g.n;
-        // ---- texel and target
-        int x, y;
-        if (g.xy) {
-            const int2 c = valid ? g.xy[i] : make_int2(0, 0);
-            x = min(max(c.x, 0), g.Wt - 1);
-            y = min(max(c.y, 0), g.Ht - 1);
-        } else {
-            const uint4 rr = philox4x32_10(make_uint4((uint32_t)i, g.step, 0x5A4Du, 0u), g.k0, g.k1);
-            x = (int)(((unsigned long long)rr.x * (unsigned)g.Wt) >> 32);
-            y = (int)(((unsigned long long)rr.y * (unsigned)g.Ht) >> 32);
-        }
-        const uint32_t px = fetch_block_texel(g.blocks, g.nbx, g.Wt, g.Ht, x, y);
-        float tgt[4];
-        tgt[0] = __fdiv_rn((float)(px & 0xffu), 255.f);
-        tgt[1] = __fdiv_rn((float)((px >> 8) & 0xffu), 255.f);
-        tgt[2] = __fdiv_rn((float)((px >> 16) & 0xffu), 255.f);
-        tgt[3] = __fdiv_rn((float)(px >> 24), 255.f);
-        // ---- features
-        int tap[2][4];
-        float tw[2][4];
-        float f[16];
-#pragma unroll
-        for (int gi = 0; gi < 2; ++gi) {
-            bilinear_taps(g, gi, x, y, tap[gi], tw[gi]);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float acc = 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc = __fmaf_rn(tw[gi][k], __ldg(lat[gi] + (size_t)tap[gi][k] * 8 + c), acc);
-                f[gi * 8 + c] = acc;
+    for (int r = 0; r < g.rounds; ++r) {
+        const int i0 = (blockIdx.x * g.rounds + r) * kT;
+        // ---- texels of the round
+        if (tid < kT) {
+            const int i = i0 + tid;
+            int x, y;
+            if (g.xy) {
+                const int2 c = i < g.n ? g.xy[i] : make_int2(0, 0);
+                x = min(max(c.x, 0), g.Wt - 1);
+                y = min(max(c.y, 0), g.Ht - 1);
+            } else {
+                const uint4 rr = philox4x32_10(make_uint4((uint32_t)i, g.step, 0x5A4Du, 0u), g.k0, g.k1);
+                x = (int)(((unsigned long long)rr.x * (unsigned)g.Wt) >> 32);
+                y = (int)(((unsigned long long)rr.y * (unsigned)g.Ht) >> 32);
             }
+            XY[tid] = make_int2(x, y);
         }
-        float *Fr = F + tid * kRowF, *H1r = H1 + tid * kRow, *H2r = H2 + tid * kRow;
-        float *D1r = D1 + tid * kRow, *D2r = D2 + tid * kRow, *DYr = DY + tid * 4;
+        __syncthreads();
+        // ---- features: texel t, grid q/2, channels 4(q%2) .. +3
+        {
+            const int t = tid & (kT - 1), q = tid >> 7, gi = q >> 1, c0 = (q & 1) * 4;
+            const int2 c = XY[t];
+            int tap[4];
+            float tw[4];
+            bilinear_taps(g, gi, c.x, c.y, tap, tw);
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < 16; k += 4)
-            st4(Fr + k, valid ? make_float4(f[k], f[k + 1], f[k + 2], f[k + 3]) : make_float4(0.f, 0.f, 0.f, 0.f));
-        // ---- forward (features are valid for every texel; rows of invalid ones are masked below)
+            const float *lg = g.params + kOffLat + (gi ? lat1 : 0);
+            for (int k = 0; k < 4; ++k) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(lg + (size_t)tap[k] * 8 + c0));
+                acc[0] = __fmaf_rn(tw[k], v.x, acc[0]);
+                acc[1] = __fmaf_rn(tw[k], v.y, acc[1]);
+                acc[2] = __fmaf_rn(tw[k], v.z, acc[2]);
+                acc[3] = __fmaf_rn(tw[k], v.w, acc[3]);
+            }
 #pragma unroll
-        for (int k = 0; k < 16; k += 4) st4(D1r + k, make_float4(f[k], f[k + 1], f[k + 2], f[k + 3]));
-        dense_fwd<16, 64>(W1, B1, D1r, H1r);
-        dense_fwd<64, 64>(W2, B2, H1r, H2r);
-        float dy[4];
+            for (int j = 0; j < 4; ++j) F[(gi * 8 + c0 + j) * kLd + t] = acc[j];
+        }
+        __syncthreads();
+        // ---- H1 = relu(W1 F + b1), H2 = relu(W2 H1 + b2)
+        {
+            float acc[4][4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = B1[m0 + i];
+            mm44<16>(W1t, 64, F, m0, n0, acc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                st4(H1 + (m0 + i) * kLd + n0, make_float4(fmaxf(acc[i][0], 0.f), fmaxf(acc[i][1], 0.f),
+                                                          fmaxf(acc[i][2], 0.f), fmaxf(acc[i][3], 0.f)));
+        }
+        __syncthreads();
+        {
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = B2[m0 + i];
+            mm44<64>(W2t, 64, H1, m0, n0, acc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                st4(H2 + (m0 + i) * kLd + n0, make_float4(fmaxf(acc[i][0], 0.f), fmaxf(acc[i][1], 0.f),
+                                                          fmaxf(acc[i][2], 0.f), fmaxf(acc[i][3], 0.f)));
+        }
+        __syncthreads();
+        // ---- output channel c of texel t, its error and dY = 2 e / batch
+        {
+            const int t = tid & (kT - 1), c = tid >> 7;
+            const bool valid = i0 + t < g.n;
             float a = B3[c];
 #pragma unroll 4
             for (int k = 0; k < 64; k += 4) {
-                const float4 hv = ld4(H2r + k), w = ld4(W3 + c * 64 + k);
-                a = __fmaf_rn(w.x, hv.x, a);
-                a = __fmaf_rn(w.y, hv.y, a);
-                a = __fmaf_rn(w.z, hv.z, a);
-                a = __fmaf_rn(w.w, hv.w, a);
+                const float4 wv = ld4(W3 + c * 64 + k);
+                a = __fmaf_rn(wv.x, H2[k * kLd + t], a);
+                a = __fmaf_rn(wv.y, H2[(k + 1) * kLd + t], a);
+                a = __fmaf_rn(wv.z, H2[(k + 2) * kLd + t], a);
+                a = __fmaf_rn(wv.w, H2[(k + 3) * kLd + t], a);
             }
-            const float e = __fsub_rn(a, tgt[c]);
-            if (valid) loss = __fmaf_rn(e, e, loss);
-            dy[c] = valid ? __fmul_rn(e, g.dscale) : 0.f;
-        }
-        st4(DYr, make_float4(dy[0], dy[1], dy[2], dy[3]));
-        // ---- backward: dh2 = W3^T dy (masked), dh1 = W2^T dh2 (masked), df = W1^T dh1
-        dense_bwd<64, 4>(W3, DYr, H2r, D2r);
-        dense_bwd<64, 64>(W2, D2r, H1r, D1r);
-        float df[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) df[k] = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < 64; ++j) {
-            const float d = D1r[j];
-#pragma unroll
-            for (int k = 0; k < 16; k += 4) {
-                const float4 w = ld4(W1 + j * 16 + k);
-                df[k] = __fmaf_rn(w.x, d, df[k]);
-                df[k + 1] = __fmaf_rn(w.y, d, df[k + 1]);
-                df[k + 2] = __fmaf_rn(w.z, d, df[k + 2]);
-                df[k + 3] = __fmaf_rn(w.w, d, df[k + 3]);
-            }
-        }
-        // ---- latent-grid gradient: each feature is a bilinear blend of 4 taps
-        if (valid) {
-#pragma unroll
-            for (int gi = 0; gi < 2; ++gi)
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const long long v = to_fix(__fmul_rn(tw[gi][k], df[gi * 8 + c]));
-                        if (v) atomicAdd(reinterpret_cast<unsigned long long *>(glat[gi] + (size_t)tap[gi][k] * 8 + c),
-                                         (unsigned long long)v);
-                    }
+            const int2 xy = XY[t];
+            const uint32_t px = fetch_block_texel(g.blocks, g.nbx, g.Wt, g.Ht, xy.x, xy.y);
+            const float tgt = __fdiv_rn((float)((px >> (8 * c)) & 0xffu), 255.f);
+            const float e = __fsub_rn(a, tgt);
+            E[c * kT + t] = e;
+            DY[c * kLd + t] = valid ? __fmul_rn(e, g.dscale) : 0.f;
         }
         __syncthreads();
-        // ---- weight gradients of the 128 texels, summed in a fixed order
-        {
-            float aW2[32], aW1[8], aW3[2], aB, aB3;
+        // ---- loss (texel order, channels in order); dW3 += dY H2^T; dH2 = (W3^T dY) masked by H2 > 0
+        if (tid < kT && i0 + tid < g.n) {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) aW2[q] = ACC[q * 128 + tid];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) aW1[q] = ACC[(32 + q) * 128 + tid];
-            aW3[0] = ACC[40 * 128 + tid];
-            aW3[1] = ACC[41 * 128 + tid];
-            aB = ACC[42 * 128 + tid];
-            aB3 = ACC[43 * 128 + tid];
-#pragma unroll 1
-            for (int s = 0; s < kThreads; ++s) {
-                const float d2 = D2[s * kRow + j2], d1 = D1[s * kRow + j2];
-#pragma unroll
-                for (int q = 0; q < 32; ++q) aW2[q] = __fmaf_rn(d2, H1[s * kRow + i2 + q], aW2[q]);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) aW1[q] = __fmaf_rn(d1, F[s * kRowF + k1 + q], aW1[q]);
-                const float dyc = DY[s * 4 + c3];
-                aW3[0] = __fmaf_rn(dyc, H2[s * kRow + i3], aW3[0]);
-                aW3[1] = __fmaf_rn(dyc, H2[s * kRow + i3 + 1], aW3[1]);
-                aB = __fadd_rn(aB, tid < 64 ? D1[s * kRow + tid] : D2[s * kRow + tid - 64]);
-                if (tid < 4) aB3 = __fadd_rn(aB3, DY[s * 4 + tid]);
+            for (int c = 0; c < 4; ++c) loss = __fmaf_rn(E[c * kT + tid], E[c * kT + tid], loss);
+        }
+        if (tid < 256) {
+            const float *dy = DY + (tid >> 6) * kLd, *h = H2 + (tid & 63) * kLd;
+#pragma unroll 4
+            for (int t = 0; t < kT; t += 4) {
+                const float4 a = ld4(dy + t), b = ld4(h + t);
+                aW3 = __fmaf_rn(a.x, b.x, aW3);
+                aW3 = __fmaf_rn(a.y, b.y, aW3);
+                aW3 = __fmaf_rn(a.z, b.z, aW3);
+                aW3 = __fmaf_rn(a.w, b.w, aW3);
             }
+        }
+        {
+            float acc[4][4] = {};
+            mm44<4>(W3, 64, DY, m0, n0, acc);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) ACC[q * 128 + tid] = aW2[q];
+            for (int i = 0; i < 4; ++i) {
+                const float4 h = ld4(H2 + (m0 + i) * kLd + n0);
+                st4(D2 + (m0 + i) * kLd + n0, make_float4(h.x > 0.f ? acc[i][0] : 0.f, h.y > 0.f ? acc[i][1] : 0.f,
+                                                          h.z > 0.f ? acc[i][2] : 0.f, h.w > 0.f ? acc[i][3] : 0.f));
+            }
+        }
+        __syncthreads();
+        // ---- dW2 += dH2 H1^T; dH1 = (W2^T dH2) masked by H1 > 0
+        {
+            const float *a0 = D2 + m2 * kLd, *a1 = D2 + (m2 + 4) * kLd;
+            const float *b0 = H1 + n2 * kLd;
+#pragma unroll 2
+            for (int t = 0; t < kT; t += 4) {
+                const float4 x0 = ld4(a0 + t), x1 = ld4(a1 + t);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) ACC[(32 + q) * 128 + tid] = aW1[q];
-            ACC[40 * 128 + tid] = aW3[0];
-            ACC[41 * 128 + tid] = aW3[1];
-            ACC[42 * 128 + tid] = aB;
-            ACC[43 * 128 + tid] = aB3;
+                for (int j = 0; j < 4; ++j) {
+                    const float4 y = ld4(b0 + 8 * j * kLd + t);
+                    aW2[0][j] = __fmaf_rn(x0.x, y.x, aW2[0][j]);
+                    aW2[0][j] = __fmaf_rn(x0.y, y.y, aW2[0][j]);
+                    aW2[0][j] = __fmaf_rn(x0.z, y.z, aW2[0][j]);
+                    aW2[0][j] = __fmaf_rn(x0.w, y.w, aW2[0][j]);
+                    aW2[1][j] = __fmaf_rn(x1.x, y.x, aW2[1][j]);
+                    aW2[1][j] = __fmaf_rn(x1.y, y.y, aW2[1][j]);
+                    aW2[1][j] = __fmaf_rn(x1.z, y.z, aW2[1][j]);
+                    aW2[1][j] = __fmaf_rn(x1.w, y.w, aW2[1][j]);
+                }
+            }
+        }
+        {
+            float acc[4][4] = {};
+            mm44<64>(W2, 64, D2, m0, n0, acc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 h = ld4(H1 + (m0 + i) * kLd + n0);
+                st4(D1 + (m0 + i) * kLd + n0, make_float4(h.x > 0.f ? acc[i][0] : 0.f, h.y > 0.f ? acc[i][1] : 0.f,
+                                                          h.z > 0.f ? acc[i][2] : 0.f, h.w > 0.f ? acc[i][3] : 0.f));
+            }
+        }
+        __syncthreads();
+        // ---- dW1 += dH1 F^T; bias sums; dF = W1^T dH1 (warps 0-3)
+        {
+            const float *a = D1 + m1 * kLd, *b0 = F + n1 * kLd, *b1 = F + (n1 + 8) * kLd;
+#pragma unroll 4
+            for (int t = 0; t < kT; t += 4) {
+                const float4 x = ld4(a + t), y0 = ld4(b0 + t), y1 = ld4(b1 + t);
+                aW1[0] = __fmaf_rn(x.x, y0.x, aW1[0]);
+                aW1[0] = __fmaf_rn(x.y, y0.y, aW1[0]);
+                aW1[0] = __fmaf_rn(x.z, y0.z, aW1[0]);
+                aW1[0] = __fmaf_rn(x.w, y0.w, aW1[0]);
+                aW1[1] = __fmaf_rn(x.x, y1.x, aW1[1]);
+                aW1[1] = __fmaf_rn(x.y, y1.y, aW1[1]);
+                aW1[1] = __fmaf_rn(x.z, y1.z, aW1[1]);
+                aW1[1] = __fmaf_rn(x.w, y1.w, aW1[1]);
+            }
+        }
+        if (tid < 132) {
+            const float *row = tid < 64 ? D2 + tid * kLd : (tid < 128 ? D1 + (tid - 64) * kLd : DY + (tid - 128) * kLd);
+#pragma unroll 4
+            for (int t = 0; t < kT; t += 4) {
+                const float4 v = ld4(row + t);
+                aB = __fadd_rn(aB, v.x);
+                aB = __fadd_rn(aB, v.y);
+                aB = __fadd_rn(aB, v.z);
+                aB = __fadd_rn(aB, v.w);
+            }
+        }
+        if (w < 4) {
+            float acc[4][4] = {};
+            const int fm = (l >> 3) * 4, fn = w * 32 + (l & 7) * 4;
+            mm44<64>(W1, 16, D1, fm, fn, acc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                st4(DF + (fm + i) * kLd + fn, make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]));
+        }
+        __syncthreads();
+        // ---- latent-grid gradient: texel t, grid q/2, taps 2(q%2), 2(q%2) + 1
+        {
+            const int t = tid & (kT - 1), q = tid >> 7, gi = q >> 1, hi = q & 1;
+            if (i0 + t < g.n) {
+                const int2 c = XY[t];
+                int tap[4];
+                float tw[4];
+                bilinear_taps(g, gi, c.x, c.y, tap, tw);
+                unsigned long long *gl = reinterpret_cast<unsigned long long *>(g.grad + kOffLat + (gi ? lat1 : 0));
+                const int ta[2] = {hi ? tap[2] : tap[0], hi ? tap[3] : tap[1]};
+                const float wa[2] = {hi ? tw[2] : tw[0], hi ? tw[3] : tw[1]};
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int ch = 0; ch < 8; ++ch) {
+                        const long long v = to_fix(__fmul_rn(wa[k], DF[(gi * 8 + ch) * kLd + t]));
+                        if (v) atomicAdd(gl + (size_t)ta[k] * 8 + ch, (unsigned long long)v);
+                    }
+            }
         }
         __syncthreads();
     }
     // ---- flush the CTA's sums
     unsigned long long *G = reinterpret_cast<unsigned long long *>(g.grad);
-#pragma unroll 4
-    for (int q = 0; q < 32; ++q) atomicAdd(G + kOffW2 + j2 * 64 + i2 + q, (unsigned long long)to_fix(ACC[q * 128 + tid]));
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-        atomicAdd(G + kOffW1 + j2 * 16 + k1 + q, (unsigned long long)to_fix(ACC[(32 + q) * 128 + tid]));
-    atomicAdd(G + kOffW3 + c3 * 64 + i3, (unsigned long long)to_fix(ACC[40 * 128 + tid]));
-    atomicAdd(G + kOffW3 + c3 * 64 + i3 + 1, (unsigned long long)to_fix(ACC[41 * 128 + tid]));
-    atomicAdd(G + (tid < 64 ? kOffB1 + tid : kOffB2 + tid - 64), (unsigned long long)to_fix(ACC[42 * 128 + tid]));
-    if (tid < 4) atomicAdd(G + kOffB3 + tid, (unsigned long long)to_fix(ACC[43 * 128 + tid]));
-    LS[tid] = loss;
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            atomicAdd(G + kOffW2 + (m2 + 4 * i) * 64 + n2 + 8 * j, (unsigned long long)to_fix(aW2[i][j]));
+    atomicAdd(G + kOffW1 + m1 * 16 + n1, (unsigned long long)to_fix(aW1[0]));
+    atomicAdd(G + kOffW1 + m1 * 16 + n1 + 8, (unsigned long long)to_fix(aW1[1]));
+    if (tid < 256) atomicAdd(G + kOffW3 + tid, (unsigned long long)to_fix(aW3));
+    if (tid < 132)
+        atomicAdd(G + (tid < 64 ? kOffB2 + tid : (tid < 128 ? kOffB1 + tid - 64 : kOffB3 + tid - 128)),
+                  (unsigned long long)to_fix(aB));
+    E[tid] = loss;
     __syncthreads();
     if (tid == 0) {
         float tot = 0.f;
-        for (int s = 0; s < kThreads; ++s) tot = __fadd_rn(tot, LS[s]);
+        for (int s = 0; s < kT; ++s) tot = __fadd_rn(tot, E[s]);
         atomicAdd(reinterpret_cast<unsigned long long *>(g.loss), (unsigned long long)__double2ll_rn((double)tot * kLossFix));
     }
 }
@@ -325,23 +407,75 @@ struct AdamParams {
     float *params, *m, *v;
     long long *grad;
     size_t n;
-    float lr_w, lr_lat, beta1, beta2, eps;
-    float bc1, bc2;  // 1 - beta^t
+    float beta1, beta2, eps;
+    float step_w, step_lat;  // learning rate / (1 - beta1^t), weights and latents
+    float inv_bc2;           // 1 / (1 - beta2^t)
 };
 
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// p -= step * m / (sqrt(v / (1 - beta2^t)) + eps) after the moment updates
+// (bias corrections folded into step and inv_bc2; approximate square root
+// and division, as an optimiser needs no correctly rounded update).
+__device__ __forceinline__ void adam_update(const AdamParams &a, long long gi, float step, float &p, float &m,
+                                            float &v) {
+    const float gr = __ll2float_rn(gi) * 0x1p-44f;  // fixed point back to FP32 (exact scale)
+    m = __fmaf_rn(a.beta1, m, (1.f - a.beta1) * gr);
+    v = __fmaf_rn(a.beta2, v, (1.f - a.beta2) * (gr * gr));
+    p = __fmaf_rn(-step, __fdividef(m, sqrt_approx(v * a.inv_bc2) + a.eps), p);
+}
+
+__device__ __forceinline__ void adam_quad(const AdamParams &a, float step, float4 &p, float4 &m, float4 &v,
+                                          longlong2 g01, longlong2 g23) {
+    adam_update(a, g01.x, step, p.x, m.x, v.x);
+    adam_update(a, g01.y, step, p.y, m.y, v.y);
+    adam_update(a, g23.x, step, p.z, m.z, v.z);
+    adam_update(a, g23.y, step, p.w, m.w, v.w);
+}
+
+// Four parameters per quad, two quads per iteration so that both sets of
+// loads are in flight together.  The buffer length and the start of the
+// latents are multiples of 4; the padding quad (parameters, moments and
+// gradients all zero) stays zero.
 __global__ void adam_kernel(const AdamParams a) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < a.n; i += (size_t)gridDim.x * blockDim.x) {
-        if (i >= (size_t)kWeights && i < (size_t)kOffLat) continue;
-        const long long gi = a.grad[i];
-        a.grad[i] = 0;
-        const float gr = (float)((double)gi / kFix);
-        const float m = __fmaf_rn(a.beta1, a.m[i], __fmul_rn(1.f - a.beta1, gr));
-        const float v = __fmaf_rn(a.beta2, a.v[i], __fmul_rn(1.f - a.beta2, __fmul_rn(gr, gr)));
-        a.m[i] = m;
-        a.v[i] = v;
-        const float mh = __fdiv_rn(m, a.bc1), vh = __fdiv_rn(v, a.bc2);
-        const float lr = i < (size_t)kWeights ? a.lr_w : a.lr_lat;
-        a.params[i] = __fsub_rn(a.params[i], __fdiv_rn(__fmul_rn(lr, mh), __fadd_rn(__fsqrt_rn(vh), a.eps)));
+    static_assert(kWeights % 4 == 0 && kOffLat == kWeights + 4, "one padding quad");
+    const size_t n4 = a.n / 4, stride = (size_t)gridDim.x * blockDim.x;
+    float4 *__restrict__ P = reinterpret_cast<float4 *>(a.params);
+    float4 *__restrict__ M = reinterpret_cast<float4 *>(a.m);
+    float4 *__restrict__ V = reinterpret_cast<float4 *>(a.v);
+    longlong2 *__restrict__ G = reinterpret_cast<longlong2 *>(a.grad);
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += 2 * stride) {
+        const size_t q2 = q + stride;
+        const bool two = q2 < n4;
+        const longlong2 g0 = G[2 * q], g1 = G[2 * q + 1];
+        float4 p = P[q], m = M[q], v = V[q];
+        longlong2 h0 = make_longlong2(0, 0), h1 = make_longlong2(0, 0);
+        float4 p2 = make_float4(0.f, 0.f, 0.f, 0.f), m2 = p2, v2 = p2;
+        if (two) {
+            h0 = G[2 * q2];
+            h1 = G[2 * q2 + 1];
+            p2 = P[q2];
+            m2 = M[q2];
+            v2 = V[q2];
+        }
+        adam_quad(a, q < (size_t)kWeights / 4 ? a.step_w : a.step_lat, p, m, v, g0, g1);
+        G[2 * q] = make_longlong2(0, 0);
+        G[2 * q + 1] = make_longlong2(0, 0);
+        P[q] = p;
+        M[q] = m;
+        V[q] = v;
+        if (two) {
+            adam_quad(a, q2 < (size_t)kWeights / 4 ? a.step_w : a.step_lat, p2, m2, v2, h0, h1);
+            G[2 * q2] = make_longlong2(0, 0);
+            G[2 * q2 + 1] = make_longlong2(0, 0);
+            P[q2] = p2;
+            M[q2] = m2;
+            V[q2] = v2;
+        }
     }
 }
 
@@ -475,6 +609,7 @@ GradParams grad_params(const ctf_trainer_s *t) {
     }
     g.xy = nullptr;
     g.n = 0;
+    g.rounds = 1;
     g.step = 0;
     g.k0 = (uint32_t)(t->desc.seed & 0xffffffffu);
     g.k1 = (uint32_t)(t->desc.seed >> 32);
@@ -491,9 +626,16 @@ cudaError_t launch_grad(const GradParams &g, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int ctas = (g.n + kThreads * kRounds - 1) / (kThreads * kRounds);
+    // One CTA per SM fits (shared memory and registers).  A CTA's fixed
+    // costs (weights in, sums out) favour a few rounds each: kMaxRounds once
+    // there are 128 CTAs of them, fewer below.  The split depends on the
+    // batch alone, so a step gives the same sums on any device.
+    GradParams gp = g;
+    gp.rounds = g.n / (kT * 128);
+    gp.rounds = gp.rounds < 1 ? 1 : (gp.rounds > kMaxRounds ? kMaxRounds : gp.rounds);
+    const int ctas = (g.n + kT * gp.rounds - 1) / (kT * gp.rounds);
     if (ctas == 0) return cudaSuccess;
-    grad_kernel<<<ctas, kThreads, kGradSmem, s>>>(g);
+    grad_kernel<<<ctas, kGradThreads, kGradSmem, s>>>(gp);
     return cudaGetLastError();
 }
 
@@ -642,12 +784,13 @@ int ctf_trainer_step(ctf_trainer t, int64_t steps, void *stream) {
         if (e == cudaSuccess) e = launch_grad(g, s);
         const double frac = std::fmin(1.0, (double)st / (double)t->desc.total_steps);
         const double sched = 1.0 - (1.0 - t->desc.lr_final_frac) * frac;
-        a.lr_w = (float)(t->desc.lr_weights * sched);
-        a.lr_lat = (float)(t->desc.lr_latents * sched);
-        a.bc1 = (float)(1.0 - std::pow((double)t->desc.beta1, (double)(st + 1)));
-        a.bc2 = (float)(1.0 - std::pow((double)t->desc.beta2, (double)(st + 1)));
+        const double bc1 = 1.0 - std::pow((double)t->desc.beta1, (double)(st + 1));
+        const double bc2 = 1.0 - std::pow((double)t->desc.beta2, (double)(st + 1));
+        a.step_w = (float)(t->desc.lr_weights * sched / bc1);
+        a.step_lat = (float)(t->desc.lr_latents * sched / bc1);
+        a.inv_bc2 = (float)(1.0 / bc2);
         if (e == cudaSuccess) {
-            adam_kernel<<<2048, 256, 0, s>>>(a);
+            adam_kernel<<<device_sm_count() * 8, 256, 0, s>>>(a);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) return report_cuda(e, "training step");

@@ -46,7 +46,7 @@ def test_gradients_match_fp64_oracle():
         back = _ctf.ctf_trainer_get_params(tr, desc)
         for k in params:
             np.testing.assert_array_equal(back[k], params[k])
-        n = 700  # more than one CTA (512 texels) and a ragged tail
+        n = 700  # several CTAs of 128 texels and a ragged tail
         xs, ys = g.integers(0, Wt, n), g.integers(0, Ht, n)
         xy = torch.from_numpy(np.stack([xs, ys], -1).astype(np.int32)).cuda()
         loss, grads = _ctf.ctf_trainer_gradients(tr, desc, xy, n)
@@ -59,6 +59,74 @@ def test_gradients_match_fp64_oracle():
             assert scale > 0, k
             err = np.abs(grads[k] - ref[k]).max()
             assert err <= 2e-4 * scale + 1e-9, (k, err, scale)
+    finally:
+        _ctf.ctf_trainer_destroy(tr)
+        _ctf.ctf_texture_destroy(tex)
+
+
+def _step_texels(seed, step, batch, Wt, Ht):
+    """Texels a training step samples: Philox4x32-10 of counter (i, step,
+    0x5A4D, 0) under the trainer's seed, scaled to the texture by a 32-bit
+    fixed-point multiply."""
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    r = np.stack([oracle.philox4x32_10((i, step, 0x5A4D, 0), key) for i in range(batch)]).astype(np.uint64)
+    return (r[:, 0] * Wt) >> 32, (r[:, 1] * Ht) >> 32
+
+
+def test_training_steps_follow_adam_on_fp64_gradients():
+    """Two ctf_trainer_step calls against Adam (bias-corrected, learning
+    rate decaying linearly) applied in FP64 to the oracle's gradients of the
+    same sampled texels.  Elements whose gradients are well above the FP32
+    noise must move by the reference update; the rest stay within Adam's
+    step bound."""
+    Wt = Ht = 64
+    blocks = synth.random_blocks(Wt, Ht, seed=22)
+    tex = _ctf.ctf_texture_create(Wt, Ht, blocks)
+    batch, total, seed = 1024, 10, 0x1234_0000_0077
+    lr_w, lr_l, frac, b1, b2, eps = 3e-3, 3e-2, 0.1, 0.9, 0.99, 1e-10
+    desc = _ctf.train_desc(((16, 16), (8, 8)), batch=batch, total_steps=total, lr_weights=lr_w, lr_latents=lr_l,
+                           lr_final_frac=frac, beta1=b1, beta2=b2, eps=eps, seed=seed)
+    tr = _ctf.ctf_trainer_create(tex, desc)
+    try:
+        g = np.random.default_rng(8)
+        p0 = {"lat0": g.normal(0, 0.7, (16, 16, 8)), "lat1": g.normal(0, 0.7, (8, 8, 8)),
+              "w1": g.normal(0, 0.4, (64, 16)), "b1": g.normal(0, 0.1, 64),
+              "w2": g.normal(0, 0.18, (64, 64)), "b2": g.normal(0, 0.1, 64),
+              "w3": g.normal(0, 0.15, (4, 64)), "b3": g.normal(0.5, 0.1, 4)}
+        p0 = {k: v.astype(np.float32) for k, v in p0.items()}
+        _ctf.ctf_trainer_set_params(tr, p0)
+        _ctf.ctf_trainer_step(tr, 2)
+        _ctf.ctf_sync_check()
+        got = _ctf.ctf_trainer_get_params(tr, desc)
+        # the reference: FP64 gradients of the oracle, FP64 Adam
+        p = {k: v.astype(np.float64) for k, v in p0.items()}
+        m = {k: np.zeros_like(v) for k, v in p.items()}
+        v2 = {k: np.zeros_like(v) for k, v in p.items()}
+        grads = []
+        for st in range(2):
+            xs, ys = _step_texels(seed, st, batch, Wt, Ht)
+            mlp = oracle.MLP((p["lat0"], p["lat1"]), p["w1"], p["b1"], p["w2"], p["b2"], p["w3"], p["b3"],
+                             saturate=False)
+            _, gr = oracle.mlp_loss_grad(mlp, Wt, Ht, xs, ys, _decoded(blocks, Wt, Ht, xs, ys))
+            grads.append(gr)
+            sched = 1.0 - (1.0 - frac) * min(1.0, st / total)
+            t = st + 1
+            for k in p:
+                lr = (lr_l if k.startswith("lat") else lr_w) * sched
+                m[k] = b1 * m[k] + (1 - b1) * gr[k]
+                v2[k] = b2 * v2[k] + (1 - b2) * gr[k] ** 2
+                p[k] = p[k] - lr / (1 - b1 ** t) * m[k] / (np.sqrt(v2[k] / (1 - b2 ** t)) + eps)
+        for k in p:
+            lr = lr_l if k.startswith("lat") else lr_w
+            u_ref = p[k] - p0[k]
+            u_gpu = got[k].astype(np.float64) - p0[k]
+            well = np.ones(u_ref.shape, bool)
+            for gr in grads:
+                well &= np.abs(gr[k]) > 1e-2 * np.abs(gr[k]).max()
+            assert well.mean() > 0.3, (k, well.mean())
+            err = np.abs(u_gpu - u_ref)[well].max()
+            assert err <= 2e-3 * lr, (k, err, lr)
+            assert np.abs(u_gpu).max() <= 2.5 * lr, k
     finally:
         _ctf.ctf_trainer_destroy(tr)
         _ctf.ctf_texture_destroy(tex)
