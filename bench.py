@@ -368,8 +368,10 @@ def bench_batch(args, dev, stream, learned_tex, block_tex):
     magnification range inside [0.25, 64] and textures alternating a 2048^2
     block texture and the learned 4096^2 FP16 texture: 64 views of sizes
     uniform in [256, 3840] x [256, 2160], and 256 small views of sizes
-    uniform in [64, 512]^2.  Each set: one autotuned persistent launch per
-    kind replayed from a CUDA graph against sequential ctf_filter calls."""
+    uniform in [64, 512]^2.  Each set: one autotuned batch (its own launch
+    for every view of at least solo_tiles warp tiles, one persistent launch
+    per kind for the rest) replayed from a CUDA graph against sequential
+    ctf_filter calls."""
     out = _bench_batch_set(args, dev, stream, learned_tex, block_tex, 64, {})
     out["small_views"] = _bench_batch_set(args, dev, stream, learned_tex, block_tex, 256,
                                           {"min_w": 64, "min_h": 64, "max_w": 512, "max_h": 512})
@@ -398,6 +400,9 @@ def _bench_batch_set(args, dev, stream, learned_tex, block_tex, n_views, sizes):
     k = max(3, min(args.steps, 10))
     ms_graph = _timed_views(lambda: _ctf.ctf_batch_graph_launch(g, stream=stream), k, 2, None, stream)
     fo = {"tile_w": best.filter.tile_w, "tile_h": best.filter.tile_h, "mask_dim": 11}
+    tw, th = best.filter.tile_w, best.filter.tile_h
+    n_solo = sum(1 for v in views if best.solo_tiles > 0 and
+                 ((v["width"] + tw - 1) // tw) * ((v["height"] + th - 1) // th) >= best.solo_tiles)
 
     def sequential():
         for v in views:
@@ -433,6 +438,7 @@ def _bench_batch_set(args, dev, stream, learned_tex, block_tex, n_views, sizes):
             "pixels": npix, "input_gen_s": gen_s,
             "textures": "2048^2 block / 4096^2 learned FP16 alternating" if learned_tex is not None else "2048^2 block",
             "algorithm": "mask11+stf", "autotuned": best.as_dict(), "autotune_best_ms": tune_ms,
+            "solo_views": n_solo,
             "graph_pixels_per_s": npix / tg, "graph_ms": tg * 1e3,
             "sequential_pixels_per_s": npix / ts, "sequential_ms": ts * 1e3, "graph_vs_sequential": ts / tg,
             "evals_per_pixel": st["texel_evals"] / max(1, st["pixels_active"]), "by_kind": kinds,

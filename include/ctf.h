@@ -338,12 +338,14 @@ int ctf_trainer_load(ctf_texture exact_src, const char *path, ctf_trainer *out);
 int ctf_texture_compare(ctf_texture exact_ref, ctf_texture learned, double *mse_rgb, double *max_abs, void *stream);
 
 /* Batched filtering: many views, each with its own texture (block or
- * learned), size, magnification and buffers, in two persistent launches on
- * the stream, one per kind of texel evaluation (block views first).  Block
- * views: CTAs of 8 warps, every warp takes items of 32 warp tiles from an
- * atomic counter.  Learned views: CTAs of 4 warps that keep their tensor
- * memory for the whole launch take items of 4 warp tiles (one per warp,
- * sharing an MLP chain), items_per_fetch at a time.  Every view is filtered
+ * learned), size, magnification and buffers.  Views of at least solo_tiles
+ * warp tiles run as their own launches of the single-view kernels (they fill
+ * the GPU alone); the others share two persistent launches on the stream,
+ * one per kind of texel evaluation (block views first).  Block views: CTAs
+ * of 8 warps, every warp takes items of 32 warp tiles from an atomic
+ * counter.  Learned views: CTAs of 4 warps that keep their tensor memory
+ * for the whole launch take items of 8 warp tiles (4 for per-pixel 4-tap)
+ * that share MLP chains, items_per_fetch at a time.  Every view is filtered
  * exactly as ctf_filter would filter it with the same options. */
 typedef struct {
     ctf_texture tex;            /* block or learned-decode texture */
@@ -359,11 +361,14 @@ typedef struct {
  *   filter           tile shape, budget, mask_dim, edge_remap (as ctf_filter)
  *   items_per_fetch  learned views: items taken per fetch, 1..64      [4]
  *   ctas_per_sm      learned views: persistent CTAs per SM, 1..4       [4]
+ *   solo_tiles       views of at least this many warp tiles get their own
+ *                    launch; 0: every view in the persistent launches [16384]
  * (the block-view launch always fills every SM to its occupancy limit). */
 typedef struct {
     ctf_filter_opts filter;
     int items_per_fetch;
     int ctas_per_sm;
+    int solo_tiles;
 } ctf_batch_opts;
 
 /* Filter nviews (1..4096) views in one launch (asynchronous unless stats is
@@ -371,8 +376,9 @@ typedef struct {
 int ctf_filter_batch(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t seed, const ctf_batch_opts *opts,
                      ctf_stats *stats, void *stream);
 
-/* The same batch captured once into a CUDA graph (counter reset and both
- * persistent launches) and replayed with ctf_batch_graph_launch.  The views'
+/* The same batch captured once into a CUDA graph (the solo launches, the
+ * counter reset and both persistent launches) and replayed with
+ * ctf_batch_graph_launch.  The views'
  * buffers are baked in: they must stay valid and at the same addresses. */
 typedef struct ctf_batch_graph_s *ctf_batch_graph;
 int ctf_batch_graph_create(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t seed,
@@ -381,8 +387,9 @@ int ctf_batch_graph_launch(ctf_batch_graph g, void *stream);
 int ctf_batch_graph_destroy(ctf_batch_graph g);
 
 /* Time every warp tile (8x4, 4x8, 16x2) x items_per_fetch (1, 2, 4, 8) x
- * ctas_per_sm (2, 4) on these views (best of 3 runs each, CUDA events on the
- * stream) and return the fastest in *best (budget, mask_dim and edge_remap
+ * ctas_per_sm (2, 4) on these views, then solo_tiles (0, 4096, 16384,
+ * 65536) at the best of those (best of 3 runs each, CUDA events on the
+ * stream), and return the fastest in *best (budget, mask_dim and edge_remap
  * from *base, or the defaults).  Note that the warp tile changes which
  * warps succeed, hence the texel choices: every tile shape is a valid
  * filtering, and results are reproducible for a fixed shape. */

@@ -420,7 +420,8 @@ class ctf_view(ctypes.Structure):
 
 
 class ctf_batch_opts(ctypes.Structure):
-    _fields_ = [("filter", ctf_filter_opts), ("items_per_fetch", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+    _fields_ = [("filter", ctf_filter_opts), ("items_per_fetch", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("solo_tiles", ctypes.c_int)]
 
     def as_dict(self):
         f = self.filter
@@ -428,14 +429,14 @@ class ctf_batch_opts(ctypes.Structure):
                 "edge_remap": f.edge_remap, "group_dedup": f.group_dedup, "fallback": f.fallback,
                 "texels_per_lane": f.texels_per_lane,
                 "items_per_fetch": self.items_per_fetch,
-                "ctas_per_sm": self.ctas_per_sm}
+                "ctas_per_sm": self.ctas_per_sm, "solo_tiles": self.solo_tiles}
 
 
 def batch_opts(tile_w=8, tile_h=4, budget=32, mask_dim=16, edge_remap=1, items_per_fetch=4, ctas_per_sm=4,
-               group_dedup=0, fallback=0, texels_per_lane=1):
+               group_dedup=0, fallback=0, texels_per_lane=1, solo_tiles=16384):
     o = ctf_batch_opts()
     o.filter = ctf_filter_opts(tile_w, tile_h, budget, mask_dim, edge_remap, group_dedup, fallback, texels_per_lane)
-    o.items_per_fetch, o.ctas_per_sm = items_per_fetch, ctas_per_sm
+    o.items_per_fetch, o.ctas_per_sm, o.solo_tiles = items_per_fetch, ctas_per_sm, solo_tiles
     return o
 
 

@@ -1,6 +1,9 @@
 // ctf_batch.cu -- many views of uneven size and magnification in two
 // persistent launches (one per kind of texel evaluation), optionally captured
 // together into one CUDA graph, with an autotuner over the launch shape.
+// Views large enough to fill the GPU alone (solo_tiles) are launched on
+// their own with the single-view kernels, which then lose nothing to the
+// persistent kernels' per-item view bookkeeping.
 //
 // Block views: persistent CTAs of 8 warps, like the per-view exact kernel;
 // every warp takes items of 32 consecutive warp tiles of one view from an
@@ -324,6 +327,7 @@ struct ResolvedBatch {
     int tile_w = 8, tile_h = 4, budget = 32, mask_dim = 16, edge_remap = 1, group_dedup = 0, fallback = 0;
     int tpl = 1;
     int items_per_fetch = 4, ctas_per_sm = 4;
+    int solo_tiles = 16384;
 };
 
 int resolve(const ctf_batch_opts *o, ResolvedBatch *r) {
@@ -340,6 +344,7 @@ int resolve(const ctf_batch_opts *o, ResolvedBatch *r) {
     if (o->filter.filter != 0) return report(CTF_ERR_UNSUPPORTED, "batches take the bilinear filter only");
     r->items_per_fetch = o->items_per_fetch;
     r->ctas_per_sm = o->ctas_per_sm;
+    r->solo_tiles = o->solo_tiles;
     const bool shape_ok = (r->tile_w == 8 && r->tile_h == 4) || (r->tile_w == 4 && r->tile_h == 8) ||
                           (r->tile_w == 16 && r->tile_h == 2);
     if (!shape_ok) return report(CTF_ERR_ARG, "tile %dx%d not one of 8x4, 4x8, 16x2", r->tile_w, r->tile_h);
@@ -353,15 +358,17 @@ int resolve(const ctf_batch_opts *o, ResolvedBatch *r) {
     if (r->items_per_fetch < 1 || r->items_per_fetch > 64)
         return report(CTF_ERR_ARG, "items_per_fetch %d outside [1, 64]", r->items_per_fetch);
     if (r->ctas_per_sm < 1 || r->ctas_per_sm > 4) return report(CTF_ERR_ARG, "ctas_per_sm %d outside [1, 4]", r->ctas_per_sm);
+    if (r->solo_tiles < 0) return report(CTF_ERR_ARG, "solo_tiles %d is negative", r->solo_tiles);
     return CTF_OK;
 }
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-// Host-side plan of a batch: the device view table and, per kind, the view
-// indices and item prefix.
+// Host-side plan of a batch: the device view table, the views launched on
+// their own, and, per kind, the other views' indices and item prefix.
 struct Plan {
     std::vector<BatchViewDev> views;
+    std::vector<int> solo;
     std::vector<int> index[2];           // [0] block views, [1] learned views
     std::vector<long long> begin[2];
     long long items[2] = {0, 0};
@@ -411,6 +418,10 @@ int make_plan(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t see
             return report(CTF_ERR_UNSUPPORTED,
                           "view %d: fallbacks C and C+ and two texels per lane are built for block textures only", i);
         if (d.learned) d.m = mlp_device_view(v.tex);
+        if (r.solo_tiles > 0 && p.n_tiles >= r.solo_tiles) {
+            plan->solo.push_back(i);
+            continue;
+        }
         const int kind = d.learned ? 1 : 0;
         const long long per_item = d.learned ? mlp_group_tiles((int)alg) : kBlockItemTiles;
         plan->index[kind].push_back(i);
@@ -473,10 +484,19 @@ cudaError_t upload_plan(const Plan &plan, DevPlan *dp, cudaStream_t s) {
     return e;
 }
 
-// Counter reset, then the block-view kernel, then the learned-view kernel,
-// all on stream s (so a capture of s records the whole batch).
+// The solo views (the single-view kernels), the counter reset, then the
+// block-view kernel, then the learned-view kernel, all on stream s (so a
+// capture of s records the whole batch).
 cudaError_t launch_plan(const Plan &plan, const DevPlan &dp, int alg, const ResolvedBatch &r,
                         unsigned long long *stats, int *err, cudaStream_t s) {
+    for (int i : plan.solo) {
+        ExactParams p = plan.views[i].p;
+        p.stats = stats;
+        const cudaError_t le = plan.views[i].learned
+                                   ? launch_mlp_filter(p, plan.views[i].m, alg, r.tile_w, r.mask_dim, err, s)
+                                   : launch_exact_filter(p, alg, r.tile_w, r.mask_dim, s);
+        if (le != cudaSuccess) return le;
+    }
     cudaError_t e = cudaMemsetAsync(dp.counter, 0, 16, s);
     if (e != cudaSuccess) return e;
     for (int k = 0; k < 2; ++k) {
@@ -594,8 +614,10 @@ int ctf_batch_graph_create(const ctf_view *views, int nviews, ctf_algorithm alg,
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = upload_plan(plan, &g->plan, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    // the kernel attribute must be set before capture
+    // the kernel attributes must be set before capture
     if (e == cudaSuccess && plan.items[1]) e = prepare_batch(pick(true, (int)alg, r.tile_w, r.mask_dim, false));
+    for (int i : plan.solo)
+        if (e == cudaSuccess && plan.views[i].learned) e = prepare_mlp_filter((int)alg, r.tile_w, r.mask_dim);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t le = launch_plan(plan, g->plan, (int)alg, r, nullptr, err, s);
@@ -655,6 +677,7 @@ int ctf_batch_autotune(const ctf_view *views, int nviews, ctf_algorithm alg, uin
         b0.filter.filter = 0;
         b0.items_per_fetch = 4;
         b0.ctas_per_sm = 4;
+        b0.solo_tiles = 16384;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -663,9 +686,27 @@ int ctf_batch_autotune(const ctf_view *views, int nviews, ctf_algorithm alg, uin
     const int shapes[3][2] = {{8, 4}, {4, 8}, {16, 2}};
     const int fetches[4] = {1, 2, 4, 8};
     const int ctas[2] = {2, 4};
+    const int solos[4] = {0, 4096, 16384, 65536};
     double bestt = 1e30;
     ctf_batch_opts bestc = b0;
     int rc = CTF_OK;
+    auto time_config = [&](const ctf_batch_opts &c) {
+        rc = ctf_filter_batch(views, nviews, alg, seed, &c, nullptr, stream);  // warm-up
+        float best_run = 1e30f;
+        for (int rep = 0; rep < 3 && !rc; ++rep) {
+            cudaEventRecord(e0, s);
+            rc = ctf_filter_batch(views, nviews, alg, seed, &c, nullptr, stream);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best_run = std::min(best_run, ms);
+        }
+        if (!rc && best_run < bestt) {
+            bestt = best_run;
+            bestc = c;
+        }
+    };
     for (int si = 0; si < 3 && !rc; ++si)
         for (int fi = 0; fi < 4 && !rc; ++fi)
             for (int ci = 0; ci < 2 && !rc; ++ci) {
@@ -674,23 +715,15 @@ int ctf_batch_autotune(const ctf_view *views, int nviews, ctf_algorithm alg, uin
                 c.filter.tile_h = shapes[si][1];
                 c.items_per_fetch = fetches[fi];
                 c.ctas_per_sm = ctas[ci];
-                rc = ctf_filter_batch(views, nviews, alg, seed, &c, nullptr, stream);  // warm-up
-                if (rc) break;
-                float best_run = 1e30f;
-                for (int rep = 0; rep < 3 && !rc; ++rep) {
-                    cudaEventRecord(e0, s);
-                    rc = ctf_filter_batch(views, nviews, alg, seed, &c, nullptr, stream);
-                    cudaEventRecord(e1, s);
-                    cudaEventSynchronize(e1);
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    best_run = std::min(best_run, ms);
-                }
-                if (!rc && best_run < bestt) {
-                    bestt = best_run;
-                    bestc = c;
-                }
+                time_config(c);
             }
+    const ctf_batch_opts shaped = bestc;
+    for (int k = 0; k < 4 && !rc; ++k) {
+        if (solos[k] == shaped.solo_tiles) continue;
+        ctf_batch_opts c = shaped;
+        c.solo_tiles = solos[k];
+        time_config(c);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;

@@ -98,6 +98,9 @@ const DecodeTables *device_decode_tables();
 // Learned decode (ctf_mlp.cu).
 cudaError_t launch_mlp_decode(const MlpDevice &m, int Wt, int Ht, const int2 *xy, int n, float4 *out, int *err,
                               cudaStream_t stream);
+// Sets the learned filter kernel's attributes without launching it (needed
+// before a stream capture records a launch of it).
+cudaError_t prepare_mlp_filter(int alg, int tile_w, int mask_dim);
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                               cudaStream_t stream);
 MlpDevice mlp_device_view(const ctf_texture_s *t);

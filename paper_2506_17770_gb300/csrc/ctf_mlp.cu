@@ -160,6 +160,17 @@ cudaError_t launch_mlp_decode(const MlpDevice &m, int Wt, int Ht, const int2 *xy
     return cudaGetLastError();
 }
 
+cudaError_t prepare_mlp_filter(int alg, int tile_w, int mask_dim) {
+    FilterFn fn = nullptr;
+    switch (tile_w) {
+    case 8: fn = pick_alg<8>(alg, mask_dim); break;
+    case 4: fn = pick_alg<4>(alg, mask_dim); break;
+    case 16: fn = pick_alg<16>(alg, mask_dim); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return fn ? prepare(fn) : cudaErrorInvalidValue;
+}
+
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                               cudaStream_t stream) {
     FilterFn fn = nullptr;

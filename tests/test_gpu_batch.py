@@ -150,6 +150,7 @@ def test_autotune_picks_a_consistent_configuration(textures):
     d = best.as_dict()
     assert (d["tile_w"], d["tile_h"]) in ((8, 4), (4, 8), (16, 2))
     assert d["items_per_fetch"] in (1, 2, 4, 8) and d["ctas_per_sm"] in (2, 4) and ms > 0
+    assert d["solo_tiles"] in (0, 4096, 16384, 65536)
     _ctf.ctf_filter_batch(views, "box", 1, best)
     _ctf.ctf_sync_check()
     fopts = {"tile_w": d["tile_w"], "tile_h": d["tile_h"]}
@@ -194,3 +195,42 @@ def test_batch_fallback_cplus_equals_per_view_calls(textures):
     lv = [v for v in _make_views(textures, n=4, seed=23) if v["kind"] != "block"][:1]
     with pytest.raises(_ctf.CtfError):
         _ctf.ctf_filter_batch(lv, "mask", 5, o)
+
+
+@pytest.mark.parametrize("solo", [1, 400])
+def test_batch_solo_views_equal_per_view_calls(textures, solo):
+    """Views of at least solo_tiles warp tiles run as their own launches of
+    the single-view kernels, the others in the persistent launches: every
+    view and the summed counters equal per-view calls either way, directly
+    and replayed from a graph (solo 400 puts a learned and two block views
+    on their own here)."""
+    views = _make_views(textures, n=9, seed=19)
+    tiles = [((v["width"] + 7) // 8) * ((v["height"] + 3) // 4) for v in views]
+    alone = [t >= solo for t in tiles]
+    assert any(alone) and (solo == 1 or not all(alone))
+    o = _ctf.batch_opts(tile_w=8, tile_h=4, mask_dim=11, items_per_fetch=2, ctas_per_sm=4, solo_tiles=solo)
+    st = _ctf.ctf_filter_batch(views, "mask", 9, o, stats=True)
+    _ctf.ctf_sync_check()
+    fopts = {"tile_w": 8, "tile_h": 4, "mask_dim": 11}
+    singles, refs = [], []
+    for v in views:
+        ref, ref_ev, ref_st = _single(v, "mask", 9, fopts)
+        singles.append(ref_st)
+        refs.append((ref, ref_ev))
+        H, W = v["height"], v["width"]
+        assert np.array_equal(v["out_rgba"].cpu().numpy()[:H, :W].view(np.uint32), ref[:H, :W].view(np.uint32))
+        assert np.array_equal(v["out_evals"].cpu().numpy()[:H, :W], ref_ev[:H, :W])
+    assert st == _sum_stats(singles)
+    for v in views:
+        v["out_rgba"].fill_(-1.0)
+        v["out_evals"].fill_(7)
+    g = _ctf.ctf_batch_graph_create(views, "mask", 9, o)
+    try:
+        _ctf.ctf_batch_graph_launch(g)
+        _ctf.ctf_sync_check()
+    finally:
+        _ctf.ctf_batch_graph_destroy(g)
+    for v, (ref, ref_ev) in zip(views, refs):
+        H, W = v["height"], v["width"]
+        assert np.array_equal(v["out_rgba"].cpu().numpy()[:H, :W].view(np.uint32), ref[:H, :W].view(np.uint32))
+        assert np.array_equal(v["out_evals"].cpu().numpy()[:H, :W], ref_ev[:H, :W])
