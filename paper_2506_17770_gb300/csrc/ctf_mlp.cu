@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kRows) mlp_decode_kernel(const MlpDevice m, in
 // Learned-decode filter: 4 warps, one pixel tile each per iteration.
 // ---------------------------------------------------------------------------
 template <int ALG, int TW, int MD>
-__global__ void __launch_bounds__(kRows) mlp_filter_kernel(const ExactParams p, const MlpDevice m, int *err) {
+__global__ void __launch_bounds__(kRows, 4) mlp_filter_kernel(const ExactParams p, const MlpDevice m, int *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned long long block_stats[kNumStats];
     Chain ch;
@@ -91,12 +91,18 @@ __global__ void __launch_bounds__(kRows) mlp_filter_kernel(const ExactParams p, 
 #pragma unroll
     for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
     constexpr int kTiles = mlp_group_tiles(ALG);
+    // the collaborative algorithms other than List Merge stage the next
+    // group's pixel inputs in shared memory while a group runs
+    constexpr bool kStaged = ALG != ALG_4TAP && ALG != ALG_LIST;
     const long long n_iter = (p.n_tiles + kTiles - 1) / kTiles;
+    if (kStaged && blockIdx.x < n_iter) stage_group<ALG, TW>(p, (long long)blockIdx.x * kTiles, sm);
     bool ok = true;
     for (long long it = blockIdx.x; it < n_iter && ok; it += gridDim.x) {
+        const long long next = it + gridDim.x < n_iter ? (it + gridDim.x) * kTiles : -1;
         if (ALG == ALG_4TAP) ok = mlp_warp_tile<ALG, TW, MD>(p, m, ch, it * kTiles + warp, lane, lt, T, cnt, inv_a1, err);
-        else ok = mlp_group<ALG, TW, MD>(p, m, ch, it * kTiles, lane, lt, T, cnt, inv_a1, err);
+        else ok = mlp_group<ALG, TW, MD, kStaged>(p, m, ch, it * kTiles, lane, lt, T, cnt, inv_a1, err, next);
     }
+    if (kStaged) cp_async_wait_all();  // no copy outlives the kernel (a failed chain leaves early)
     if (p.stats) {
         if (lane == 0) {
 #pragma unroll
@@ -182,6 +188,7 @@ cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg,
     }
     if (!fn) return cudaErrorInvalidValue;
     if (p.n_tiles == 0) return cudaSuccess;
+    if (p.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile positions use 32-bit arithmetic
     cudaError_t e = prepare(fn);
     if (e != cudaSuccess) return e;
     const long long iters = (p.n_tiles + mlp_group_tiles(alg) - 1) / mlp_group_tiles(alg);

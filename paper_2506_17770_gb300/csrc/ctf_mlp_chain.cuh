@@ -45,6 +45,14 @@ constexpr int kSmTexList = kSmX;                      // 8 tiles x 32 x int2 (2 
 constexpr int kSmHashKey = kSmH;                      // 512 x u64
 constexpr int kSmHashRow = kSmH + 512 * 8;            // 512 x u8
 constexpr int kSmBytes = kSmNUnique + 16;
+// Pixel inputs of the next group, copied in with cp.async while the current
+// group runs (single-view filter; not for List Merge, whose hash tables use
+// the same space): uv, Jacobian, and the aligned 32-bit word that holds the
+// pixel's coverage byte.
+constexpr int kSmStageUV = kSmList;                 // 256 x float2
+constexpr int kSmStageJac = kSmStageUV + 256 * 8;   // 256 x float4
+constexpr int kSmStageCov = kSmStageJac + 256 * 16;  // 256 x u32
+static_assert(kSmStageCov + 256 * 4 <= kSmRanks, "staging fits in the List Merge tables");
 // Reserve enough shared memory that at most 4 CTAs share an SM: 4 x 128 TMEM
 // columns fill the SM's 512 (5 x 54 KB exceed the SM's 228 KB).
 constexpr int kSmRequest = 54 * 1024;
@@ -62,6 +70,90 @@ struct Chain {
     uint64_t *bar;
     uint32_t phase;
 };
+
+// Position of tile first + g (0 <= g < 8) from the position of `first`: one
+// 32-bit division per group instead of a 64-bit division per tile and phase
+// (a view has fewer than 2^31 tiles).
+struct TilePos {
+    uint32_t bx0, by0, tiles_x;
+};
+
+__device__ __forceinline__ TilePos tile_pos0(const ExactParams &p, long long first) {
+    TilePos t;
+    t.tiles_x = (uint32_t)p.tiles_x;
+    const uint32_t f = (uint32_t)first;
+    t.by0 = f / t.tiles_x;
+    t.bx0 = f - t.by0 * t.tiles_x;
+    return t;
+}
+
+__device__ __forceinline__ void tile_pos(const TilePos &t, int g, int &bx, int &by) {
+    uint32_t x = t.bx0 + (uint32_t)g, y = t.by0;
+    while (x >= t.tiles_x) {
+        x -= t.tiles_x;
+        ++y;
+    }
+    bx = (int)x;
+    by = (int)y;
+}
+
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// Asynchronous global -> shared copies of 4, 8 or 16 bytes (both addresses
+// aligned to the size), with the evict-first L2 policy of streamed pixels.
+template <int N>
+__device__ __forceinline__ void cp_async(void *dst, const void *src, uint64_t pol) {
+    const uint32_t d = tc::smem_addr(dst);
+    if constexpr (N == 16)
+        asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "l"(pol)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(N),
+                     "l"(pol)
+                     : "memory");
+}
+
+// The 4-byte-aligned word that holds coverage byte idx, when the whole word
+// lies inside the coverage array (else 0: the byte is read directly).
+__device__ __forceinline__ const uint32_t *cov_word(const ExactParams &p, uint32_t idx) {
+    const uintptr_t b = reinterpret_cast<uintptr_t>(p.cov), a = (b + idx) & ~(uintptr_t)3;
+    const uintptr_t end = b + (uintptr_t)p.W * (uintptr_t)p.H;
+    return a >= b && a + 4 <= end ? reinterpret_cast<const uint32_t *>(a) : nullptr;
+}
+
+// Issue the copies of the pixel inputs of group `first` (slots 4h + warp,
+// one lane per pixel, as step 1 reads them) into the staging buffers.
+template <int ALG, int TW>
+__device__ __forceinline__ void stage_group(const ExactParams &p, long long first, unsigned char *sm) {
+    constexpr int TH = 32 / TW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tx = lane % TW, ty = lane / TW;
+    const uint64_t pol = evict_first_policy();
+    const TilePos tp = tile_pos0(p, first);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int g = 4 * h + warp, e = 32 * g + lane;
+        const long long tile = first + g;
+        if (tile >= p.n_tiles) continue;
+        int bx, by;
+        tile_pos(tp, g, bx, by);
+        const int px = bx * TW + tx, py = by * TH + ty;
+        if (px >= p.W || py >= p.H) continue;
+        const uint32_t idx = (uint32_t)py * (uint32_t)p.W + (uint32_t)px;
+        cp_async<8>(sm + kSmStageUV + 8 * e, p.uv + idx, pol);
+        if (ALG >= ALG_LIST) cp_async<16>(sm + kSmStageJac + 16 * e, p.jac + idx, pol);
+        if (p.cov) {
+            const uint32_t *w = cov_word(p, idx);
+            if (w) cp_async<4>(sm + kSmStageCov + 4 * e, w, pol);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Features of texel (x, y) (inside the texture) in FP32.
 __device__ __forceinline__ void texel_features(const MlpDevice &m, int x, int y, float f[kMlpIn]) {
@@ -247,6 +339,7 @@ __device__ __forceinline__ bool mlp_chain(Chain &ch, bool fp8, float4 &out, int 
         tc::commit(ch.bar);
     }
     timed_out |= !tc::mbar_wait(ch.bar, ch.phase, kMaxTries);
+    __syncwarp();  // the lanes may leave the wait apart; tcgen05.ld needs the whole warp
     ch.phase ^= 1u;
     tc::fence_after_sync();
     hidden_epilogue(sm, lane_base + 0, b1, s1, a2, fp8, tid);
@@ -268,6 +361,7 @@ __device__ __forceinline__ bool mlp_chain(Chain &ch, bool fp8, float4 &out, int 
         tc::commit(ch.bar);
     }
     timed_out |= !tc::mbar_wait(ch.bar, ch.phase, kMaxTries);
+    __syncwarp();  // the lanes may leave the wait apart; tcgen05.ld needs the whole warp
     ch.phase ^= 1u;
     tc::fence_after_sync();
     // the layer-2 MMAs have read H1, so H2 may overwrite it
@@ -290,6 +384,7 @@ __device__ __forceinline__ bool mlp_chain(Chain &ch, bool fp8, float4 &out, int 
         tc::commit(ch.bar);
     }
     timed_out |= !tc::mbar_wait(ch.bar, ch.phase, kMaxTries);
+    __syncwarp();  // the lanes may leave the wait apart; tcgen05.ld needs the whole warp
     ch.phase ^= 1u;
     tc::fence_after_sync();
     float d[16];
@@ -340,6 +435,7 @@ __device__ __forceinline__ void chain_teardown(const Chain &ch) {
     tc::fence_before_sync();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
+        __syncwarp();  // tcgen05.dealloc needs the whole warp
         tc::fence_after_sync();
         tc::tmem_dealloc(ch.tmem, kTmemCols);
     }
@@ -360,7 +456,8 @@ __device__ __forceinline__ bool mlp_warp_tile(const ExactParams &p, const MlpDev
     const float fW = (float)p.Wt, fH = (float)p.Ht;
     bool ok = true;
     const bool valid = tile < p.n_tiles;
-    const int bx = valid ? (int)(tile % p.tiles_x) : 0, by = valid ? (int)(tile / p.tiles_x) : 0;
+    const uint32_t t32 = (uint32_t)tile, tiles_x = (uint32_t)p.tiles_x;  // fewer than 2^31 tiles
+    const int by = valid ? (int)(t32 / tiles_x) : 0, bx = valid ? (int)(t32 - (uint32_t)by * tiles_x) : 0;
     const int px = bx * TW + tx, py = by * TH + ty;
     const bool inside = valid && px < p.W && py < p.H;
     const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
@@ -489,10 +586,13 @@ __device__ __forceinline__ bool mlp_warp_tile(const ExactParams &p, const MlpDev
 // group), and every pixel then gathers its taps from the rows.  Which thread
 // computes a texel does not change its value: the rows of an MMA are
 // independent.  Returns false (for every thread alike) if a chain gave up.
-template <int ALG, int TW, int MD>
+// With kStaged the group's pixel inputs were staged by stage_group, and the
+// inputs of group `next` (if not negative) are staged while this one runs.
+template <int ALG, int TW, int MD, bool kStaged = false>
 __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice &m, Chain &ch, long long first,
                                           int lane, uint32_t lt, ListTable *T, Counters &cnt, const float *inv_a1,
-                                          int *err) {
+                                          int *err, long long next = -1) {
+    static_assert(!kStaged || ALG != ALG_LIST, "List Merge keeps its tables where the staging buffers are");
     constexpr int TH = 32 / TW;
     unsigned char *sm = ch.sm;
     const int warp = threadIdx.x >> 5, tx = lane % TW, ty = lane / TW;
@@ -508,19 +608,35 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
     // texlist[32 g + rank], and each pixel keeps (s, t) and a packed word:
     // bits 0-19 the list indices of its 4 taps (success) or of its own texel
     // (bits 0-4, fallback), 20-22 its count, 23 active, 24 inside, 25 success.
+    if (kStaged) cp_async_wait_all();  // this thread's own copies
+    const TilePos tp = tile_pos0(p, first);
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
         const int g = 4 * h + warp;
         const long long tile = first + g;
         const bool valid = tile < p.n_tiles;
-        const int bx = valid ? (int)(tile % p.tiles_x) : 0, by = valid ? (int)(tile / p.tiles_x) : 0;
+        int bx = 0, by = 0;
+        if (valid) tile_pos(tp, g, bx, by);
         const int px = bx * TW + tx, py = by * TH + ty;
         const bool inside = valid && px < p.W && py < p.H;
         const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
         float2 uv = make_float2(0.f, 0.f);
         float4 jac = make_float4(0.f, 0.f, 0.f, 0.f);
         bool covered = inside;
-        if (inside) {
+        if (inside && kStaged) {
+            const int e = 32 * g + lane;
+            uv = *reinterpret_cast<const float2 *>(sm + kSmStageUV + 8 * e);
+            if (ALG >= ALG_LIST) jac = *reinterpret_cast<const float4 *>(sm + kSmStageJac + 16 * e);
+            if (p.cov) {
+                if (cov_word(p, idx)) {
+                    const uint32_t w = *reinterpret_cast<const uint32_t *>(sm + kSmStageCov + 4 * e);
+                    const uint32_t sh = 8u * (uint32_t)(reinterpret_cast<uintptr_t>(p.cov + idx) & 3);
+                    covered = ((w >> sh) & 0xffu) != 0;
+                } else {
+                    covered = __ldcs(p.cov + idx) != 0;
+                }
+            }
+        } else if (inside) {
             uv = __ldcs(p.uv + idx);
             if (ALG >= ALG_LIST) jac = __ldcs(p.jac + idx);
             if (p.cov) covered = __ldcs(p.cov + idx) != 0;
@@ -553,6 +669,9 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
         pix_st[32 * g + lane] = make_float2(ps.s, ps.t);
         pix_info[32 * g + lane] = info;
     }
+    // the staged inputs have been read (by the thread that copied them):
+    // the next group's copies overlap everything below
+    if (kStaged && next >= 0) stage_group<ALG, TW>(p, next, sm);
     __syncthreads();
 
     // ---- rows.  Without group_dedup slot g owns rows [base_g, base_g +
@@ -674,8 +793,8 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
         const int g = 4 * h + warp;
         const uint32_t info = pix_info[32 * g + lane];
         if (!((info >> 24) & 1u)) continue;  // outside the frame (or no tile)
-        const long long tile = first + g;
-        const int bx = (int)(tile % p.tiles_x), by = (int)(tile / p.tiles_x);
+        int bx, by;
+        tile_pos(tp, g, bx, by);
         const uint32_t idx = (uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx);
         const int b = h == 0 ? my_base[0] : my_base[1];
         const bool dedup = p.group_dedup != 0;

@@ -235,3 +235,34 @@ def test_learned_textures_refuse_fallback_c(tex64):
     uv, jac, cov = _scene(37, 21, 12)
     with pytest.raises(_ctf.CtfError):
         gpu_filter(tex64, uv, jac, cov, "mask", {"fallback": 1})
+
+
+@pytest.mark.parametrize("alg", ["stf", "box", "mask"])
+def test_staged_inputs_equal_the_batch_kernel(tex64, alg):
+    """The single-view learned filter copies each next group's pixel inputs
+    (uv, Jacobian, the coverage word) into shared memory with cp.async while
+    a group runs; the persistent batch kernel reads them directly.  On a
+    ragged view of several groups per CTA, with a band of uncovered pixels
+    (groups with no texel to evaluate) and the coverage array at an odd byte
+    offset, both give the same image and counts."""
+    W, H = 1283, 797
+    uv, jac, cov = _scene(W, H, 21)
+    cov[:, :300] = 0
+    big = torch.zeros(W * H + 8, dtype=torch.uint8, device="cuda")
+    big[3:3 + W * H] = torch.from_numpy(cov.reshape(-1)).cuda()
+    d_cov = big[3:3 + W * H].view(H, W)
+    d_uv, d_jac = torch.from_numpy(uv).cuda(), torch.from_numpy(jac).cuda()
+    out = torch.full((H, W, 4), -3.0, device="cuda")
+    ev = torch.full((H, W), 77, dtype=torch.uint8, device="cuda")
+    st = _ctf.ctf_filter(tex64.h, d_uv, d_jac, d_cov, W, H, 5, alg, 9, {"mask_dim": 11}, out, ev, stats=True)
+    view = {"tex": tex64.h, "uv": d_uv, "jac": d_jac, "coverage": d_cov, "width": W, "height": H, "view_id": 5,
+            "out_rgba": torch.full((H, W, 4), -1.0, device="cuda"),
+            "out_evals": torch.full((H, W), 7, dtype=torch.uint8, device="cuda")}
+    o = _ctf.batch_opts(mask_dim=11, solo_tiles=0)
+    stb = _ctf.ctf_filter_batch([view], alg, 9, o, stats=True)
+    _ctf.ctf_sync_check()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), view["out_rgba"].cpu().numpy().view(np.uint32))
+    np.testing.assert_array_equal(ev.cpu().numpy(), view["out_evals"].cpu().numpy())
+    assert st == stb
+    assert st["pixels_active"] == int(cov.sum())
+    assert st["tiles_empty"] >= 300 // 8 * (H // 4)
