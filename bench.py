@@ -60,8 +60,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="headline only (for profiling)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-decode workload")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-views workload")
-    ap.add_argument("--train-steps", type=int, default=2048, help="training steps (learned)")
-    ap.add_argument("--train-batch", type=int, default=32768, help="texels per training step (learned)")
+    ap.add_argument("--train-steps", type=int, default=8192, help="training steps (learned)")
+    ap.add_argument("--train-batch", type=int, default=8192, help="texels per training step (learned)")
     return ap.parse_args()
 
 
@@ -249,7 +249,7 @@ def bench_learned(args, dev, stream, flush, peaks):
     gradient noise + checker edges), block-encoded, learned by the library's
     trainer into two latent grids (1024^2, 512^2, 8 ch) and a 16-64-64-4 MLP
     from texels of its exact decode (`--train-steps` x `--train-batch`
-    texels, 2048 x 32768 = 64M by default); then a 3840x2160 view
+    texels, 8192 x 8192 = 64M by default); then a 3840x2160 view
     with magnification log-uniform in [1, 16] filtered with the learned
     decode (FP16 and FP8) by per-pixel 4-tap and the collaborative
     algorithms."""
@@ -264,8 +264,8 @@ def bench_learned(args, dev, stream, flush, peaks):
     res["input_gen_s"] = time.perf_counter() - t0
     exact = _ctf.ctf_texture_create(4096, 4096, blocks)
     steps, batch = args.train_steps, args.train_batch
-    desc = _ctf.train_desc(((1024, 1024), (512, 512)), batch=batch, total_steps=steps, lr_weights=2e-2,
-                           lr_latents=2e-1, lr_final_frac=0.05, seed=3)
+    desc = _ctf.train_desc(((1024, 1024), (512, 512)), batch=batch, total_steps=steps, lr_weights=1e-2,
+                           lr_latents=1e-1, lr_final_frac=0.02, seed=3)
     tr = _ctf.ctf_trainer_create(exact, desc)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -274,7 +274,7 @@ def bench_learned(args, dev, stream, flush, peaks):
     train_s = time.perf_counter() - t0
     res["training"] = {"steps": steps, "batch": batch, "texels": steps * batch, "seconds": train_s,
                        "texels_per_s": steps * batch / train_s,
-                       "schedule": "Adam, lr 2e-2 (weights) / 2e-1 (latents), linear decay to 5% over all steps"}
+                       "schedule": "Adam, lr 1e-2 (weights) / 1e-1 (latents), linear decay to 2% over all steps"}
     texs = {"fp16": _ctf.ctf_trainer_export(tr, _ctf.CTF_EVAL_MLP_FP16),
             "fp8": _ctf.ctf_trainer_export(tr, _ctf.CTF_EVAL_MLP_FP8)}
     for k, t in texs.items():
