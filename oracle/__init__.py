@@ -63,12 +63,13 @@ def _load():
             lib.oracle_decode_rgba8.argtypes = [P, i32, i32, i32, i32, P]
             lib.oracle_stf_offset.argtypes = [i32, i32, i32, u64, ctypes.c_float, ctypes.c_float, P, P]
             lib.oracle_filter.argtypes = [P, i32, i32, P, P, P, i32, i32, i32, i32, u64, i32, i32, i32,
-                                          i32, i32, i32, i32, i32, i32, P, P, P, P, P]
+                                          i32, i32, i32, i32, i32, i32, i32, P, P, P, P, P]
             lib.oracle_filter.restype = i32
             lib.oracle_cplus_source.argtypes = [i32, i32, i32]
             lib.oracle_cplus_source.restype = i32
             lib.oracle_filter_learned_f64.argtypes = [P, i32, i32, P, P, P, i32, i32, i32, i32, u64, i32,
-                                                      i32, i32, i32, i32, i32, i32, i32, i32, P, P, P, P, P]
+                                                      i32, i32, i32, i32, i32, i32, i32, i32, i32, P, P, P, P,
+                                                      P]
             lib.oracle_filter_learned_f64.restype = i32
             lib.oracle_mlp_features_f64.argtypes = [P, i32, i32, i32, i32, P]
             lib.oracle_mlp_texel_f64.argtypes = [P, i32, i32, i32, i32, P]
@@ -139,10 +140,12 @@ def stf_offset(px, py, view, seed, s, t):
 # ---------------------------------------------------------------------------
 def filter_frame(blocks, Wt, Ht, uv, jac, coverage=None, *, view=0, alg=ALG_BOX, seed=0,
                  tile_w=8, tile_h=4, budget=32, mask_dim=16, edge_remap=1, group_tiles=0, fallback=0,
-                 texels_per_lane=1, filter=0, want_tiles=False):
+                 texels_per_lane=1, filter=0, y_offset=0, want_tiles=False):
     """Filter one W x H frame with the exact block decode (FP32 arithmetic).
 
     fallback: 0 one-tap STF, 1 fallback C, 2 fallback C+ for over-budget tiles.
+    y_offset: the frame is the band of a larger view that starts at this row
+    (a multiple of tile_h); it enters only the per-pixel STF counters.
     group_tiles > 0: stats["texel_evals_unique"] counts the distinct clamped
     texels evaluated per group of that many consecutive tiles.
     Returns (rgba[H,W,4] float32, evals[H,W] uint8, stats dict[, tile_path, tile_n]).
@@ -161,7 +164,7 @@ def filter_frame(blocks, Wt, Ht, uv, jac, coverage=None, *, view=0, alg=ALG_BOX,
     stats = np.zeros(9, np.int64)
     rc = _load().oracle_filter(_ptr(b), Wt, Ht, _ptr(uv), _ptr(jac), _ptr(cov), W, H, view, alg, seed,
                                tile_w, tile_h, budget, mask_dim, edge_remap, group_tiles, fallback,
-                               texels_per_lane, filter, _ptr(out),
+                               texels_per_lane, filter, y_offset, _ptr(out),
                                _ptr(ev),
                                _ptr(tp), _ptr(tn), _ptr(stats))
     if rc != 0:
@@ -241,7 +244,7 @@ def mlp_loss_grad(mlp: MLP, Wt, Ht, xs, ys, targets):
 
 def filter_frame_learned_f64(mlp: MLP, Wt, Ht, uv, jac, coverage=None, *, view=0, alg=ALG_MASK, seed=0,
                              tile_w=8, tile_h=4, budget=32, mask_dim=16, edge_remap=1, group_tiles=0, fallback=0,
-                             texels_per_lane=1, filter=0):
+                             texels_per_lane=1, filter=0, y_offset=0):
     """Same selection as filter_frame, texel values from the FP64 MLP, filter in FP64."""
     uv = np.ascontiguousarray(uv, dtype=np.float32)
     jac = np.ascontiguousarray(jac, dtype=np.float32)
@@ -252,7 +255,7 @@ def filter_frame_learned_f64(mlp: MLP, Wt, Ht, uv, jac, coverage=None, *, view=0
     stats = np.zeros(9, np.int64)
     rc = _load().oracle_filter_learned_f64(mlp.ref, Wt, Ht, _ptr(uv), _ptr(jac), _ptr(cov), W, H, view, alg,
                                            seed, tile_w, tile_h, budget, mask_dim, edge_remap, group_tiles,
-                                           fallback, texels_per_lane, filter, _ptr(out),
+                                           fallback, texels_per_lane, filter, y_offset, _ptr(out),
                                            _ptr(ev), None, None, _ptr(stats))
     if rc != 0:
         raise ValueError(f"oracle_filter_learned_f64 rejected its arguments (rc={rc})")

@@ -226,7 +226,8 @@ static void fetch_texel(const texel_source *src, int x, int y, float vf[4], doub
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int active;
-    int px, py;
+    int px, py;       /* pixel in the frame passed in */
+    int ry;           /* its row in the full view (py + the band's first row): STF counter word 1 */
     int ulx, uly;     /* upper-left integer texel of the 2x2 footprint */
     float s, t;       /* local coordinates in the 2x2 footprint, in [0,1) */
     int minified;
@@ -408,11 +409,11 @@ static void stf_lane(const texel_source *src, const pixel_setup *p, int filter, 
     float gx = 1.0f, gy = 1.0f;
     if (filter == FILTER_BILINEAR) {
         int dx, dy;
-        oracle_stf_offset(p->px, p->py, view, seed, p->s, p->t, &dx, &dy);
+        oracle_stf_offset(p->px, p->ry, view, seed, p->s, p->t, &dx, &dy);
         *tx = p->ulx + dx;
         *ty = p->uly + dy;
     } else {
-        uint32_t ctr[4] = {(uint32_t)p->px, (uint32_t)p->py, (uint32_t)view, 0u};
+        uint32_t ctr[4] = {(uint32_t)p->px, (uint32_t)p->ry, (uint32_t)view, 0u};
         uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
         uint32_t r[4];
         oracle_philox4x32_10(ctr, key, r);
@@ -533,7 +534,7 @@ static void fallback_c(const texel_source *src, const pixel_setup *lane, uint32_
     float xi2[32];
     for (int i = 0; i < na; ++i) {
         const pixel_setup *p = &lane[act[i]];
-        uint32_t ctr[4] = {(uint32_t)p->px, (uint32_t)p->py, (uint32_t)view, 0u};
+        uint32_t ctr[4] = {(uint32_t)p->px, (uint32_t)p->ry, (uint32_t)view, 0u};
         uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
         uint32_t r[4];
         oracle_philox4x32_10(ctr, key, r);
@@ -671,6 +672,9 @@ static void fallback_c(const texel_source *src, const pixel_setup *lane, uint32_
  *   group_tiles    0, or the size of the tile groups (consecutive tile
  *                  indices, at most 8) whose distinct evaluated texels
  *                  stats[8] counts; 4TAP is never grouped
+ *   y0             row of the full view at which this frame starts (a band
+ *                  of whole tile rows: y0 a multiple of tile_h); it only
+ *                  enters the STF counters, which are per pixel of the view
  *   stats[9]       tiles_total, tiles_empty, tiles_direct, tiles_success,
  *                  tiles_fallback_budget, tiles_fallback_minified,
  *                  pixels_active, texel_evals (sum of evals), and the
@@ -680,9 +684,11 @@ static void fallback_c(const texel_source *src, const pixel_setup *lane, uint32_
 static int oracle_filter_ex(const texel_source *src, const float *uv, const float *jac, const uint8_t *cov,
                             int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h,
                             int budget, int mask_dim, int edge_remap, int group_tiles, int fallback, int tpl,
-                            int filter, int fp64, float *out, double *outd, uint8_t *evals,
+                            int filter, int y0, int fp64, float *out, double *outd, uint8_t *evals,
                             int32_t *tile_path, int32_t *tile_n, int64_t *stats_out)
 {
+    if (y0 < 0 || y0 % tile_h != 0)
+        return -1;
     if (tpl != 1 && tpl != 2)
         return -1;
     if (filter < 0 || filter > 2 || (filter != FILTER_BILINEAR && (fallback != 0 || tpl != 1)))
@@ -722,6 +728,7 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
             for (int l = 0; l < 32; ++l) {
                 int px = bx * tile_w + l % tile_w, py = by * tile_h + l / tile_w;
                 setup_pixel(uv, jac, cov, W, H, src->Wt, src->Ht, px, py, &lane[l]);
+                lane[l].ry = py + y0;
                 if (lane[l].active) {
                     A |= 1u << l;
                     any_minified |= lane[l].minified;
@@ -954,14 +961,14 @@ static int oracle_filter_ex(const texel_source *src, const float *uv, const floa
 /* Exact block decode, FP32 arithmetic with the rounding described above. */
 int oracle_filter(const uint8_t *blocks, int Wt, int Ht, const float *uv, const float *jac, const uint8_t *cov,
                   int W, int H, int view, int alg, uint64_t seed, int tile_w, int tile_h, int budget,
-                  int mask_dim, int edge_remap, int group_tiles, int fallback, int tpl, int filter, float *out,
-                  uint8_t *evals, int32_t *tile_path, int32_t *tile_n, int64_t *stats)
+                  int mask_dim, int edge_remap, int group_tiles, int fallback, int tpl, int filter, int y0,
+                  float *out, uint8_t *evals, int32_t *tile_path, int32_t *tile_n, int64_t *stats)
 {
     if (Wt <= 0 || Ht <= 0 || Wt % 4 || Ht % 4 || !blocks)
         return -1;
     texel_source src = {0, Wt, Ht, blocks, NULL};
     return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
-                            edge_remap, group_tiles, fallback, tpl, filter, 0, out, NULL, evals, tile_path,
+                            edge_remap, group_tiles, fallback, tpl, filter, y0, 0, out, NULL, evals, tile_path,
                             tile_n, stats);
 }
 
@@ -969,13 +976,13 @@ int oracle_filter(const uint8_t *blocks, int Wt, int Ht, const float *uv, const 
 int oracle_filter_learned_f64(const void *mlp, int Wt, int Ht, const float *uv, const float *jac,
                               const uint8_t *cov, int W, int H, int view, int alg, uint64_t seed, int tile_w,
                               int tile_h, int budget, int mask_dim, int edge_remap, int group_tiles,
-                              int fallback, int tpl, int filter, double *outd, uint8_t *evals,
+                              int fallback, int tpl, int filter, int y0, double *outd, uint8_t *evals,
                               int32_t *tile_path, int32_t *tile_n, int64_t *stats)
 {
     if (Wt <= 0 || Ht <= 0 || !mlp)
         return -1;
     texel_source src = {1, Wt, Ht, NULL, mlp};
     return oracle_filter_ex(&src, uv, jac, cov, W, H, view, alg, seed, tile_w, tile_h, budget, mask_dim,
-                            edge_remap, group_tiles, fallback, tpl, filter, 1, NULL, outd, evals, tile_path,
+                            edge_remap, group_tiles, fallback, tpl, filter, y0, 1, NULL, outd, evals, tile_path,
                             tile_n, stats);
 }

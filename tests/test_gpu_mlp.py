@@ -266,3 +266,54 @@ def test_staged_inputs_equal_the_batch_kernel(tex64, alg):
     assert st == stb
     assert st["pixels_active"] == int(cov.sum())
     assert st["tiles_empty"] >= 300 // 8 * (H // 4)
+
+
+def test_learned_full_view_bands_match_fp64_oracle():
+    """The 3840x2160 learned view of the benchmark (4096^2 texture, latent
+    grids 1024^2 and 512^2, magnification 1 to 16) filtered with Mask-11 in
+    the launch the bench times (one launch over the whole view, 8x4 tiles).
+    Three bands of 16 rows (top, middle, bottom) against the FP64 oracle run
+    on those rows alone (y_offset keeps the STF draws of the whole view):
+    counts bit-exact, pixels within the FP16 bound of their footprint's
+    texels."""
+    Wt = Ht = 4096
+    lat, p = random_params(7, Wt, Ht)
+    h = _ctf.ctf_texture_create_mlp(Wt, Ht, _ctf.CTF_EVAL_MLP_FP16, lat, *p)
+    try:
+        st = _ctf.ctf_mlp_export(h, (lat[0].shape, lat[1].shape))
+        mlp = oracle.MLP((st["lat0"], st["lat1"]), st["w1"], st["b1"], st["w2"], st["b2"], st["w3"], st["b3"])
+        sc = synth.perspective_view(3840, 2160, Wt, Ht, 1.0, 16.0, seed=2)
+        W, H = sc.W, sc.H
+        d_uv, d_jac, d_cov = (torch.from_numpy(a).cuda() for a in (sc.uv, sc.jac, sc.coverage))
+        out = torch.full((H, W, 4), -3.0, device="cuda")
+        ev = torch.full((H, W), 77, dtype=torch.uint8, device="cuda")
+        _ctf.ctf_filter(h, d_uv, d_jac, d_cov, W, H, 0, "mask", 0, {"mask_dim": 11}, out, ev)
+        _ctf.ctf_sync_check()
+        out, ev = out.cpu().numpy(), ev.cpu().numpy()
+        w1, w2, w3 = (st[k].astype(np.float64) for k in ("w1", "w2", "w3"))
+        for y0 in (0, 1000, H - 16):
+            band = slice(y0, y0 + 16)
+            ref, ref_ev, _ = oracle.filter_frame_learned_f64(mlp, Wt, Ht, sc.uv[band], sc.jac[band],
+                                                             sc.coverage[band], alg=ALGS["mask"], mask_dim=11,
+                                                             y_offset=y0)
+            np.testing.assert_array_equal(ev[band], ref_ev)
+            # FP16 bound of every texel of the band's 2x2 footprints
+            uv = sc.uv[band]
+            x0 = np.floor(uv[..., 0] * np.float32(Wt) - np.float32(0.5)).astype(np.int64)
+            y0_ = np.floor(uv[..., 1] * np.float32(Ht) - np.float32(0.5)).astype(np.int64)
+            taps = [(np.clip(x0 + dx, 0, Wt - 1), np.clip(y0_ + dy, 0, Ht - 1)) for dy in (0, 1) for dx in (0, 1)]
+            keys = np.unique(np.concatenate([ty.ravel() * Wt + tx.ravel() for tx, ty in taps]))
+            F = np.stack([oracle.mlp_features(mlp, Wt, Ht, int(k % Wt), int(k // Wt)) for k in keys])
+            h1 = np.maximum(F @ w1.T + st["b1"], 0)
+            h2 = np.maximum(h1 @ w2.T + st["b2"], 0)
+            e_h1 = U16 * h1 + (U16 * np.abs(F)) @ np.abs(w1).T
+            e_h2 = U16 * h2 + e_h1 @ np.abs(w2).T
+            kb = 1.5 * (e_h2 @ np.abs(w3).T) + 1e-5
+            tol = np.zeros(uv.shape[:2] + (4,))
+            for tx, ty in taps:
+                tol = np.maximum(tol, kb[np.searchsorted(keys, ty * Wt + tx)])
+            err = np.abs(out[band].astype(np.float64) - ref)
+            assert (sc.coverage[band] != 0).sum() > 0.8 * 16 * W
+            assert np.all(err <= tol), (y0, err.max(), (err / tol).max())
+    finally:
+        _ctf.ctf_texture_destroy(h)

@@ -673,3 +673,32 @@ def test_edge_cases(oracle_lib):
         o.filter_frame(blocks, 16, 16, uv, jac, tile_w=4, tile_h=4)
     with pytest.raises(ValueError):
         o.filter_frame(blocks, 16, 16, uv, jac, alg=o.ALG_MASK, mask_dim=12)
+
+
+# ---------------------------------------------------------------------------
+# Bands of a view
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("alg,fallback", [(2, 0), (3, 0), (4, 0), (4, 2)])
+def test_band_equals_rows_of_the_whole_view(oracle_lib, alg, fallback):
+    """A band of whole tile rows filtered on its own with y_offset gives the
+    same pixels and counts as those rows of the whole view (the offset enters
+    only the per-pixel STF counters; the scene has minified and over-budget
+    tiles, so the stochastic draws are exercised), and it is refused when it
+    would split tile rows."""
+    Wt = Ht = 256
+    blocks = synth.random_blocks(Wt, Ht, seed=5)
+    sc = synth.ground_plane_with_quads(160, 96, Wt, Ht)
+    kw = dict(alg=alg, seed=77, view=3, mask_dim=11, fallback=fallback)
+    full, full_ev, st = oracle_lib.filter_frame(blocks, Wt, Ht, sc.uv, sc.jac, sc.coverage, **kw)
+    assert st["tiles_fallback_minified"] > 0 and st["tiles_success"] > 0
+    y0, y1 = 40, 72
+    band, band_ev, _ = oracle_lib.filter_frame(blocks, Wt, Ht, sc.uv[y0:y1], sc.jac[y0:y1], sc.coverage[y0:y1],
+                                              y_offset=y0, **kw)
+    assert np.array_equal(band.view(np.uint32), full[y0:y1].view(np.uint32))
+    assert np.array_equal(band_ev, full_ev[y0:y1])
+    # without the offset the STF draws of the band are those of other pixels
+    moved, _, _ = oracle_lib.filter_frame(blocks, Wt, Ht, sc.uv[y0:y1], sc.jac[y0:y1], sc.coverage[y0:y1], **kw)
+    assert not np.array_equal(moved.view(np.uint32), full[y0:y1].view(np.uint32))
+    with pytest.raises(ValueError):
+        oracle_lib.filter_frame(blocks, Wt, Ht, sc.uv[y0 + 2:y1], sc.jac[y0 + 2:y1], sc.coverage[y0 + 2:y1],
+                                y_offset=y0 + 2, **kw)
