@@ -295,8 +295,8 @@ def bench_learned(args, dev, stream, flush, peaks):
     runs = {}
     for tname in ("fp16", "fp8"):
         tex = texs[tname]
-        for name in ("4tap", "mask", "mask_group_dedup", "box", "list_merge"):
-            if tname == "fp8" and name in ("box", "list_merge"):
+        for name in ("4tap", "stf", "mask", "mask_group_dedup", "box", "list_merge"):
+            if tname == "fp8" and name in ("stf", "box", "list_merge"):
                 continue
             alg = "mask" if name.startswith("mask") else name
             o = opts11 if name == "mask" else ({"mask_dim": 11, "group_dedup": 1} if name == "mask_group_dedup"
@@ -310,7 +310,7 @@ def bench_learned(args, dev, stream, flush, peaks):
             flops = st["texel_evals_unique"] * 10752  # evaluations done
             peak = peaks["bf16"] * (2.0 if tname == "fp8" else 1.0)
             runs[f"{tname}_{name}"] = {
-                "pixels_per_s": npix / t, "ms_per_view": t * 1e3,
+                "pixels_per_s": npix / t, "ms_per_view": t * 1e3, "us_per_mpixel": t * 1e6 / (npix / 1e6),
                 "evals_per_pixel": st["texel_evals"] / max(1, st["pixels_active"]),
                 "evaluations_done_per_pixel": st["texel_evals_unique"] / max(1, st["pixels_active"]),
                 "texel_evals_per_s": st["texel_evals"] / t,
