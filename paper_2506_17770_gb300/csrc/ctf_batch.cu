@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, batch_min_blocks<ALG>()) bat
     constexpr bool kJac = ALG >= ALG_LIST;
     __shared__ DecodeTables tabs;
     __shared__ int rank_slots[kBlockWarps][64];
-    __shared__ unsigned long long fb_keys[kBlockWarps][32];  // fallback C / C+ texel keys
+    __shared__ FbTable fb_tab[kBlockWarps];  // fallback C / C+ texel lookups
     __shared__ unsigned long long block_stats[kNumStats];
     __shared__ int s_begin[kSmViews];
     __shared__ __align__(16) ExactParams s_params[kBlockWarps];  // each warp's current view
@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, batch_min_blocks<ALG>()) bat
 #pragma unroll
         for (int s = 0; s < 8; ++s) T->keys[lane * 8 + s] = kEmpty;
     }
+    if (kFb) fb_clear(&fb_tab[warp], lane);  // the fallback's texel table starts empty
     __syncthreads();
     const int tx = lane % TW, ty = lane / TW;
     const uint32_t lt = lanemask_lt();
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, batch_min_blocks<ALG>()) bat
             const uint32_t nidx = nby * (TH * W) + nbx * TW + lane_off;
             const Inputs nxt = load_inputs_any<kJac>(p, ninside, nidx);
             filter_tile<ALG, TW, MD, true, kFb>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
-                                           &tabs, T, rank_slots[warp], fb_keys[warp], cnt);
+                                           &tabs, T, rank_slots[warp], &fb_tab[warp], cnt);
             bx = nbx;
             by = nby;
             inside = ninside;

@@ -109,12 +109,57 @@ __device__ __forceinline__ float4 filter4(const float w[4], const float3 t[4]) {
 // produced texels of its footprint that have nonzero weight by eq. 1:
 // exact bilinear when all are present, the texel itself when one is, else
 // fma(1 - S_w, S_p / N, S_wp) per channel (tap order, FP32 RN).
-// `keys` is a per-warp array of 32 64-bit words in shared memory.
-// Warp-collective; kept out of line so that it does not weigh on the
+// The texels a lane looks for are found in a per-warp open-addressing hash
+// table in shared memory (64 slots for at most 32 keys), empty between
+// tiles.  Warp-collective; kept out of line so that it does not weigh on the
 // registers of the common path.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long texel_key(int x, int y) {
     return ((unsigned long long)(uint32_t)y << 32) | (uint32_t)x;
+}
+
+// no texel: x = INT_MIN is never a texel coordinate (|x| < 2^22 + 2)
+constexpr unsigned long long kNoTexel = 0x8000000080000000ull;
+
+struct FbTable {
+    unsigned long long key[64];  // kNoTexel = empty
+    unsigned char lane[64];      // the lane that inserted the key
+};
+
+__device__ __forceinline__ unsigned fb_hash(unsigned long long k) {
+    return (((uint32_t)k * 0x9E3779B1u) ^ ((uint32_t)(k >> 32) * 0x85EBCA77u)) >> 26;
+}
+
+// Insert texel key k for `lane`; a key already present keeps its lane.
+__device__ __forceinline__ void fb_insert(FbTable *t, unsigned long long k, int lane) {
+    unsigned h = fb_hash(k);
+    for (int probe = 0; probe < 64; ++probe) {  // at most 32 keys in 64 slots: the probe ends
+        const unsigned long long old = atomicCAS(&t->key[h], kNoTexel, k);
+        if (old == kNoTexel) {
+            t->lane[h] = (unsigned char)lane;
+            return;
+        }
+        if (old == k) return;
+        h = (h + 1) & 63u;
+    }
+}
+
+// The lane that inserted texel key k, or -1.
+__device__ __forceinline__ int fb_find(const FbTable *t, unsigned long long k) {
+    unsigned h = fb_hash(k);
+    for (int probe = 0; probe < 64; ++probe) {
+        const unsigned long long v = t->key[h];
+        if (v == k) return t->lane[h];
+        if (v == kNoTexel) return -1;
+        h = (h + 1) & 63u;
+    }
+    return -1;
+}
+
+// Empty the table (every lane two slots); the caller syncs the warp.
+__device__ __forceinline__ void fb_clear(FbTable *t, int lane) {
+    t->key[lane] = kNoTexel;
+    t->key[lane + 32] = kNoTexel;
 }
 
 struct FallbackOut {
@@ -135,9 +180,7 @@ struct FallbackArgs {
 
 __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ulx, int uly, float s, float t,
                                                    bool active, int px, int py, uint32_t A, int lane, uint32_t lt,
-                                                   const DecodeTables *tabs, unsigned long long *keys) {
-    // no texel: x = INT_MIN is never a texel coordinate (|x| < 2^22 + 2)
-    constexpr unsigned long long kNone = 0x8000000080000000ull;
+                                                   const DecodeTables *tabs, FbTable *tab) {
     const int na = __popc(A);
     const int ai = __popc(A & lt);
     int dx = 0, dy = 0;
@@ -152,7 +195,7 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
         const uint32_t grp = __match_any_sync(FULL, skey);
         const uint32_t L = __ballot_sync(FULL, active && (__ffs(grp) - 1) == lane);
         const int n = __popc(L);
-        keys[lane] = active ? skey : kNone;
+        if (active) fb_insert(tab, skey, lane);
         __syncwarp();
         const int lead = nth_set_lane(L, active && ai < n ? ai : 0);
         const int ux = __shfl_sync(FULL, sx, lead), uy = __shfl_sync(FULL, sy, lead);
@@ -176,10 +219,7 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
             bool cand[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const unsigned long long tk = texel_key(sux + (k & 1), suy + (k >> 1));
-                bool in_set = false;
-#pragma unroll 8
-                for (int j = 0; j < 32; ++j) in_set |= keys[j] == tk;
+                const bool in_set = fb_find(tab, texel_key(sux + (k & 1), suy + (k >> 1))) >= 0;
                 cand[k] = w[k] > 0.f && !in_set;
             }
             float wc = 0.f;
@@ -212,6 +252,8 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
             }
         }
         __syncwarp();
+        fb_clear(tab, lane);
+        __syncwarp();
     }
     // produce; every lane decodes (non-producers their own clamped texel)
     float3 val;
@@ -220,7 +262,7 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
         const uint2 blk = __ldg(fa.blocks + (uint32_t)(y >> 2) * (uint32_t)fa.nbx + (uint32_t)(x >> 2));
         val = decode_texel_f(blk, x, y, tabs);
     }
-    keys[lane] = produce ? texel_key(qx, qy) : kNone;
+    if (produce) fb_insert(tab, texel_key(qx, qy), lane);
     __syncwarp();
     // eq. 1: the produced texels of the pixel's footprint with nonzero weight
     float w[4];
@@ -230,10 +272,8 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
     int nz = 0, N = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const unsigned long long tk = texel_key(ulx + (k & 1), uly + (k >> 1));
-        int found = -1;
-#pragma unroll 8
-        for (int j = 31; j >= 0; --j) found = keys[j] == tk ? j : found;
+        // any lane that produced the texel holds its value
+        const int found = fb_find(tab, texel_key(ulx + (k & 1), uly + (k >> 1)));
         pres[k] = active && w[k] > 0.f && found >= 0;
         srcl[k] = found >= 0 ? found : lane;
         nz += w[k] > 0.f ? 1 : 0;
@@ -246,7 +286,9 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
         tv[k].y = __shfl_sync(FULL, val.y, srcl[k]);
         tv[k].z = __shfl_sync(FULL, val.z, srcl[k]);
     }
-    __syncwarp();  // keys free for the next tile
+    __syncwarp();
+    fb_clear(tab, lane);  // empty for the next tile
+    __syncwarp();
     FallbackOut o;
     o.res = make_float4(0.f, 0.f, 0.f, 0.f);
     o.count = produce ? 1u : 0u;
@@ -296,7 +338,7 @@ constexpr int min_blocks() {
 template <int ALG, int TW, int MD, bool kStats, bool kExt = false>
 __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &in, int px, int py, bool inside,
                                             uint32_t idx, int lane, uint32_t lt, const DecodeTables *tabs,
-                                            ListTable *T, int *ranks, unsigned long long *fbkeys, Counters &cnt) {
+                                            ListTable *T, int *ranks, FbTable *fbtab, Counters &cnt) {
     PixelSetup ps;
     ps.active = in.covered;
     setup_coords(in.uv, (float)p.Wt, (float)p.Ht, ps);
@@ -345,7 +387,7 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
             fa.k1 = p.k1;
             fa.mode = p.fallback;
             const FallbackOut fo =
-                fallback_blend(fa, ps.ulx, ps.uly, ps.s, ps.t, ps.active, px, py, sel.A, lane, lt, tabs, fbkeys);
+                fallback_blend(fa, ps.ulx, ps.uly, ps.s, ps.t, ps.active, px, py, sel.A, lane, lt, tabs, fbtab);
             if (kStats) {  // select_tile counted one evaluation per active lane
                 const int d = __popc(__ballot_sync(FULL, fo.count != 0)) - __popc(sel.A);
                 cnt.v[kStatTexelEvals] += d;

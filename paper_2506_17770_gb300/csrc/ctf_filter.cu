@@ -36,12 +36,12 @@ constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
 template <int ALG, int TW, int MD, bool kStats, bool kFb>
-__global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kernel(const ExactParams p) {
+__global__ void __launch_bounds__(kThreads, kFb ? 4 : min_blocks<ALG>()) exact_filter_kernel(const ExactParams p) {
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
     __shared__ DecodeTables tabs;
     __shared__ int rank_slots[kWarps][64];
-    __shared__ unsigned long long fb_keys[kWarps][32];  // fallback C / C+ texel keys
+    __shared__ FbTable fb_tab[kWarps];  // fallback C / C+ texel lookups
     __shared__ unsigned long long block_stats[kNumStats];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
 
@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kern
 #pragma unroll
         for (int s = 0; s < 8; ++s) T->keys[lane * 8 + s] = kEmpty;
     }
+    if (kFb) fb_clear(&fb_tab[warp], lane);  // the fallback's texel table starts empty
 
     const int tx = lane % TW, ty = lane / TW;
     const uint32_t lt = lanemask_lt();
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<ALG>()) exact_filter_kern
         const Inputs nxt = load_inputs_any<kJac>(p, ninside, nidx);
 
         filter_tile<ALG, TW, MD, kStats, kFb>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
-                                         &tabs, T, rank_slots[warp], fb_keys[warp], cnt);
+                                         &tabs, T, rank_slots[warp], &fb_tab[warp], cnt);
 
         bx = nbx;
         by = nby;
