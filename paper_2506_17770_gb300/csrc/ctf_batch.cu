@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, batch_min_blocks<ALG>()) bat
             const bool ninside = i + 1u < n_item && nbx < lim_x && nby < lim_y;
             const uint32_t nidx = nby * (TH * W) + nbx * TW + lane_off;
             const Inputs nxt = load_inputs_any<kJac>(p, ninside, nidx);
-            filter_tile<ALG, TW, MD, true, kFb>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
+            filter_tile<ALG, TW, MD, true, kFb ? kExtFallback | kExtTwo : 0>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
                                            &tabs, T, rank_slots[warp], &fb_tab[warp], cnt);
             bx = nbx;
             by = nby;

@@ -332,10 +332,12 @@ constexpr int min_blocks() {
     return ALG >= ALG_LIST ? 5 : 1;
 }
 
-// kExt: the kernel variant for the optional extensions, fallbacks C / C+
-// (p.fallback != 0) and two texels per lane (p.tpl == 2); the other variant
-// carries no code for them.
-template <int ALG, int TW, int MD, bool kStats, bool kExt = false>
+// kExt: the code for the optional extensions that a kernel variant carries,
+// fallbacks C / C+ (kExtFallback, for p.fallback != 0) and two texels per
+// lane (kExtTwo, for p.tpl == 2); the variant without either carries none.
+constexpr int kExtFallback = 1, kExtTwo = 2;
+
+template <int ALG, int TW, int MD, bool kStats, int kExt = 0>
 __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &in, int px, int py, bool inside,
                                             uint32_t idx, int lane, uint32_t lt, const DecodeTables *tabs,
                                             ListTable *T, int *ranks, FbTable *fbtab, Counters &cnt) {
@@ -374,8 +376,9 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
             count = 4;
         }
     } else {
-        const Selection sel = select_tile<ALG, MD, kStats, true, kExt>(p, ps, in.jac, px, py, lane, lt, T, ranks, cnt);
-        if (kExt && ALG >= ALG_LIST && p.fallback != 0 && sel.path == PATH_FALLBACK_BUDGET) {
+        const Selection sel =
+            select_tile<ALG, MD, kStats, true, (kExt & kExtTwo) != 0>(p, ps, in.jac, px, py, lane, lt, T, ranks, cnt);
+        if ((kExt & kExtFallback) && ALG >= ALG_LIST && p.fallback != 0 && sel.path == PATH_FALLBACK_BUDGET) {
             // fallback C or C+ in place of one-tap STF
             FallbackArgs fa;
             fa.blocks = p.blocks;
@@ -400,7 +403,7 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
         // lanes that produce nothing decode their own upper-left texel, which
         // the warp reads anyway, and drop it
         const float3 val = fetch_decode(p, sel.tx, sel.ty, tabs);
-        const bool two = kExt && ALG >= ALG_LIST && p.tpl == 2;
+        const bool two = (kExt & kExtTwo) && ALG >= ALG_LIST && p.tpl == 2;
         if (sel.path == PATH_SUCCESS) {
             // step 3: gather the 2x2 taps from their producers and filter
             float3 t[4];

@@ -35,8 +35,8 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
-template <int ALG, int TW, int MD, bool kStats, bool kFb>
-__global__ void __launch_bounds__(kThreads, kFb ? 4 : min_blocks<ALG>()) exact_filter_kernel(const ExactParams p) {
+template <int ALG, int TW, int MD, bool kStats, int kExt>
+__global__ void __launch_bounds__(kThreads, kExt ? 4 : min_blocks<ALG>()) exact_filter_kernel(const ExactParams p) {
     constexpr int TH = 32 / TW;
     constexpr bool kJac = ALG >= ALG_LIST;
     __shared__ DecodeTables tabs;
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kThreads, kFb ? 4 : min_blocks<ALG>()) exact_f
 #pragma unroll
         for (int s = 0; s < 8; ++s) T->keys[lane * 8 + s] = kEmpty;
     }
-    if (kFb) fb_clear(&fb_tab[warp], lane);  // the fallback's texel table starts empty
+    if (kExt & kExtFallback) fb_clear(&fb_tab[warp], lane);  // the fallback's texel table starts empty
 
     const int tx = lane % TW, ty = lane / TW;
     const uint32_t lt = lanemask_lt();
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads, kFb ? 4 : min_blocks<ALG>()) exact_f
         const uint32_t nidx = nby * (TH * W) + nbx * TW + lane_off;
         const Inputs nxt = load_inputs_any<kJac>(p, ninside, nidx);
 
-        filter_tile<ALG, TW, MD, kStats, kFb>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
+        filter_tile<ALG, TW, MD, kStats, kExt>(p, cur, (int)(bx * TW) + tx, (int)(by * TH) + ty, inside, idx, lane, lt,
                                          &tabs, T, rank_slots[warp], &fb_tab[warp], cnt);
 
         bx = nbx;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kThreads, kFb ? 4 : min_blocks<ALG>()) exact_f
         cur = nxt;
     }
 
-    if (kStats) {
+    if (kStats && p.stats) {  // (the extension variants always count; p.stats decides)
         if (lane == 0) {
 #pragma unroll
             for (int i = 0; i < kNumStats; ++i)
@@ -116,19 +116,26 @@ __global__ void __launch_bounds__(kThreads, kFb ? 4 : min_blocks<ALG>()) exact_f
 
 using KernelFn = void (*)(const ExactParams);
 
-// The collaborative algorithms have a second variant for the optional
-// extensions (fallbacks C / C+, two texels per lane).
+// The collaborative algorithms have variants for the optional extensions
+// (fallbacks C / C+, two texels per lane, both).  These are built with the
+// counters only (kStats; a null stats pointer skips the final sums), which
+// halves their number.
 template <int ALG, int TW, int MD, bool kStats>
-KernelFn pick_fb(bool fb) {
-    if constexpr (ALG >= ALG_LIST) {
-        return fb ? exact_filter_kernel<ALG, TW, MD, kStats, true> : exact_filter_kernel<ALG, TW, MD, kStats, false>;
+KernelFn pick_fb(int ext) {
+    if constexpr (ALG >= ALG_LIST && kStats) {
+        switch (ext) {
+        case kExtFallback: return exact_filter_kernel<ALG, TW, MD, kStats, kExtFallback>;
+        case kExtTwo: return exact_filter_kernel<ALG, TW, MD, kStats, kExtTwo>;
+        case kExtFallback | kExtTwo: return exact_filter_kernel<ALG, TW, MD, kStats, kExtFallback | kExtTwo>;
+        default: return exact_filter_kernel<ALG, TW, MD, kStats, 0>;
+        }
     } else {
-        return exact_filter_kernel<ALG, TW, MD, kStats, false>;
+        return exact_filter_kernel<ALG, TW, MD, kStats, 0>;
     }
 }
 
 template <int ALG, int TW, bool kStats>
-KernelFn pick_mask(int md, bool fb) {
+KernelFn pick_mask(int md, int fb) {
     if constexpr (ALG == ALG_MASK) {
         return md == 11 ? pick_fb<ALG, TW, 11, kStats>(fb) : pick_fb<ALG, TW, 16, kStats>(fb);
     } else {
@@ -137,7 +144,7 @@ KernelFn pick_mask(int md, bool fb) {
 }
 
 template <int TW, bool kStats>
-KernelFn pick_alg(int alg, int md, bool fb) {
+KernelFn pick_alg(int alg, int md, int fb) {
     switch (alg) {
     case ALG_4TAP: return pick_mask<ALG_4TAP, TW, kStats>(md, fb);
     case ALG_STF: return pick_mask<ALG_STF, TW, kStats>(md, fb);
@@ -165,11 +172,12 @@ int device_sm_count() {
 
 cudaError_t launch_exact_filter(const ExactParams &p, int alg, int tile_w, int mask_dim, cudaStream_t stream) {
     KernelFn fn = nullptr;
-    const bool st = p.stats != nullptr, fb = p.fallback != 0 || p.tpl == 2;
+    const bool st = p.stats != nullptr;
+    const int fb = (p.fallback != 0 ? kExtFallback : 0) | (p.tpl == 2 ? kExtTwo : 0);
     switch (tile_w) {
-    case 8: fn = st ? pick_alg<8, true>(alg, mask_dim, fb) : pick_alg<8, false>(alg, mask_dim, fb); break;
-    case 4: fn = st ? pick_alg<4, true>(alg, mask_dim, fb) : pick_alg<4, false>(alg, mask_dim, fb); break;
-    case 16: fn = st ? pick_alg<16, true>(alg, mask_dim, fb) : pick_alg<16, false>(alg, mask_dim, fb); break;
+    case 8: fn = st || fb ? pick_alg<8, true>(alg, mask_dim, fb) : pick_alg<8, false>(alg, mask_dim, 0); break;
+    case 4: fn = st || fb ? pick_alg<4, true>(alg, mask_dim, fb) : pick_alg<4, false>(alg, mask_dim, 0); break;
+    case 16: fn = st || fb ? pick_alg<16, true>(alg, mask_dim, fb) : pick_alg<16, false>(alg, mask_dim, 0); break;
     default: return cudaErrorInvalidValue;
     }
     if (!fn) return cudaErrorInvalidValue;
