@@ -71,6 +71,34 @@ int scratch_stats(unsigned long long **out) {
     return CTF_OK;
 }
 
+// Copy streams and events of the banded host path, per device (created on
+// first use, guarded by g_scratch_mutex).
+constexpr int kMaxBands = 4;
+struct HostPipe {
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t ev[2 * kMaxBands + 2] = {};
+    bool ready = false;
+};
+HostPipe g_pipe[kMaxDevices];
+
+int host_pipe(HostPipe **out) {
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_scratch_mutex);
+    HostPipe &h = g_pipe[dev];
+    if (!h.ready) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h.in, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h.out, cudaStreamNonBlocking);
+        for (int i = 0; i < 2 * kMaxBands + 2 && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&h.ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "host copy streams");
+        h.ready = true;
+    }
+    *out = &h;
+    return CTF_OK;
+}
+
 int scratch_stage(size_t bytes, void **out) {
     int dev = 0;
     int rc = current_device(&dev);
@@ -151,10 +179,14 @@ int validate_filter_args(ctf_texture tex, const float *uv, const float *jac, int
     return CTF_OK;
 }
 
+// y0: the frame is the band of a view that starts at this row (whole tile
+// rows); it enters only the STF counters, so a view filtered band by band
+// gives the image of one call on the whole view.
 int run_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t *coverage, int width, int height,
                int view_id, ctf_algorithm alg, uint64_t seed, const ResolvedOpts &ro, float *out,
-               uint8_t *evals, unsigned long long *dstats, cudaStream_t stream) {
+               uint8_t *evals, unsigned long long *dstats, cudaStream_t stream, int y0 = 0) {
     ctf::ExactParams p;
+    p.y0 = y0;
     p.blocks = static_cast<const uint2 *>(tex->blocks);
     p.Wt = tex->width;
     p.Ht = tex->height;
@@ -465,23 +497,61 @@ int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host
     float *d_out = reinterpret_cast<float *>(base + b_uv + b_jac);
     uint8_t *d_cov = reinterpret_cast<uint8_t *>(base + b_uv + b_jac + b_out);
     uint8_t *d_ev = reinterpret_cast<uint8_t *>(base + b_uv + b_jac + b_out + b_cov);
-    cudaError_t e = cudaMemcpyAsync(d_uv, uv_host, np * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && need_jac) e = cudaMemcpyAsync(d_jac, jac_host, np * 16, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && coverage_host) e = cudaMemcpyAsync(d_cov, coverage_host, np, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
     unsigned long long *dstats = nullptr;
     if (stats) {
         rc = scratch_stats(&dstats);
         if (rc) return rc;
-        e = cudaMemsetAsync(dstats, 0, sizeof(unsigned long long) * ctf::kNumStats, s);
+        cudaError_t e = cudaMemsetAsync(dstats, 0, sizeof(unsigned long long) * ctf::kNumStats, s);
         if (e != cudaSuccess) return cuda_fail(e, "clearing stats");
     }
-    rc = run_filter(tex, d_uv, d_jac, coverage_host ? d_cov : nullptr, width, height, view_id, alg, seed, ro, d_out,
-                    out_evals_host ? d_ev : nullptr, dstats, s);
+    // Bands of whole tile rows (a multiple of 8 rows fits every tile shape):
+    // the copy-in of band b + 1, the filter of band b and the copy-out of
+    // band b - 1 run at once (copy streams and the caller's stream, ordered
+    // by events).  Each band is filtered as a frame that starts at its row
+    // of the view, which gives the image and counts of one call on the whole
+    // view; group_dedup views stay whole (their distinct-texel count depends
+    // on the groups).
+    HostPipe *hp = nullptr;
+    rc = host_pipe(&hp);
     if (rc) return rc;
-    e = cudaMemcpyAsync(out_rgba_host, d_out, np * 16, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && out_evals_host) e = cudaMemcpyAsync(out_evals_host, d_ev, np, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    const int nb = (ro.group_dedup || np < ((size_t)1 << 20)) ? 1 : kMaxBands;
+    const int rows = ((height + nb - 1) / nb + 7) & ~7;
+    const size_t W = (size_t)width;
+    cudaEvent_t ev_start = hp->ev[0], ev_done = hp->ev[2 * kMaxBands + 1];
+    cudaError_t e = cudaEventRecord(ev_start, s);  // the caller's earlier work on s comes first
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->in, ev_start, 0);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+        const int r0 = b * rows, r1 = std::min(height, r0 + rows);
+        if (r0 >= r1) break;
+        const size_t o = (size_t)r0 * W, n = (size_t)(r1 - r0) * W;
+        e = cudaMemcpyAsync(d_uv + 2 * o, uv_host + 2 * o, n * 8, cudaMemcpyHostToDevice, hp->in);
+        if (e == cudaSuccess && need_jac)
+            e = cudaMemcpyAsync(d_jac + 4 * o, jac_host + 4 * o, n * 16, cudaMemcpyHostToDevice, hp->in);
+        if (e == cudaSuccess && coverage_host)
+            e = cudaMemcpyAsync(d_cov + o, coverage_host + o, n, cudaMemcpyHostToDevice, hp->in);
+        if (e == cudaSuccess) e = cudaEventRecord(hp->ev[1 + b], hp->in);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    for (int b = 0; b < nb; ++b) {
+        const int r0 = b * rows, r1 = std::min(height, r0 + rows);
+        if (r0 >= r1) break;
+        const size_t o = (size_t)r0 * W, n = (size_t)(r1 - r0) * W;
+        e = cudaStreamWaitEvent(s, hp->ev[1 + b], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "band ordering");
+        rc = run_filter(tex, d_uv + 2 * o, d_jac + 4 * o, coverage_host ? d_cov + o : nullptr, width, r1 - r0,
+                        view_id, alg, seed, ro, d_out + 4 * o, out_evals_host ? d_ev + o : nullptr, dstats, s, r0);
+        if (rc) return rc;
+        e = cudaEventRecord(hp->ev[1 + kMaxBands + b], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->out, hp->ev[1 + kMaxBands + b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out_rgba_host + 4 * o, d_out + 4 * o, n * 16, cudaMemcpyDeviceToHost, hp->out);
+        if (e == cudaSuccess && out_evals_host)
+            e = cudaMemcpyAsync(out_evals_host + o, d_ev + o, n, cudaMemcpyDeviceToHost, hp->out);
+        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    }
+    e = cudaEventRecord(ev_done, hp->out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_done, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "band ordering");
     if (stats) return read_stats(dstats, stats, s);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");

@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) bicubic_filter_kernel(const ExactPar
                 cnt.v[kStatTexelEvals] += nactive;
                 cnt.v[kStatTexelEvalsUnique] += nactive;
             }
-            uint4 r = philox4x32_10(make_uint4((uint32_t)px, (uint32_t)py, (uint32_t)p.view, 0u), p.k0, p.k1);
+            uint4 r = philox4x32_10(make_uint4((uint32_t)px, (uint32_t)(py + p.y0), (uint32_t)p.view, 0u), p.k0, p.k1);
             float gx, gy;
             const int i = pick_tap(wx, __fmul_rn((float)(r.x >> 8), 5.9604644775390625e-08f), gx);
             const int j = pick_tap(wy, __fmul_rn((float)(r.y >> 8), 5.9604644775390625e-08f), gy);

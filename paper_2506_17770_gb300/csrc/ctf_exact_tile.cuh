@@ -174,6 +174,7 @@ struct FallbackArgs {
     const uint2 *blocks;
     int Wt, Ht, nbx;
     int view;
+    int y0;  // row of the whole view at which the frame starts
     uint32_t k0, k1;
     int mode;
 };
@@ -185,7 +186,7 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
     const int ai = __popc(A & lt);
     int dx = 0, dy = 0;
     float xi2 = 0.f;
-    if (active) stf_draw(px, py, fa.view, fa.k0, fa.k1, s, t, dx, dy, xi2);
+    if (active) stf_draw(px, py + fa.y0, fa.view, fa.k0, fa.k1, s, t, dx, dy, xi2);
     const int sx = ulx + dx, sy = uly + dy;
     int qx = sx, qy = sy;  // the texel this lane produces
     bool produce = active;
@@ -386,6 +387,7 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
             fa.Ht = p.Ht;
             fa.nbx = p.nbx;
             fa.view = p.view;
+            fa.y0 = p.y0;
             fa.k0 = p.k0;
             fa.k1 = p.k1;
             fa.mode = p.fallback;

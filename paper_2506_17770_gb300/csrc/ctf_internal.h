@@ -60,6 +60,7 @@ enum StatIndex {
 struct __align__(16) ExactParams {
     const uint2 *blocks;  // (Wt/4)*(Ht/4) blocks
     int Wt, Ht, nbx;
+    int y0;               // row of the whole view at which this frame starts (a band of it): STF counters use y0 + py
     const float2 *uv;
     const float4 *jac;
     const uint8_t *cov;   // nullable

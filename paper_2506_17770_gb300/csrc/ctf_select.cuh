@@ -243,7 +243,7 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
         if (kStats && kUnique) cnt.v[kStatTexelEvalsUnique] += nactive;
         if (ps.active) {
             int dx, dy;
-            stf_offset(px, py, p.view, p.k0, p.k1, ps.s, ps.t, dx, dy);
+            stf_offset(px, py + p.y0, p.view, p.k0, p.k1, ps.s, ps.t, dx, dy);
             sel.produce = true;
             sel.my_rank = __popc(A & lt);  // producers are the active lanes
             sel.tx = ps.ulx + dx;

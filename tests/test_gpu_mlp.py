@@ -317,3 +317,20 @@ def test_learned_full_view_bands_match_fp64_oracle():
             assert np.all(err <= tol), (y0, err.max(), (err / tol).max())
     finally:
         _ctf.ctf_texture_destroy(h)
+
+
+@pytest.mark.parametrize("alg", ["stf", "mask"])
+def test_learned_host_entry_point_matches_device(tex64, alg):
+    """ctf_filter_host on a learned texture, in row bands (more than 2^20
+    pixels): image and counts equal one ctf_filter call on the whole view."""
+    W, H = 1400, 800
+    uv, jac, cov = _scene(W, H, 31)
+    out_d, ev_d, st_d = gpu_filter(tex64, uv, jac, cov, alg, {"mask_dim": 11}, seed=5)
+    assert st_d["tiles_fallback_minified"] + st_d["tiles_direct"] > 0
+    h = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (uv, jac, cov)]
+    out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+    ev = torch.empty((H, W), dtype=torch.uint8).pin_memory()
+    st = _ctf.ctf_filter_host(tex64.h, h[0], h[1], h[2], W, H, 0, alg, 5, {"mask_dim": 11}, out, ev, stats=True)
+    assert st == st_d
+    assert np.array_equal(out.numpy().view(np.uint32), out_d.view(np.uint32))
+    assert np.array_equal(ev.numpy(), ev_d)
