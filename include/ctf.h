@@ -203,12 +203,15 @@ int ctf_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t
 /* ctf_filter on HOST buffers: copies uv, jac (and coverage) to device memory
  * that the library owns and reuses, filters, copies the image and counts
  * back, and waits for the stream before returning.  Host buffers that are
- * page-locked (cudaHostAlloc / cudaHostRegister) copy fastest.  Views of at
- * least 2^20 pixels (without group_dedup) go in 4 bands of whole tile rows,
- * so that the copy-in of one band, the filtering of the previous one and the
- * copy-out of the one before overlap (two library-owned copy streams; the
- * filter runs on `stream`); each band is filtered as the part of the view
- * it is, and the results equal those of ctf_filter on the whole view. */
+ * page-locked (cudaHostAlloc / cudaHostRegister) are not copied at all for
+ * a block texture: the kernel reads the inputs and writes the image and
+ * counts in host memory in place (over NVLink-C2C on a Grace-Blackwell
+ * node).  Otherwise, views of at least 2^20 pixels (without group_dedup) go
+ * in 4 bands of whole tile rows, so that the copy-in of one band, the
+ * filtering of the previous one and the copy-out of the one before overlap
+ * (two library-owned copy streams; the filter runs on `stream`); each band
+ * is filtered as the part of the view it is.  The results always equal
+ * those of ctf_filter on the whole view. */
 int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host, const uint8_t *coverage_host,
                     int width, int height, int view_id, ctf_algorithm alg, uint64_t seed,
                     const ctf_filter_opts *opts, float *out_rgba_host, uint8_t *out_evals_host,

@@ -470,6 +470,27 @@ int ctf_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t
     return CTF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The device address of page-locked host memory that the GPU can read and
+// write in place (mapped into the unified address space), or nullptr for
+// pageable memory.
+void *mapped_host(const void *h) {
+    if (!h) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();  // an unknown pointer is pageable memory here
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host, const uint8_t *coverage_host,
                     int width, int height, int view_id, ctf_algorithm alg, uint64_t seed,
                     const ctf_filter_opts *opts, float *out_rgba_host, uint8_t *out_evals_host, ctf_stats *stats,
@@ -485,6 +506,33 @@ int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host
         return CTF_OK;
     }
     const bool need_jac = alg != CTF_ALG_4TAP && alg != CTF_ALG_STF;
+    // Page-locked buffers and a block texture: the kernel reads the inputs
+    // and writes the image and counts in host memory itself (over
+    // NVLink-C2C on a Grace-Blackwell node), with no staging copies.  (The
+    // learned-decode kernels copy their inputs with cp.async and keep the
+    // staged path.)
+    if (tex->mode == CTF_EVAL_BLOCK) {
+        void *m_uv = mapped_host(uv_host), *m_jac = need_jac ? mapped_host(jac_host) : nullptr;
+        void *m_cov = mapped_host(coverage_host), *m_out = mapped_host(out_rgba_host);
+        void *m_ev = mapped_host(out_evals_host);
+        if (m_uv && (m_jac || !need_jac) && (m_cov || !coverage_host) && m_out && (m_ev || !out_evals_host)) {
+            unsigned long long *dstats = nullptr;
+            if (stats) {
+                rc = scratch_stats(&dstats);
+                if (rc) return rc;
+                cudaError_t e = cudaMemsetAsync(dstats, 0, sizeof(unsigned long long) * ctf::kNumStats, s);
+                if (e != cudaSuccess) return cuda_fail(e, "clearing stats");
+            }
+            rc = run_filter(tex, static_cast<const float *>(m_uv), static_cast<const float *>(m_jac),
+                            static_cast<const uint8_t *>(m_cov), width, height, view_id, alg, seed, ro,
+                            static_cast<float *>(m_out), static_cast<uint8_t *>(m_ev), dstats, s);
+            if (rc) return rc;
+            if (stats) return read_stats(dstats, stats, s);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+            return CTF_OK;
+        }
+    }
     // staging layout: uv | jac | out | coverage | evals, each 256-byte aligned
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_uv = up(np * 8), b_jac = up(np * 16), b_out = up(np * 16), b_cov = up(np), b_ev = up(np);

@@ -293,25 +293,29 @@ def test_fig4_thresholds_on_gpu(built):
                                       ("mask", {"texels_per_lane": 2, "budget": 64}),
                                       ("mask", {"filter": 2}), ("box", {"tile_w": 16, "tile_h": 2, "filter": 1})])
 def test_host_entry_point_matches_device(frame, alg, opts):
-    """ctf_filter_host filters a view of more than 2^20 pixels in row bands
-    whose copies overlap the filtering of their neighbours; every band is a
-    frame that starts at its row of the view, so the image and counts equal
-    one ctf_filter call on the whole view (the STF draws of minified and
-    over-budget tiles included)."""
+    """ctf_filter_host on page-locked buffers filters them in place (the
+    kernel reads and writes host memory); on pageable buffers it stages them
+    in 4 row bands of a view of more than 2^20 pixels, whose copies overlap
+    the filtering of their neighbours, each band filtered as the part of the
+    view it is.  Either way the image and counts equal one ctf_filter call on
+    the whole view (the STF draws of minified and over-budget tiles
+    included)."""
     tex, sc = frame
     H, W = sc.H, sc.W
     assert W * H >= 1 << 20
     g = gpu_filter(tex, sc.uv, sc.jac, sc.coverage, alg, opts=opts, seed=3)
     assert g[2]["tiles_fallback_minified"] + g[2]["tiles_direct"] > 0
-    uv = torch.from_numpy(sc.uv).pin_memory()
-    jac = torch.from_numpy(sc.jac).pin_memory()
-    cov = torch.from_numpy(sc.coverage).pin_memory()
-    out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
-    ev = torch.empty((H, W), dtype=torch.uint8).pin_memory()
-    st = _ctf.ctf_filter_host(tex.h, uv, jac, cov, W, H, 0, alg, 3, opts, out, ev, stats=True)
-    assert st == g[2]
-    assert np.array_equal(out.numpy().view(np.uint32), g[0].view(np.uint32))
-    assert np.array_equal(ev.numpy(), g[1])
+    for pinned in (True, False):
+        def host(a):
+            t = torch.from_numpy(np.ascontiguousarray(a))
+            return t.pin_memory() if pinned else t.clone()
+        uv, jac, cov = host(sc.uv), host(sc.jac), host(sc.coverage)
+        out = host(np.zeros((H, W, 4), np.float32))
+        ev = host(np.zeros((H, W), np.uint8))
+        st = _ctf.ctf_filter_host(tex.h, uv, jac, cov, W, H, 0, alg, 3, opts, out, ev, stats=True)
+        assert st == g[2], pinned
+        assert np.array_equal(out.numpy().view(np.uint32), g[0].view(np.uint32)), pinned
+        assert np.array_equal(ev.numpy(), g[1]), pinned
 
 
 def test_argument_errors(mixed):
