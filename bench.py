@@ -445,6 +445,22 @@ def _bench_batch_set(args, dev, stream, learned_tex, block_tex, n_views, sizes):
             "l2": f"not flushed: {npix * 42 / 1e6:.0f} MB of pixel I/O per pass, above the 129 MB L2"}
 
 
+def max_over_ranks(x, device):
+    """The largest of the ranks' values (the slowest rank's time per step),
+    returned on every rank (NCCL tensors on the GPU, gloo ones on the CPU)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world, npix_per_rank, ms_per_step):
+    """Whole-job pixels/s: every rank filters its own view of npix_per_rank
+    pixels per step (no exchange between ranks), the job as slow as its
+    slowest rank."""
+    return world * npix_per_rank / (ms_per_step * 1e-3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -551,11 +567,9 @@ def ours_arm(args):
     clk = clocks.stop()
     ms_per_step = ms / args.steps
     if world > 1:
-        t = torch.tensor([ms_per_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_per_step = float(t.item())
+        ms_per_step = max_over_ranks(ms_per_step, dev)
     st = stats_of(alg, opts)
-    value = world * npix / (ms_per_step * 1e-3)
+    value = weak_scaling_value(world, npix, ms_per_step)
     evpp = st["texel_evals"] / max(1, st["pixels_active"])
 
     if rank != 0:
