@@ -53,6 +53,7 @@ struct GradParams {
     uint32_t k0, k1;       // Philox key
     float dscale;          // 2 / batch
     long long *grad;       // fixed-point gradient accumulators (same layout as params)
+    uint32_t *touched;     // one bit per latent cell (grid 0 cells, then grid 1) whose gradient a texel reached
     long long *loss;       // fixed-point sum of squared errors
 };
 
@@ -370,13 +371,17 @@ __global__ void __launch_bounds__(kGradThreads, 1) grad_kernel(const GradParams 
                 unsigned long long *gl = reinterpret_cast<unsigned long long *>(g.grad + kOffLat + (gi ? lat1 : 0));
                 const int ta[2] = {hi ? tap[2] : tap[0], hi ? tap[3] : tap[1]};
                 const float wa[2] = {hi ? tw[2] : tw[0], hi ? tw[3] : tw[1]};
+                const uint32_t cell0 = gi ? (uint32_t)(lat1 / 8) : 0u;
 #pragma unroll
-                for (int k = 0; k < 2; ++k)
+                for (int k = 0; k < 2; ++k) {
+                    const uint32_t cell = cell0 + (uint32_t)ta[k];
+                    atomicOr(g.touched + (cell >> 5), 1u << (cell & 31u));
 #pragma unroll
                     for (int ch = 0; ch < 8; ++ch) {
                         const long long v = to_fix(__fmul_rn(wa[k], DF[(gi * 8 + ch) * kLd + t]));
                         if (v) atomicAdd(gl + (size_t)ta[k] * 8 + ch, (unsigned long long)v);
                     }
+                }
             }
         }
         __syncthreads();
@@ -406,6 +411,7 @@ __global__ void __launch_bounds__(kGradThreads, 1) grad_kernel(const GradParams 
 struct AdamParams {
     float *params, *m, *v;
     long long *grad;
+    const uint32_t *touched;  // latent cells with a gradient this step (the others' gradients are zero)
     size_t n;
     float beta1, beta2, eps;
     float step_w, step_lat;  // learning rate / (1 - beta1^t), weights and latents
@@ -437,6 +443,16 @@ __device__ __forceinline__ void adam_quad(const AdamParams &a, float step, float
     adam_update(a, g23.y, step, p.w, m.w, v.w);
 }
 
+// Whether quad q has a gradient to read: the weights always, a latent quad
+// (half of a cell's 8 channels) when a texel of the step reached its cell.
+// The gradient of any other latent is exactly zero, so skipping its read and
+// its clearing leaves every update bit for bit the same.
+__device__ __forceinline__ bool quad_has_grad(const AdamParams &a, size_t q) {
+    if (q < (size_t)kOffLat / 4) return true;
+    const size_t cell = (4 * q - kOffLat) >> 3;
+    return (__ldg(a.touched + (cell >> 5)) >> (cell & 31)) & 1u;
+}
+
 // Four parameters per quad, two quads per iteration so that both sets of
 // loads are in flight together.  The buffer length and the start of the
 // latents are multiples of 4; the padding quad (parameters, moments and
@@ -448,30 +464,38 @@ __global__ void adam_kernel(const AdamParams a) {
     float4 *__restrict__ M = reinterpret_cast<float4 *>(a.m);
     float4 *__restrict__ V = reinterpret_cast<float4 *>(a.v);
     longlong2 *__restrict__ G = reinterpret_cast<longlong2 *>(a.grad);
+    const longlong2 z = make_longlong2(0, 0);
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += 2 * stride) {
         const size_t q2 = q + stride;
         const bool two = q2 < n4;
-        const longlong2 g0 = G[2 * q], g1 = G[2 * q + 1];
+        const bool gq = quad_has_grad(a, q), gq2 = two && quad_has_grad(a, q2);
+        const longlong2 g0 = gq ? G[2 * q] : z, g1 = gq ? G[2 * q + 1] : z;
         float4 p = P[q], m = M[q], v = V[q];
-        longlong2 h0 = make_longlong2(0, 0), h1 = make_longlong2(0, 0);
+        longlong2 h0 = z, h1 = z;
         float4 p2 = make_float4(0.f, 0.f, 0.f, 0.f), m2 = p2, v2 = p2;
         if (two) {
-            h0 = G[2 * q2];
-            h1 = G[2 * q2 + 1];
+            if (gq2) {
+                h0 = G[2 * q2];
+                h1 = G[2 * q2 + 1];
+            }
             p2 = P[q2];
             m2 = M[q2];
             v2 = V[q2];
         }
         adam_quad(a, q < (size_t)kWeights / 4 ? a.step_w : a.step_lat, p, m, v, g0, g1);
-        G[2 * q] = make_longlong2(0, 0);
-        G[2 * q + 1] = make_longlong2(0, 0);
+        if (gq) {
+            G[2 * q] = z;
+            G[2 * q + 1] = z;
+        }
         P[q] = p;
         M[q] = m;
         V[q] = v;
         if (two) {
             adam_quad(a, q2 < (size_t)kWeights / 4 ? a.step_w : a.step_lat, p2, m2, v2, h0, h1);
-            G[2 * q2] = make_longlong2(0, 0);
-            G[2 * q2 + 1] = make_longlong2(0, 0);
+            if (gq2) {
+                G[2 * q2] = z;
+                G[2 * q2 + 1] = z;
+            }
             P[q2] = p2;
             M[q2] = m2;
             V[q2] = v2;
@@ -588,6 +612,8 @@ struct ctf_trainer_s {
     size_t nparams = 0;
     float *params = nullptr, *m = nullptr, *v = nullptr;
     long long *grad = nullptr, *loss = nullptr;
+    uint32_t *touched = nullptr;  // latent cells a step's texels reached (zero between steps)
+    size_t touched_words = 0;
     int64_t step = 0;
 };
 
@@ -615,6 +641,7 @@ GradParams grad_params(const ctf_trainer_s *t) {
     g.k1 = (uint32_t)(t->desc.seed >> 32);
     g.dscale = 0.f;
     g.grad = t->grad;
+    g.touched = t->touched;
     g.loss = t->loss;
     return g;
 }
@@ -658,6 +685,7 @@ void free_trainer(ctf_trainer_s *t) {
     cudaFree(t->m);
     cudaFree(t->v);
     cudaFree(t->grad);
+    cudaFree(t->touched);
     cudaFree(t->loss);
     delete t;
 }
@@ -674,7 +702,10 @@ int alloc_trainer(ctf_texture src, const ctf_train_desc *d, ctf_trainer_s **out)
     t->Ht = src->height;
     for (int g = 0; g < 2; ++g) t->n_lat[g] = (size_t)d->latent_w[g] * d->latent_h[g] * 8;
     t->nparams = kOffLat + t->n_lat[0] + t->n_lat[1];
+    t->touched_words = ((t->n_lat[0] + t->n_lat[1]) / 8 + 31) / 32;
     cudaError_t e = cudaMalloc(&t->params, t->nparams * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&t->touched, t->touched_words * 4);
+    if (e == cudaSuccess) e = cudaMemset(t->touched, 0, t->touched_words * 4);
     if (e == cudaSuccess) e = cudaMalloc(&t->m, t->nparams * 4);
     if (e == cudaSuccess) e = cudaMalloc(&t->v, t->nparams * 4);
     if (e == cudaSuccess) e = cudaMalloc(&t->grad, t->nparams * 8);
@@ -773,6 +804,7 @@ int ctf_trainer_step(ctf_trainer t, int64_t steps, void *stream) {
     a.m = t->m;
     a.v = t->v;
     a.grad = t->grad;
+    a.touched = t->touched;
     a.n = t->nparams;
     a.beta1 = t->desc.beta1;
     a.beta2 = t->desc.beta2;
@@ -793,6 +825,7 @@ int ctf_trainer_step(ctf_trainer t, int64_t steps, void *stream) {
             adam_kernel<<<device_sm_count() * 8, 256, 0, s>>>(a);
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess) e = cudaMemsetAsync(t->touched, 0, t->touched_words * 4, s);
         if (e != cudaSuccess) return report_cuda(e, "training step");
         t->step = st + 1;
     }
@@ -820,6 +853,7 @@ int ctf_trainer_gradients(ctf_trainer t, const int32_t *xy, int n, double *loss,
     e = cudaMemcpy(h.data(), t->grad, t->nparams * 8, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(&hl, t->loss, 8, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(t->grad, 0, t->nparams * 8);
+    if (e == cudaSuccess) e = cudaMemset(t->touched, 0, t->touched_words * 4);
     if (e != cudaSuccess) return report_cuda(e, "reading gradients");
     if (loss) *loss = (double)hl / kLossFix / (double)n;
     if (grads) {
