@@ -18,10 +18,14 @@
 // the library's error word and every thread of the CTA leaves together.
 //
 // Two kernels use the chain: a decode of an explicit list of texels, and the
-// learned-decode filter, in which each of the 4 warps runs step 1 of the
-// collaborative flow on its own pixel tile and writes the texel its lane
-// produces into the lane's own row (row 32*warp + lane), so that after the
-// chain every lane holds its own texel value and the gather is a shuffle.
+// learned-decode filter.  In the filter, per-pixel 4-tap gives each warp one
+// pixel tile (its lane's row per tap, four chains per iteration); the
+// collaborative algorithms and STF give each warp two tiles of a group of 8,
+// pack the group's texel lists into consecutive rows (one or two chains) and
+// gather every pixel's taps from the rows (ctf_mlp_chain.cuh, mlp_group).
+// The next group's uv and Jacobian are copied into shared memory with
+// cp.async while a group runs (not for List Merge, whose tables use that
+// space).
 #include <cstdint>
 #include <mutex>
 #include <set>
@@ -69,7 +73,8 @@ __global__ void __launch_bounds__(kRows) mlp_decode_kernel(const MlpDevice m, in
 }
 
 // ---------------------------------------------------------------------------
-// Learned-decode filter: 4 warps, one pixel tile each per iteration.
+// Learned-decode filter: 4 warps; a group of 8 pixel tiles (4 for per-pixel
+// 4-tap) per CTA iteration.
 // ---------------------------------------------------------------------------
 template <int ALG, int TW, int MD>
 __global__ void __launch_bounds__(kRows, 4) mlp_filter_kernel(const ExactParams p, const MlpDevice m, int *err) {
