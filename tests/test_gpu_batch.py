@@ -234,3 +234,64 @@ def test_batch_solo_views_equal_per_view_calls(textures, solo):
         H, W = v["height"], v["width"]
         assert np.array_equal(v["out_rgba"].cpu().numpy()[:H, :W].view(np.uint32), ref[:H, :W].view(np.uint32))
         assert np.array_equal(v["out_evals"].cpu().numpy()[:H, :W], ref_ev[:H, :W])
+
+
+def test_full_size_uneven_views():
+    """The benchmark's batch of 64 uneven views (256..3840 x 256..2160, 179
+    Mpixel; 2048^2 block and 4096^2 learned FP16 textures alternating), Mask-11
+    with 8x4 tiles: the persistent batch (solo_tiles 0) and the default batch
+    (large views in their own launches) both give every view bit for bit as a
+    ctf_filter call on it, and 16-row bands of block views equal the oracle run
+    on those rows of the view (y_offset)."""
+    blocks = synth.random_blocks(2048, 2048, seed=41)
+    tb = _ctf.ctf_texture_create(2048, 2048, blocks)
+    lat, p = _learned_params(9, 4096, 4096)
+    tl = _ctf.ctf_texture_create_mlp(4096, 4096, _ctf.CTF_EVAL_MLP_FP16, lat, *p)
+    try:
+        raw = synth.uneven_views(64, textures=((2048, 2048), (4096, 4096)))
+        views = []
+        for i, (sc, ti) in enumerate(raw):
+            views.append({"tex": tb if ti == 0 else tl, "sc": sc, "width": sc.W, "height": sc.H, "view_id": i,
+                          "uv": torch.from_numpy(sc.uv).cuda(), "jac": torch.from_numpy(sc.jac).cuda(),
+                          "coverage": torch.from_numpy(sc.coverage).cuda(),
+                          "out_rgba": torch.empty((sc.H, sc.W, 4), device="cuda"),
+                          "out_evals": torch.empty((sc.H, sc.W), dtype=torch.uint8, device="cuda")})
+        assert sum(v["width"] * v["height"] for v in views) > 150e6
+        fo = {"tile_w": 8, "tile_h": 4, "mask_dim": 11}
+        ref = []
+        for v in views:
+            o = torch.empty_like(v["out_rgba"])
+            e = torch.empty_like(v["out_evals"])
+            _ctf.ctf_filter(v["tex"], v["uv"], v["jac"], v["coverage"], v["width"], v["height"], v["view_id"], "mask",
+                            0, fo, o, e)
+            ref.append((o, e))
+        _ctf.ctf_sync_check()
+        for solo in (0, 16384):
+            for v in views:
+                v["out_rgba"].fill_(-1.0)
+                v["out_evals"].fill_(7)
+            _ctf.ctf_filter_batch(views, "mask", 0, _ctf.batch_opts(mask_dim=11, solo_tiles=solo))
+            _ctf.ctf_sync_check()
+            for v, (o, e) in zip(views, ref):
+                assert torch.equal(v["out_rgba"].view(torch.int32), o.view(torch.int32)), (solo, v["view_id"])
+                assert torch.equal(v["out_evals"], e), (solo, v["view_id"])
+        # oracle bands of three block views
+        checked = 0
+        for v, (o, e) in zip(views, ref):
+            if v["tex"] is not tb or v["height"] < 64:
+                continue
+            sc = v["sc"]
+            y0 = (v["height"] // 2) & ~3
+            band = slice(y0, y0 + 16)
+            r_out, r_ev, _ = oracle.filter_frame(blocks, 2048, 2048, sc.uv[band], sc.jac[band], sc.coverage[band],
+                                                 view=v["view_id"], alg=oracle.ALG_MASK, seed=0, mask_dim=11,
+                                                 y_offset=y0)
+            np.testing.assert_array_equal(e[band].cpu().numpy(), r_ev)
+            assert np.array_equal(o[band].cpu().numpy().view(np.uint32), r_out.view(np.uint32))
+            checked += 1
+            if checked == 3:
+                break
+        assert checked == 3
+    finally:
+        _ctf.ctf_texture_destroy(tl)
+        _ctf.ctf_texture_destroy(tb)
