@@ -274,6 +274,13 @@ int ctf_mlp_decode(ctf_texture tex, const int32_t *xy, int n, float *out_rgba, v
  * record is then cleared). */
 int ctf_sync_check(void *stream);
 
+/* Self-test of the bounded waits: one CTA waits on an mbarrier that nothing
+ * arrives on, gives up after `polls` tries (1..2^24) as the library's kernels
+ * do when an MMA does not complete, and records CTF_ERR_TIMEOUT, which the
+ * next ctf_sync_check reports (and clears).  The context stays usable.
+ * Returns CTF_ERR_ARG for polls outside the range, else the launch status. */
+int ctf_selftest_bounded_wait(uint32_t polls, void *stream);
+
 /* Training of the learned decode on texels of an exact block texture (the
  * decoder the network stands in for, which also judges its error).  A
  * trainer holds FP32 master parameters (latents, weights, biases) and Adam

@@ -301,6 +301,12 @@ def ctf_sync_check(stream=None):
     _check(load().ctf_sync_check(_stream(stream)))
 
 
+def ctf_selftest_bounded_wait(polls, stream=None):
+    """Launch the bounded-wait self-test (a wait that runs out after `polls`
+    tries and records CTF_ERR_TIMEOUT for the next ctf_sync_check)."""
+    _check(load().ctf_selftest_bounded_wait(ctypes.c_uint32(int(polls)), _stream(stream)))
+
+
 # ---------------------------------------------------------------------------
 # Training
 # ---------------------------------------------------------------------------

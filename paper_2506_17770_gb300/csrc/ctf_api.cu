@@ -397,6 +397,17 @@ int ctf_sync_check(void *stream) {
     return CTF_OK;
 }
 
+int ctf_selftest_bounded_wait(uint32_t polls, void *stream) {
+    g_last_error.clear();
+    if (polls < 1 || polls > (1u << 24)) return fail(CTF_ERR_ARG, "polls %u outside [1, 2^24]", polls);
+    int *err = nullptr;
+    int rc = ctf::device_error_word(&err);
+    if (rc) return rc;
+    cudaError_t e = ctf::launch_bounded_wait_selftest(polls, err, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
+    return CTF_OK;
+}
+
 int ctf_texture_create(const ctf_texture_desc *desc, ctf_texture *out) {
     g_last_error.clear();
     if (!desc || !out) return fail(CTF_ERR_ARG, "desc and out must not be NULL");

@@ -102,6 +102,9 @@ cudaError_t launch_mlp_decode(const MlpDevice &m, int Wt, int Ht, const int2 *xy
 // Sets the learned filter kernel's attributes without launching it (needed
 // before a stream capture records a launch of it).
 cudaError_t prepare_mlp_filter(int alg, int tile_w, int mask_dim);
+
+// One CTA whose bounded mbarrier wait runs out and records CTF_ERR_TIMEOUT.
+cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t stream);
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                               cudaStream_t stream);
 MlpDevice mlp_device_view(const ctf_texture_s *t);

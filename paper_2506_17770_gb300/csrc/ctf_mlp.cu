@@ -120,6 +120,20 @@ __global__ void __launch_bounds__(kRows, 4) mlp_filter_kernel(const ExactParams 
         atomicAdd(p.stats + threadIdx.x, block_stats[threadIdx.x]);
 }
 
+// An mbarrier that nothing arrives on: every thread's bounded wait gives up
+// and the CTA records a timeout, as the chain does for an MMA that never
+// completes.
+__global__ void bounded_wait_selftest_kernel(uint32_t polls, int *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    const bool done = tc::mbar_wait(&bar, 0, polls);
+    if (__syncthreads_or(!done) && threadIdx.x == 0) atomicExch(err, CTF_ERR_TIMEOUT);
+}
+
 using FilterFn = void (*)(const ExactParams, const MlpDevice, int *);
 
 template <int ALG, int TW>
@@ -180,6 +194,11 @@ cudaError_t prepare_mlp_filter(int alg, int tile_w, int mask_dim) {
     default: return cudaErrorInvalidValue;
     }
     return fn ? prepare(fn) : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t stream) {
+    bounded_wait_selftest_kernel<<<1, kRows, 0, stream>>>(polls, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,

@@ -55,3 +55,7 @@ def test_status_strings_and_argument_errors_without_gpu(lib):
     with pytest.raises(_ctf.CtfError) as ei:
         _ctf.ctf_texture_create(6, 8, 0)
     assert ei.value.status == _ctf.CTF_ERR_ARG
+    # the bounded-wait self-test checks its argument before any CUDA call
+    with pytest.raises(_ctf.CtfError) as ei:
+        _ctf.ctf_selftest_bounded_wait(0)
+    assert ei.value.status == _ctf.CTF_ERR_ARG

@@ -334,3 +334,19 @@ def test_learned_host_entry_point_matches_device(tex64, alg):
     assert st == st_d
     assert np.array_equal(out.numpy().view(np.uint32), out_d.view(np.uint32))
     assert np.array_equal(ev.numpy(), ev_d)
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(tex64):
+    """A kernel whose mbarrier wait nobody completes gives up after its bound,
+    records CTF_ERR_TIMEOUT for the next ctf_sync_check (which clears it), and
+    the next filter call runs and gives its usual result."""
+    uv, jac, cov = _scene(37, 21, 12)
+    before = gpu_filter(tex64, uv, jac, cov, "mask", {"mask_dim": 11})
+    _ctf.ctf_selftest_bounded_wait(1 << 12)
+    with pytest.raises(_ctf.CtfError) as ei:
+        _ctf.ctf_sync_check()
+    assert ei.value.status == _ctf.CTF_ERR_TIMEOUT
+    _ctf.ctf_sync_check()  # the record is cleared
+    after = gpu_filter(tex64, uv, jac, cov, "mask", {"mask_dim": 11})
+    assert np.array_equal(after[0].view(np.uint32), before[0].view(np.uint32))
+    assert np.array_equal(after[1], before[1]) and after[2] == before[2]
