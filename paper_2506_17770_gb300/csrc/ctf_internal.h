@@ -108,6 +108,12 @@ cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t 
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                               cudaStream_t stream);
 MlpDevice mlp_device_view(const ctf_texture_s *t);
+// The learned filter with warps specialised by role (ctf_mlp_ws.cu), which
+// launch_mlp_filter uses for STF, Box and Mask Sampling without group_dedup.
+bool mlp_filter_ws_applies(const ExactParams &p, int alg);
+cudaError_t prepare_mlp_filter_ws(int alg, int tile_w, int mask_dim);
+cudaError_t launch_mlp_filter_ws(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim,
+                                 int *err, cudaStream_t stream);
 
 // Error reporting shared by the C ABI translation units (ctf_api.cu).
 int report(int status, const char *fmt, ...);

@@ -25,7 +25,9 @@
 // gather every pixel's taps from the rows (ctf_mlp_chain.cuh, mlp_group).
 // The next group's uv and Jacobian are copied into shared memory with
 // cp.async while a group runs (not for List Merge, whose tables use that
-// space).
+// space).  STF, Box and Mask Sampling without group_dedup run instead in the
+// kernel whose warps are specialised by role (ctf_mlp_ws.cu), which gives the
+// same outputs.
 #include <cstdint>
 #include <mutex>
 #include <set>
@@ -193,7 +195,11 @@ cudaError_t prepare_mlp_filter(int alg, int tile_w, int mask_dim) {
     case 16: fn = pick_alg<16>(alg, mask_dim); break;
     default: return cudaErrorInvalidValue;
     }
-    return fn ? prepare(fn) : cudaErrorInvalidValue;
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = prepare(fn);
+    if (e == cudaSuccess && (alg == ALG_STF || alg == ALG_BOX || alg == ALG_MASK))
+        e = prepare_mlp_filter_ws(alg, tile_w, mask_dim);
+    return e;
 }
 
 cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t stream) {
@@ -213,6 +219,7 @@ cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg,
     if (!fn) return cudaErrorInvalidValue;
     if (p.n_tiles == 0) return cudaSuccess;
     if (p.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile positions use 32-bit arithmetic
+    if (mlp_filter_ws_applies(p, alg)) return launch_mlp_filter_ws(p, m, alg, tile_w, mask_dim, err, stream);
     cudaError_t e = prepare(fn);
     if (e != cudaSuccess) return e;
     const long long iters = (p.n_tiles + mlp_group_tiles(alg) - 1) / mlp_group_tiles(alg);

@@ -77,9 +77,51 @@ class LearnedTex:
         _ctf.ctf_texture_destroy(self.h)
 
 
+class LearnedTexFP8:
+    """E4M3 texture of the same random parameters.  The activation ranges are
+    those of the FP64 network over every texel (times 1.1), so nothing
+    saturates.  Per-texel bound as for FP16, with E4M3's relative rounding
+    2^-4 plus half its subnormal spacing (2^-10 in scaled units) per layer
+    input, through |W_eff| with W_eff = s_o q[o][k] / a_k as stored."""
+
+    def __init__(self, Wt, Ht, seed=1):
+        self.Wt, self.Ht = Wt, Ht
+        lat, p = random_params(seed, Wt, Ht)
+        full = oracle.MLP((lat[0], lat[1]), *p)
+        ys, xs = np.meshgrid(np.arange(Ht), np.arange(Wt), indexing="ij")
+        xs, ys = xs.ravel(), ys.ravel()
+        F = np.stack([oracle.mlp_features(full, Wt, Ht, int(x), int(y)) for x, y in zip(xs, ys)])
+        h1 = np.maximum(F @ p[0].T.astype(np.float64) + p[1], 0)
+        h2 = np.maximum(h1 @ p[2].T.astype(np.float64) + p[3], 0)
+        amax = [(1.1 * np.abs(a).max(axis=0) + 1e-3).astype(np.float32) for a in (F, h1, h2)]
+        self.h = _ctf.ctf_texture_create_mlp(Wt, Ht, _ctf.CTF_EVAL_MLP_FP8, lat, *p, act_absmax=amax)
+        st = _ctf.ctf_mlp_export(self.h, (lat[0].shape, lat[1].shape))
+        weff = [(st[f"ws{l}"][:, None] * st[w] / st[f"as{l}"][None, :]).astype(np.float64)
+                for l, w in enumerate(("w1", "w2", "w3"))]
+        self.mlp = oracle.MLP((st["lat0"], st["lat1"]), weff[0], st["b1"], weff[1], st["b2"], weff[2], st["b3"])
+        F = np.stack([oracle.mlp_features(self.mlp, Wt, Ht, int(x), int(y)) for x, y in zip(xs, ys)])
+        h1 = np.maximum(F @ weff[0].T + st["b1"], 0)
+        h2 = np.maximum(h1 @ weff[1].T + st["b2"], 0)
+        u = 2.0 ** -4
+        e_f = u * np.abs(F) + 2.0 ** -10 * st["as0"]
+        e_h1 = u * h1 + 2.0 ** -10 * st["as1"] + e_f @ np.abs(weff[0]).T
+        e_h2 = u * h2 + 2.0 ** -10 * st["as2"] + e_h1 @ np.abs(weff[1]).T
+        self.bound = (2.0 * (e_h2 @ np.abs(weff[2]).T) + 1e-5).reshape(Ht, Wt, 4)
+
+    def close(self):
+        _ctf.ctf_texture_destroy(self.h)
+
+
 @pytest.fixture(scope="module")
 def tex64():
     t = LearnedTex(64, 64, seed=1)
+    yield t
+    t.close()
+
+
+@pytest.fixture(scope="module")
+def tex64_fp8():
+    t = LearnedTexFP8(64, 64, seed=1)
     yield t
     t.close()
 
@@ -190,6 +232,37 @@ def test_learned_filter_matches_fp64_oracle(tex64, alg, W, H, seed):
         tol = _pixel_bounds(tex64, uv)
         err = np.abs(out - ref)
         assert np.all(err <= tol), (alg, opts, err.max())
+
+
+@pytest.mark.parametrize("alg", list(ALGS))
+def test_fp8_filter_matches_fp64_oracle_and_every_kernel_agrees(tex64_fp8, alg):
+    """The FP8 E4M3 filter on a ragged view: counts bit-exact and pixels
+    within the E4M3 bound of the FP64 oracle; the kernel with one role per
+    warp (taken with group_dedup) and the persistent batch kernel give the
+    same image bitwise as the single-view kernel."""
+    W, H = 133, 70
+    uv, jac, cov = _scene(W, H, 17)
+    out, ev, st = gpu_filter(tex64_fp8, uv, jac, cov, alg, {"mask_dim": 11})
+    ref, ref_ev, ref_st = oracle.filter_frame_learned_f64(tex64_fp8.mlp, 64, 64, uv, jac, cov, alg=ALGS[alg],
+                                                          seed=0, mask_dim=11)
+    np.testing.assert_array_equal(ev, ref_ev)
+    assert st == ref_st
+    err = np.abs(out - ref)
+    tol = _pixel_bounds(tex64_fp8, uv)
+    assert np.all(err <= tol), (alg, err.max(), (err / tol).max())
+    assert err.max() > 0  # E4M3 rounding shows
+    if alg != "4tap":
+        out1 = gpu_filter(tex64_fp8, uv, jac, cov, alg, {"mask_dim": 11, "group_dedup": 1})[0]
+        assert np.array_equal(out1.view(np.uint32), out.view(np.uint32))
+    view = {"tex": tex64_fp8.h, "uv": torch.from_numpy(uv).cuda(), "jac": torch.from_numpy(jac).cuda(),
+            "coverage": torch.from_numpy(cov).cuda(), "width": W, "height": H, "view_id": 0,
+            "out_rgba": torch.full((H, W, 4), -1.0, device="cuda"),
+            "out_evals": torch.full((H, W), 7, dtype=torch.uint8, device="cuda")}
+    stb = _ctf.ctf_filter_batch([view], alg, 0, _ctf.batch_opts(mask_dim=11, solo_tiles=0), stats=True)
+    _ctf.ctf_sync_check()
+    assert np.array_equal(view["out_rgba"].cpu().numpy().view(np.uint32), out.view(np.uint32))
+    np.testing.assert_array_equal(view["out_evals"].cpu().numpy(), ev)
+    assert stb == st
 
 
 def test_learned_success_equals_learned_4tap_bitwise(tex64):
