@@ -215,8 +215,9 @@ def ctf_filter(tex, uv, jac, coverage, width, height, view_id, alg, seed, opts, 
 def ctf_filter_host(tex, uv, jac, coverage, width, height, view_id, alg, seed, opts, out_rgba, out_evals,
                     stats: bool = False, stream=None):
     """ctf_filter on host buffers: page-locked buffers of a block texture in
-    place (the kernel reads and writes host memory), others staged through
-    library-owned device buffers; synchronous."""
+    place (the kernel reads the inputs and writes the image in host memory;
+    the counts come back in one copy), others staged through library-owned
+    device buffers; synchronous."""
     st = ctf_stats() if stats else None
     rc = load().ctf_filter_host(tex, _ptr(uv), _ptr(jac), _ptr(coverage), int(width), int(height),
                                 int(view_id), _alg(alg), int(seed) % 2**64,

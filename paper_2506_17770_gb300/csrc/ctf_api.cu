@@ -518,15 +518,24 @@ int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host
     }
     const bool need_jac = alg != CTF_ALG_4TAP && alg != CTF_ALG_STF;
     // Page-locked buffers and a block texture: the kernel reads the inputs
-    // and writes the image and counts in host memory itself (over
-    // NVLink-C2C on a Grace-Blackwell node), with no staging copies.  (The
+    // and writes the image in host memory itself (over NVLink-C2C on a
+    // Grace-Blackwell node), with no staging copies.  The counts, one byte
+    // per pixel, go to device memory and come back in one copy after the
+    // kernel: written in place they would cross the link as 8-byte pieces
+    // of 128-byte lines, which took longer than the copy.  (The
     // learned-decode kernels copy their inputs with cp.async and keep the
     // staged path.)
     if (tex->mode == CTF_EVAL_BLOCK) {
         void *m_uv = mapped_host(uv_host), *m_jac = need_jac ? mapped_host(jac_host) : nullptr;
         void *m_cov = mapped_host(coverage_host), *m_out = mapped_host(out_rgba_host);
-        void *m_ev = mapped_host(out_evals_host);
-        if (m_uv && (m_jac || !need_jac) && (m_cov || !coverage_host) && m_out && (m_ev || !out_evals_host)) {
+        if (m_uv && (m_jac || !need_jac) && (m_cov || !coverage_host) && m_out) {
+            uint8_t *d_ev = nullptr;
+            if (out_evals_host) {
+                void *stage = nullptr;
+                rc = scratch_stage(np, &stage);
+                if (rc) return rc;
+                d_ev = static_cast<uint8_t *>(stage);
+            }
             unsigned long long *dstats = nullptr;
             if (stats) {
                 rc = scratch_stats(&dstats);
@@ -536,8 +545,12 @@ int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host
             }
             rc = run_filter(tex, static_cast<const float *>(m_uv), static_cast<const float *>(m_jac),
                             static_cast<const uint8_t *>(m_cov), width, height, view_id, alg, seed, ro,
-                            static_cast<float *>(m_out), static_cast<uint8_t *>(m_ev), dstats, s);
+                            static_cast<float *>(m_out), d_ev, dstats, s);
             if (rc) return rc;
+            if (d_ev) {
+                cudaError_t e = cudaMemcpyAsync(out_evals_host, d_ev, np, cudaMemcpyDeviceToHost, s);
+                if (e != cudaSuccess) return cuda_fail(e, "copying counts");
+            }
             if (stats) return read_stats(dstats, stats, s);
             cudaError_t e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");

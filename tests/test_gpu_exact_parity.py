@@ -294,24 +294,25 @@ def test_fig4_thresholds_on_gpu(built):
                                       ("mask", {"filter": 2}), ("box", {"tile_w": 16, "tile_h": 2, "filter": 1})])
 def test_host_entry_point_matches_device(frame, alg, opts):
     """ctf_filter_host on page-locked buffers filters them in place (the
-    kernel reads and writes host memory); on pageable buffers it stages them
-    in 4 row bands of a view of more than 2^20 pixels, whose copies overlap
-    the filtering of their neighbours, each band filtered as the part of the
-    view it is.  Either way the image and counts equal one ctf_filter call on
-    the whole view (the STF draws of minified and over-budget tiles
-    included)."""
+    kernel reads the inputs and writes the image in host memory; the counts
+    come back in one copy, into page-locked or pageable memory); on pageable
+    buffers it stages them in 4 row bands of a view of more than 2^20
+    pixels, whose copies overlap the filtering of their neighbours, each band
+    filtered as the part of the view it is.  Either way the image and counts
+    equal one ctf_filter call on the whole view (the STF draws of minified
+    and over-budget tiles included)."""
     tex, sc = frame
     H, W = sc.H, sc.W
     assert W * H >= 1 << 20
     g = gpu_filter(tex, sc.uv, sc.jac, sc.coverage, alg, opts=opts, seed=3)
     assert g[2]["tiles_fallback_minified"] + g[2]["tiles_direct"] > 0
-    for pinned in (True, False):
-        def host(a):
+    for pinned, ev_pinned in ((True, True), (True, False), (False, False)):
+        def host(a, pin=pinned):
             t = torch.from_numpy(np.ascontiguousarray(a))
-            return t.pin_memory() if pinned else t.clone()
+            return t.pin_memory() if pin else t.clone()
         uv, jac, cov = host(sc.uv), host(sc.jac), host(sc.coverage)
         out = host(np.zeros((H, W, 4), np.float32))
-        ev = host(np.zeros((H, W), np.uint8))
+        ev = host(np.full((H, W), 77, np.uint8), ev_pinned)
         st = _ctf.ctf_filter_host(tex.h, uv, jac, cov, W, H, 0, alg, 3, opts, out, ev, stats=True)
         assert st == g[2], pinned
         assert np.array_equal(out.numpy().view(np.uint32), g[0].view(np.uint32)), pinned
