@@ -668,8 +668,9 @@ def ours_arm(args):
             "cpu_baseline": cpu,
             "e2e": {"value": npix / e2e_s, "unit": "pixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "entry_point": "ctf_filter_host",
-                    "transfer": "page-locked host buffers, read and written in place by the kernel over NVLink-C2C; "
-                                "three buffer sets in turn (261 MB, above L2)"},
+                    "transfer": "page-locked host buffers: inputs read and the image written in place by the kernel "
+                                "over NVLink-C2C, the counts copied back in one copy; three buffer sets in turn "
+                                "(261 MB, above L2)"},
             "learned": learned,
             "batch": batch,
             "gpu_launches": args.steps,
