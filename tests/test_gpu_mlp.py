@@ -265,6 +265,25 @@ def test_fp8_filter_matches_fp64_oracle_and_every_kernel_agrees(tex64_fp8, alg):
     assert stb == st
 
 
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 37), (37, 1), (8, 4), (9, 5), (64, 3)])
+@pytest.mark.parametrize("alg", ["stf", "box", "mask", "list_merge"])
+def test_learned_tiny_and_uncovered_views(tex64, W, H, alg):
+    """Views of one pixel, one row, one column, one tile and a few ragged
+    tiles (a group of 8 tiles with most slots empty): counts and statistics
+    bit-exact, pixels within the FP16 bound; with nothing covered, zeros."""
+    uv, jac, cov = _scene(W, H, 5)
+    cov[:] = 1
+    out, ev, st = gpu_filter(tex64, uv, jac, cov, alg, {"mask_dim": 11})
+    ref, ref_ev, ref_st = oracle.filter_frame_learned_f64(tex64.mlp, 64, 64, uv, jac, cov, alg=ALGS[alg], seed=0,
+                                                          mask_dim=11)
+    np.testing.assert_array_equal(ev, ref_ev)
+    assert st == ref_st
+    assert np.all(np.abs(out - ref) <= _pixel_bounds(tex64, uv))
+    out, ev, st = gpu_filter(tex64, uv, jac, np.zeros_like(cov), alg, {"mask_dim": 11})
+    assert st["pixels_active"] == 0 and st["tiles_empty"] == st["tiles_total"] > 0
+    assert not out.any() and not ev.any()
+
+
 def test_learned_success_equals_learned_4tap_bitwise(tex64):
     sc = synth.magnified_plane(128, 128, 64, 64, scale=0.25)
     ref = gpu_filter(tex64, sc.uv, sc.jac, None, "4tap")[0]
