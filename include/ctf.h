@@ -275,6 +275,11 @@ int ctf_mlp_decode(ctf_texture tex, const int32_t *xy, int n, float *out_rgba, v
  * record is then cleared). */
 int ctf_sync_check(void *stream);
 
+/* The same as ctf_sync_check, under the name of the problem statement's
+ * interface (asynchronous device errors are reported by the next call or
+ * by this one). */
+int ctf_stream_status(void *stream);
+
 /* Self-test of the bounded waits: one CTA waits on an mbarrier that nothing
  * arrives on, gives up after `polls` tries (1..2^24) as the library's kernels
  * do when an MMA does not complete, and records CTF_ERR_TIMEOUT, which the
@@ -352,6 +357,40 @@ int ctf_trainer_load(ctf_texture exact_src, const char *path, ctf_trainer *out);
  * and the largest absolute channel difference.  PSNR = -10 log10(mse).
  * Synchronous. */
 int ctf_texture_compare(ctf_texture exact_ref, ctf_texture learned, double *mse_rgb, double *max_abs, void *stream);
+
+/* One-call training of a learned texture on the exact decode of exact_src
+ * (the paper's costly texel evaluation, Sec. 4.3.1, here a neural decoder
+ * fitted to the block texture): a trainer with `desc` runs
+ * desc->total_steps steps on the stream, its parameters are exported as a
+ * learned texture of `mode` (*out_mlp, owned by the caller), that texture
+ * is compared with exact_src over every texel, and the trainer is
+ * destroyed.  report (nullable, host) receives the steps, texels sampled,
+ * wall time and error.  Synchronous.  Errors: those of ctf_trainer_create,
+ * ctf_trainer_step, ctf_trainer_export and ctf_texture_compare; nothing is
+ * returned on failure. */
+typedef struct {
+    int64_t steps, texels;   /* optimisation steps and texels sampled */
+    double seconds;          /* wall time of the steps, stream drained */
+    double mse_rgb, max_abs; /* exported texture vs exact_src, every texel */
+    double psnr_db;          /* -10 log10(mse_rgb) */
+} ctf_train_report;
+int ctf_mlp_train(ctf_texture exact_src, const ctf_train_desc *desc, ctf_eval_mode mode, ctf_texture *out_mlp,
+                  ctf_train_report *report, void *stream);
+
+/* Texture checkpoints: a block texture's blocks, or a learned texture's
+ * stored (quantised) parameters, in a versioned binary file with an FNV-1a
+ * checksum.  ctf_checkpoint_load reads and checks the whole file (magic,
+ * version, mode, sizes, checksum: CTF_ERR_CORRUPT on a mismatch, CTF_ERR_ARG
+ * if it cannot be read) before any device work, then builds a texture on
+ * the current device that filters bit for bit like the saved one (*out,
+ * owned by the caller).  Layout, little-endian: "CTFTEX01", uint32 version
+ * 1, int32 mode, width, height, latent_w[0], latent_h[0], latent_w[1],
+ * latent_h[1] (0 for block textures); the payload: the blocks, or float32
+ * latent[0], latent[1], w1, b1, w2, b2, w3, b3 as stored and, for FP8,
+ * weight_scale[0..2] and act_scale[0..2]; then the uint64 FNV-1a of every
+ * byte before it. */
+int ctf_checkpoint_save(ctf_texture tex, const char *path);
+int ctf_checkpoint_load(const char *path, ctf_texture *out);
 
 /* Batched filtering: many views, each with its own texture (block or
  * learned), size, magnification and buffers.  Views of at least solo_tiles

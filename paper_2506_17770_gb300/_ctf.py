@@ -115,6 +115,10 @@ def _bind_optional(lib):
         "ctf_trainer_save": ([P, ctypes.c_char_p], I),
         "ctf_trainer_load": ([P, ctypes.c_char_p, P], I),
         "ctf_texture_compare": ([P, P, P, P, P], I),
+        "ctf_mlp_train": ([P, P, I, P, P, P], I),
+        "ctf_checkpoint_save": ([P, ctypes.c_char_p], I),
+        "ctf_checkpoint_load": ([ctypes.c_char_p, P], I),
+        "ctf_stream_status": ([P], I),
         "ctf_filter_batch": ([P, I, I, U64, P, P, P], I),
         "ctf_batch_graph_create": ([P, I, I, U64, P, P], I),
         "ctf_batch_graph_launch": ([P, P], I),
@@ -302,6 +306,11 @@ def ctf_sync_check(stream=None):
     _check(load().ctf_sync_check(_stream(stream)))
 
 
+def ctf_stream_status(stream=None):
+    """ctf_sync_check under the interface's other name."""
+    _check(load().ctf_stream_status(_stream(stream)))
+
+
 def ctf_selftest_bounded_wait(polls, stream=None):
     """Launch the bounded-wait self-test (a wait that runs out after `polls`
     tries and records CTF_ERR_TIMEOUT for the next ctf_sync_check)."""
@@ -417,6 +426,33 @@ def ctf_texture_compare(exact_tex, learned_tex, stream=None):
     _check(load().ctf_texture_compare(exact_tex, learned_tex, ctypes.byref(mse), ctypes.byref(mx),
                                       _stream(stream)))
     return mse.value, mx.value
+
+
+class ctf_train_report(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("texels", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("mse_rgb", ctypes.c_double), ("max_abs", ctypes.c_double), ("psnr_db", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def ctf_mlp_train(exact_tex, desc, mode, stream=None):
+    """Train, export and compare in one call: (learned texture, report dict)."""
+    out = ctypes.c_void_p()
+    rep = ctf_train_report()
+    _check(load().ctf_mlp_train(exact_tex, ctypes.byref(desc), int(mode), ctypes.byref(out), ctypes.byref(rep),
+                                _stream(stream)))
+    return out, rep.as_dict()
+
+
+def ctf_checkpoint_save(tex, path):
+    _check(load().ctf_checkpoint_save(tex, path.encode()))
+
+
+def ctf_checkpoint_load(path):
+    out = ctypes.c_void_p()
+    _check(load().ctf_checkpoint_load(path.encode(), ctypes.byref(out)))
+    return out
 
 
 # ---------------------------------------------------------------------------

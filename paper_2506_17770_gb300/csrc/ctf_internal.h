@@ -108,6 +108,20 @@ cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t 
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                               cudaStream_t stream);
 MlpDevice mlp_device_view(const ctf_texture_s *t);
+// Uploads a learned texture's stored (already quantised) parameters: the
+// FP16 latent grids and the operand image (ctf_mlp_host.cu).  On failure the
+// caller frees what was allocated.
+int upload_mlp_texture(ctf_texture_s *t);
+
+// 64-bit FNV-1a over n bytes, continuing from h (checkpoint checksums).
+inline uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *b = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
 // The learned filter with warps specialised by role (ctf_mlp_ws.cu), which
 // launch_mlp_filter uses for STF, Box and Mask Sampling without group_dedup.
 bool mlp_filter_ws_applies(const ExactParams &p, int alg);

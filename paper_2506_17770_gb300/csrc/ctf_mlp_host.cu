@@ -1,6 +1,7 @@
 // ctf_mlp_host.cu -- C ABI of the learned texel decode: texture creation
-// (quantisation to FP16 or FP8 E4M3 and packing of the tensor-core operand
-// image), export of the stored parameters, and decode of a texel list.
+// (quantisation to FP16 or FP8 E4M3, then the upload of the stored values:
+// FP16 latent grids and the tensor-core operand image), export of the stored
+// parameters, and decode of a texel list.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -35,6 +36,56 @@ float e4m3_value(uint8_t b) {
 }
 
 }  // namespace
+
+int upload_mlp_texture(ctf_texture_s *t) {
+    const bool fp8 = t->mode == CTF_EVAL_MLP_FP8;
+    // latents: the stored values are FP16 numbers, so the conversion is exact
+    for (int g = 0; g < 2; ++g) {
+        const size_t n = t->s_lat[g].size();
+        std::vector<__half> h(n);
+        for (size_t i = 0; i < n; ++i) h[i] = __float2half_rn(t->s_lat[g][i]);
+        cudaError_t e = cudaMalloc(&t->lat[g], n * sizeof(__half));
+        if (e == cudaSuccess) e = cudaMemcpy(t->lat[g], h.data(), n * sizeof(__half), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return report_cuda(e, "latent upload");
+    }
+    // operand image: weights (FP16 or E4M3 numbers, converted exactly), biases, scales
+    std::vector<unsigned char> img(kImgBytes, 0);
+    auto put_f32 = [&](int off, int i, float v) { std::memcpy(img.data() + off + 4 * i, &v, 4); };
+    for (int i = 0; i < kMlpHidden; ++i) {
+        put_f32(kImgB1, i, t->s_b1[i]);
+        put_f32(kImgB2, i, t->s_b2[i]);
+    }
+    for (int i = 0; i < kMlpOut; ++i) put_f32(kImgB3, i, t->s_b3[i]);
+    const std::vector<float> *S[3] = {&t->s_w1, &t->s_w2, &t->s_w3};
+    const int nin[3] = {kMlpIn, kMlpHidden, kMlpHidden};
+    const int rows[3] = {kMlpHidden, kMlpHidden, kMlpOut};
+    const int imgoff[3] = {kImgW1, kImgW2, kImgW3};
+    if (!fp8) {
+        const int Kimg[3] = {16, 64, 64};
+        for (int l = 0; l < 3; ++l)
+            for (int o = 0; o < rows[l]; ++o)
+                for (int k = 0; k < nin[l]; ++k) {
+                    const __half h = __float2half_rn((*S[l])[(size_t)o * nin[l] + k]);
+                    std::memcpy(img.data() + imgoff[l] + core_offset(o, k, Kimg[l], 2), &h, 2);
+                }
+    } else {
+        const int Kimg[3] = {32, 64, 64};
+        const int soff[3] = {kImgS1, kImgS2, kImgS3};
+        const int aoff[3] = {kImgA1, kImgA2, kImgA3};
+        for (int l = 0; l < 3; ++l) {
+            for (int k = 0; k < nin[l]; ++k) put_f32(aoff[l], k, 1.0f / t->s_ascale[l][k]);
+            for (int o = 0; o < rows[l]; ++o) {
+                put_f32(soff[l], o, t->s_wscale[l][o]);
+                for (int k = 0; k < nin[l]; ++k)
+                    img[imgoff[l] + core_offset(o, k, Kimg[l], 1)] = e4m3((*S[l])[(size_t)o * nin[l] + k]);
+            }
+        }
+    }
+    cudaError_t e = cudaMalloc(&t->img, kImgBytes);
+    if (e == cudaSuccess) e = cudaMemcpy(t->img, img.data(), kImgBytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return report_cuda(e, "operand image upload");
+    return CTF_OK;
+}
 
 MlpDevice mlp_device_view(const ctf_texture_s *t) {
     MlpDevice m;
@@ -103,58 +154,30 @@ int ctf_texture_create_mlp(const ctf_mlp_desc *d, ctf_texture *out) {
 
     // latents: FP16, round to nearest
     for (int g = 0; g < 2; ++g) {
-        const size_t n = lat[g].size();
-        std::vector<__half> h(n);
-        t->s_lat[g].resize(n);
-        for (size_t i = 0; i < n; ++i) {
-            h[i] = __float2half_rn(lat[g][i]);
-            t->s_lat[g][i] = __half2float(h[i]);
-        }
-        cudaError_t e = cudaMalloc(&t->lat[g], n * sizeof(__half));
-        if (e == cudaSuccess) e = cudaMemcpy(t->lat[g], h.data(), n * sizeof(__half), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return bail(report_cuda(e, "latent upload"));
+        t->s_lat[g].resize(lat[g].size());
+        for (size_t i = 0; i < lat[g].size(); ++i) t->s_lat[g][i] = __half2float(__float2half_rn(lat[g][i]));
     }
-
-    // operand image
-    std::vector<unsigned char> img(kImgBytes, 0);
-    auto put_f32 = [&](int off, int i, float v) { std::memcpy(img.data() + off + 4 * i, &v, 4); };
     t->s_b1 = b1;
     t->s_b2 = b2;
     t->s_b3 = b3;
-    for (int i = 0; i < kMlpHidden; ++i) {
-        put_f32(kImgB1, i, b1[i]);
-        put_f32(kImgB2, i, b2[i]);
-    }
-    for (int i = 0; i < kMlpOut; ++i) put_f32(kImgB3, i, b3[i]);
     const std::vector<float> *W[3] = {&w1, &w2, &w3};
     std::vector<float> *S[3] = {&t->s_w1, &t->s_w2, &t->s_w3};
     const int rows[3] = {kMlpHidden, kMlpHidden, kMlpOut};
-    const int imgoff[3] = {kImgW1, kImgW2, kImgW3};
     if (!fp8) {
-        const int Kimg[3] = {16, 64, 64};
         for (int l = 0; l < 3; ++l) {
             S[l]->resize((size_t)rows[l] * nin[l]);
-            for (int o = 0; o < rows[l]; ++o)
-                for (int k = 0; k < nin[l]; ++k) {
-                    const __half h = __float2half_rn((*W[l])[(size_t)o * nin[l] + k]);
-                    (*S[l])[(size_t)o * nin[l] + k] = __half2float(h);
-                    std::memcpy(img.data() + imgoff[l] + core_offset(o, k, Kimg[l], 2), &h, 2);
-                }
+            for (size_t i = 0; i < S[l]->size(); ++i) (*S[l])[i] = __half2float(__float2half_rn((*W[l])[i]));
         }
     } else {
         // activation scales a[k] = absmax / 448 per input channel; weights
         // W'[o][k] = W[o][k] * a[k] scaled per output channel by s[o] =
         // max_k |W'[o][k]| / 448; stored q = e4m3(W' / s).  Then
         // sum_k e4m3(x_k / a_k) * q[o][k] * s[o] approximates (W x)[o].
-        const int Kimg[3] = {32, 64, 64};
-        const int soff[3] = {kImgS1, kImgS2, kImgS3};
-        const int aoff[3] = {kImgA1, kImgA2, kImgA3};
         for (int l = 0; l < 3; ++l) {
             std::vector<float> a(nin[l]);
             for (int k = 0; k < nin[l]; ++k) {
                 const float m = amax[l][k];
                 a[k] = m > 0.f ? m / 448.0f : 1.0f;
-                put_f32(aoff[l], k, 1.0f / a[k]);
             }
             t->s_ascale[l] = a;
             S[l]->resize((size_t)rows[l] * nin[l]);
@@ -164,18 +187,13 @@ int ctf_texture_create_mlp(const ctf_mlp_desc *d, ctf_texture *out) {
                 for (int k = 0; k < nin[l]; ++k) mx = std::fmax(mx, std::fabs((*W[l])[(size_t)o * nin[l] + k] * a[k]));
                 const float s = mx > 0.f ? mx / 448.0f : 1.0f;
                 t->s_wscale[l][o] = s;
-                put_f32(soff[l], o, s);
-                for (int k = 0; k < nin[l]; ++k) {
-                    const uint8_t q = e4m3((*W[l])[(size_t)o * nin[l] + k] * a[k] / s);
-                    (*S[l])[(size_t)o * nin[l] + k] = e4m3_value(q);
-                    img[imgoff[l] + core_offset(o, k, Kimg[l], 1)] = q;
-                }
+                for (int k = 0; k < nin[l]; ++k)
+                    (*S[l])[(size_t)o * nin[l] + k] = e4m3_value(e4m3((*W[l])[(size_t)o * nin[l] + k] * a[k] / s));
             }
         }
     }
-    cudaError_t e = cudaMalloc(&t->img, kImgBytes);
-    if (e == cudaSuccess) e = cudaMemcpy(t->img, img.data(), kImgBytes, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return bail(report_cuda(e, "operand image upload"));
+    rc = upload_mlp_texture(t);
+    if (rc) return bail(rc);
     *out = t;
     return CTF_OK;
 }

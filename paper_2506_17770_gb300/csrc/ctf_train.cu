@@ -744,15 +744,6 @@ void arrays_of(const ctf_mlp_arrays *a, float *p[8]) {
     p[7] = a->b3;
 }
 
-uint64_t fnv1a(const void *data, size_t n, uint64_t h) {
-    const unsigned char *b = static_cast<const unsigned char *>(data);
-    for (size_t i = 0; i < n; ++i) {
-        h ^= b[i];
-        h *= 1099511628211ull;
-    }
-    return h;
-}
-
 constexpr char kMagic[8] = {'C', 'T', 'F', 'T', 'R', 'N', '0', '1'};
 constexpr uint32_t kVersion = 1;
 

@@ -59,3 +59,59 @@ def test_status_strings_and_argument_errors_without_gpu(lib):
     with pytest.raises(_ctf.CtfError) as ei:
         _ctf.ctf_selftest_bounded_wait(0)
     assert ei.value.status == _ctf.CTF_ERR_ARG
+
+
+def _fnv1a(data):
+    h = 14695981039346656037
+    for b in data:
+        h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _texture_file(mode, w, h, lat, payload, version=1):
+    import struct
+    body = b"CTFTEX01" + struct.pack("<I7i", version, mode, w, h, *lat) + payload
+    return body + struct.pack("<Q", _fnv1a(body))
+
+
+def test_malformed_texture_checkpoints_are_refused_without_gpu(lib, tmp_path):
+    """ctf_checkpoint_load reads and checks the whole file before any device
+    work: a missing file, a foreign file, a bad checksum, another version,
+    impossible sizes, a payload of the wrong length and a weight that FP16
+    cannot hold are each refused."""
+    import struct
+    import numpy as np
+    from paper_2506_17770_gb300 import _ctf
+    with pytest.raises(_ctf.CtfError) as ei:
+        _ctf.ctf_checkpoint_load(str(tmp_path / "missing.ctftex"))
+    assert ei.value.status == _ctf.CTF_ERR_ARG
+    # an FP16 texture with 1x1 latent grids: 8 + 8 + 1024 + 64 + 4096 + 64 + 256 + 4 floats
+    n = 8 + 8 + 1024 + 64 + 4096 + 64 + 256 + 4
+    good = np.zeros(n, np.float32).tobytes()
+    bad_value = np.zeros(n, np.float32)
+    bad_value[16] = 0.1  # w1[0][0] is not an FP16 number
+    cases = {
+        "foreign": b"\x7fELF" + bytes(100),
+        "checksum": _texture_file(1, 64, 64, (1, 1, 1, 1), good)[:-1] + b"\x00",
+        "version": _texture_file(1, 64, 64, (1, 1, 1, 1), good, version=2),
+        "mode": _texture_file(7, 64, 64, (1, 1, 1, 1), good),
+        "block_sides": _texture_file(0, 6, 8, (0, 0, 0, 0), bytes(16)),
+        "block_length": _texture_file(0, 8, 8, (0, 0, 0, 0), bytes(24)),
+        "latent_side": _texture_file(1, 64, 64, (0, 1, 1, 1), good),
+        "length": _texture_file(1, 64, 64, (1, 1, 1, 1), good[:-4]),
+        "value": _texture_file(1, 64, 64, (1, 1, 1, 1), bad_value.tobytes()),
+    }
+    for name, raw in cases.items():
+        path = tmp_path / (name + ".ctftex")
+        path.write_bytes(raw)
+        with pytest.raises(_ctf.CtfError) as ei:
+            _ctf.ctf_checkpoint_load(str(path))
+        assert ei.value.status == _ctf.CTF_ERR_CORRUPT, (name, _ctf.ctf_last_error())
+
+
+def test_mlp_train_checks_its_arguments_without_gpu(lib):
+    from paper_2506_17770_gb300 import _ctf
+    desc = _ctf.train_desc(((8, 8), (4, 4)), batch=64, total_steps=1)
+    with pytest.raises(_ctf.CtfError) as ei:
+        _ctf.ctf_mlp_train(None, desc, _ctf.CTF_EVAL_BLOCK)
+    assert ei.value.status == _ctf.CTF_ERR_ARG

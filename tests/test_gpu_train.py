@@ -238,3 +238,109 @@ def test_fp8_export_matches_fp64_oracle(procedural256):
         _ctf.ctf_texture_destroy(t8)
     finally:
         _ctf.ctf_trainer_destroy(tr)
+
+
+def _params_of(tex, desc, fp8):
+    shapes = ((desc.latent_h[0], desc.latent_w[0], 8), (desc.latent_h[1], desc.latent_w[1], 8))
+    st = _ctf.ctf_mlp_export(tex, shapes)
+    return {k: v for k, v in st.items() if fp8 or not (k.startswith("ws") or k.startswith("as"))}
+
+
+def test_mlp_train_is_the_trainer_in_one_call(procedural256):
+    """ctf_mlp_train gives the texture of create + step + export, bit for
+    bit (training is deterministic), and reports its error against the exact
+    texture as ctf_texture_compare measures it."""
+    tex, _ = procedural256
+    desc = _ctf.train_desc(((64, 64), (32, 32)), batch=8192, total_steps=40, seed=5)
+    for mode in (_ctf.CTF_EVAL_MLP_FP16, _ctf.CTF_EVAL_MLP_FP8):
+        one, rep = _ctf.ctf_mlp_train(tex, desc, mode)
+        tr = _ctf.ctf_trainer_create(tex, desc)
+        try:
+            _ctf.ctf_trainer_step(tr, 40)
+            ref = _ctf.ctf_trainer_export(tr, mode)
+        finally:
+            _ctf.ctf_trainer_destroy(tr)
+        try:
+            fp8 = mode == _ctf.CTF_EVAL_MLP_FP8
+            a, b = _params_of(one, desc, fp8), _params_of(ref, desc, fp8)
+            for k in a:
+                assert np.array_equal(a[k].view(np.uint32), b[k].view(np.uint32)), (mode, k)
+            mse, mx = _ctf.ctf_texture_compare(tex, one)
+            assert rep["steps"] == 40 and rep["texels"] == 40 * 8192 and rep["seconds"] > 0
+            # the mean is summed in parallel, in no fixed order
+            assert rep["mse_rgb"] == pytest.approx(mse, rel=1e-12) and rep["max_abs"] == mx
+            assert rep["psnr_db"] == pytest.approx(_psnr(mse), abs=1e-9)
+        finally:
+            _ctf.ctf_texture_destroy(one)
+            _ctf.ctf_texture_destroy(ref)
+    with pytest.raises(_ctf.CtfError) as ei:
+        _ctf.ctf_mlp_train(tex, desc, _ctf.CTF_EVAL_BLOCK)
+    assert ei.value.status == _ctf.CTF_ERR_ARG
+
+
+def test_texture_checkpoints_round_trip_bit_for_bit(procedural256):
+    """A block, an FP16 and an FP8 texture saved and loaded back: the same
+    stored parameters, the same decoded texels and the same filtered image
+    bit for bit; a flipped byte or a cut file is refused."""
+    tex, _ = procedural256
+    desc = _ctf.train_desc(((64, 64), (32, 32)), batch=8192, total_steps=30, seed=8)
+    tr = _ctf.ctf_trainer_create(tex, desc)
+    try:
+        _ctf.ctf_trainer_step(tr, 30)
+        learned = {m: _ctf.ctf_trainer_export(tr, m) for m in (_ctf.CTF_EVAL_MLP_FP16, _ctf.CTF_EVAL_MLP_FP8)}
+    finally:
+        _ctf.ctf_trainer_destroy(tr)
+    sc = synth.perspective_view(200, 120, 256, 256, 1.0, 8.0, seed=4)
+    d_uv, d_jac, d_cov = (torch.from_numpy(a).cuda() for a in (sc.uv, sc.jac, sc.coverage))
+    g = np.random.default_rng(2)
+    xy = torch.from_numpy(np.stack([g.integers(0, 256, 500), g.integers(0, 256, 500)], -1).astype(np.int32)).cuda()
+
+    def filtered(t):
+        out = torch.empty((sc.H, sc.W, 4), device="cuda")
+        ev = torch.empty((sc.H, sc.W), dtype=torch.uint8, device="cuda")
+        _ctf.ctf_filter(t, d_uv, d_jac, d_cov, sc.W, sc.H, 0, "mask", 3, {"mask_dim": 11}, out, ev)
+        _ctf.ctf_sync_check()
+        return out.cpu().numpy(), ev.cpu().numpy()
+
+    d = tempfile.mkdtemp()
+    try:
+        for name, t in (("block", tex), ("fp16", learned[_ctf.CTF_EVAL_MLP_FP16]),
+                        ("fp8", learned[_ctf.CTF_EVAL_MLP_FP8])):
+            path = os.path.join(d, name + ".ctftex")
+            _ctf.ctf_checkpoint_save(t, path)
+            back = _ctf.ctf_checkpoint_load(path)
+            try:
+                a, b = filtered(t), filtered(back)
+                assert np.array_equal(a[0].view(np.uint32), b[0].view(np.uint32)), name
+                assert np.array_equal(a[1], b[1]), name
+                if name != "block":
+                    fp8 = name == "fp8"
+                    pa, pb = _params_of(t, desc, fp8), _params_of(back, desc, fp8)
+                    for k in pa:
+                        assert np.array_equal(pa[k].view(np.uint32), pb[k].view(np.uint32)), (name, k)
+                    oa, ob = torch.empty((500, 4), device="cuda"), torch.empty((500, 4), device="cuda")
+                    _ctf.ctf_mlp_decode(t, xy, 500, oa)
+                    _ctf.ctf_mlp_decode(back, xy, 500, ob)
+                    _ctf.ctf_sync_check()
+                    assert torch.equal(oa, ob), name
+            finally:
+                _ctf.ctf_texture_destroy(back)
+            raw = bytearray(open(path, "rb").read())
+            for bad_raw in (raw[:-1], raw[:60] + bytes([raw[60] ^ 1]) + raw[61:]):
+                bad = os.path.join(d, "bad.ctftex")
+                open(bad, "wb").write(bytes(bad_raw))
+                with pytest.raises(_ctf.CtfError) as ei:
+                    _ctf.ctf_checkpoint_load(bad)
+                assert ei.value.status == _ctf.CTF_ERR_CORRUPT, name
+    finally:
+        for t in learned.values():
+            _ctf.ctf_texture_destroy(t)
+
+
+def test_stream_status_is_the_sync_check():
+    _ctf.ctf_stream_status()
+    _ctf.ctf_selftest_bounded_wait(1 << 10)
+    with pytest.raises(_ctf.CtfError) as ei:
+        _ctf.ctf_stream_status()
+    assert ei.value.status == _ctf.CTF_ERR_TIMEOUT
+    _ctf.ctf_stream_status()
