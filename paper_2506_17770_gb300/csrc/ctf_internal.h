@@ -123,7 +123,7 @@ inline uint64_t fnv1a(const void *data, size_t n, uint64_t h = 14695981039346656
     return h;
 }
 // The learned filter with warps specialised by role (ctf_mlp_ws.cu), which
-// launch_mlp_filter uses for STF, Box and Mask Sampling without group_dedup.
+// launch_mlp_filter uses for STF, Box and Mask Sampling.
 bool mlp_filter_ws_applies(const ExactParams &p, int alg);
 cudaError_t prepare_mlp_filter_ws(int alg, int tile_w, int mask_dim);
 cudaError_t launch_mlp_filter_ws(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim,

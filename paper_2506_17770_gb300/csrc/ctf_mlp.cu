@@ -17,17 +17,15 @@
 // tracked with an mbarrier whose waits are bounded: a wait that gives up sets
 // the library's error word and every thread of the CTA leaves together.
 //
-// Two kernels use the chain: a decode of an explicit list of texels, and the
-// learned-decode filter.  In the filter, per-pixel 4-tap gives each warp one
-// pixel tile (its lane's row per tap, four chains per iteration); the
-// collaborative algorithms and STF give each warp two tiles of a group of 8,
-// pack the group's texel lists into consecutive rows (one or two chains) and
-// gather every pixel's taps from the rows (ctf_mlp_chain.cuh, mlp_group).
-// The next group's uv and Jacobian are copied into shared memory with
-// cp.async while a group runs (not for List Merge, whose tables use that
-// space).  STF, Box and Mask Sampling without group_dedup run instead in the
-// kernel whose warps are specialised by role (ctf_mlp_ws.cu), which gives the
-// same outputs.
+// Two kernels here use the chain: a decode of an explicit list of texels, and
+// the learned-decode filter for per-pixel 4-tap and List Merge.  Per-pixel
+// 4-tap gives each warp one pixel tile (its lane's row per tap, four chains
+// per iteration); List Merge gives each warp two tiles of a group of 8, packs
+// the group's texel lists into consecutive rows (one or two chains) and
+// gathers every pixel's taps from the rows (ctf_mlp_chain.cuh, mlp_group;
+// the persistent batch kernel runs the same for every algorithm).  STF, Box
+// and Mask Sampling on single views run in the kernel whose warps are
+// specialised by role (ctf_mlp_ws.cu), which gives the same outputs.
 #include <cstdint>
 #include <mutex>
 #include <set>
@@ -75,8 +73,8 @@ __global__ void __launch_bounds__(kRows) mlp_decode_kernel(const MlpDevice m, in
 }
 
 // ---------------------------------------------------------------------------
-// Learned-decode filter: 4 warps; a group of 8 pixel tiles (4 for per-pixel
-// 4-tap) per CTA iteration.
+// Learned-decode filter for per-pixel 4-tap and List Merge: 4 warps; a group
+// of 8 pixel tiles (4 for per-pixel 4-tap) per CTA iteration.
 // ---------------------------------------------------------------------------
 template <int ALG, int TW, int MD>
 __global__ void __launch_bounds__(kRows, 4) mlp_filter_kernel(const ExactParams p, const MlpDevice m, int *err) {
@@ -98,18 +96,12 @@ __global__ void __launch_bounds__(kRows, 4) mlp_filter_kernel(const ExactParams 
 #pragma unroll
     for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
     constexpr int kTiles = mlp_group_tiles(ALG);
-    // the collaborative algorithms other than List Merge stage the next
-    // group's pixel inputs in shared memory while a group runs
-    constexpr bool kStaged = ALG != ALG_4TAP && ALG != ALG_LIST;
     const long long n_iter = (p.n_tiles + kTiles - 1) / kTiles;
-    if (kStaged && blockIdx.x < n_iter) stage_group<ALG, TW>(p, (long long)blockIdx.x * kTiles, sm);
     bool ok = true;
     for (long long it = blockIdx.x; it < n_iter && ok; it += gridDim.x) {
-        const long long next = it + gridDim.x < n_iter ? (it + gridDim.x) * kTiles : -1;
         if (ALG == ALG_4TAP) ok = mlp_warp_tile<ALG, TW, MD>(p, m, ch, it * kTiles + warp, lane, lt, T, cnt, inv_a1, err);
-        else ok = mlp_group<ALG, TW, MD, kStaged>(p, m, ch, it * kTiles, lane, lt, T, cnt, inv_a1, err, next);
+        else ok = mlp_group<ALG, TW, MD>(p, m, ch, it * kTiles, lane, lt, T, cnt, inv_a1, err);
     }
-    if (kStaged) cp_async_wait_all();  // no copy outlives the kernel (a failed chain leaves early)
     if (p.stats) {
         if (lane == 0) {
 #pragma unroll
@@ -147,14 +139,12 @@ FilterFn pick_mask(int md) {
     }
 }
 
+// (STF, Box and Mask Sampling run in mlp_filter_ws_kernel.)
 template <int TW>
 FilterFn pick_alg(int alg, int md) {
     switch (alg) {
     case ALG_4TAP: return pick_mask<ALG_4TAP, TW>(md);
-    case ALG_STF: return pick_mask<ALG_STF, TW>(md);
     case ALG_LIST: return pick_mask<ALG_LIST, TW>(md);
-    case ALG_BOX: return pick_mask<ALG_BOX, TW>(md);
-    case ALG_MASK: return pick_mask<ALG_MASK, TW>(md);
     default: return nullptr;
     }
 }
@@ -188,6 +178,7 @@ cudaError_t launch_mlp_decode(const MlpDevice &m, int Wt, int Ht, const int2 *xy
 }
 
 cudaError_t prepare_mlp_filter(int alg, int tile_w, int mask_dim) {
+    if (alg == ALG_STF || alg == ALG_BOX || alg == ALG_MASK) return prepare_mlp_filter_ws(alg, tile_w, mask_dim);
     FilterFn fn = nullptr;
     switch (tile_w) {
     case 8: fn = pick_alg<8>(alg, mask_dim); break;
@@ -195,11 +186,7 @@ cudaError_t prepare_mlp_filter(int alg, int tile_w, int mask_dim) {
     case 16: fn = pick_alg<16>(alg, mask_dim); break;
     default: return cudaErrorInvalidValue;
     }
-    if (!fn) return cudaErrorInvalidValue;
-    cudaError_t e = prepare(fn);
-    if (e == cudaSuccess && (alg == ALG_STF || alg == ALG_BOX || alg == ALG_MASK))
-        e = prepare_mlp_filter_ws(alg, tile_w, mask_dim);
-    return e;
+    return fn ? prepare(fn) : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t stream) {
@@ -209,6 +196,7 @@ cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t 
 
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                               cudaStream_t stream) {
+    if (mlp_filter_ws_applies(p, alg)) return launch_mlp_filter_ws(p, m, alg, tile_w, mask_dim, err, stream);
     FilterFn fn = nullptr;
     switch (tile_w) {
     case 8: fn = pick_alg<8>(alg, mask_dim); break;
@@ -219,7 +207,6 @@ cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg,
     if (!fn) return cudaErrorInvalidValue;
     if (p.n_tiles == 0) return cudaSuccess;
     if (p.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile positions use 32-bit arithmetic
-    if (mlp_filter_ws_applies(p, alg)) return launch_mlp_filter_ws(p, m, alg, tile_w, mask_dim, err, stream);
     cudaError_t e = prepare(fn);
     if (e != cudaSuccess) return e;
     const long long iters = (p.n_tiles + mlp_group_tiles(alg) - 1) / mlp_group_tiles(alg);

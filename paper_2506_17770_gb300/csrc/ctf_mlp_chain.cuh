@@ -45,14 +45,6 @@ constexpr int kSmTexList = kSmX;                      // 8 tiles x 32 x int2 (2 
 constexpr int kSmHashKey = kSmH;                      // 512 x u64
 constexpr int kSmHashRow = kSmH + 512 * 8;            // 512 x u8
 constexpr int kSmBytes = kSmNUnique + 16;
-// Pixel inputs of the next group, copied in with cp.async while the current
-// group runs (single-view filter; not for List Merge, whose hash tables use
-// the same space): uv, Jacobian, and the aligned 32-bit word that holds the
-// pixel's coverage byte.
-constexpr int kSmStageUV = kSmList;                 // 256 x float2
-constexpr int kSmStageJac = kSmStageUV + 256 * 8;   // 256 x float4
-constexpr int kSmStageCov = kSmStageJac + 256 * 16;  // 256 x u32
-static_assert(kSmStageCov + 256 * 4 <= kSmRanks, "staging fits in the List Merge tables");
 // Reserve enough shared memory that at most 4 CTAs share an SM: 4 x 128 TMEM
 // columns fill the SM's 512 (5 x 54 KB exceed the SM's 228 KB).
 constexpr int kSmRequest = 54 * 1024;
@@ -96,64 +88,6 @@ __device__ __forceinline__ void tile_pos(const TilePos &t, int g, int &bx, int &
     bx = (int)x;
     by = (int)y;
 }
-
-__device__ __forceinline__ uint64_t evict_first_policy() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-// Asynchronous global -> shared copies of 4, 8 or 16 bytes (both addresses
-// aligned to the size), with the evict-first L2 policy of streamed pixels.
-template <int N>
-__device__ __forceinline__ void cp_async(void *dst, const void *src, uint64_t pol) {
-    const uint32_t d = tc::smem_addr(dst);
-    if constexpr (N == 16)
-        asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "l"(pol)
-                     : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(N),
-                     "l"(pol)
-                     : "memory");
-}
-
-// The 4-byte-aligned word that holds coverage byte idx, when the whole word
-// lies inside the coverage array (else 0: the byte is read directly).
-__device__ __forceinline__ const uint32_t *cov_word(const ExactParams &p, uint32_t idx) {
-    const uintptr_t b = reinterpret_cast<uintptr_t>(p.cov), a = (b + idx) & ~(uintptr_t)3;
-    const uintptr_t end = b + (uintptr_t)p.W * (uintptr_t)p.H;
-    return a >= b && a + 4 <= end ? reinterpret_cast<const uint32_t *>(a) : nullptr;
-}
-
-// Issue the copies of the pixel inputs of group `first` (slots 4h + warp,
-// one lane per pixel, as step 1 reads them) into the staging buffers.
-template <int ALG, int TW>
-__device__ __forceinline__ void stage_group(const ExactParams &p, long long first, unsigned char *sm) {
-    constexpr int TH = 32 / TW;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tx = lane % TW, ty = lane / TW;
-    const uint64_t pol = evict_first_policy();
-    const TilePos tp = tile_pos0(p, first);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int g = 4 * h + warp, e = 32 * g + lane;
-        const long long tile = first + g;
-        if (tile >= p.n_tiles) continue;
-        int bx, by;
-        tile_pos(tp, g, bx, by);
-        const int px = bx * TW + tx, py = by * TH + ty;
-        if (px >= p.W || py >= p.H) continue;
-        const uint32_t idx = (uint32_t)py * (uint32_t)p.W + (uint32_t)px;
-        cp_async<8>(sm + kSmStageUV + 8 * e, p.uv + idx, pol);
-        if (ALG >= ALG_LIST) cp_async<16>(sm + kSmStageJac + 16 * e, p.jac + idx, pol);
-        if (p.cov) {
-            const uint32_t *w = cov_word(p, idx);
-            if (w) cp_async<4>(sm + kSmStageCov + 4 * e, w, pol);
-        }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Features of texel (x, y) (inside the texture) in FP32.
 __device__ __forceinline__ void texel_features(const MlpDevice &m, int x, int y, float f[kMlpIn]) {
@@ -586,13 +520,10 @@ __device__ __forceinline__ bool mlp_warp_tile(const ExactParams &p, const MlpDev
 // group), and every pixel then gathers its taps from the rows.  Which thread
 // computes a texel does not change its value: the rows of an MMA are
 // independent.  Returns false (for every thread alike) if a chain gave up.
-// With kStaged the group's pixel inputs were staged by stage_group, and the
-// inputs of group `next` (if not negative) are staged while this one runs.
-template <int ALG, int TW, int MD, bool kStaged = false>
+template <int ALG, int TW, int MD>
 __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice &m, Chain &ch, long long first,
                                           int lane, uint32_t lt, ListTable *T, Counters &cnt, const float *inv_a1,
-                                          int *err, long long next = -1) {
-    static_assert(!kStaged || ALG != ALG_LIST, "List Merge keeps its tables where the staging buffers are");
+                                          int *err) {
     constexpr int TH = 32 / TW;
     unsigned char *sm = ch.sm;
     const int warp = threadIdx.x >> 5, tx = lane % TW, ty = lane / TW;
@@ -608,7 +539,6 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
     // texlist[32 g + rank], and each pixel keeps (s, t) and a packed word:
     // bits 0-19 the list indices of its 4 taps (success) or of its own texel
     // (bits 0-4, fallback), 20-22 its count, 23 active, 24 inside, 25 success.
-    if (kStaged) cp_async_wait_all();  // this thread's own copies
     const TilePos tp = tile_pos0(p, first);
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
@@ -623,20 +553,7 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
         float2 uv = make_float2(0.f, 0.f);
         float4 jac = make_float4(0.f, 0.f, 0.f, 0.f);
         bool covered = inside;
-        if (inside && kStaged) {
-            const int e = 32 * g + lane;
-            uv = *reinterpret_cast<const float2 *>(sm + kSmStageUV + 8 * e);
-            if (ALG >= ALG_LIST) jac = *reinterpret_cast<const float4 *>(sm + kSmStageJac + 16 * e);
-            if (p.cov) {
-                if (cov_word(p, idx)) {
-                    const uint32_t w = *reinterpret_cast<const uint32_t *>(sm + kSmStageCov + 4 * e);
-                    const uint32_t sh = 8u * (uint32_t)(reinterpret_cast<uintptr_t>(p.cov + idx) & 3);
-                    covered = ((w >> sh) & 0xffu) != 0;
-                } else {
-                    covered = __ldcs(p.cov + idx) != 0;
-                }
-            }
-        } else if (inside) {
+        if (inside) {
             uv = __ldcs(p.uv + idx);
             if (ALG >= ALG_LIST) jac = __ldcs(p.jac + idx);
             if (p.cov) covered = __ldcs(p.cov + idx) != 0;
@@ -669,9 +586,6 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
         pix_st[32 * g + lane] = make_float2(ps.s, ps.t);
         pix_info[32 * g + lane] = info;
     }
-    // the staged inputs have been read (by the thread that copied them):
-    // the next group's copies overlap everything below
-    if (kStaged && next >= 0) stage_group<ALG, TW>(p, next, sm);
     __syncthreads();
 
     // ---- rows.  Without group_dedup slot g owns rows [base_g, base_g +

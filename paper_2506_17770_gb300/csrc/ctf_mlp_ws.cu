@@ -1,5 +1,5 @@
 // ctf_mlp_ws.cu -- learned-decode filter with warps specialised by role, for
-// STF, Box and Mask Sampling on single views (without group_dedup).
+// STF, Box and Mask Sampling on single views (with or without group_dedup).
 //
 // A CTA of 256 threads (four per SM) takes the groups of 8 pixel tiles g0,
 // g0 + G, ... (G = gridDim.x) in turn:
@@ -20,7 +20,9 @@
 // written), gathered (row values read).  Every wait is bounded; a wait that
 // gives up records CTF_ERR_TIMEOUT and the waiting role stops, so the kernel
 // always ends.  Each group gets the same rows, texel values, image and counts
-// as mlp_group in ctf_mlp_chain.cuh.
+// as mlp_group in ctf_mlp_chain.cuh; with group_dedup the consumer merges
+// the group's lists in a hash table first, so that each distinct texel takes
+// one row, and a per-stage row map sends every list entry to its row.
 #include <cstdint>
 #include <mutex>
 #include <set>
@@ -57,7 +59,8 @@ constexpr int kWsInfo = kWsST + 256 * 8;                     // 256 x uint32 per
 constexpr int kWsCount = kWsInfo + 256 * 4;                  // 8 x int texels per tile (producers)
 constexpr int kWsBase = kWsCount + 32;                       // 8 x int first row per tile (consumer)
 constexpr int kWsOut = kWsBase + 32;                         // 256 x float4 row values
-constexpr int kWsStageBytes = kWsOut + 256 * 16;
+constexpr int kWsRowMap = kWsOut + 256 * 16;                 // 256 x u8 list entry -> row (group_dedup)
+constexpr int kWsStageBytes = kWsRowMap + 256;
 constexpr int kWsBars = kWsStage0 + 2 * kWsStageBytes;       // full[2], empty[2], done[2], gathered[2]
 constexpr int kWsBytes = kWsBars + 8 * 8;
 static_assert(kWsStage0 % 16 == 0 && kWsStageBytes % 16 == 0 && kWsOut % 16 == 0, "16-byte buffers");
@@ -308,7 +311,7 @@ __device__ __forceinline__ void ws_step1(const ExactParams &p, long long first, 
 // (its row values written by the consumer): gather, filter, store.
 template <int TW>
 __device__ __forceinline__ void ws_gather(const ExactParams &p, long long first, int g, const unsigned char *st,
-                                          int lane) {
+                                          int lane, bool dedup) {
     constexpr int TH = 32 / TW;
     const int tx = lane % TW, ty = lane / TW;
     const float2 *pix_st = reinterpret_cast<const float2 *>(st + kWsST);
@@ -319,6 +322,8 @@ __device__ __forceinline__ void ws_gather(const ExactParams &p, long long first,
     // the slot's first row, from the consumer (the other slots' counts may
     // already belong to a later group)
     const int base = reinterpret_cast<const int *>(st + kWsBase)[g];
+    const unsigned char *rowmap = st + kWsRowMap + 32 * g;
+    auto row_of = [&](uint32_t i) { return dedup ? (int)rowmap[i] : base + (int)i; };
     int bx, by;
     tile_pos(tile_pos0(p, first), g, bx, by);
     const uint32_t idx = (uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx);
@@ -332,7 +337,7 @@ __device__ __forceinline__ void ws_gather(const ExactParams &p, long long first,
             float2 rg = make_float2(0.f, 0.f), ba = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float4 t = outrow[base + (int)((info >> (5 * k)) & 31u)];
+                const float4 t = outrow[row_of((info >> (5 * k)) & 31u)];
                 const float2 wk = make_float2(w[k], w[k]);
                 rg = __ffma2_rn(wk, make_float2(t.x, t.y), rg);
                 ba = __ffma2_rn(wk, make_float2(t.z, t.w), ba);
@@ -340,7 +345,7 @@ __device__ __forceinline__ void ws_gather(const ExactParams &p, long long first,
             result = make_float4(rg.x, rg.y, ba.x, ba.y);
             cv = (uint8_t)((info >> 20) & 7u);
         } else {
-            result = outrow[base + (int)(info & 31u)];
+            result = outrow[row_of(info & 31u)];
             cv = 1;
         }
     }
@@ -348,7 +353,8 @@ __device__ __forceinline__ void ws_gather(const ExactParams &p, long long first,
     if (p.evals) p.evals[idx] = cv;
 }
 
-template <int ALG, int TW, int MD>
+// kDedup: group_dedup (the variant without it carries no code for it).
+template <int ALG, int TW, int MD, bool kDedup>
 __global__ void __launch_bounds__(kWsThreads, 4) mlp_filter_ws_kernel(const ExactParams p, const MlpDevice m,
                                                                       int *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -372,6 +378,7 @@ __global__ void __launch_bounds__(kWsThreads, 4) mlp_filter_ws_kernel(const Exac
     for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
     const long long n_groups = (p.n_tiles + kGroupTiles - 1) / kGroupTiles;
     const long long G = gridDim.x;
+    constexpr bool dedup = kDedup;
 
     if (warp < 4) {
         // ---------------- consumer ----------------
@@ -387,38 +394,101 @@ __global__ void __launch_bounds__(kWsThreads, 4) mlp_filter_ws_kernel(const Exac
                 if (tid == 0) atomicExch(err, CTF_ERR_TIMEOUT);
                 break;
             }
-            // rows: slot g owns rows [base_g, base_g + count[g]) in slot order
-            const int *count = reinterpret_cast<const int *>(st + kWsCount);
-            const int2 *texlist = reinterpret_cast<const int2 *>(st + kWsTex);
-            int R = 0, start[kGroupTiles];
-#pragma unroll
-            for (int g = 0; g < kGroupTiles; ++g) {
-                start[g] = R;
-                R += count[g];
-            }
-            int2 xy[2] = {make_int2(0, 0), make_int2(0, 0)};
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int row = kRows * c + tid;
-                if (row < R) {
-                    int g = 0;
-#pragma unroll
-                    for (int k = 1; k < kGroupTiles; ++k) g = row >= start[k] ? k : g;
-                    int b = start[0];
-#pragma unroll
-                    for (int k = 1; k < kGroupTiles; ++k) b = k == g ? start[k] : b;
-                    xy[c] = texlist[32 * g + (row - b)];
-                }
-            }
-            if (tid == 0) cnt.v[kStatTexelEvalsUnique] += R;
-            if (tid < kGroupTiles) reinterpret_cast<int *>(st + kWsBase)[tid] = start[tid];
-            cons_sync();  // every consumer thread has read the lists and counts
-            if (tid == 0) mbar_arrive(ws_bar(sm, kBarEmpty, s));
-            // the row values of this stage are free once the gather of group j - 2 is done
+            // the row values and row map of this stage are free once the
+            // gather of group j - 2 is done (it always is by now: each
+            // producer warp gathers group j - 2 before its step 1 of group j)
             if (j >= 2 && cons_or(!tc::mbar_wait(ws_bar(sm, kBarGathered, s), par ^ 1u, kMaxTries))) {
                 if (tid == 0) atomicExch(err, CTF_ERR_TIMEOUT);
                 break;
             }
+            const int *count = reinterpret_cast<const int *>(st + kWsCount);
+            int2 *texlist = reinterpret_cast<int2 *>(st + kWsTex);
+            int R = 0;
+            int2 xy[2] = {make_int2(0, 0), make_int2(0, 0)};
+            if (dedup) {
+                // the distinct texels of the group get rows in the order their
+                // first list entries win a 512-slot hash table (in H, which no
+                // MMA reads between chains); the row map sends every list
+                // entry to its texel's row
+                unsigned long long *hkey = reinterpret_cast<unsigned long long *>(sm + kSmH);
+                unsigned char *hrow = sm + kSmH + 512 * 8;
+                int *nuniq = reinterpret_cast<int *>(sm + kSmH + 512 * 8 + 512);
+                for (int i = tid; i < 512; i += kRows) hkey[i] = ~0ull;
+                if (tid == 0) *nuniq = 0;
+                cons_sync();
+                int slot[2] = {0, 0};
+                bool has[2] = {false, false}, won[2] = {false, false};
+                int2 t2[2] = {make_int2(0, 0), make_int2(0, 0)};
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int e = tid + kRows * c, g = e >> 5;
+                    int n_g = count[0];
+#pragma unroll
+                    for (int k = 1; k < kGroupTiles; ++k) n_g = g == k ? count[k] : n_g;
+                    if ((e & 31) < n_g) {
+                        has[c] = true;
+                        t2[c] = texlist[e];
+                        const unsigned long long key =
+                            ((unsigned long long)(uint32_t)t2[c].y << 32) | (uint32_t)t2[c].x;
+                        unsigned h = (((uint32_t)t2[c].x * 0x9E3779B1u) ^ ((uint32_t)t2[c].y * 0x85EBCA77u)) >> 23;
+                        // at most 256 keys in 512 slots: the probe always ends
+                        for (int probe = 0; probe < 512; ++probe) {
+                            const unsigned long long old = atomicCAS(&hkey[h], ~0ull, key);
+                            if (old == ~0ull || old == key) {
+                                won[c] = old == ~0ull;
+                                slot[c] = (int)h;
+                                break;
+                            }
+                            h = (h + 1) & 511u;
+                        }
+                    }
+                }
+                cons_sync();  // every list entry is in the table; the lists have been read
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (won[c]) {
+                        const int row = atomicAdd(nuniq, 1);
+                        hrow[slot[c]] = (unsigned char)row;
+                        texlist[row] = t2[c];  // the distinct texels reuse the list space
+                    }
+                }
+                cons_sync();
+                unsigned char *rowmap = st + kWsRowMap;
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+                    if (has[c]) rowmap[tid + kRows * c] = hrow[slot[c]];
+                R = *nuniq;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int row = kRows * c + tid;
+                    if (row < R) xy[c] = texlist[row];
+                }
+            } else {
+                // slot g owns rows [base_g, base_g + count[g]) in slot order
+                int start[kGroupTiles];
+#pragma unroll
+                for (int g = 0; g < kGroupTiles; ++g) {
+                    start[g] = R;
+                    R += count[g];
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int row = kRows * c + tid;
+                    if (row < R) {
+                        int g = 0;
+#pragma unroll
+                        for (int k = 1; k < kGroupTiles; ++k) g = row >= start[k] ? k : g;
+                        int b = start[0];
+#pragma unroll
+                        for (int k = 1; k < kGroupTiles; ++k) b = k == g ? start[k] : b;
+                        xy[c] = texlist[32 * g + (row - b)];
+                    }
+                }
+                if (tid < kGroupTiles) reinterpret_cast<int *>(st + kWsBase)[tid] = start[tid];
+            }
+            if (tid == 0) cnt.v[kStatTexelEvalsUnique] += R;
+            cons_sync();  // every consumer thread has read the lists, counts and distinct texels
+            if (tid == 0) mbar_arrive(ws_bar(sm, kBarEmpty, s));
             float4 *outrow = reinterpret_cast<float4 *>(st + kWsOut);
             const int passes = (R + kRows - 1) / kRows;
             bool ok = true;
@@ -473,7 +543,8 @@ __global__ void __launch_bounds__(kWsThreads, 4) mlp_filter_ws_kernel(const Exac
                 }
 #pragma unroll 1
                 for (int k = 0; k < kWsSlotsPerProducer; ++k)
-                    ws_gather<TW>(p, (grp - G) * kGroupTiles, kWsSlotsPerProducer * pw + k, ws_stage(sm, s1), lane);
+                    ws_gather<TW>(p, (grp - G) * kGroupTiles, kWsSlotsPerProducer * pw + k, ws_stage(sm, s1), lane,
+                                  dedup);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(ws_bar(sm, kBarGathered, s1));
             }
@@ -493,12 +564,13 @@ __global__ void __launch_bounds__(kWsThreads, 4) mlp_filter_ws_kernel(const Exac
 
 using WsFn = void (*)(const ExactParams, const MlpDevice, int *);
 
-template <int TW>
+template <int TW, bool kDedup>
 WsFn ws_pick(int alg, int md) {
     switch (alg) {
-    case ALG_STF: return mlp_filter_ws_kernel<ALG_STF, TW, 16>;
-    case ALG_BOX: return mlp_filter_ws_kernel<ALG_BOX, TW, 16>;
-    case ALG_MASK: return md == 11 ? mlp_filter_ws_kernel<ALG_MASK, TW, 11> : mlp_filter_ws_kernel<ALG_MASK, TW, 16>;
+    case ALG_STF: return mlp_filter_ws_kernel<ALG_STF, TW, 16, kDedup>;
+    case ALG_BOX: return mlp_filter_ws_kernel<ALG_BOX, TW, 16, kDedup>;
+    case ALG_MASK:
+        return md == 11 ? mlp_filter_ws_kernel<ALG_MASK, TW, 11, kDedup> : mlp_filter_ws_kernel<ALG_MASK, TW, 16, kDedup>;
     default: return nullptr;
     }
 }
@@ -522,29 +594,34 @@ cudaError_t ws_prepare(WsFn fn) {
     return e;
 }
 
-WsFn ws_kernel(int alg, int tile_w, int mask_dim) {
+WsFn ws_kernel(int alg, int tile_w, int mask_dim, bool dedup) {
     switch (tile_w) {
-    case 8: return ws_pick<8>(alg, mask_dim);
-    case 4: return ws_pick<4>(alg, mask_dim);
-    case 16: return ws_pick<16>(alg, mask_dim);
+    case 8: return dedup ? ws_pick<8, true>(alg, mask_dim) : ws_pick<8, false>(alg, mask_dim);
+    case 4: return dedup ? ws_pick<4, true>(alg, mask_dim) : ws_pick<4, false>(alg, mask_dim);
+    case 16: return dedup ? ws_pick<16, true>(alg, mask_dim) : ws_pick<16, false>(alg, mask_dim);
     default: return nullptr;
     }
 }
 
 }  // namespace
 
-bool mlp_filter_ws_applies(const ExactParams &p, int alg) {
-    return (alg == ALG_STF || alg == ALG_BOX || alg == ALG_MASK) && !p.group_dedup;
+bool mlp_filter_ws_applies(const ExactParams &, int alg) {
+    return alg == ALG_STF || alg == ALG_BOX || alg == ALG_MASK;
 }
 
 cudaError_t prepare_mlp_filter_ws(int alg, int tile_w, int mask_dim) {
-    WsFn fn = ws_kernel(alg, tile_w, mask_dim);
-    return fn ? ws_prepare(fn) : cudaErrorInvalidValue;
+    cudaError_t e = cudaErrorInvalidValue;
+    for (bool dedup : {false, true}) {
+        WsFn fn = ws_kernel(alg, tile_w, mask_dim, dedup);
+        e = fn ? ws_prepare(fn) : cudaErrorInvalidValue;
+        if (e != cudaSuccess) break;
+    }
+    return e;
 }
 
 cudaError_t launch_mlp_filter_ws(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim,
                                  int *err, cudaStream_t stream) {
-    WsFn fn = ws_kernel(alg, tile_w, mask_dim);
+    WsFn fn = ws_kernel(alg, tile_w, mask_dim, p.group_dedup != 0);
     if (!fn) return cudaErrorInvalidValue;
     if (p.n_tiles == 0) return cudaSuccess;
     if (p.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile positions use 32-bit arithmetic

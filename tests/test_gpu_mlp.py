@@ -237,9 +237,9 @@ def test_learned_filter_matches_fp64_oracle(tex64, alg, W, H, seed):
 @pytest.mark.parametrize("alg", list(ALGS))
 def test_fp8_filter_matches_fp64_oracle_and_every_kernel_agrees(tex64_fp8, alg):
     """The FP8 E4M3 filter on a ragged view: counts bit-exact and pixels
-    within the E4M3 bound of the FP64 oracle; the kernel with one role per
-    warp (taken with group_dedup) and the persistent batch kernel give the
-    same image bitwise as the single-view kernel."""
+    within the E4M3 bound of the FP64 oracle; the same call with group_dedup
+    and the persistent batch kernel (one role per warp) give the same image
+    bitwise."""
     W, H = 133, 70
     uv, jac, cov = _scene(W, H, 17)
     out, ev, st = gpu_filter(tex64_fp8, uv, jac, cov, alg, {"mask_dim": 11})
@@ -329,14 +329,16 @@ def test_learned_textures_refuse_fallback_c(tex64):
         gpu_filter(tex64, uv, jac, cov, "mask", {"fallback": 1})
 
 
+@pytest.mark.parametrize("dedup", [0, 1])
 @pytest.mark.parametrize("alg", ["stf", "box", "mask"])
-def test_staged_inputs_equal_the_batch_kernel(tex64, alg):
-    """The single-view learned filter copies each next group's pixel inputs
-    (uv, Jacobian, the coverage word) into shared memory with cp.async while
-    a group runs; the persistent batch kernel reads them directly.  On a
-    ragged view of several groups per CTA, with a band of uncovered pixels
-    (groups with no texel to evaluate) and the coverage array at an odd byte
-    offset, both give the same image and counts."""
+def test_specialised_warps_equal_the_batch_kernel(tex64, alg, dedup):
+    """The single-view learned filter runs step 1 and the gather in producer
+    warps and the MMA chains in a consumer warpgroup, handing groups over
+    through two stages of buffers; the persistent batch kernel does all of it
+    in every warp.  On a ragged view of several groups per CTA, with a band
+    of uncovered pixels (groups with no texel to evaluate) and the coverage
+    array at an odd byte offset, both give the same image and counts, with
+    and without group_dedup."""
     W, H = 1283, 797
     uv, jac, cov = _scene(W, H, 21)
     cov[:, :300] = 0
@@ -346,11 +348,12 @@ def test_staged_inputs_equal_the_batch_kernel(tex64, alg):
     d_uv, d_jac = torch.from_numpy(uv).cuda(), torch.from_numpy(jac).cuda()
     out = torch.full((H, W, 4), -3.0, device="cuda")
     ev = torch.full((H, W), 77, dtype=torch.uint8, device="cuda")
-    st = _ctf.ctf_filter(tex64.h, d_uv, d_jac, d_cov, W, H, 5, alg, 9, {"mask_dim": 11}, out, ev, stats=True)
+    st = _ctf.ctf_filter(tex64.h, d_uv, d_jac, d_cov, W, H, 5, alg, 9, {"mask_dim": 11, "group_dedup": dedup}, out, ev,
+                         stats=True)
     view = {"tex": tex64.h, "uv": d_uv, "jac": d_jac, "coverage": d_cov, "width": W, "height": H, "view_id": 5,
             "out_rgba": torch.full((H, W, 4), -1.0, device="cuda"),
             "out_evals": torch.full((H, W), 7, dtype=torch.uint8, device="cuda")}
-    o = _ctf.batch_opts(mask_dim=11, solo_tiles=0)
+    o = _ctf.batch_opts(mask_dim=11, solo_tiles=0, group_dedup=dedup)
     stb = _ctf.ctf_filter_batch([view], alg, 9, o, stats=True)
     _ctf.ctf_sync_check()
     assert np.array_equal(out.cpu().numpy().view(np.uint32), view["out_rgba"].cpu().numpy().view(np.uint32))
