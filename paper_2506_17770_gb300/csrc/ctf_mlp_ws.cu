@@ -15,7 +15,7 @@
 // registers from the producers to the consumer with setmaxnreg (128 x 80 +
 // 128 x 48 = 256 x 64, so the increase is always granted).
 // Two stages of group buffers (texel lists, per-pixel words, tile counts,
-// row values) alternate between consecutive groups.  Four pairs of mbarriers
+// row values, row map) alternate between consecutive groups.  Four pairs of mbarriers
 // hand them over: full (step 1 done), empty (lists read), done (row values
 // written), gathered (row values read).  Every wait is bounded; a wait that
 // gives up records CTF_ERR_TIMEOUT and the waiting role stops, so the kernel
