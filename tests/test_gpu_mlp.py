@@ -77,6 +77,35 @@ class LearnedTex:
         _ctf.ctf_texture_destroy(self.h)
 
 
+def fp8_weights(st):
+    """W_eff = s_o q[o][k] / a_k of an exported E4M3 texture, in FP64."""
+    return [(st[f"ws{l}"][:, None] * st[w] / st[f"as{l}"][None, :]).astype(np.float64)
+            for l, w in enumerate(("w1", "w2", "w3"))]
+
+
+def fp8_texel_bound(F, weff, st):
+    """Per-texel bound of the E4M3 path for features F (rows): relative
+    rounding 2^-4 plus half the subnormal spacing (2^-10 in scaled units) per
+    layer input, propagated through |W_eff|, times 2, plus 1e-5."""
+    h1 = np.maximum(F @ weff[0].T + st["b1"], 0)
+    h2 = np.maximum(h1 @ weff[1].T + st["b2"], 0)
+    u = 2.0 ** -4
+    e_f = u * np.abs(F) + 2.0 ** -10 * st["as0"]
+    e_h1 = u * h1 + 2.0 ** -10 * st["as1"] + e_f @ np.abs(weff[0]).T
+    e_h2 = u * h2 + 2.0 ** -10 * st["as2"] + e_h1 @ np.abs(weff[1]).T
+    return 2.0 * (e_h2 @ np.abs(weff[2]).T) + 1e-5
+
+
+def fp8_act_absmax(lat, p, Wt, Ht, xs, ys, margin):
+    """Per-channel ranges of the FP32 network's layer inputs over texels
+    (xs, ys), times `margin`."""
+    full = oracle.MLP((lat[0], lat[1]), *p)
+    F = np.stack([oracle.mlp_features(full, Wt, Ht, int(x), int(y)) for x, y in zip(xs, ys)])
+    h1 = np.maximum(F @ p[0].T.astype(np.float64) + p[1], 0)
+    h2 = np.maximum(h1 @ p[2].T.astype(np.float64) + p[3], 0)
+    return [(margin * np.abs(a).max(axis=0) + 1e-3).astype(np.float32) for a in (F, h1, h2)]
+
+
 class LearnedTexFP8:
     """E4M3 texture of the same random parameters.  The activation ranges are
     those of the FP64 network over every texel (times 1.1), so nothing
@@ -87,26 +116,15 @@ class LearnedTexFP8:
     def __init__(self, Wt, Ht, seed=1):
         self.Wt, self.Ht = Wt, Ht
         lat, p = random_params(seed, Wt, Ht)
-        full = oracle.MLP((lat[0], lat[1]), *p)
         ys, xs = np.meshgrid(np.arange(Ht), np.arange(Wt), indexing="ij")
         xs, ys = xs.ravel(), ys.ravel()
-        F = np.stack([oracle.mlp_features(full, Wt, Ht, int(x), int(y)) for x, y in zip(xs, ys)])
-        h1 = np.maximum(F @ p[0].T.astype(np.float64) + p[1], 0)
-        h2 = np.maximum(h1 @ p[2].T.astype(np.float64) + p[3], 0)
-        amax = [(1.1 * np.abs(a).max(axis=0) + 1e-3).astype(np.float32) for a in (F, h1, h2)]
+        amax = fp8_act_absmax(lat, p, Wt, Ht, xs, ys, 1.1)
         self.h = _ctf.ctf_texture_create_mlp(Wt, Ht, _ctf.CTF_EVAL_MLP_FP8, lat, *p, act_absmax=amax)
         st = _ctf.ctf_mlp_export(self.h, (lat[0].shape, lat[1].shape))
-        weff = [(st[f"ws{l}"][:, None] * st[w] / st[f"as{l}"][None, :]).astype(np.float64)
-                for l, w in enumerate(("w1", "w2", "w3"))]
+        weff = fp8_weights(st)
         self.mlp = oracle.MLP((st["lat0"], st["lat1"]), weff[0], st["b1"], weff[1], st["b2"], weff[2], st["b3"])
         F = np.stack([oracle.mlp_features(self.mlp, Wt, Ht, int(x), int(y)) for x, y in zip(xs, ys)])
-        h1 = np.maximum(F @ weff[0].T + st["b1"], 0)
-        h2 = np.maximum(h1 @ weff[1].T + st["b2"], 0)
-        u = 2.0 ** -4
-        e_f = u * np.abs(F) + 2.0 ** -10 * st["as0"]
-        e_h1 = u * h1 + 2.0 ** -10 * st["as1"] + e_f @ np.abs(weff[0]).T
-        e_h2 = u * h2 + 2.0 ** -10 * st["as2"] + e_h1 @ np.abs(weff[1]).T
-        self.bound = (2.0 * (e_h2 @ np.abs(weff[2]).T) + 1e-5).reshape(Ht, Wt, 4)
+        self.bound = fp8_texel_bound(F, weff, st).reshape(Ht, Wt, 4)
 
     def close(self):
         _ctf.ctf_texture_destroy(self.h)
@@ -363,20 +381,28 @@ def test_specialised_warps_equal_the_batch_kernel(tex64, alg, dedup):
     assert st["tiles_empty"] >= 300 // 8 * (H // 4)
 
 
-def test_learned_full_view_bands_match_fp64_oracle():
+@pytest.mark.parametrize("fp8", [False, True])
+def test_learned_full_view_bands_match_fp64_oracle(fp8):
     """The 3840x2160 learned view of the benchmark (4096^2 texture, latent
     grids 1024^2 and 512^2, magnification 1 to 16) filtered with Mask-11 in
-    the launch the bench times (one launch over the whole view, 8x4 tiles).
-    Three bands of 16 rows (top, middle, bottom) against the FP64 oracle run
-    on those rows alone (y_offset keeps the STF draws of the whole view):
-    counts bit-exact, pixels within the FP16 bound of their footprint's
-    texels."""
+    the launch the bench times (one launch over the whole view, 8x4 tiles),
+    FP16 and FP8.  Three bands of 16 rows (top, middle, bottom) against the
+    FP64 oracle run on those rows alone (y_offset keeps the STF draws of the
+    whole view): counts bit-exact, pixels within the FP16 (or E4M3) bound of
+    their footprint's texels.  The FP8 activation ranges come from 20,000
+    sampled texels, times 3, so that no activation saturates."""
     Wt = Ht = 4096
     lat, p = random_params(7, Wt, Ht)
-    h = _ctf.ctf_texture_create_mlp(Wt, Ht, _ctf.CTF_EVAL_MLP_FP16, lat, *p)
+    if fp8:
+        g = np.random.default_rng(11)
+        amax = fp8_act_absmax(lat, p, Wt, Ht, g.integers(0, Wt, 20000), g.integers(0, Ht, 20000), 3.0)
+        h = _ctf.ctf_texture_create_mlp(Wt, Ht, _ctf.CTF_EVAL_MLP_FP8, lat, *p, act_absmax=amax)
+    else:
+        h = _ctf.ctf_texture_create_mlp(Wt, Ht, _ctf.CTF_EVAL_MLP_FP16, lat, *p)
     try:
         st = _ctf.ctf_mlp_export(h, (lat[0].shape, lat[1].shape))
-        mlp = oracle.MLP((st["lat0"], st["lat1"]), st["w1"], st["b1"], st["w2"], st["b2"], st["w3"], st["b3"])
+        weff = fp8_weights(st) if fp8 else [st[k].astype(np.float64) for k in ("w1", "w2", "w3")]
+        mlp = oracle.MLP((st["lat0"], st["lat1"]), weff[0], st["b1"], weff[1], st["b2"], weff[2], st["b3"])
         sc = synth.perspective_view(3840, 2160, Wt, Ht, 1.0, 16.0, seed=2)
         W, H = sc.W, sc.H
         d_uv, d_jac, d_cov = (torch.from_numpy(a).cuda() for a in (sc.uv, sc.jac, sc.coverage))
@@ -385,25 +411,28 @@ def test_learned_full_view_bands_match_fp64_oracle():
         _ctf.ctf_filter(h, d_uv, d_jac, d_cov, W, H, 0, "mask", 0, {"mask_dim": 11}, out, ev)
         _ctf.ctf_sync_check()
         out, ev = out.cpu().numpy(), ev.cpu().numpy()
-        w1, w2, w3 = (st[k].astype(np.float64) for k in ("w1", "w2", "w3"))
+        w1, w2, w3 = weff
         for y0 in (0, 1000, H - 16):
             band = slice(y0, y0 + 16)
             ref, ref_ev, _ = oracle.filter_frame_learned_f64(mlp, Wt, Ht, sc.uv[band], sc.jac[band],
                                                              sc.coverage[band], alg=ALGS["mask"], mask_dim=11,
                                                              y_offset=y0)
             np.testing.assert_array_equal(ev[band], ref_ev)
-            # FP16 bound of every texel of the band's 2x2 footprints
+            # bound of every texel of the band's 2x2 footprints
             uv = sc.uv[band]
             x0 = np.floor(uv[..., 0] * np.float32(Wt) - np.float32(0.5)).astype(np.int64)
             y0_ = np.floor(uv[..., 1] * np.float32(Ht) - np.float32(0.5)).astype(np.int64)
             taps = [(np.clip(x0 + dx, 0, Wt - 1), np.clip(y0_ + dy, 0, Ht - 1)) for dy in (0, 1) for dx in (0, 1)]
             keys = np.unique(np.concatenate([ty.ravel() * Wt + tx.ravel() for tx, ty in taps]))
             F = np.stack([oracle.mlp_features(mlp, Wt, Ht, int(k % Wt), int(k // Wt)) for k in keys])
-            h1 = np.maximum(F @ w1.T + st["b1"], 0)
-            h2 = np.maximum(h1 @ w2.T + st["b2"], 0)
-            e_h1 = U16 * h1 + (U16 * np.abs(F)) @ np.abs(w1).T
-            e_h2 = U16 * h2 + e_h1 @ np.abs(w2).T
-            kb = 1.5 * (e_h2 @ np.abs(w3).T) + 1e-5
+            if fp8:
+                kb = fp8_texel_bound(F, weff, st)
+            else:
+                h1 = np.maximum(F @ w1.T + st["b1"], 0)
+                h2 = np.maximum(h1 @ w2.T + st["b2"], 0)
+                e_h1 = U16 * h1 + (U16 * np.abs(F)) @ np.abs(w1).T
+                e_h2 = U16 * h2 + e_h1 @ np.abs(w2).T
+                kb = 1.5 * (e_h2 @ np.abs(w3).T) + 1e-5
             tol = np.zeros(uv.shape[:2] + (4,))
             for tx, ty in taps:
                 tol = np.maximum(tol, kb[np.searchsorted(keys, ty * Wt + tx)])
