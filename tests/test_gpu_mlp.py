@@ -239,7 +239,7 @@ def gpu_filter(tex, uv, jac, cov, alg, opts=None, seed=0):
 @pytest.mark.parametrize("W,H,seed", [(128, 64, 11), (37, 21, 12)])
 def test_learned_filter_matches_fp64_oracle(tex64, alg, W, H, seed):
     uv, jac, cov = _scene(W, H, seed)
-    for opts in (None, {"tile_w": 4, "tile_h": 8, "mask_dim": 11}):
+    for opts in (None, {"tile_w": 4, "tile_h": 8, "mask_dim": 11}, {"tile_w": 16, "tile_h": 2, "mask_dim": 11}):
         o = {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 16, "edge_remap": 1}
         o.update(opts or {})
         out, ev, st = gpu_filter(tex64, uv, jac, cov, alg, opts)
