@@ -203,9 +203,8 @@ int ctf_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t
 /* ctf_filter on HOST buffers: copies uv, jac (and coverage) to device memory
  * that the library owns and reuses, filters, copies the image and counts
  * back, and waits for the stream before returning.  Host buffers that are
- * page-locked (cudaHostAlloc / cudaHostRegister) are not copied at all for
- * a block texture: the kernel reads the inputs and writes the image in host
- * memory in place (over NVLink-C2C on a Grace-Blackwell node), and the
+ * page-locked (cudaHostAlloc / cudaHostRegister) are not copied at all:
+ * the kernel reads the inputs and writes the image in host memory in place (over NVLink-C2C on a Grace-Blackwell node), and the
  * counts come back in one copy from library-owned device memory (so
  * out_evals_host need not be page-locked).  Otherwise, views of at least 2^20 pixels (without group_dedup) go
  * in 4 bands of whole tile rows, so that the copy-in of one band, the

@@ -218,7 +218,7 @@ def ctf_filter(tex, uv, jac, coverage, width, height, view_id, alg, seed, opts, 
 
 def ctf_filter_host(tex, uv, jac, coverage, width, height, view_id, alg, seed, opts, out_rgba, out_evals,
                     stats: bool = False, stream=None):
-    """ctf_filter on host buffers: page-locked buffers of a block texture in
+    """ctf_filter on host buffers: page-locked buffers in
     place (the kernel reads the inputs and writes the image in host memory;
     the counts come back in one copy), others staged through library-owned
     device buffers; synchronous."""

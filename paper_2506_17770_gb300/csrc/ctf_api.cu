@@ -517,15 +517,13 @@ int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host
         return CTF_OK;
     }
     const bool need_jac = alg != CTF_ALG_4TAP && alg != CTF_ALG_STF;
-    // Page-locked buffers and a block texture: the kernel reads the inputs
-    // and writes the image in host memory itself (over NVLink-C2C on a
-    // Grace-Blackwell node), with no staging copies.  The counts, one byte
-    // per pixel, go to device memory and come back in one copy after the
-    // kernel: written in place they would cross the link as 8-byte pieces
-    // of 128-byte lines, which took longer than the copy.  (The
-    // learned-decode kernels copy their inputs with cp.async and keep the
-    // staged path.)
-    if (tex->mode == CTF_EVAL_BLOCK) {
+    // Page-locked buffers: the kernel reads the inputs and writes the image
+    // in host memory itself (over NVLink-C2C on a Grace-Blackwell node), with
+    // no staging copies.  The counts, one byte per pixel, go to device memory
+    // and come back in one copy after the kernel: written in place they would
+    // cross the link as 8-byte pieces of 128-byte lines, which took longer
+    // than the copy.
+    {
         void *m_uv = mapped_host(uv_host), *m_jac = need_jac ? mapped_host(jac_host) : nullptr;
         void *m_cov = mapped_host(coverage_host), *m_out = mapped_host(out_rgba_host);
         if (m_uv && (m_jac || !need_jac) && (m_cov || !coverage_host) && m_out) {
