@@ -29,7 +29,11 @@ constexpr int kImgB1 = 12288;
 constexpr int kImgB2 = kImgB1 + 256;
 constexpr int kImgB3 = kImgB2 + 256;
 // FP8 extras: output scales of layers 1..3 (64, 64, 16 floats) and the
-// activation scales of the inputs of layers 1..3 (32, 64, 64 floats).
+// inverse activation scales of the inputs of layers 1..3 (32, 64, 64
+// floats).  The output scales and biases of layers 1 and 2 are stored
+// multiplied by the inverse activation scale of the next layer's input,
+// which the hidden epilogues then need no more (layer 1's inputs, the
+// features, are scaled by A1).
 constexpr int kImgS1 = kImgB3 + 64;
 constexpr int kImgS2 = kImgS1 + 256;
 constexpr int kImgS3 = kImgS2 + 256;

@@ -187,10 +187,11 @@ __device__ __forceinline__ void store_zero_x_row(unsigned char *sm, int row) {
 }
 
 // Hidden epilogue: TMEM columns [col, col+64) of this thread's row -> bias,
-// ReLU -> next layer's A operand (FP16, or E4M3 after multiplying by the
-// inverse activation scales of the next layer's inputs).
+// ReLU -> next layer's A operand (FP16; or E4M3, with the output scale and
+// the bias of an FP8 texture already multiplied on the host by the inverse
+// activation scale of the next layer's input).
 __device__ __forceinline__ void hidden_epilogue(unsigned char *sm, uint32_t taddr, const float *bias,
-                                                const float *oscale, const float *inv_a, bool fp8, int row) {
+                                                const float *oscale, bool fp8, int row) {
     float d[64];
 #pragma unroll
     for (int q = 0; q < 4; ++q) tc::tmem_ld16(taddr + 16 * q, d + 16 * q);
@@ -214,17 +215,14 @@ __device__ __forceinline__ void hidden_epilogue(unsigned char *sm, uint32_t tadd
         }
     } else {
         const float2 *o2 = reinterpret_cast<const float2 *>(oscale);
-        const float2 *i2 = reinterpret_cast<const float2 *>(inv_a);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             uint32_t w[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int k = 16 * c + 4 * i;
-                float2 t0 = __ffma2_rn(make_float2(d[k], d[k + 1]), o2[k / 2], b2[k / 2]);
-                float2 t1 = __ffma2_rn(make_float2(d[k + 2], d[k + 3]), o2[k / 2 + 1], b2[k / 2 + 1]);
-                t0 = __fmul2_rn(t0, i2[k / 2]);
-                t1 = __fmul2_rn(t1, i2[k / 2 + 1]);
+                const float2 t0 = __ffma2_rn(make_float2(d[k], d[k + 1]), o2[k / 2], b2[k / 2]);
+                const float2 t1 = __ffma2_rn(make_float2(d[k + 2], d[k + 3]), o2[k / 2 + 1], b2[k / 2 + 1]);
                 w[i] = (uint32_t)relu_e4m3x2(t0.x, t0.y) | ((uint32_t)relu_e4m3x2(t1.x, t1.y) << 16);
             }
             *reinterpret_cast<uint4 *>(H + core_offset(row, 16 * c, 64, 1)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -244,8 +242,6 @@ __device__ __forceinline__ bool mlp_chain(Chain &ch, bool fp8, float4 &out, int 
     const float *s1 = reinterpret_cast<const float *>(sm + kImgS1);
     const float *s2 = reinterpret_cast<const float *>(sm + kImgS2);
     const float *s3 = reinterpret_cast<const float *>(sm + kImgS3);
-    const float *a2 = reinterpret_cast<const float *>(sm + kImgA2);
-    const float *a3 = reinterpret_cast<const float *>(sm + kImgA3);
     const uint32_t lane_base = ch.tmem + ((uint32_t)(32 * warp) << 16);
     const uint32_t sX = tc::smem_addr(sm + kSmX), sH = tc::smem_addr(sm + kSmH);
     const uint32_t sW1 = tc::smem_addr(sm + kImgW1), sW2 = tc::smem_addr(sm + kImgW2),
@@ -276,7 +272,7 @@ __device__ __forceinline__ bool mlp_chain(Chain &ch, bool fp8, float4 &out, int 
     __syncwarp();  // the lanes may leave the wait apart; tcgen05.ld needs the whole warp
     ch.phase ^= 1u;
     tc::fence_after_sync();
-    hidden_epilogue(sm, lane_base + 0, b1, s1, a2, fp8, tid);
+    hidden_epilogue(sm, lane_base + 0, b1, s1, fp8, tid);
     // ---- layer 2: D[64..128) = H1 * W2^T
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -299,7 +295,7 @@ __device__ __forceinline__ bool mlp_chain(Chain &ch, bool fp8, float4 &out, int 
     ch.phase ^= 1u;
     tc::fence_after_sync();
     // the layer-2 MMAs have read H1, so H2 may overwrite it
-    hidden_epilogue(sm, lane_base + 64, b2, s2, a3, fp8, tid);
+    hidden_epilogue(sm, lane_base + 64, b2, s2, fp8, tid);
     // ---- layer 3: D[0..16) = H2 * W3^T
     tc::fence_proxy_async();
     tc::fence_before_sync();

@@ -51,9 +51,13 @@ int upload_mlp_texture(ctf_texture_s *t) {
     // operand image: weights (FP16 or E4M3 numbers, converted exactly), biases, scales
     std::vector<unsigned char> img(kImgBytes, 0);
     auto put_f32 = [&](int off, int i, float v) { std::memcpy(img.data() + off + 4 * i, &v, 4); };
+    // FP8: the hidden layers' output scales and biases are multiplied by the
+    // inverse activation scale of the next layer's input, so that one FMA
+    // gives the next E4M3 operand's value (the scales are positive, so the
+    // ReLU commutes with them)
     for (int i = 0; i < kMlpHidden; ++i) {
-        put_f32(kImgB1, i, t->s_b1[i]);
-        put_f32(kImgB2, i, t->s_b2[i]);
+        put_f32(kImgB1, i, fp8 ? t->s_b1[i] * (1.0f / t->s_ascale[1][i]) : t->s_b1[i]);
+        put_f32(kImgB2, i, fp8 ? t->s_b2[i] * (1.0f / t->s_ascale[2][i]) : t->s_b2[i]);
     }
     for (int i = 0; i < kMlpOut; ++i) put_f32(kImgB3, i, t->s_b3[i]);
     const std::vector<float> *S[3] = {&t->s_w1, &t->s_w2, &t->s_w3};
@@ -75,7 +79,7 @@ int upload_mlp_texture(ctf_texture_s *t) {
         for (int l = 0; l < 3; ++l) {
             for (int k = 0; k < nin[l]; ++k) put_f32(aoff[l], k, 1.0f / t->s_ascale[l][k]);
             for (int o = 0; o < rows[l]; ++o) {
-                put_f32(soff[l], o, t->s_wscale[l][o]);
+                put_f32(soff[l], o, l < 2 ? t->s_wscale[l][o] * (1.0f / t->s_ascale[l + 1][o]) : t->s_wscale[l][o]);
                 for (int k = 0; k < nin[l]; ++k)
                     img[imgoff[l] + core_offset(o, k, Kimg[l], 1)] = e4m3((*S[l])[(size_t)o * nin[l] + k]);
             }

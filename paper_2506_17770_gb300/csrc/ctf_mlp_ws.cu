@@ -102,11 +102,10 @@ __device__ __forceinline__ bool cons_or(bool v) {
 // one-pass form): TMEM columns [col, col + 64) of this thread's row -> bias,
 // ReLU -> the next layer's A operand, as in hidden_epilogue.
 __device__ __forceinline__ void ws_hidden_epilogue(unsigned char *sm, uint32_t taddr, const float *bias,
-                                                   const float *oscale, const float *inv_a, bool fp8, int row) {
+                                                   const float *oscale, bool fp8, int row) {
     unsigned char *H = sm + kSmH;
     const float2 *b2 = reinterpret_cast<const float2 *>(bias);
     const float2 *o2 = reinterpret_cast<const float2 *>(oscale);
-    const float2 *i2 = reinterpret_cast<const float2 *>(inv_a);
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         float d[32];
@@ -133,10 +132,8 @@ __device__ __forceinline__ void ws_hidden_epilogue(unsigned char *sm, uint32_t t
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int k = 16 * c + 4 * i, kk = 32 * half + k;
-                    float2 t0 = __ffma2_rn(make_float2(d[k], d[k + 1]), o2[kk / 2], b2[kk / 2]);
-                    float2 t1 = __ffma2_rn(make_float2(d[k + 2], d[k + 3]), o2[kk / 2 + 1], b2[kk / 2 + 1]);
-                    t0 = __fmul2_rn(t0, i2[kk / 2]);
-                    t1 = __fmul2_rn(t1, i2[kk / 2 + 1]);
+                    const float2 t0 = __ffma2_rn(make_float2(d[k], d[k + 1]), o2[kk / 2], b2[kk / 2]);
+                    const float2 t1 = __ffma2_rn(make_float2(d[k + 2], d[k + 3]), o2[kk / 2 + 1], b2[kk / 2 + 1]);
                     w[i] = (uint32_t)relu_e4m3x2(t0.x, t0.y) | ((uint32_t)relu_e4m3x2(t1.x, t1.y) << 16);
                 }
                 *reinterpret_cast<uint4 *>(H + core_offset(row, 32 * half + 16 * c, 64, 1)) =
@@ -159,8 +156,6 @@ __device__ __forceinline__ bool ws_chain(Chain &ch, bool fp8, float4 &out, int *
     const float *s1 = reinterpret_cast<const float *>(sm + kImgS1);
     const float *s2 = reinterpret_cast<const float *>(sm + kImgS2);
     const float *s3 = reinterpret_cast<const float *>(sm + kImgS3);
-    const float *a2 = reinterpret_cast<const float *>(sm + kImgA2);
-    const float *a3 = reinterpret_cast<const float *>(sm + kImgA3);
     const uint32_t lane_base = ch.tmem + ((uint32_t)(32 * warp) << 16);
     const uint32_t sX = tc::smem_addr(sm + kSmX), sH = tc::smem_addr(sm + kSmH);
     const uint32_t sW1 = tc::smem_addr(sm + kImgW1), sW2 = tc::smem_addr(sm + kImgW2),
@@ -188,7 +183,7 @@ __device__ __forceinline__ bool ws_chain(Chain &ch, bool fp8, float4 &out, int *
     __syncwarp();
     ch.phase ^= 1u;
     tc::fence_after_sync();
-    ws_hidden_epilogue(sm, lane_base + 0, b1, s1, a2, fp8, tid);
+    ws_hidden_epilogue(sm, lane_base + 0, b1, s1, fp8, tid);
     // ---- layer 2: D[64..128) = H1 * W2^T
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -211,7 +206,7 @@ __device__ __forceinline__ bool ws_chain(Chain &ch, bool fp8, float4 &out, int *
     ch.phase ^= 1u;
     tc::fence_after_sync();
     // the layer-2 MMAs have read H1, so H2 may overwrite it
-    ws_hidden_epilogue(sm, lane_base + 64, b2, s2, a3, fp8, tid);
+    ws_hidden_epilogue(sm, lane_base + 64, b2, s2, fp8, tid);
     // ---- layer 3: D[0..16) = H2 * W3^T
     tc::fence_proxy_async();
     tc::fence_before_sync();
