@@ -286,6 +286,24 @@ int ctf_stream_status(void *stream);
  * Returns CTF_ERR_ARG for polls outside the range, else the launch status. */
 int ctf_selftest_bounded_wait(uint32_t polls, void *stream);
 
+/* Host-side fault injection for tests (the paper has no counterpart).  Every
+ * device allocation the library makes (textures, trainers, batch plans, the
+ * staging and stats scratch, the decode tables) goes through one internal
+ * routine.  ctf_debug_device_allocations returns how many times it has been
+ * called in this process, failed attempts included; a test reads it before
+ * and after a call to show that the call allocated nothing.
+ * ctf_debug_live_allocations returns how many of them succeeded and have not
+ * been freed yet (a call that fails must leave it as it found it).
+ * ctf_debug_fail_allocations(skip, n) lets the next `skip` allocations
+ * through and makes the n after them fail as if the device were out of
+ * memory, without calling CUDA: the entry point that needed the memory
+ * returns CTF_ERR_OOM after freeing what it had taken, and the CUDA context
+ * stays usable.  n = 0 disarms it; negative arguments return CTF_ERR_ARG.
+ * Both are thread-safe. */
+int64_t ctf_debug_device_allocations(void);
+int64_t ctf_debug_live_allocations(void);
+int ctf_debug_fail_allocations(int skip, int n);
+
 /* Training of the learned decode on texels of an exact block texture (the
  * decoder the network stands in for, which also judges its error).  A
  * trainer holds FP32 master parameters (latents, weights, biases) and Adam
@@ -469,8 +487,10 @@ int ctf_batch_autotune(const ctf_view *views, int nviews, ctf_algorithm alg, uin
  *    contents (the stats counters are cleared at the start of each call);
  *    calls whose GPU work overlaps (other streams, other threads) race on
  *    it, so serialise them;
- *  - the first call on a device looks up the array's device address and
- *    caches it; make that first call before any stream capture. */
+ *  - the first call on a device looks up the device addresses of the array
+ *    and of the library's error word (a static __device__ int, which the
+ *    learned-decode kernels use to report a wait that gave up) and caches
+ *    them; make that first call before any stream capture. */
 #define CTF_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ctf_filter_host_noalloc(ctf_texture tex, const float *uv_host, const float *jac_host,
                             const uint8_t *coverage_host, int width, int height, int view_id, ctf_algorithm alg,

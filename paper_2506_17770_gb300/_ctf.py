@@ -124,6 +124,9 @@ def _bind_optional(lib):
         "ctf_batch_graph_launch": ([P, P], I),
         "ctf_batch_graph_destroy": ([P], I),
         "ctf_batch_autotune": ([P, I, I, U64, P, P, P, P], I),
+        "ctf_debug_device_allocations": ([], ctypes.c_int64),
+        "ctf_debug_live_allocations": ([], ctypes.c_int64),
+        "ctf_debug_fail_allocations": ([I, I], I),
     }
     for name, (argtypes, restype) in table.items():
         if hasattr(lib, name):
@@ -315,6 +318,22 @@ def ctf_selftest_bounded_wait(polls, stream=None):
     """Launch the bounded-wait self-test (a wait that runs out after `polls`
     tries and records CTF_ERR_TIMEOUT for the next ctf_sync_check)."""
     _check(load().ctf_selftest_bounded_wait(ctypes.c_uint32(int(polls)), _stream(stream)))
+
+
+def ctf_debug_device_allocations():
+    """Device allocations the library has attempted in this process."""
+    return int(load().ctf_debug_device_allocations())
+
+
+def ctf_debug_live_allocations():
+    """Device allocations of the library that are currently held."""
+    return int(load().ctf_debug_live_allocations())
+
+
+def ctf_debug_fail_allocations(n, skip=0):
+    """Let the library's next `skip` device allocations through, then make
+    the n after them fail (CTF_ERR_OOM); n = 0 disarms."""
+    _check(load().ctf_debug_fail_allocations(int(skip), int(n)))
 
 
 # ---------------------------------------------------------------------------

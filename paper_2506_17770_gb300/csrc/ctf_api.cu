@@ -1,5 +1,6 @@
 // ctf_api.cu -- the C ABI (include/ctf.h): argument validation, texture
 // objects, per-device scratch, error reporting.  No exception crosses the ABI.
+#include <atomic>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -61,7 +62,7 @@ int scratch_stats(unsigned long long **out) {
     std::lock_guard<std::mutex> lk(g_scratch_mutex);
     DeviceScratch &s = g_scratch[dev];
     if (!s.stats) {
-        cudaError_t e = cudaMalloc(&s.stats, sizeof(unsigned long long) * ctf::kNumStats);
+        cudaError_t e = ctf::dev_malloc(&s.stats, sizeof(unsigned long long) * ctf::kNumStats);
         if (e != cudaSuccess) {
             s.stats = nullptr;
             return cuda_fail(e, "cudaMalloc(stats)");
@@ -108,11 +109,11 @@ int scratch_stage(size_t bytes, void **out) {
     if (s.stage_bytes < bytes) {
         if (s.stage) {
             cudaDeviceSynchronize();
-            cudaFree(s.stage);
+            ctf::dev_free(s.stage);
         }
         s.stage = nullptr;
         s.stage_bytes = 0;
-        cudaError_t e = cudaMalloc(&s.stage, bytes);
+        cudaError_t e = ctf::dev_malloc(&s.stage, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(stage)");
         s.stage_bytes = bytes;
     }
@@ -270,10 +271,10 @@ const DecodeTables *device_decode_tables() {
         t.val[i] = num / 255.0f;
     }
     DecodeTables *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, sizeof(DecodeTables));
+    cudaError_t e = ctf::dev_malloc(&d, sizeof(DecodeTables));
     if (e == cudaSuccess) e = cudaMemcpy(d, &t, sizeof(DecodeTables), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        if (d) cudaFree(d);
+        if (d) ctf::dev_free(d);
         report_cuda(e, "decode tables");
         return nullptr;
     }
@@ -301,6 +302,11 @@ int report_cuda(cudaError_t e, const char *what) { return cuda_fail(e, what); }
 
 void clear_error() { g_last_error.clear(); }
 
+// The error word lives in the module's own device memory (zero at load), so
+// no call that needs it allocates.  Host code only holds the symbol's
+// host-side stand-in; its device address is looked up once per device.
+static __device__ int g_device_error_word;
+
 int device_error_word(int **out) {
     int dev = 0;
     int rc = current_device(&dev);
@@ -308,15 +314,50 @@ int device_error_word(int **out) {
     std::lock_guard<std::mutex> lk(g_scratch_mutex);
     DeviceScratch &s = g_scratch[dev];
     if (!s.err) {
-        cudaError_t e = cudaMalloc(&s.err, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(s.err, 0, sizeof(int));
-        if (e != cudaSuccess) {
-            s.err = nullptr;
-            return cuda_fail(e, "cudaMalloc(error word)");
-        }
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_device_error_word);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(error word)");
+        s.err = static_cast<int *>(p);
     }
     *out = s.err;
     return CTF_OK;
+}
+
+std::mutex g_alloc_mutex;
+long long g_alloc_calls = 0, g_alloc_live = 0;
+int g_alloc_skip = 0, g_alloc_fail = 0;  // let `skip` through, then fail `fail`
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    bool fail_now = false;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mutex);
+        ++g_alloc_calls;
+        if (g_alloc_fail > 0) {
+            if (g_alloc_skip > 0) {
+                --g_alloc_skip;
+            } else {
+                --g_alloc_fail;
+                fail_now = true;
+            }
+        }
+    }
+    if (fail_now) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_alloc_mutex);
+        ++g_alloc_live;
+    }
+    return e;
+}
+
+void dev_free(void *p) {
+    if (!p) return;
+    cudaFree(p);
+    std::lock_guard<std::mutex> lk(g_alloc_mutex);
+    --g_alloc_live;
 }
 
 }  // namespace ctf
@@ -397,6 +438,25 @@ int ctf_sync_check(void *stream) {
     return CTF_OK;
 }
 
+int64_t ctf_debug_device_allocations(void) {
+    std::lock_guard<std::mutex> lk(ctf::g_alloc_mutex);
+    return (int64_t)ctf::g_alloc_calls;
+}
+
+int64_t ctf_debug_live_allocations(void) {
+    std::lock_guard<std::mutex> lk(ctf::g_alloc_mutex);
+    return (int64_t)ctf::g_alloc_live;
+}
+
+int ctf_debug_fail_allocations(int skip, int n) {
+    g_last_error.clear();
+    if (skip < 0 || n < 0) return fail(CTF_ERR_ARG, "skip = %d and n = %d must not be negative", skip, n);
+    std::lock_guard<std::mutex> lk(ctf::g_alloc_mutex);
+    ctf::g_alloc_skip = skip;
+    ctf::g_alloc_fail = n;
+    return CTF_OK;
+}
+
 int ctf_selftest_bounded_wait(uint32_t polls, void *stream) {
     g_last_error.clear();
     if (polls < 1 || polls > (1u << 24)) return fail(CTF_ERR_ARG, "polls %u outside [1, 2^24]", polls);
@@ -425,20 +485,20 @@ int ctf_texture_create(const ctf_texture_desc *desc, ctf_texture *out) {
     t->mode = CTF_EVAL_BLOCK;
     cudaGetDevice(&t->device);
     const size_t bytes = (size_t)(W / 4) * (size_t)(H / 4) * 8;
-    cudaError_t e = cudaMalloc(&t->blocks, bytes);
+    cudaError_t e = ctf::dev_malloc(&t->blocks, bytes);
     if (e != cudaSuccess) {
         delete t;
         return cuda_fail(e, "cudaMalloc(blocks)");
     }
     e = cudaMemcpy(t->blocks, desc->blocks, bytes, cudaMemcpyDefault);
     if (e != cudaSuccess) {
-        cudaFree(t->blocks);
+        ctf::dev_free(t->blocks);
         delete t;
         return cuda_fail(e, "copying blocks");
     }
     t->tables = ctf::device_decode_tables();
     if (!t->tables) {
-        cudaFree(t->blocks);
+        ctf::dev_free(t->blocks);
         delete t;
         return CTF_ERR_CUDA;
     }
@@ -450,10 +510,10 @@ int ctf_texture_destroy(ctf_texture tex) {
     g_last_error.clear();
     if (!tex) return CTF_OK;
     cudaDeviceSynchronize();
-    if (tex->blocks) cudaFree(tex->blocks);
+    if (tex->blocks) ctf::dev_free(tex->blocks);
     for (int g = 0; g < 2; ++g)
-        if (tex->lat[g]) cudaFree(tex->lat[g]);
-    if (tex->img) cudaFree(tex->img);
+        if (tex->lat[g]) ctf::dev_free(tex->lat[g]);
+    if (tex->img) ctf::dev_free(tex->img);
     delete tex;
     return CTF_OK;
 }

@@ -457,11 +457,11 @@ cudaError_t upload_plan(const Plan &plan, DevPlan *dp, cudaStream_t s) {
     if (dp->bytes < need) {
         if (dp->buf) {
             cudaStreamSynchronize(s);
-            cudaFree(dp->buf);
+            ctf::dev_free(dp->buf);
         }
         dp->buf = nullptr;
         dp->bytes = 0;
-        cudaError_t e = cudaMalloc(&dp->buf, need);
+        cudaError_t e = ctf::dev_malloc(&dp->buf, need);
         if (e != cudaSuccess) return e;
         dp->bytes = need;
     }
@@ -630,7 +630,7 @@ int ctf_batch_graph_create(const ctf_view *views, int nviews, ctf_algorithm alg,
     if (e != cudaSuccess) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
         if (g->graph) cudaGraphDestroy(g->graph);
-        if (g->plan.buf) cudaFree(g->plan.buf);
+        if (g->plan.buf) ctf::dev_free(g->plan.buf);
         delete g;
         return report_cuda(e, "batch graph capture");
     }
@@ -653,7 +653,7 @@ int ctf_batch_graph_destroy(ctf_batch_graph g) {
     cudaDeviceSynchronize();
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
-    if (g->plan.buf) cudaFree(g->plan.buf);
+    if (g->plan.buf) ctf::dev_free(g->plan.buf);
     delete g;
     return CTF_OK;
 }

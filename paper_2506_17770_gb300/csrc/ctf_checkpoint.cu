@@ -199,8 +199,8 @@ int ctf_checkpoint_load(const char *path, ctf_texture *out) {
     const int rc = upload_mlp_texture(t);
     if (rc) {
         for (int g = 0; g < 2; ++g)
-            if (t->lat[g]) cudaFree(t->lat[g]);
-        if (t->img) cudaFree(t->img);
+            if (t->lat[g]) ctf::dev_free(t->lat[g]);
+        if (t->img) ctf::dev_free(t->img);
         delete t;
         return rc;
     }

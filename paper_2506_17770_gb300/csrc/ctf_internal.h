@@ -133,8 +133,21 @@ cudaError_t launch_mlp_filter_ws(const ExactParams &p, const MlpDevice &m, int a
 int report(int status, const char *fmt, ...);
 int report_cuda(cudaError_t e, const char *what);
 void clear_error();
-// Per-device error word that bounded device waits set (ctf_api.cu).
+// Per-device error word that bounded device waits set (ctf_api.cu).  It is a
+// file-scope __device__ int looked up once per device, so obtaining it never
+// allocates.
 int device_error_word(int **out);
+
+// Every device allocation of the library goes through here (ctf_api.cu): it
+// counts the calls and, when ctf_debug_fail_allocations armed it, fails
+// without calling cudaMalloc (cudaErrorMemoryAllocation, no sticky error).
+cudaError_t dev_malloc(void **p, size_t bytes);
+template <typename T> inline cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+// Frees what dev_malloc gave (NULL is ignored) and keeps the count of live
+// allocations that the test hooks report.
+void dev_free(void *p);
 
 }  // namespace ctf
 

@@ -44,7 +44,7 @@ int upload_mlp_texture(ctf_texture_s *t) {
         const size_t n = t->s_lat[g].size();
         std::vector<__half> h(n);
         for (size_t i = 0; i < n; ++i) h[i] = __float2half_rn(t->s_lat[g][i]);
-        cudaError_t e = cudaMalloc(&t->lat[g], n * sizeof(__half));
+        cudaError_t e = ctf::dev_malloc(&t->lat[g], n * sizeof(__half));
         if (e == cudaSuccess) e = cudaMemcpy(t->lat[g], h.data(), n * sizeof(__half), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return report_cuda(e, "latent upload");
     }
@@ -85,7 +85,7 @@ int upload_mlp_texture(ctf_texture_s *t) {
             }
         }
     }
-    cudaError_t e = cudaMalloc(&t->img, kImgBytes);
+    cudaError_t e = ctf::dev_malloc(&t->img, kImgBytes);
     if (e == cudaSuccess) e = cudaMemcpy(t->img, img.data(), kImgBytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return report_cuda(e, "operand image upload");
     return CTF_OK;
@@ -126,8 +126,8 @@ int ctf_texture_create_mlp(const ctf_mlp_desc *d, ctf_texture *out) {
     if (!t) return report(CTF_ERR_OOM, "host allocation");
     auto bail = [&](int rc) {
         for (int g = 0; g < 2; ++g)
-            if (t->lat[g]) cudaFree(t->lat[g]);
-        if (t->img) cudaFree(t->img);
+            if (t->lat[g]) ctf::dev_free(t->lat[g]);
+        if (t->img) ctf::dev_free(t->img);
         delete t;
         return rc;
     };

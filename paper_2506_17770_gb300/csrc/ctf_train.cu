@@ -681,12 +681,12 @@ int check_desc(const ctf_train_desc *d) {
 
 void free_trainer(ctf_trainer_s *t) {
     if (!t) return;
-    cudaFree(t->params);
-    cudaFree(t->m);
-    cudaFree(t->v);
-    cudaFree(t->grad);
-    cudaFree(t->touched);
-    cudaFree(t->loss);
+    ctf::dev_free(t->params);
+    ctf::dev_free(t->m);
+    ctf::dev_free(t->v);
+    ctf::dev_free(t->grad);
+    ctf::dev_free(t->touched);
+    ctf::dev_free(t->loss);
     delete t;
 }
 
@@ -703,13 +703,13 @@ int alloc_trainer(ctf_texture src, const ctf_train_desc *d, ctf_trainer_s **out)
     for (int g = 0; g < 2; ++g) t->n_lat[g] = (size_t)d->latent_w[g] * d->latent_h[g] * 8;
     t->nparams = kOffLat + t->n_lat[0] + t->n_lat[1];
     t->touched_words = ((t->n_lat[0] + t->n_lat[1]) / 8 + 31) / 32;
-    cudaError_t e = cudaMalloc(&t->params, t->nparams * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&t->touched, t->touched_words * 4);
+    cudaError_t e = ctf::dev_malloc(&t->params, t->nparams * 4);
+    if (e == cudaSuccess) e = ctf::dev_malloc(&t->touched, t->touched_words * 4);
     if (e == cudaSuccess) e = cudaMemset(t->touched, 0, t->touched_words * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&t->m, t->nparams * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&t->v, t->nparams * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&t->grad, t->nparams * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&t->loss, 8);
+    if (e == cudaSuccess) e = ctf::dev_malloc(&t->m, t->nparams * 4);
+    if (e == cudaSuccess) e = ctf::dev_malloc(&t->v, t->nparams * 4);
+    if (e == cudaSuccess) e = ctf::dev_malloc(&t->grad, t->nparams * 8);
+    if (e == cudaSuccess) e = ctf::dev_malloc(&t->loss, 8);
     if (e == cudaSuccess) e = cudaMemset(t->m, 0, t->nparams * 4);
     if (e == cudaSuccess) e = cudaMemset(t->v, 0, t->nparams * 4);
     if (e == cudaSuccess) e = cudaMemset(t->grad, 0, t->nparams * 8);
@@ -917,7 +917,7 @@ int ctf_trainer_export(ctf_trainer t, ctf_eval_mode mode, ctf_texture *out) {
     std::vector<float> amax(144, 0.f);
     if (mode == CTF_EVAL_MLP_FP8) {
         unsigned *dmax = nullptr;
-        cudaError_t e = cudaMalloc(&dmax, 144 * 4);
+        cudaError_t e = ctf::dev_malloc(&dmax, 144 * 4);
         if (e == cudaSuccess) e = cudaMemset(dmax, 0, 144 * 4);
         if (e == cudaSuccess) {
             GradParams g = grad_params(t);
@@ -925,7 +925,7 @@ int ctf_trainer_export(ctf_trainer t, ctf_eval_mode mode, ctf_texture *out) {
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaMemcpy(amax.data(), dmax, 144 * 4, cudaMemcpyDeviceToHost);
-        cudaFree(dmax);
+        ctf::dev_free(dmax);
         if (e != cudaSuccess) return report_cuda(e, "activation statistics");
         d.act_absmax[0] = amax.data();
         d.act_absmax[1] = amax.data() + 16;
@@ -1047,10 +1047,10 @@ int ctf_texture_compare(ctf_texture ref, ctf_texture learned, double *mse_rgb, d
     float4 *dec = nullptr;
     double *sse = nullptr;
     unsigned *mx = nullptr;
-    cudaError_t e = cudaMalloc(&xy, (size_t)chunk * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&dec, (size_t)chunk * 16);
-    if (e == cudaSuccess) e = cudaMalloc(&sse, 8);
-    if (e == cudaSuccess) e = cudaMalloc(&mx, 4);
+    cudaError_t e = ctf::dev_malloc(&xy, (size_t)chunk * 8);
+    if (e == cudaSuccess) e = ctf::dev_malloc(&dec, (size_t)chunk * 16);
+    if (e == cudaSuccess) e = ctf::dev_malloc(&sse, 8);
+    if (e == cudaSuccess) e = ctf::dev_malloc(&mx, 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(sse, 0, 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(mx, 0, 4, s);
     const MlpDevice m = mlp_device_view(learned);
@@ -1070,10 +1070,10 @@ int ctf_texture_compare(ctf_texture ref, ctf_texture learned, double *mse_rgb, d
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_sse, sse, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_mx, mx, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(xy);
-    cudaFree(dec);
-    cudaFree(sse);
-    cudaFree(mx);
+    ctf::dev_free(xy);
+    ctf::dev_free(dec);
+    ctf::dev_free(sse);
+    ctf::dev_free(mx);
     if (e != cudaSuccess) return report_cuda(e, "texture comparison");
     if (mse_rgb) *mse_rgb = h_sse / (3.0 * (double)total);
     if (max_abs) {

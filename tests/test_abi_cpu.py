@@ -115,3 +115,34 @@ def test_mlp_train_checks_its_arguments_without_gpu(lib):
     with pytest.raises(_ctf.CtfError) as ei:
         _ctf.ctf_mlp_train(None, desc, _ctf.CTF_EVAL_BLOCK)
     assert ei.value.status == _ctf.CTF_ERR_ARG
+
+
+def test_every_device_allocation_goes_through_the_counted_routine():
+    """The allocation test hooks (and the no-allocation entry point's test,
+    which reads the counter) rely on this: no source file of the library
+    calls a CUDA allocator or cudaFree except the one counted routine."""
+    csrc = os.path.join(ROOT, "paper_2506_17770_gb300", "csrc")
+    pat = re.compile(r"\b(cudaMalloc\w*|cudaFree\w*|cudaHostAlloc|cuMem(Alloc|Free)\w*)\s*\(")
+    offenders = []
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
+                       + glob.glob(os.path.join(csrc, "*.h"))):
+        src = open(path).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        src = re.sub(r'"(\\.|[^"\\])*"', '""', src)
+        for m in pat.finditer(src):
+            offenders.append((os.path.basename(path), m.group(1), src[:m.start()].count("\n") + 1))
+    allowed = [o for o in offenders if o[0] == "ctf_api.cu" and o[1] in ("cudaMalloc", "cudaFree")]
+    assert len(allowed) == 2, offenders
+    assert not [o for o in offenders if o not in allowed], offenders
+
+
+def test_allocation_hook_checks_its_arguments_without_gpu(lib):
+    from paper_2506_17770_gb300 import _ctf
+    for skip, n in ((0, -1), (-1, 1)):
+        with pytest.raises(_ctf.CtfError) as ei:
+            _ctf.ctf_debug_fail_allocations(n, skip=skip)
+        assert ei.value.status == _ctf.CTF_ERR_ARG
+    _ctf.ctf_debug_fail_allocations(0)
+    assert _ctf.ctf_debug_device_allocations() >= 0
+    assert _ctf.ctf_debug_live_allocations() >= 0
