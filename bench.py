@@ -449,7 +449,7 @@ def cpu_baseline(arrays, meta, stride=8, views=1, what=""):
             "sample": f"{views} pass{'es' if views > 1 else ''} over the whole {W}x{H} view {what}in bands of "
                       f"16 rows, one process per host core ({cores}), {el:.2f} s",
             "single_thread": {"value": st_px / st_s, "unit": "pixels/s", "cores": 1,
-                              "sample": f"every {stride}th band of 16 rows ({st_px} pixels), {st_s:.2f} s"},
+                              "sample": f"one band of 16 rows in every {stride} ({st_px} pixels), {st_s:.2f} s"},
             "texel_evals_per_pixel": evs / max(1, act)}
 
 

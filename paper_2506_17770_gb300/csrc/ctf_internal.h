@@ -122,9 +122,14 @@ inline uint64_t fnv1a(const void *data, size_t n, uint64_t h = 14695981039346656
     }
     return h;
 }
-// The learned filter with warps specialised by role (ctf_mlp_ws.cu), which
-// launch_mlp_filter uses for STF, Box and Mask Sampling.
+// The learned filters with warps specialised by role, which
+// launch_mlp_filter uses for STF, Box and Mask Sampling: the features
+// computed by the selecting warps (ctf_mlp_ws2.cu), and with group_dedup the
+// consumer merging the group's lists (ctf_mlp_ws.cu).
 bool mlp_filter_ws_applies(const ExactParams &p, int alg);
+cudaError_t prepare_mlp_filter_pf(int alg, int tile_w, int mask_dim);
+cudaError_t launch_mlp_filter_pf(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim,
+                                 int *err, cudaStream_t stream);
 cudaError_t prepare_mlp_filter_ws(int alg, int tile_w, int mask_dim);
 cudaError_t launch_mlp_filter_ws(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim,
                                  int *err, cudaStream_t stream);

@@ -178,7 +178,10 @@ cudaError_t launch_mlp_decode(const MlpDevice &m, int Wt, int Ht, const int2 *xy
 }
 
 cudaError_t prepare_mlp_filter(int alg, int tile_w, int mask_dim) {
-    if (alg == ALG_STF || alg == ALG_BOX || alg == ALG_MASK) return prepare_mlp_filter_ws(alg, tile_w, mask_dim);
+    if (alg == ALG_STF || alg == ALG_BOX || alg == ALG_MASK) {
+        cudaError_t e = prepare_mlp_filter_pf(alg, tile_w, mask_dim);
+        return e == cudaSuccess ? prepare_mlp_filter_ws(alg, tile_w, mask_dim) : e;
+    }
     FilterFn fn = nullptr;
     switch (tile_w) {
     case 8: fn = pick_alg<8>(alg, mask_dim); break;
@@ -196,7 +199,9 @@ cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t 
 
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                               cudaStream_t stream) {
-    if (mlp_filter_ws_applies(p, alg)) return launch_mlp_filter_ws(p, m, alg, tile_w, mask_dim, err, stream);
+    if (mlp_filter_ws_applies(p, alg))
+        return p.group_dedup ? launch_mlp_filter_ws(p, m, alg, tile_w, mask_dim, err, stream)
+                             : launch_mlp_filter_pf(p, m, alg, tile_w, mask_dim, err, stream);
     FilterFn fn = nullptr;
     switch (tile_w) {
     case 8: fn = pick_alg<8>(alg, mask_dim); break;

@@ -153,10 +153,10 @@ __device__ __forceinline__ uint16_t pack_e4m3x2(float a, float b) {
     return (uint16_t)v;
 }
 
-// Row `row` of the layer-1 A operand from 16 features.
-__device__ __forceinline__ void store_x_row(unsigned char *sm, int row, const float f[kMlpIn], bool fp8,
-                                            const float *inv_a) {
-    unsigned char *X = sm + kSmX;
+// Row `row` of a layer-1 A operand at X (K-major core matrices, 32 bytes a
+// row) from 16 features.
+__device__ __forceinline__ void store_x_row_at(unsigned char *X, int row, const float f[kMlpIn], bool fp8,
+                                               const float *inv_a) {
     if (!fp8) {
         uint4 c0 = make_uint4(pack_half2(f[0], f[1]), pack_half2(f[2], f[3]), pack_half2(f[4], f[5]),
                               pack_half2(f[6], f[7]));
@@ -178,6 +178,12 @@ __device__ __forceinline__ void store_x_row(unsigned char *sm, int row, const fl
         *reinterpret_cast<uint4 *>(X + core_offset(row, 0, 32, 1)) = make_uint4(w[0], w[1], w[2], w[3]);
         *reinterpret_cast<uint4 *>(X + core_offset(row, 16, 32, 1)) = make_uint4(0u, 0u, 0u, 0u);
     }
+}
+
+// Row `row` of the layer-1 A operand of the chain area from 16 features.
+__device__ __forceinline__ void store_x_row(unsigned char *sm, int row, const float f[kMlpIn], bool fp8,
+                                            const float *inv_a) {
+    store_x_row_at(sm + kSmX, row, f, fp8, inv_a);
 }
 
 __device__ __forceinline__ void store_zero_x_row(unsigned char *sm, int row) {

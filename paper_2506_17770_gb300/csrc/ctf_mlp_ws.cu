@@ -589,11 +589,14 @@ cudaError_t ws_prepare(WsFn fn) {
     return e;
 }
 
+// Only the group_dedup variant is launched: without the option the
+// producers compute the features themselves (ctf_mlp_ws2.cu).
 WsFn ws_kernel(int alg, int tile_w, int mask_dim, bool dedup) {
+    if (!dedup) return nullptr;
     switch (tile_w) {
-    case 8: return dedup ? ws_pick<8, true>(alg, mask_dim) : ws_pick<8, false>(alg, mask_dim);
-    case 4: return dedup ? ws_pick<4, true>(alg, mask_dim) : ws_pick<4, false>(alg, mask_dim);
-    case 16: return dedup ? ws_pick<16, true>(alg, mask_dim) : ws_pick<16, false>(alg, mask_dim);
+    case 8: return ws_pick<8, true>(alg, mask_dim);
+    case 4: return ws_pick<4, true>(alg, mask_dim);
+    case 16: return ws_pick<16, true>(alg, mask_dim);
     default: return nullptr;
     }
 }
@@ -605,13 +608,8 @@ bool mlp_filter_ws_applies(const ExactParams &, int alg) {
 }
 
 cudaError_t prepare_mlp_filter_ws(int alg, int tile_w, int mask_dim) {
-    cudaError_t e = cudaErrorInvalidValue;
-    for (bool dedup : {false, true}) {
-        WsFn fn = ws_kernel(alg, tile_w, mask_dim, dedup);
-        e = fn ? ws_prepare(fn) : cudaErrorInvalidValue;
-        if (e != cudaSuccess) break;
-    }
-    return e;
+    WsFn fn = ws_kernel(alg, tile_w, mask_dim, true);
+    return fn ? ws_prepare(fn) : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_mlp_filter_ws(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim,

@@ -1,0 +1,592 @@
+// ctf_mlp_ws2.cu -- learned-decode filter for STF, Box and Mask Sampling on
+// single views: warps specialised by role, with the texel features computed
+// by the warps that select the texels.
+//
+// A CTA of 256 threads (four per SM) takes the groups of 8 pixel tiles g0,
+// g0 + G, ... (G = gridDim.x) in turn:
+//   - warpgroup 1 (warps 4-7, the producers, two tiles of the group each)
+//     runs step 1 of the collaborative flow (Sec. 3) on its tiles, packs the
+//     texel lists of the group into consecutive rows (tile order, list order
+//     within a tile), and writes the features of its own rows straight into
+//     the group's layer-1 operand buffer in the tensor cores' layout; later
+//     it gathers, filters and stores the group's pixels from the row values;
+//   - warpgroup 0 (warps 0-3, the consumer) owns the 128 TMEM lanes and runs
+//     the tcgen05 MLP chain(s) over the group's rows: three MMA layers, the
+//     two hidden epilogues (bias, ReLU, conversion to the next operand) and
+//     the output epilogue into the row values.
+// One consumer thread issues the MMAs and polls their barrier; the other
+// consumer threads wait at a named barrier (no polling).  Warps whose 32
+// rows all lie past the group's last row skip their epilogues.
+// Two stages of group buffers (operand rows, whose first 4 KB the row values
+// overwrite once the rows have been consumed, per-pixel words, counts and
+// first rows) alternate between consecutive groups.  The producers hand a
+// stage over with a full barrier (four arrivals) and get it back with a done
+// barrier (one arrival); a named barrier among the producers at the start
+// of each group orders their own reuse of a stage.  Every wait is bounded; a
+// wait that gives up records CTF_ERR_TIMEOUT and both roles leave.
+// The CTA starts with 64 registers per thread; setmaxnreg gives the
+// producers 72 and the consumer 56 (128 x 72 + 128 x 56 = 256 x 64).
+// Each pixel gets the same texels, texel values, image and counts as the
+// other learned kernels: the rows of an MMA are independent, so where a
+// texel's row sits does not change its value.
+#include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include "ctf_device.cuh"
+#include "ctf_internal.h"
+#include "ctf_mlp.cuh"
+#include "ctf_select.cuh"
+#include "tc_ops.cuh"
+#include "ctf_mlp_chain.cuh"
+
+namespace ctf {
+namespace {
+
+constexpr int kPThreads = 256;
+constexpr int kPProducerWarps = 4;
+constexpr int kPSlots = kGroupTiles / kPProducerWarps;  // pixel tiles of the group per producer warp
+constexpr int kPLaunchRegs = 64, kPConsumerRegs = 56, kPProducerRegs = 72;
+static_assert(128 * kPConsumerRegs + 32 * kPProducerWarps * kPProducerRegs == kPThreads * kPLaunchRegs,
+              "the register split adds up to the launch's registers");
+
+// Shared memory (bytes).  The operand image sits at 0 with the offsets of
+// ctf_mlp.cuh; then the hidden-layer operand H, the MMA barrier and TMEM
+// slot, the stage hand-over barriers, the producers' Mask rank slots and
+// texel lists, and two stages.
+constexpr int kPH = kImgBytes;                   // 128 rows x 128 B
+constexpr int kPBar = kPH + 16384;               // MMA barrier (8 B), TMEM base (4 B)
+constexpr int kPTmem = kPBar + 8;
+constexpr int kPHand = kPBar + 16;               // full[2], done[2]
+constexpr int kPRanks = kPHand + 32;             // producer warps x 32 ints
+constexpr int kPList = kPRanks + kPProducerWarps * 32 * 4;  // 8 slots x 32 int2 texel lists
+constexpr int kPStage0 = kPList + kGroupTiles * 32 * 8;
+// one stage
+constexpr int kPX = 0;                           // 256 rows x 32 B layer-1 operand; row values overlay 0..4095
+constexpr int kPST = kPX + 8192;                 // 256 x float2 (s, t)
+constexpr int kPInfo = kPST + 2048;              // 256 x uint32 per-pixel words
+constexpr int kPCount = kPInfo + 1024;           // 8 x int texels per tile
+constexpr int kPBase = kPCount + 32;             // 8 x int first row per tile
+constexpr int kPRows = kPBase + 32;              // int: rows of the group
+constexpr int kPStageBytes = kPRows + 16;
+constexpr int kPBytes = kPStage0 + 2 * kPStageBytes;
+static_assert(kPH % 16 == 0 && kPStage0 % 16 == 0 && kPStageBytes % 16 == 0, "16-byte operand buffers");
+// four CTAs per SM: 4 x 128 TMEM columns, shared memory and 256 x 64 registers each
+static_assert(4 * (kPBytes + 1024 + 128) <= 228 * 1024, "four CTAs per SM fit");
+static_assert(5 * kPThreads * kPLaunchRegs > 65536, "a fifth CTA, which would find no free TMEM, never fits");
+
+__device__ __forceinline__ unsigned char *p_stage(unsigned char *sm, int s) { return sm + kPStage0 + s * kPStageBytes; }
+__device__ __forceinline__ uint64_t *p_full(unsigned char *sm, int s) {
+    return reinterpret_cast<uint64_t *>(sm + kPHand) + s;
+}
+__device__ __forceinline__ uint64_t *p_done(unsigned char *sm, int s) {
+    return reinterpret_cast<uint64_t *>(sm + kPHand) + 2 + s;
+}
+
+__device__ __forceinline__ void p_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
+}
+
+// Named barriers: 1 among the 128 consumer threads, 2 among the 128
+// producer threads (0 stays __syncthreads).
+__device__ __forceinline__ void cons_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void prod_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+
+// Barrier `id` among 128 threads, returning whether any of them passed true.
+template <int id>
+__device__ __forceinline__ bool bar_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(id)
+        : "memory");
+    return r != 0;
+}
+
+// Hidden epilogue of a warp's 32 rows: TMEM columns [taddr, taddr + 64) of
+// this thread's row -> bias, ReLU -> row `row` of H (FP16; or E4M3 with the
+// output scale and the bias of an FP8 texture already multiplied on the host
+// by the inverse activation scale of the next layer's input).  The same
+// operations, in the same order, as the other learned kernels' epilogue.
+__device__ __forceinline__ void p_hidden_epilogue(unsigned char *H, uint32_t taddr, const float *bias,
+                                                  const float *oscale, bool fp8, int row) {
+    const float4 *b4 = reinterpret_cast<const float4 *>(bias);
+    const float4 *o4 = reinterpret_cast<const float4 *>(oscale);
+    // 16 columns at a time (an FP16 pair of core-matrix rows, or one E4M3 one)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float d[16];
+        tc::tmem_ld16(taddr + 16 * q, d);
+        tc::tmem_wait_ld();
+        if (!fp8) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                uint32_t w[4];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int k = 8 * c + 4 * i;  // columns 16 q + k .. + 3
+                    const float4 b = b4[(16 * q + k) / 4];
+                    const float2 t0 = __fadd2_rn(make_float2(d[k], d[k + 1]), make_float2(b.x, b.y));
+                    const float2 t1 = __fadd2_rn(make_float2(d[k + 2], d[k + 3]), make_float2(b.z, b.w));
+                    w[2 * i] = relu_half2(t0.x, t0.y);
+                    w[2 * i + 1] = relu_half2(t1.x, t1.y);
+                }
+                *reinterpret_cast<uint4 *>(H + core_offset(row, 16 * q + 8 * c, 64, 2)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        } else {
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * i;
+                const float4 b = b4[(16 * q + k) / 4], o = o4[(16 * q + k) / 4];
+                const float2 t0 = __ffma2_rn(make_float2(d[k], d[k + 1]), make_float2(o.x, o.y), make_float2(b.x, b.y));
+                const float2 t1 =
+                    __ffma2_rn(make_float2(d[k + 2], d[k + 3]), make_float2(o.z, o.w), make_float2(b.z, b.w));
+                w[i] = (uint32_t)relu_e4m3x2(t0.x, t0.y) | ((uint32_t)relu_e4m3x2(t1.x, t1.y) << 16);
+            }
+            *reinterpret_cast<uint4 *>(H + core_offset(row, 16 * q, 64, 1)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// One MMA layer's completion: thread 0 polls the barrier, the other
+// consumer threads wait at the consumer barrier, which also carries the
+// outcome to all of them.  Returns false (for every consumer thread alike)
+// if the MMAs did not complete within the bound.
+__device__ __forceinline__ bool p_layer_done(uint64_t *bar, uint32_t &phase, int *err) {
+    bool ok = true;
+    if (threadIdx.x == 0) ok = tc::mbar_wait(bar, phase, kMaxTries);
+    phase ^= 1u;
+    __syncwarp();  // the barrier below is .aligned: warp 0 reconverges first
+    if (bar_or<1>(!ok)) {
+        if (threadIdx.x == 0) atomicExch(err, CTF_ERR_TIMEOUT);
+        return false;
+    }
+    tc::fence_after_sync();
+    return true;
+}
+
+// The three layers for the 128 rows of chain c of a stage (layer-1 operand
+// at sX).  `live`: this warp has rows below the group's row count (else it
+// skips its epilogues, whose rows nobody reads).  Consumer threads only.
+__device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64_t *bar, uint32_t &phase,
+                                        uint32_t sX, bool fp8, bool live, float4 &out, int *err) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    unsigned char *H = sm + kPH;
+    const float *b1 = reinterpret_cast<const float *>(sm + kImgB1);
+    const float *b2 = reinterpret_cast<const float *>(sm + kImgB2);
+    const float *b3 = reinterpret_cast<const float *>(sm + kImgB3);
+    const float *s1 = reinterpret_cast<const float *>(sm + kImgS1);
+    const float *s2 = reinterpret_cast<const float *>(sm + kImgS2);
+    const float *s3 = reinterpret_cast<const float *>(sm + kImgS3);
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    const uint32_t sH = tc::smem_addr(H);
+    const uint32_t sW1 = tc::smem_addr(sm + kImgW1), sW2 = tc::smem_addr(sm + kImgW2),
+                   sW3 = tc::smem_addr(sm + kImgW3);
+    const uint32_t kstep = 256;              // 32 bytes of K per 8-row group
+    const uint32_t sboX = 256u;              // K = 32 bytes per row, FP16 and E4M3 alike
+    const uint32_t sboH = fp8 ? 512u : 1024u;  // 64 elements per row
+    const int nk = fp8 ? 2 : 4;              // MMAs over K = 64
+    const uint32_t id64 = fp8 ? tc::idesc_e4m3(128, 64) : tc::idesc_f16(128, 64);
+    const uint32_t id16 = fp8 ? tc::idesc_e4m3(128, 16) : tc::idesc_f16(128, 16);
+
+    // ---- layer 1: D[0..64) = X W1^T (the producers made X visible to the
+    // tensor cores before the full barrier; the last chain's TMEM reads are
+    // ordered before this issue by the barrier that ended it)
+    if (tid == 0) {
+        tc::fence_after_sync();
+        const uint64_t a = tc::smem_desc(sX, 128, sboX), b = tc::smem_desc(sW1, 128, sboX);
+        if (fp8) tc::mma_e4m3(tmem, a, b, id64, false);
+        else tc::mma_f16(tmem, a, b, id64, false);
+        tc::commit(bar);
+    }
+    if (!p_layer_done(bar, phase, err)) return false;
+    if (live) p_hidden_epilogue(H, lane_base + 0, b1, s1, fp8, tid);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    cons_bar();
+    // ---- layer 2: D[64..128) = H1 W2^T
+    if (tid == 0) {
+        tc::fence_after_sync();
+        for (int j = 0; j < nk; ++j) {
+            const uint64_t a = tc::smem_desc(sH + j * kstep, 128, sboH);
+            const uint64_t b = tc::smem_desc(sW2 + j * kstep, 128, sboH);
+            if (fp8) tc::mma_e4m3(tmem + 64, a, b, id64, j > 0);
+            else tc::mma_f16(tmem + 64, a, b, id64, j > 0);
+        }
+        tc::commit(bar);
+    }
+    if (!p_layer_done(bar, phase, err)) return false;
+    // the layer-2 MMAs have read H1, so H2 may overwrite it
+    if (live) p_hidden_epilogue(H, lane_base + 64, b2, s2, fp8, tid);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    cons_bar();
+    // ---- layer 3: D[0..16) = H2 W3^T
+    if (tid == 0) {
+        tc::fence_after_sync();
+        for (int j = 0; j < nk; ++j) {
+            const uint64_t a = tc::smem_desc(sH + j * kstep, 128, sboH);
+            const uint64_t b = tc::smem_desc(sW3 + j * kstep, 128, sboH);
+            if (fp8) tc::mma_e4m3(tmem, a, b, id16, j > 0);
+            else tc::mma_f16(tmem, a, b, id16, j > 0);
+        }
+        tc::commit(bar);
+    }
+    if (!p_layer_done(bar, phase, err)) return false;
+    if (live) {
+        uint32_t r[4];
+        tc::tmem_ld4(lane_base + 0, r);
+        tc::tmem_wait_ld();
+        float o[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float d = __uint_as_float(r[c]);
+            const float v = fp8 ? __fmaf_rn(d, s3[c], b3[c]) : __fadd_rn(d, b3[c]);
+            o[c] = fminf(fmaxf(v, 0.f), 1.f);
+        }
+        out = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    // the next chain's layer 1 overwrites D[0..64): every TMEM read of this
+    // chain is ordered before it by the caller's consumer barrier
+    tc::fence_before_sync();
+    return true;
+}
+
+// Producer: step 1 on tile slot g of the group at `first` into stage st:
+// per pixel (s, t) and the packed word of the other learned kernels (bits
+// 0-19 the list indices of its 4 taps on success, else of its own texel;
+// 20-22 its count; 23 active; 24 inside; 25 success), the slot's texel count,
+// and the slot's texel list (clamped) at list[32 g + rank].
+template <int ALG, int TW, int MD>
+__device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp, long long first, int g,
+                                        unsigned char *st, int2 *list, int lane, uint32_t lt, int *ranks,
+                                        Counters &cnt) {
+    constexpr int TH = 32 / TW;
+    const int tx = lane % TW, ty = lane / TW;
+    float2 *pix_st = reinterpret_cast<float2 *>(st + kPST);
+    uint32_t *pix_info = reinterpret_cast<uint32_t *>(st + kPInfo);
+    const long long tile = first + g;
+    const bool valid = tile < p.n_tiles;
+    int bx = 0, by = 0;
+    if (valid) tile_pos(tp, g, bx, by);
+    const int px = bx * TW + tx, py = by * TH + ty;
+    const bool inside = valid && px < p.W && py < p.H;
+    const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
+    float2 uv = make_float2(0.f, 0.f);
+    float4 jac = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool covered = inside;
+    if (inside) {
+        uv = __ldcs(p.uv + idx);
+        if (ALG >= ALG_LIST) jac = __ldcs(p.jac + idx);
+        if (p.cov) covered = __ldcs(p.cov + idx) != 0;
+    }
+    PixelSetup ps;
+    ps.active = covered;
+    setup_coords(uv, (float)p.Wt, (float)p.Ht, ps);
+    Selection sel;
+    if (valid) {
+        sel = select_tile<ALG, MD, true, false>(p, ps, jac, px, py, lane, lt, nullptr, ranks, cnt);
+    } else {
+        sel.path = PATH_EMPTY;
+        sel.A = 0;
+        sel.produce = false;
+        sel.count = 0;
+        sel.my_rank = 0;
+    }
+    if (sel.produce)
+        list[32 * g + sel.my_rank] = make_int2(min(max(sel.tx, 0), p.Wt - 1), min(max(sel.ty, 0), p.Ht - 1));
+    const bool succ = sel.path == PATH_SUCCESS;
+    const int n = succ ? sel.n : __popc(sel.A);
+    if (lane == 0) reinterpret_cast<int *>(st + kPCount)[g] = n;
+    uint32_t info = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) info |= ((uint32_t)sel.rk[k] & 31u) << (5 * k);
+    info = succ ? info : ((uint32_t)sel.my_rank & 31u);
+    info |= ((uint32_t)sel.count << 20) | (ps.active ? 1u << 23 : 0u) | (inside ? 1u << 24 : 0u) |
+            (succ ? 1u << 25 : 0u);
+    pix_st[32 * g + lane] = make_float2(ps.s, ps.t);
+    pix_info[32 * g + lane] = info;
+}
+
+// Producer: step 3 for tile slot g of the group at `first` from stage st
+// (row values written by the consumer): gather, filter, store.
+template <int TW>
+__device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp, int g, const unsigned char *st,
+                                         int lane) {
+    constexpr int TH = 32 / TW;
+    const int tx = lane % TW, ty = lane / TW;
+    const uint32_t info = reinterpret_cast<const uint32_t *>(st + kPInfo)[32 * g + lane];
+    if (!((info >> 24) & 1u)) return;  // outside the frame (or no tile)
+    const float4 *outrow = reinterpret_cast<const float4 *>(st + kPX) + reinterpret_cast<const int *>(st + kPBase)[g];
+    int bx, by;
+    tile_pos(tp, g, bx, by);
+    const uint32_t idx = (uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx);
+    float4 result = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint8_t cv = 0;
+    if ((info >> 23) & 1u) {
+        if ((info >> 25) & 1u) {
+            const float2 s = reinterpret_cast<const float2 *>(st + kPST)[32 * g + lane];
+            float w[4];
+            bilinear_weights(s.x, s.y, w);
+            float2 rg = make_float2(0.f, 0.f), ba = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 t = outrow[(info >> (5 * k)) & 31u];
+                const float2 wk = make_float2(w[k], w[k]);
+                rg = __ffma2_rn(wk, make_float2(t.x, t.y), rg);
+                ba = __ffma2_rn(wk, make_float2(t.z, t.w), ba);
+            }
+            result = make_float4(rg.x, rg.y, ba.x, ba.y);
+            cv = (uint8_t)((info >> 20) & 7u);
+        } else {
+            result = outrow[info & 31u];
+            cv = 1;
+        }
+    }
+    __stcs(p.out + idx, result);
+    if (p.evals) p.evals[idx] = cv;
+}
+
+template <int ALG, int TW, int MD>
+__global__ void __launch_bounds__(kPThreads, 4) mlp_filter_pf_kernel(const ExactParams p, const MlpDevice m, int *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ unsigned long long block_stats[kNumStats];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *mma_bar = reinterpret_cast<uint64_t *>(sm + kPBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kPTmem);
+    if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
+    {
+        const uint4 *src = m.img;
+        uint4 *dst = reinterpret_cast<uint4 *>(sm + kImgW1);
+        for (int i = threadIdx.x; i < kImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    if (threadIdx.x == 0) {
+        tc::mbar_init(mma_bar, 1);
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(p_full(sm, s), kPProducerWarps);
+            tc::mbar_init(p_done(sm, s), 1);
+        }
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const float *inv_a1 = reinterpret_cast<const float *>(sm + kImgA1);
+    Counters cnt;
+#pragma unroll
+    for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
+    const long long n_groups = (p.n_tiles + kGroupTiles - 1) / kGroupTiles;
+    const long long G = gridDim.x;
+    const bool fp8 = m.fp8 != 0;
+
+    if (warp < 4) {
+        // ---------------- consumer ----------------
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kPConsumerRegs));
+        const int tid = threadIdx.x;
+        uint32_t phase = 0;
+        for (long long j = 0;; ++j) {
+            const long long grp = blockIdx.x + j * G;
+            if (grp >= n_groups) break;
+            const int s = (int)(j & 1);
+            const uint32_t par = (uint32_t)((j >> 1) & 1);
+            unsigned char *st = p_stage(sm, s);
+            bool ok = true;
+            if (tid == 0) ok = tc::mbar_wait(p_full(sm, s), par, kMaxTries);
+            __syncwarp();
+            if (bar_or<1>(!ok)) {
+                if (tid == 0) atomicExch(err, CTF_ERR_TIMEOUT);
+                break;
+            }
+            const int R = *reinterpret_cast<const int *>(st + kPRows);
+            const int passes = (R + kRows - 1) / kRows;
+            float4 *outrow = reinterpret_cast<float4 *>(st + kPX);
+            const uint32_t sX = tc::smem_addr(st + kPX);
+            for (int c = 0; c < passes && ok; ++c) {
+                const bool live = kRows * c + 32 * warp < R;
+                float4 v;
+                ok = p_chain(sm, tmem, mma_bar, phase, sX + 4096u * (uint32_t)c, fp8, live, v, err);
+                // chain c's outputs overwrite operand rows of chain 0, which its
+                // layer-1 MMA has read; chain 1's operand rows (bytes 4096 on)
+                // are untouched
+                if (ok && live) outrow[kRows * c + tid] = v;
+                cons_bar();
+            }
+            if (!ok) break;
+            if (tid == 0) p_arrive(p_done(sm, s));
+        }
+    } else {
+        // ---------------- producers: kPSlots tile slots per warp ----------------
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kPProducerRegs));
+        const int pw = warp - 4;
+        const uint32_t lt = lanemask_lt();
+        int *ranks = reinterpret_cast<int *>(sm + kPRanks) + 32 * pw;
+        int2 *list = reinterpret_cast<int2 *>(sm + kPList);
+        const int pt = threadIdx.x - 128;  // producer thread 0..127
+        for (long long j = 0;; ++j) {
+            const long long grp = blockIdx.x + j * G;
+            const bool have = grp < n_groups;  // uniform over the CTA
+            if (have) {
+                const int s = (int)(j & 1);
+                unsigned char *st = p_stage(sm, s);
+                // every producer warp has gathered group j - 2 from this stage
+                // (the consumer was done with it before that gather began) and
+                // read the texel lists of group j - 1
+                __syncwarp();
+                prod_bar();
+                const long long first = grp * kGroupTiles;
+                const TilePos tp = tile_pos0(p, first);
+#pragma unroll 1
+                for (int k = 0; k < kPSlots; ++k)
+                    p_step1<ALG, TW, MD>(p, tp, first, kPSlots * pw + k, st, list, lane, lt, ranks, cnt);
+                __syncwarp();
+                prod_bar();  // every slot's list and count is in place
+                // rows: slot g owns [start_g, start_g + count_g) in slot order;
+                // this thread's rows pt and pt + 128 fall in slots g0 and g1
+                const int *count = reinterpret_cast<const int *>(st + kPCount);
+                int R = 0, g0 = 0, b0 = 0, g1 = 0, b1 = 0, mybase = 0;
+#pragma unroll
+                for (int g = 0; g < kGroupTiles; ++g) {
+                    if (pt >= R) {
+                        g0 = g;
+                        b0 = R;
+                    }
+                    if (pt + kRows >= R) {
+                        g1 = g;
+                        b1 = R;
+                    }
+                    if (pt == g) mybase = R;
+                    R += count[g];
+                }
+                if (pt < kGroupTiles) reinterpret_cast<int *>(st + kPBase)[pt] = mybase;
+                if (pt == 0) {
+                    *reinterpret_cast<int *>(st + kPRows) = R;
+                    cnt.v[kStatTexelEvalsUnique] += R;
+                }
+                // features of rows pt and pt + 128, in the tensor cores' operand
+                // layout
+#pragma unroll 1
+                for (int c = 0; c < 2; ++c) {
+                    const int row = pt + kRows * c;
+                    if (row >= R) break;
+                    const int2 t = c == 0 ? list[32 * g0 + (row - b0)] : list[32 * g1 + (row - b1)];
+                    float f[kMlpIn];
+                    texel_features(m, t.x, t.y, f);
+                    store_x_row_at(st + kPX, row, f, fp8, inv_a1);
+                }
+                tc::fence_proxy_async();  // generic-proxy writes -> the MMAs' async proxy
+                __syncwarp();
+                if (lane == 0) p_arrive(p_full(sm, s));
+            }
+            if (j >= 1) {
+                // gather group j - 1 once its row values are written
+                const int s1 = (int)((j - 1) & 1);
+                const uint32_t par1 = (uint32_t)(((j - 1) >> 1) & 1);
+                bool ok = true;
+                if (lane == 0) ok = tc::mbar_wait(p_done(sm, s1), par1, kMaxTries);
+                __syncwarp();
+                if (bar_or<2>(!ok)) {
+                    if (threadIdx.x == 128) atomicExch(err, CTF_ERR_TIMEOUT);
+                    break;
+                }
+                const TilePos tp1 = tile_pos0(p, (grp - G) * kGroupTiles);
+#pragma unroll 1
+                for (int k = 0; k < kPSlots; ++k) p_gather<TW>(p, tp1, kPSlots * pw + k, p_stage(sm, s1), lane);
+            }
+            if (!have) break;
+        }
+    }
+
+    if (p.stats && lane == 0) {
+#pragma unroll
+        for (int i = 0; i < kNumStats; ++i)
+            if (cnt.v[i]) atomicAdd(&block_stats[i], (unsigned long long)cnt.v[i]);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();  // tcgen05.dealloc needs the whole warp
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
+    if (p.stats && threadIdx.x < kNumStats && block_stats[threadIdx.x])
+        atomicAdd(p.stats + threadIdx.x, block_stats[threadIdx.x]);
+}
+
+using PfFn = void (*)(const ExactParams, const MlpDevice, int *);
+
+template <int TW>
+PfFn pf_pick(int alg, int md) {
+    switch (alg) {
+    case ALG_STF: return mlp_filter_pf_kernel<ALG_STF, TW, 16>;
+    case ALG_BOX: return mlp_filter_pf_kernel<ALG_BOX, TW, 16>;
+    case ALG_MASK: return md == 11 ? mlp_filter_pf_kernel<ALG_MASK, TW, 11> : mlp_filter_pf_kernel<ALG_MASK, TW, 16>;
+    default: return nullptr;
+    }
+}
+
+PfFn pf_kernel(int alg, int tile_w, int mask_dim) {
+    switch (tile_w) {
+    case 8: return pf_pick<8>(alg, mask_dim);
+    case 4: return pf_pick<4>(alg, mask_dim);
+    case 16: return pf_pick<16>(alg, mask_dim);
+    default: return nullptr;
+    }
+}
+
+cudaError_t pf_prepare(PfFn fn) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(dev, reinterpret_cast<const void *>(fn));
+    if (done.count(key)) return cudaSuccess;
+    // setmaxnreg.inc waits until the consumer has released what it asks for:
+    // the split only adds up if the kernel starts with kPLaunchRegs registers
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs != kPLaunchRegs) return cudaErrorInvalidDeviceFunction;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kPBytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
+
+}  // namespace
+
+cudaError_t prepare_mlp_filter_pf(int alg, int tile_w, int mask_dim) {
+    PfFn fn = pf_kernel(alg, tile_w, mask_dim);
+    return fn ? pf_prepare(fn) : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_mlp_filter_pf(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
+                                 cudaStream_t stream) {
+    PfFn fn = pf_kernel(alg, tile_w, mask_dim);
+    if (!fn) return cudaErrorInvalidValue;
+    if (p.n_tiles == 0) return cudaSuccess;
+    if (p.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile positions use 32-bit arithmetic
+    cudaError_t e = pf_prepare(fn);
+    if (e != cudaSuccess) return e;
+    const long long groups = (p.n_tiles + kGroupTiles - 1) / kGroupTiles;
+    const long long cap = (long long)device_sm_count() * 4;
+    const int grid = (int)(groups < cap ? groups : cap);
+    fn<<<grid, kPThreads, kPBytes, stream>>>(p, m, err);
+    return cudaGetLastError();
+}
+
+}  // namespace ctf
