@@ -47,12 +47,19 @@
 namespace ctf {
 namespace {
 
-constexpr int kPThreads = 256;
 constexpr int kPProducerWarps = 4;
+constexpr int kPProducerThreads = 32 * kPProducerWarps;
+constexpr int kPThreads = kRows + kPProducerThreads;
 constexpr int kPSlots = kGroupTiles / kPProducerWarps;  // pixel tiles of the group per producer warp
-constexpr int kPLaunchRegs = 64, kPConsumerRegs = 56, kPProducerRegs = 72;
-static_assert(128 * kPConsumerRegs + 32 * kPProducerWarps * kPProducerRegs == kPThreads * kPLaunchRegs,
+constexpr int kPCtasPerSm = kPProducerWarps == 4 ? 4 : 3;
+constexpr int kPLaunchRegs = (65536 / (kPThreads * kPCtasPerSm)) & ~7;
+// with four producer warps setmaxnreg moves registers from the consumer to them
+constexpr bool kPSplitRegs = kPProducerWarps == 4;
+constexpr int kPConsumerRegs = 56, kPProducerRegs = 72;
+static_assert(!kPSplitRegs || kRows * kPConsumerRegs + kPProducerThreads * kPProducerRegs == kPThreads * kPLaunchRegs,
               "the register split adds up to the launch's registers");
+static_assert(kGroupTiles % kPProducerWarps == 0 && 2 * kRows % kPProducerThreads == 0, "role shapes");
+constexpr int kPFeatRounds = 2 * kRows / kPProducerThreads;  // rows per producer thread, at most
 
 // Shared memory (bytes).  The operand image sits at 0 with the offsets of
 // ctf_mlp.cuh; then the hidden-layer operand H, the MMA barrier and TMEM
@@ -75,9 +82,9 @@ constexpr int kPRows = kPBase + 32;              // int: rows of the group
 constexpr int kPStageBytes = kPRows + 16;
 constexpr int kPBytes = kPStage0 + 2 * kPStageBytes;
 static_assert(kPH % 16 == 0 && kPStage0 % 16 == 0 && kPStageBytes % 16 == 0, "16-byte operand buffers");
-// four CTAs per SM: 4 x 128 TMEM columns, shared memory and 256 x 64 registers each
-static_assert(4 * (kPBytes + 1024 + 128) <= 228 * 1024, "four CTAs per SM fit");
-static_assert(5 * kPThreads * kPLaunchRegs > 65536, "a fifth CTA, which would find no free TMEM, never fits");
+// kPCtasPerSm CTAs per SM fit, and no more than four (4 x 128 TMEM columns)
+static_assert(kPCtasPerSm * (kPBytes + 1024 + 128) <= 228 * 1024, "the CTAs of an SM fit in shared memory");
+static_assert(65536 / (kPThreads * kPLaunchRegs) <= 4, "at most four CTAs share an SM's TMEM");
 
 __device__ __forceinline__ unsigned char *p_stage(unsigned char *sm, int s) { return sm + kPStage0 + s * kPStageBytes; }
 __device__ __forceinline__ uint64_t *p_full(unsigned char *sm, int s) {
@@ -91,22 +98,22 @@ __device__ __forceinline__ void p_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
 }
 
-// Named barriers: 1 among the 128 consumer threads, 2 among the 128
-// producer threads (0 stays __syncthreads).
+// Named barriers: 1 among the 128 consumer threads, 2 among the producer
+// threads (0 stays __syncthreads).
 __device__ __forceinline__ void cons_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-__device__ __forceinline__ void prod_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+__device__ __forceinline__ void prod_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kPProducerThreads) : "memory"); }
 
-// Barrier `id` among 128 threads, returning whether any of them passed true.
-template <int id>
+// Barrier `id` among n threads, returning whether any of them passed true.
+template <int id, int n>
 __device__ __forceinline__ bool bar_or(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, %2, 128, q;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)v), "n"(id)
+        : "r"((uint32_t)v), "n"(id), "n"(n)
         : "memory");
     return r != 0;
 }
@@ -167,7 +174,7 @@ __device__ __forceinline__ bool p_layer_done(uint64_t *bar, uint32_t &phase, int
     if (threadIdx.x == 0) ok = tc::mbar_wait(bar, phase, kMaxTries);
     phase ^= 1u;
     __syncwarp();  // the barrier below is .aligned: warp 0 reconverges first
-    if (bar_or<1>(!ok)) {
+    if (bar_or<1, kRows>(!ok)) {
         if (threadIdx.x == 0) atomicExch(err, CTF_ERR_TIMEOUT);
         return false;
     }
@@ -358,7 +365,7 @@ __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp
 }
 
 template <int ALG, int TW, int MD>
-__global__ void __launch_bounds__(kPThreads, 4) mlp_filter_pf_kernel(const ExactParams p, const MlpDevice m, int *err) {
+__global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(const ExactParams p, const MlpDevice m, int *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned long long block_stats[kNumStats];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -396,7 +403,7 @@ __global__ void __launch_bounds__(kPThreads, 4) mlp_filter_pf_kernel(const Exact
 
     if (warp < 4) {
         // ---------------- consumer ----------------
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kPConsumerRegs));
+        if (kPSplitRegs) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kPConsumerRegs));
         const int tid = threadIdx.x;
         uint32_t phase = 0;
         for (long long j = 0;; ++j) {
@@ -408,7 +415,7 @@ __global__ void __launch_bounds__(kPThreads, 4) mlp_filter_pf_kernel(const Exact
             bool ok = true;
             if (tid == 0) ok = tc::mbar_wait(p_full(sm, s), par, kMaxTries);
             __syncwarp();
-            if (bar_or<1>(!ok)) {
+            if (bar_or<1, kRows>(!ok)) {
                 if (tid == 0) atomicExch(err, CTF_ERR_TIMEOUT);
                 break;
             }
@@ -431,12 +438,12 @@ __global__ void __launch_bounds__(kPThreads, 4) mlp_filter_pf_kernel(const Exact
         }
     } else {
         // ---------------- producers: kPSlots tile slots per warp ----------------
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kPProducerRegs));
+        if (kPSplitRegs) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kPProducerRegs));
         const int pw = warp - 4;
         const uint32_t lt = lanemask_lt();
         int *ranks = reinterpret_cast<int *>(sm + kPRanks) + 32 * pw;
         int2 *list = reinterpret_cast<int2 *>(sm + kPList);
-        const int pt = threadIdx.x - 128;  // producer thread 0..127
+        const int pt = threadIdx.x - kRows;  // producer thread
         for (long long j = 0;; ++j) {
             const long long grp = blockIdx.x + j * G;
             const bool have = grp < n_groups;  // uniform over the CTA
@@ -456,7 +463,8 @@ __global__ void __launch_bounds__(kPThreads, 4) mlp_filter_pf_kernel(const Exact
                 __syncwarp();
                 prod_bar();  // every slot's list and count is in place
                 // rows: slot g owns [start_g, start_g + count_g) in slot order;
-                // this thread's rows pt and pt + 128 fall in slots g0 and g1
+                // this thread's rows pt and pt + kPProducerThreads fall in slots
+                // g0 and g1
                 const int *count = reinterpret_cast<const int *>(st + kPCount);
                 int R = 0, g0 = 0, b0 = 0, g1 = 0, b1 = 0, mybase = 0;
 #pragma unroll
@@ -465,7 +473,7 @@ __global__ void __launch_bounds__(kPThreads, 4) mlp_filter_pf_kernel(const Exact
                         g0 = g;
                         b0 = R;
                     }
-                    if (pt + kRows >= R) {
+                    if (pt + kPProducerThreads >= R) {
                         g1 = g;
                         b1 = R;
                     }
@@ -477,11 +485,11 @@ __global__ void __launch_bounds__(kPThreads, 4) mlp_filter_pf_kernel(const Exact
                     *reinterpret_cast<int *>(st + kPRows) = R;
                     cnt.v[kStatTexelEvalsUnique] += R;
                 }
-                // features of rows pt and pt + 128, in the tensor cores' operand
-                // layout
+                // features of rows pt and pt + kPProducerThreads, in the tensor
+                // cores' operand layout
 #pragma unroll 1
-                for (int c = 0; c < 2; ++c) {
-                    const int row = pt + kRows * c;
+                for (int c = 0; c < kPFeatRounds; ++c) {
+                    const int row = pt + kPProducerThreads * c;
                     if (row >= R) break;
                     const int2 t = c == 0 ? list[32 * g0 + (row - b0)] : list[32 * g1 + (row - b1)];
                     float f[kMlpIn];
@@ -499,7 +507,7 @@ __global__ void __launch_bounds__(kPThreads, 4) mlp_filter_pf_kernel(const Exact
                 bool ok = true;
                 if (lane == 0) ok = tc::mbar_wait(p_done(sm, s1), par1, kMaxTries);
                 __syncwarp();
-                if (bar_or<2>(!ok)) {
+                if (bar_or<2, kPProducerThreads>(!ok)) {
                     if (threadIdx.x == 128) atomicExch(err, CTF_ERR_TIMEOUT);
                     break;
                 }
@@ -561,7 +569,7 @@ cudaError_t pf_prepare(PfFn fn) {
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return e;
-    if (fa.numRegs != kPLaunchRegs) return cudaErrorInvalidDeviceFunction;
+    if (kPSplitRegs ? fa.numRegs != kPLaunchRegs : fa.numRegs > kPLaunchRegs) return cudaErrorInvalidDeviceFunction;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kPBytes);
     if (e == cudaSuccess) done.insert(key);
     return e;
@@ -583,7 +591,7 @@ cudaError_t launch_mlp_filter_pf(const ExactParams &p, const MlpDevice &m, int a
     cudaError_t e = pf_prepare(fn);
     if (e != cudaSuccess) return e;
     const long long groups = (p.n_tiles + kGroupTiles - 1) / kGroupTiles;
-    const long long cap = (long long)device_sm_count() * 4;
+    const long long cap = (long long)device_sm_count() * kPCtasPerSm;
     const int grid = (int)(groups < cap ? groups : cap);
     fn<<<grid, kPThreads, kPBytes, stream>>>(p, m, err);
     return cudaGetLastError();
