@@ -166,7 +166,7 @@ def kernel_source_hash(files):
 
 
 EXACT_SOURCES = ("ctf_filter.cu", "ctf_device.cuh", "ctf_exact_tile.cuh", "ctf_select.cuh")
-LEARNED_SOURCES = ("ctf_mlp_ws.cu", "ctf_mlp_chain.cuh", "ctf_mlp.cuh", "ctf_device.cuh", "ctf_select.cuh",
+LEARNED_SOURCES = ("ctf_mlp_ws2.cu", "ctf_mlp_chain.cuh", "ctf_mlp.cuh", "ctf_device.cuh", "ctf_select.cuh",
                    "tc_ops.cuh")
 
 
@@ -760,7 +760,7 @@ def learned_section(args, dev, stream, flush, rank, world):
                        "traffic": ncu_traffic("learned2160:fp16_mask11", LEARNED_SOURCES),
                        "peak_kind": peak_kind, "algorithmic_flop_per_launch": flop,
                        "flop_per_evaluation": MLP_FLOP_PER_EVAL,
-                       "kernel": "mlp_filter_ws_kernel<MASK, 8x4, 11> (FP16 operands, FP32 accumulation in TMEM)"}
+                       "kernel": "mlp_filter_pf_kernel<MASK, 8x4, 11> (FP16 operands, FP32 accumulation in TMEM)"}
     if not args.no_extras:
         res["learned"] = learned_others(args, dev, stream, flush, sc, texs, exact, peak, peak_kind)
         f = res["learned"]["filter_3840x2160"]
