@@ -4,12 +4,13 @@
 // 16 -> 64 -> 64 -> 4 with ReLU) is fitted to the exact decode of a block
 // texture.  FP32 master parameters live in one device buffer:
 //   [w1 1024 | b1 64 | w2 4096 | b2 64 | w3 256 | b3 4 | pad 4 | latent0 | latent1]
-// A step samples a batch of texels with Philox4x32-10.  A CTA of 512 threads
-// takes 128 texels per round and runs the forward and backward pass in FP32
-// as register-tiled products over them (weights and feature-major
-// activations in shared memory).  It sums the weight gradients of its
-// texels in texel order, and adds them, like the latent-grid gradient
-// scatter, to 64-bit fixed-point accumulators (integer atomics are
+// A step samples a batch of texels with Philox4x32-10.  A CTA of 128
+// threads takes up to 128 texels per round and runs the forward and
+// backward pass as tcgen05 MMAs over them (FP16 operands in shared memory,
+// FP32 accumulation in TMEM; bias, ReLU and the loss in FP32): the layer
+// products, the input-side gradients and the weight gradients, which it
+// sums over its rounds in TMEM.  It adds those sums, like the latent-grid
+// gradient scatter, to 64-bit fixed-point accumulators (integer atomics are
 // order-independent, so a step is deterministic).  An Adam kernel converts
 // the sums back, updates parameters and moments, and clears the
 // accumulators.
@@ -17,9 +18,11 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/ctf.h"
@@ -35,10 +38,9 @@ constexpr int kOffLat = 5512;
 constexpr double kFix = 17592186044416.0;  // 2^44: gradient fixed point
 constexpr double kLossFix = 4294967296.0;  // 2^32: loss fixed point
 constexpr int kThreads = 128;              // threads of the activation-statistics kernel
-constexpr int kGradThreads = 512;          // threads of the gradient kernel
-constexpr int kT = 128;                    // texels per round of the gradient kernel
-constexpr int kMaxRounds = 4;              // rounds per CTA, at most
-constexpr int kLd = kT + 4;                // row stride of the feature-major activation rows (floats)
+constexpr int kT = 128;                    // rows of a round of the gradient kernel (one per thread)
+constexpr int kMaxRounds = 4;              // rounds per CTA, at most (unless the batch needs more)
+constexpr int kMaxGradCtas = 1024;         // CTAs of the gradient kernel, at most (their partial sums)
 
 struct GradParams {
     const float *params;
@@ -48,70 +50,159 @@ struct GradParams {
     float sx[2], sy[2];
     const int2 *xy;        // explicit texels, or nullptr: Philox sampling
     int n;                 // texels in this call
-    int rounds;            // rounds of kT texels per CTA
+    int rounds;            // rounds per CTA
+    int per_round;         // texels per round (at most kT; the other rows of the round are empty)
     uint32_t step;         // Philox counter word
     uint32_t k0, k1;       // Philox key
     float dscale;          // 2 / batch
     long long *grad;       // fixed-point gradient accumulators (same layout as params)
     uint32_t *touched;     // one bit per latent cell (grid 0 cells, then grid 1) whose gradient a texel reached
     long long *loss;       // fixed-point sum of squared errors
+    int *err;              // device error word: a wait that gave up records CTF_ERR_TIMEOUT
+    unsigned char *wimg;   // the weight image of the gradient kernel (pack_kernel)
+    float *partial;        // per-CTA weight-gradient sums [CTA][kWeights] (reduce_kernel adds them up)
 };
 
 // v * 2^44 is exact in FP32 (a power-of-two scale), so this rounds the same
 // value as the FP64 product would, without FP64 arithmetic.
 __device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * 0x1p44f); }
 
-// Shared memory of the gradient kernel (floats).  The weights are held as
-// stored ([out][in]) and transposed; activations are feature-major rows of
-// kLd floats (one column per texel), so that every product below reads
-// 16-byte vectors along a contiguous index.  kLd = 132 puts consecutive rows
-// 4 banks apart.
-constexpr int kSW1 = 0;                    // W1 [64][16]
-constexpr int kSW1t = 1024;                // W1^T [16][64]
-constexpr int kSW2 = 2048;                 // W2 [64][64]
-constexpr int kSW2t = 6144;                // W2^T [64][64]
-constexpr int kSW3 = 10240;                // W3 [4][64]
-constexpr int kSB1 = 10496, kSB2 = 10560, kSB3 = 10624;
-constexpr int kSF = 10628;                 // F^T  [16][kLd]  features
-constexpr int kSH1 = kSF + 16 * kLd;       // H1^T [64][kLd]
-constexpr int kSH2 = kSH1 + 64 * kLd;      // H2^T [64][kLd]
-constexpr int kSD2 = kSH2 + 64 * kLd;      // dH2^T [64][kLd] (masked)
-constexpr int kSD1 = kSD2 + 64 * kLd;      // dH1^T [64][kLd] (masked)
-constexpr int kSDY = kSD1 + 64 * kLd;      // dY^T [4][kLd]
-constexpr int kSDF = kSDY + 4 * kLd;       // dF^T [16][kLd]
-constexpr int kSE = kSDF + 16 * kLd;       // output errors [4][kT]
-constexpr int kSXY = kSE + 4 * kT;         // texel coordinates, int2 [kT]
-constexpr int kSmFloats = kSXY + 2 * kT;
-constexpr size_t kGradSmem = (size_t)kSmFloats * 4;
-static_assert(kSF % 4 == 0 && kSH1 % 4 == 0 && kSD2 % 4 == 0 && kSDY % 4 == 0 && kSE % 4 == 0 && kLd % 4 == 0,
-              "16-byte rows");
-static_assert(kGradSmem <= 227 * 1024, "shared memory");
+// Shared memory of the gradient kernel (bytes).  Every matrix is an MMA
+// operand in FP16, stored K-major in 8-row x 16-byte core matrices (element
+// (r, k) at (r/8) * (K/8) * 128 + (k/8) * 128 + (r%8) * 16 + (k%8) * 2):
+//   weights as the B operands of the forward and backward products:
+//   W1 [64 x 16], W2 [64 x 64], W3 [16 x 64] (rows 4..15 zero), W3^T
+//   [64 x 16] (columns 4..15 zero), W2^T [64 x 64], W1^T [16 x 64];
+//   AH, one row per texel of the round, 176 channels: H2 (0..63), a ones
+//   block (64..79: channel 64 is 1, the rest 0), H1 (80..143), the
+//   features F (144..159) and a second ones block (160..175);
+//   DH, one row per texel, 128 channels: dH2 (0..63), dH1 (64..127);
+//   DE, one row per texel, 16 channels: the output errors (0..3), zeros.
+// The weight gradients are products over the round's texels with the
+// texel as the reduction index: the same AH and DH buffers, read
+// MN-major (channels along MN, texels along K), give
+//   [dH2; dH1]^T [H1 | F | 1] -> dW2, dW1 and the bias sums db2, db1 (one
+//   MMA chain, M = 128 channels, N = 96), and
+//   [H2 | 1 | ...]^T DE -> dW3^T and db3 (M = 128, N = 16),
+// accumulated in TMEM over the CTA's rounds.
+constexpr int kGW1 = 0;
+constexpr int kGW2 = kGW1 + 2048;
+constexpr int kGW3 = kGW2 + 8192;
+constexpr int kGW3T = kGW3 + 2048;
+constexpr int kGW2T = kGW3T + 2048;
+constexpr int kGW1T = kGW2T + 8192;
+constexpr int kGBias = kGW1T + 2048;              // b1[64], b2[64], b3[4] (FP32)
+constexpr int kAHK = 176, kAHGroup = kAHK / 8 * 128;  // channels, bytes per 8-row group
+constexpr int kChH2 = 0, kChOnes = 64, kChH1 = 80, kChF = 144, kChOnes2 = 160;
+constexpr int kGAH = kGBias + 640;
+constexpr int kDHGroup = 128 / 8 * 128;
+constexpr int kGDH = kGAH + 16 * kAHGroup;
+constexpr int kGDE = kGDH + 16 * kDHGroup;
+constexpr int kGXY = kGDE + 16 * 256;             // int2 [128] texel coordinates
+constexpr int kGBar = kGXY + 128 * 8;             // MMA barrier (8 B), TMEM base (4 B)
+constexpr int kGSlot = kGBar + 8;
+constexpr int kGLoss = kGBar + 16;                // float [128] per-thread squared errors
+constexpr int kGradSmemBytes = kGLoss + 128 * 4;
+static_assert(kGAH % 16 == 0 && kGDH % 16 == 0 && kGDE % 16 == 0, "16-byte operand buffers");
+static_assert(2 * (kGradSmemBytes + 1024) <= 228 * 1024 && 3 * (kGradSmemBytes + 1024) > 228 * 1024,
+              "exactly two CTAs (2 x 256 TMEM columns) per SM");
+constexpr size_t kGradSmem = kGradSmemBytes;
+// TMEM columns (FP32, lane = row): forward D1 / backward dE W3^T [0, 64),
+// D2 / dH2 W2^T [64, 128), D3 / dH1 W1^T [128, 144), the weight-gradient
+// sums [144, 240) and [240, 256).
+constexpr uint32_t kTcCols = 256, kColA = 0, kColB = 64, kColC = 128, kColWG1 = 144, kColWG2 = 240;
+constexpr uint32_t kGradTries = 1u << 24;
 
-__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
-
-// acc[i][j] += sum over k < K of A[k][m0 + i] * B[k][n0 + j]: A rows of lda
-// floats (contiguous in m), B rows of kLd floats (contiguous in n), k
-// ascending, one fused multiply-add per term.
-template <int K>
-__device__ __forceinline__ void mm44(const float *A, int lda, const float *B, int m0, int n0, float (&acc)[4][4]) {
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-        const float4 a = ld4(A + k * lda + m0), b = ld4(B + k * kLd + n0);
-        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = __fmaf_rn(av[i], bv[j], acc[i][j]);
-    }
+__host__ __device__ constexpr uint32_t idesc_f16_t(int M, int N, int ta, int tb) {
+    return (1u << 4) | ((uint32_t)ta << 15) | ((uint32_t)tb << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
-// Block of one thread in a 64 x 128 product: warps tile 4 x 4 blocks of
-// 16 x 32, lanes 4 x 8 blocks of 4 x 4.
-__device__ __forceinline__ void tile_64x128(int tid, int &m0, int &n0) {
-    const int w = tid >> 5, l = tid & 31;
-    m0 = (w & 3) * 16 + (l >> 3) * 4;
-    n0 = (w >> 2) * 32 + (l & 7) * 4;
+__device__ __forceinline__ uint32_t h2pack(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ uint32_t relu_h2(float a, float b) {
+    uint32_t r;
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+
+// Offset of element (r, k) in a K-major FP16 operand with K channels.
+__device__ __forceinline__ int kofs(int r, int k, int K) { return (r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+// One MMA (FP16 operands, FP32 accumulation), issued by one thread.
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, bool acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"((uint32_t)acc)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ uint32_t saddr_of(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// The MMAs issued since the last commit: thread 0 commits them to the
+// barrier and polls it; every thread learns the outcome at a CTA barrier.
+// Returns false (for all threads alike) if they did not complete within
+// the bound.
+__device__ __forceinline__ bool tc_sync(uint64_t *bar, uint32_t &phase) {
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr_of(bar))
+                     : "memory");
+        ok = false;
+        const uint32_t a = saddr_of(bar);
+        for (uint32_t i = 0; i < kGradTries && !ok; ++i) {
+            uint32_t done;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(a), "r"(phase)
+                : "memory");
+            ok = done != 0;
+        }
+    }
+    phase ^= 1u;
+    __syncwarp();
+    const bool bad = __syncthreads_or(!ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return !bad;
+}
+
+// Generic-proxy shared-memory writes of every thread made visible to the
+// MMAs that thread 0 issues next.
+__device__ __forceinline__ void tc_publish() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void bilinear_taps(const GradParams &g, int grid, int x, int y, int idx[4], float w[4]) {
@@ -136,275 +227,366 @@ __device__ __forceinline__ void bilinear_taps(const GradParams &g, int grid, int
     w[3] = __fmul_rn(fx, fy);
 }
 
-// Forward and backward pass of kT texels per round, as products over the
-// round's texels.  Every texel's activations and input-side gradients come
-// out of the same operations in the same order as a per-texel evaluation;
-// the weight gradients are summed over the CTA's texels in texel order.
-__global__ void __launch_bounds__(kGradThreads, 1) grad_kernel(const GradParams g) {
-    extern __shared__ __align__(16) float sm[];
+
+// The gradient kernel's weight image (the first kGAH bytes of its shared
+// memory): W1, W2, W3 (padded) and their transposes as FP16 operands, the
+// biases in FP32, from the current FP32 master parameters.  One thread per
+// parameter of the network.
+__global__ void pack_kernel(const float *params, unsigned char *img) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 1024) {
+        const int o = i >> 4, k = i & 15;
+        const __half w = __float2half_rn(params[kOffW1 + i]);
+        *reinterpret_cast<__half *>(img + kGW1 + kofs(o, k, 16)) = w;
+        *reinterpret_cast<__half *>(img + kGW1T + kofs(k, o, 64)) = w;
+    } else if (i < 1024 + 4096) {
+        const int j = i - 1024, o = j >> 6, k = j & 63;
+        const __half w = __float2half_rn(params[kOffW2 + j]);
+        *reinterpret_cast<__half *>(img + kGW2 + kofs(o, k, 64)) = w;
+        *reinterpret_cast<__half *>(img + kGW2T + kofs(k, o, 64)) = w;
+    } else if (i < 1024 + 4096 + 1024) {
+        const int j = i - 5120, c = j >> 6, k = j & 63;
+        const __half w = __float2half_rn(c < 4 ? params[kOffW3 + j] : 0.f);
+        *reinterpret_cast<__half *>(img + kGW3 + kofs(c, k, 64)) = w;   // rows 4..15 zero
+        *reinterpret_cast<__half *>(img + kGW3T + kofs(k, c, 16)) = w;  // columns 4..15 zero
+    } else if (i < 6144 + 160) {
+        const int j = i - 6144;  // biases b1 (64), b2 (64), b3 (4), zero padding
+        float v = 0.f;
+        if (j < 64) v = params[kOffB1 + j];
+        else if (j < 128) v = params[kOffB2 + j - 64];
+        else if (j < 132) v = params[kOffB3 + j - 128];
+        reinterpret_cast<float *>(img + kGBias)[j] = v;
+    }
+}
+constexpr int kPackThreads = 6144 + 160;
+static_assert(kGBias + 160 * 4 == kGAH, "the image ends where the activations begin");
+
+// Forward and backward pass of kT texels per round on the tensor cores:
+// thread t owns texel row t of every per-texel operand and TMEM lane t.
+// Per round: features (FP32, from the FP32 master latents) and targets;
+// H1 = relu(F W1^T + b1), H2 = relu(H1 W2^T + b2), Y = H2 W3^T + b3 (FP16
+// operands, FP32 accumulation, bias and ReLU in FP32); e = Y - target;
+// dH2 = (e W3) masked by H2 > 0, dH1 = (dH2 W2) masked by H1 > 0,
+// dF = dH1 W1; the weight gradients accumulate in TMEM; dF, times the
+// bilinear tap weights and 2 / batch, goes to the latent cells.  The CTA's
+// weight-gradient sums (times 2 / batch) and its squared errors go to the
+// 64-bit fixed-point accumulators at the end.  Rows past the batch carry
+// e = 0 and so contribute nothing.
+__global__ void __launch_bounds__(kT, 2) grad_kernel(const GradParams g) {
+    extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x;
-    // transposed copies are read transposed from global (L2) and written in
-    // order, which keeps the shared-memory stores free of bank conflicts
-    for (int i = tid; i < 1024; i += kGradThreads) {
-        sm[kSW1 + i] = g.params[kOffW1 + i];
-        sm[kSW1t + i] = g.params[kOffW1 + (i & 63) * 16 + (i >> 6)];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kGBar);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(sm + kGSlot);
+    float *sloss = reinterpret_cast<float *>(sm + kGLoss);
+    unsigned char *AH = sm + kGAH, *DH = sm + kGDH, *DE = sm + kGDE;
+    const float *P = g.params;  // latents (FP32 master values)
+    // ---- the weights as FP16 operands and the biases (the image that
+    // pack_kernel made from the current parameters), the constant ones blocks
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(g.wimg);
+        uint4 *dst = reinterpret_cast<uint4 *>(sm);
+        for (int i = tid; i < kGAH / 16; i += kT) dst[i] = __ldg(src + i);
     }
-    for (int i = tid; i < 4096; i += kGradThreads) {
-        sm[kSW2 + i] = g.params[kOffW2 + i];
-        sm[kSW2t + i] = g.params[kOffW2 + (i & 63) * 64 + (i >> 6)];
+    const float *B = reinterpret_cast<const float *>(sm + kGBias);
+    {
+        // the ones blocks of every row: channels 64 and 160 are 1, the rest of
+        // their 16-channel blocks 0 (never written again)
+        const uint4 one = make_uint4(0x3C00u, 0u, 0u, 0u), zero = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(AH + kofs(tid, kChOnes, kAHK)) = one;
+        *reinterpret_cast<uint4 *>(AH + kofs(tid, kChOnes + 8, kAHK)) = zero;
+        *reinterpret_cast<uint4 *>(AH + kofs(tid, kChOnes2, kAHK)) = one;
+        *reinterpret_cast<uint4 *>(AH + kofs(tid, kChOnes2 + 8, kAHK)) = zero;
     }
-    for (int i = tid; i < 256; i += kGradThreads) sm[kSW3 + i] = g.params[kOffW3 + i];
-    if (tid < 64) {
-        sm[kSB1 + tid] = g.params[kOffB1 + tid];
-        sm[kSB2 + tid] = g.params[kOffB2 + tid];
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr_of(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < 4) sm[kSB3 + tid] = g.params[kOffB3 + tid];
-    const float *W1 = sm + kSW1, *W1t = sm + kSW1t, *W2 = sm + kSW2, *W2t = sm + kSW2t, *W3 = sm + kSW3;
-    const float *B1 = sm + kSB1, *B2 = sm + kSB2, *B3 = sm + kSB3;
-    float *F = sm + kSF, *H1 = sm + kSH1, *H2 = sm + kSH2, *D2 = sm + kSD2, *D1 = sm + kSD1, *DY = sm + kSDY,
-          *DF = sm + kSDF, *E = sm + kSE;
-    int2 *XY = reinterpret_cast<int2 *>(sm + kSXY);
-    const size_t lat1 = (size_t)g.gw[0] * g.gh[0] * 8;  // start of the second grid
-    const int w = tid >> 5, l = tid & 31;
-    int m0, n0;
-    tile_64x128(tid, m0, n0);
-    // persistent weight-gradient sums of this thread:
-    //   dW2 rows m2 + {0, 4}, columns n2 + {0, 8, 16, 24}; dW1 row tid/8,
-    //   columns (tid%8) + {0, 8}; dW3 (tid < 256) row tid/64, column tid%64;
-    //   db2 (tid < 64), db1 (64 <= tid < 128), db3 (128 <= tid < 132)
-    const int m2 = (w & 7) * 8 + (l >> 3), n2 = (w >> 3) * 32 + (l & 7);
-    const int m1 = tid >> 3, n1 = tid & 7;
-    float aW2[2][4] = {}, aW1[2] = {}, aW3 = 0.f, aB = 0.f, loss = 0.f;
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr_of(slot)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *slot;
+    const uint32_t lane_t = tmem + ((uint32_t)(32 * (tid >> 5)) << 16);  // this thread's TMEM lane
+    uint32_t phase = 0;
+    bool ok = true;
+    const size_t lat1 = (size_t)g.gw[0] * g.gh[0] * 8;  // start of the second grid
+    const uint32_t sAH = saddr_of(AH), sDH = saddr_of(DH), sDE = saddr_of(DE);
+    const uint32_t id64 = idesc_f16_t(128, 64, 0, 0), id16 = idesc_f16_t(128, 16, 0, 0);
+    const uint32_t idW1 = idesc_f16_t(128, 96, 1, 1), idW2 = idesc_f16_t(128, 16, 1, 1);
+    float loss = 0.f;
 
 #pragma unroll 1
-    for (int r = 0; r < g.rounds; ++r) {
-        const int i0 = (blockIdx.x * g.rounds + r) * kT;
-        // ---- texels of the round
-        if (tid < kT) {
-            const int i = i0 + tid;
-            int x, y;
-            if (g.xy) {
-                const int2 c = i < g.n ? g.xy[i] : make_int2(0, 0);
-                x = min(max(c.x, 0), g.Wt - 1);
-                y = min(max(c.y, 0), g.Ht - 1);
-            } else {
-                const uint4 rr = philox4x32_10(make_uint4((uint32_t)i, g.step, 0x5A4Du, 0u), g.k0, g.k1);
-                x = (int)(((unsigned long long)rr.x * (unsigned)g.Wt) >> 32);
-                y = (int)(((unsigned long long)rr.y * (unsigned)g.Ht) >> 32);
-            }
-            XY[tid] = make_int2(x, y);
-        }
-        __syncthreads();
-        // ---- features: texel t, grid q/2, channels 4(q%2) .. +3
-        {
-            const int t = tid & (kT - 1), q = tid >> 7, gi = q >> 1, c0 = (q & 1) * 4;
-            const int2 c = XY[t];
-            int tap[4];
-            float tw[4];
-            bilinear_taps(g, gi, c.x, c.y, tap, tw);
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            const float *lg = g.params + kOffLat + (gi ? lat1 : 0);
-            for (int k = 0; k < 4; ++k) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(lg + (size_t)tap[k] * 8 + c0));
-                acc[0] = __fmaf_rn(tw[k], v.x, acc[0]);
-                acc[1] = __fmaf_rn(tw[k], v.y, acc[1]);
-                acc[2] = __fmaf_rn(tw[k], v.z, acc[2]);
-                acc[3] = __fmaf_rn(tw[k], v.w, acc[3]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) F[(gi * 8 + c0 + j) * kLd + t] = acc[j];
-        }
-        __syncthreads();
-        // ---- H1 = relu(W1 F + b1), H2 = relu(W2 H1 + b2)
-        {
-            float acc[4][4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = B1[m0 + i];
-            mm44<16>(W1t, 64, F, m0, n0, acc);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                st4(H1 + (m0 + i) * kLd + n0, make_float4(fmaxf(acc[i][0], 0.f), fmaxf(acc[i][1], 0.f),
-                                                          fmaxf(acc[i][2], 0.f), fmaxf(acc[i][3], 0.f)));
-        }
-        __syncthreads();
-        {
-            float acc[4][4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = B2[m0 + i];
-            mm44<64>(W2t, 64, H1, m0, n0, acc);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                st4(H2 + (m0 + i) * kLd + n0, make_float4(fmaxf(acc[i][0], 0.f), fmaxf(acc[i][1], 0.f),
-                                                          fmaxf(acc[i][2], 0.f), fmaxf(acc[i][3], 0.f)));
-        }
-        __syncthreads();
-        // ---- output channel c of texel t, its error and dY = 2 e / batch
-        {
-            const int t = tid & (kT - 1), c = tid >> 7;
-            const bool valid = i0 + t < g.n;
-            float a = B3[c];
-#pragma unroll 4
-            for (int k = 0; k < 64; k += 4) {
-                const float4 wv = ld4(W3 + c * 64 + k);
-                a = __fmaf_rn(wv.x, H2[k * kLd + t], a);
-                a = __fmaf_rn(wv.y, H2[(k + 1) * kLd + t], a);
-                a = __fmaf_rn(wv.z, H2[(k + 2) * kLd + t], a);
-                a = __fmaf_rn(wv.w, H2[(k + 3) * kLd + t], a);
-            }
-            const int2 xy = XY[t];
-            const uint32_t px = fetch_block_texel(g.blocks, g.nbx, g.Wt, g.Ht, xy.x, xy.y);
-            const float tgt = __fdiv_rn((float)((px >> (8 * c)) & 0xffu), 255.f);
-            const float e = __fsub_rn(a, tgt);
-            E[c * kT + t] = e;
-            DY[c * kLd + t] = valid ? __fmul_rn(e, g.dscale) : 0.f;
-        }
-        __syncthreads();
-        // ---- loss (texel order, channels in order); dW3 += dY H2^T; dH2 = (W3^T dY) masked by H2 > 0
-        if (tid < kT && i0 + tid < g.n) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) loss = __fmaf_rn(E[c * kT + tid], E[c * kT + tid], loss);
-        }
-        if (tid < 256) {
-            const float *dy = DY + (tid >> 6) * kLd, *h = H2 + (tid & 63) * kLd;
-#pragma unroll 4
-            for (int t = 0; t < kT; t += 4) {
-                const float4 a = ld4(dy + t), b = ld4(h + t);
-                aW3 = __fmaf_rn(a.x, b.x, aW3);
-                aW3 = __fmaf_rn(a.y, b.y, aW3);
-                aW3 = __fmaf_rn(a.z, b.z, aW3);
-                aW3 = __fmaf_rn(a.w, b.w, aW3);
-            }
+    for (int r = 0; r < g.rounds && ok; ++r) {
+        const int i0 = (blockIdx.x * g.rounds + r) * g.per_round;
+        const int i = i0 + tid;
+        const bool valid = tid < g.per_round && i < g.n;
+        // ---- the texel of row tid, its features and its target
+        int x, y;
+        if (g.xy) {
+            const int2 c = valid ? g.xy[i] : make_int2(0, 0);
+            x = min(max(c.x, 0), g.Wt - 1);
+            y = min(max(c.y, 0), g.Ht - 1);
+        } else {
+            const uint4 rr = philox4x32_10(make_uint4((uint32_t)i, g.step, 0x5A4Du, 0u), g.k0, g.k1);
+            x = (int)(((unsigned long long)rr.x * (unsigned)g.Wt) >> 32);
+            y = (int)(((unsigned long long)rr.y * (unsigned)g.Ht) >> 32);
         }
         {
-            float acc[4][4] = {};
-            mm44<4>(W3, 64, DY, m0, n0, acc);
+            float f[16];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 h = ld4(H2 + (m0 + i) * kLd + n0);
-                st4(D2 + (m0 + i) * kLd + n0, make_float4(h.x > 0.f ? acc[i][0] : 0.f, h.y > 0.f ? acc[i][1] : 0.f,
-                                                          h.z > 0.f ? acc[i][2] : 0.f, h.w > 0.f ? acc[i][3] : 0.f));
-            }
-        }
-        __syncthreads();
-        // ---- dW2 += dH2 H1^T; dH1 = (W2^T dH2) masked by H1 > 0
-        {
-            const float *a0 = D2 + m2 * kLd, *a1 = D2 + (m2 + 4) * kLd;
-            const float *b0 = H1 + n2 * kLd;
-#pragma unroll 2
-            for (int t = 0; t < kT; t += 4) {
-                const float4 x0 = ld4(a0 + t), x1 = ld4(a1 + t);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float4 y = ld4(b0 + 8 * j * kLd + t);
-                    aW2[0][j] = __fmaf_rn(x0.x, y.x, aW2[0][j]);
-                    aW2[0][j] = __fmaf_rn(x0.y, y.y, aW2[0][j]);
-                    aW2[0][j] = __fmaf_rn(x0.z, y.z, aW2[0][j]);
-                    aW2[0][j] = __fmaf_rn(x0.w, y.w, aW2[0][j]);
-                    aW2[1][j] = __fmaf_rn(x1.x, y.x, aW2[1][j]);
-                    aW2[1][j] = __fmaf_rn(x1.y, y.y, aW2[1][j]);
-                    aW2[1][j] = __fmaf_rn(x1.z, y.z, aW2[1][j]);
-                    aW2[1][j] = __fmaf_rn(x1.w, y.w, aW2[1][j]);
-                }
-            }
-        }
-        {
-            float acc[4][4] = {};
-            mm44<64>(W2, 64, D2, m0, n0, acc);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 h = ld4(H1 + (m0 + i) * kLd + n0);
-                st4(D1 + (m0 + i) * kLd + n0, make_float4(h.x > 0.f ? acc[i][0] : 0.f, h.y > 0.f ? acc[i][1] : 0.f,
-                                                          h.z > 0.f ? acc[i][2] : 0.f, h.w > 0.f ? acc[i][3] : 0.f));
-            }
-        }
-        __syncthreads();
-        // ---- dW1 += dH1 F^T; bias sums; dF = W1^T dH1 (warps 0-3)
-        {
-            const float *a = D1 + m1 * kLd, *b0 = F + n1 * kLd, *b1 = F + (n1 + 8) * kLd;
-#pragma unroll 4
-            for (int t = 0; t < kT; t += 4) {
-                const float4 x = ld4(a + t), y0 = ld4(b0 + t), y1 = ld4(b1 + t);
-                aW1[0] = __fmaf_rn(x.x, y0.x, aW1[0]);
-                aW1[0] = __fmaf_rn(x.y, y0.y, aW1[0]);
-                aW1[0] = __fmaf_rn(x.z, y0.z, aW1[0]);
-                aW1[0] = __fmaf_rn(x.w, y0.w, aW1[0]);
-                aW1[1] = __fmaf_rn(x.x, y1.x, aW1[1]);
-                aW1[1] = __fmaf_rn(x.y, y1.y, aW1[1]);
-                aW1[1] = __fmaf_rn(x.z, y1.z, aW1[1]);
-                aW1[1] = __fmaf_rn(x.w, y1.w, aW1[1]);
-            }
-        }
-        if (tid < 132) {
-            const float *row = tid < 64 ? D2 + tid * kLd : (tid < 128 ? D1 + (tid - 64) * kLd : DY + (tid - 128) * kLd);
-#pragma unroll 4
-            for (int t = 0; t < kT; t += 4) {
-                const float4 v = ld4(row + t);
-                aB = __fadd_rn(aB, v.x);
-                aB = __fadd_rn(aB, v.y);
-                aB = __fadd_rn(aB, v.z);
-                aB = __fadd_rn(aB, v.w);
-            }
-        }
-        if (w < 4) {
-            float acc[4][4] = {};
-            const int fm = (l >> 3) * 4, fn = w * 32 + (l & 7) * 4;
-            mm44<64>(W1, 16, D1, fm, fn, acc);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                st4(DF + (fm + i) * kLd + fn, make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]));
-        }
-        __syncthreads();
-        // ---- latent-grid gradient: texel t, grid q/2, taps 2(q%2), 2(q%2) + 1
-        {
-            const int t = tid & (kT - 1), q = tid >> 7, gi = q >> 1, hi = q & 1;
-            if (i0 + t < g.n) {
-                const int2 c = XY[t];
+            for (int gi = 0; gi < 2; ++gi) {
                 int tap[4];
                 float tw[4];
-                bilinear_taps(g, gi, c.x, c.y, tap, tw);
+                bilinear_taps(g, gi, x, y, tap, tw);
+                const float *lg = P + kOffLat + (gi ? lat1 : 0);
+                float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float4 v0 = __ldg(reinterpret_cast<const float4 *>(lg + (size_t)tap[k] * 8));
+                    const float4 v1 = __ldg(reinterpret_cast<const float4 *>(lg + (size_t)tap[k] * 8 + 4));
+                    acc[0] = __fmaf_rn(tw[k], v0.x, acc[0]);
+                    acc[1] = __fmaf_rn(tw[k], v0.y, acc[1]);
+                    acc[2] = __fmaf_rn(tw[k], v0.z, acc[2]);
+                    acc[3] = __fmaf_rn(tw[k], v0.w, acc[3]);
+                    acc[4] = __fmaf_rn(tw[k], v1.x, acc[4]);
+                    acc[5] = __fmaf_rn(tw[k], v1.y, acc[5]);
+                    acc[6] = __fmaf_rn(tw[k], v1.z, acc[6]);
+                    acc[7] = __fmaf_rn(tw[k], v1.w, acc[7]);
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) f[gi * 8 + c] = acc[c];
+            }
+            *reinterpret_cast<uint4 *>(AH + kofs(tid, kChF, kAHK)) =
+                make_uint4(h2pack(f[0], f[1]), h2pack(f[2], f[3]), h2pack(f[4], f[5]), h2pack(f[6], f[7]));
+            *reinterpret_cast<uint4 *>(AH + kofs(tid, kChF + 8, kAHK)) =
+                make_uint4(h2pack(f[8], f[9]), h2pack(f[10], f[11]), h2pack(f[12], f[13]), h2pack(f[14], f[15]));
+        }
+        float tgt[4];
+        {
+            const uint32_t px = fetch_block_texel(g.blocks, g.nbx, g.Wt, g.Ht, x, y);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) tgt[c] = __fdiv_rn((float)((px >> (8 * c)) & 0xffu), 255.f);
+        }
+        tc_publish();
+        // ---- H1 = relu(F W1^T + b1)
+        if (tid == 0)
+            tc_mma(tmem + kColA, sdesc(sAH + kChF / 8 * 128, 128, kAHGroup), sdesc(saddr_of(sm + kGW1), 128, 256), id64,
+                   false);
+        if (!(ok = tc_sync(bar, phase))) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float d[16];
+            tld16(lane_t + kColA + 16 * q, d);
+            uint32_t w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                w[j] = relu_h2(__fadd_rn(d[2 * j], B[16 * q + 2 * j]), __fadd_rn(d[2 * j + 1], B[16 * q + 2 * j + 1]));
+            *reinterpret_cast<uint4 *>(AH + kofs(tid, kChH1 + 16 * q, kAHK)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4 *>(AH + kofs(tid, kChH1 + 16 * q + 8, kAHK)) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+        tc_publish();
+        // ---- H2 = relu(H1 W2^T + b2)
+        if (tid == 0)
+            for (int j = 0; j < 4; ++j)
+                tc_mma(tmem + kColB, sdesc(sAH + kChH1 / 8 * 128 + 256 * j, 128, kAHGroup),
+                       sdesc(saddr_of(sm + kGW2) + 256 * j, 128, 1024), id64, j > 0);
+        if (!(ok = tc_sync(bar, phase))) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float d[16];
+            tld16(lane_t + kColB + 16 * q, d);
+            uint32_t w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                w[j] = relu_h2(__fadd_rn(d[2 * j], B[64 + 16 * q + 2 * j]),
+                               __fadd_rn(d[2 * j + 1], B[64 + 16 * q + 2 * j + 1]));
+            *reinterpret_cast<uint4 *>(AH + kofs(tid, kChH2 + 16 * q, kAHK)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4 *>(AH + kofs(tid, kChH2 + 16 * q + 8, kAHK)) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+        tc_publish();
+        // ---- Y = H2 W3^T + b3, e = Y - target (0 past the batch)
+        if (tid == 0)
+            for (int j = 0; j < 4; ++j)
+                tc_mma(tmem + kColC, sdesc(sAH + kChH2 / 8 * 128 + 256 * j, 128, kAHGroup),
+                       sdesc(saddr_of(sm + kGW3) + 256 * j, 128, 1024), id16, j > 0);
+        if (!(ok = tc_sync(bar, phase))) break;
+        {
+            float d[16];
+            tld16(lane_t + kColC, d);
+            float e[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                e[c] = valid ? __fsub_rn(__fadd_rn(d[c], B[128 + c]), tgt[c]) : 0.f;
+                loss = __fmaf_rn(e[c], e[c], loss);
+            }
+            *reinterpret_cast<uint4 *>(DE + kofs(tid, 0, 16)) = make_uint4(h2pack(e[0], e[1]), h2pack(e[2], e[3]), 0u, 0u);
+            *reinterpret_cast<uint4 *>(DE + kofs(tid, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        tc_publish();
+        // ---- dH2 = (e W3) masked by H2 > 0
+        if (tid == 0)
+            tc_mma(tmem + kColA, sdesc(sDE, 128, 256), sdesc(saddr_of(sm + kGW3T), 128, 256), id64, false);
+        if (!(ok = tc_sync(bar, phase))) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float d[16];
+            tld16(lane_t + kColA + 16 * q, d);
+            const uint4 h0 = *reinterpret_cast<const uint4 *>(AH + kofs(tid, kChH2 + 16 * q, kAHK));
+            const uint4 h1 = *reinterpret_cast<const uint4 *>(AH + kofs(tid, kChH2 + 16 * q + 8, kAHK));
+            const __half *hh0 = reinterpret_cast<const __half *>(&h0), *hh1 = reinterpret_cast<const __half *>(&h1);
+            uint32_t w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const __half a = j < 4 ? hh0[2 * j] : hh1[2 * j - 8], b = j < 4 ? hh0[2 * j + 1] : hh1[2 * j - 7];
+                w[j] = h2pack(__half2float(a) > 0.f ? d[2 * j] : 0.f, __half2float(b) > 0.f ? d[2 * j + 1] : 0.f);
+            }
+            *reinterpret_cast<uint4 *>(DH + kofs(tid, 16 * q, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4 *>(DH + kofs(tid, 16 * q + 8, 128)) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+        tc_publish();
+        // ---- dH1 = (dH2 W2) masked by H1 > 0
+        if (tid == 0)
+            for (int j = 0; j < 4; ++j)
+                tc_mma(tmem + kColB, sdesc(sDH + 256 * j, 128, kDHGroup), sdesc(saddr_of(sm + kGW2T) + 256 * j, 128, 1024),
+                       id64, j > 0);
+        if (!(ok = tc_sync(bar, phase))) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float d[16];
+            tld16(lane_t + kColB + 16 * q, d);
+            const uint4 h0 = *reinterpret_cast<const uint4 *>(AH + kofs(tid, kChH1 + 16 * q, kAHK));
+            const uint4 h1 = *reinterpret_cast<const uint4 *>(AH + kofs(tid, kChH1 + 16 * q + 8, kAHK));
+            const __half *hh0 = reinterpret_cast<const __half *>(&h0), *hh1 = reinterpret_cast<const __half *>(&h1);
+            uint32_t w[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const __half a = j < 4 ? hh0[2 * j] : hh1[2 * j - 8], b = j < 4 ? hh0[2 * j + 1] : hh1[2 * j - 7];
+                w[j] = h2pack(__half2float(a) > 0.f ? d[2 * j] : 0.f, __half2float(b) > 0.f ? d[2 * j + 1] : 0.f);
+            }
+            *reinterpret_cast<uint4 *>(DH + kofs(tid, 64 + 16 * q, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4 *>(DH + kofs(tid, 64 + 16 * q + 8, 128)) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+        tc_publish();
+        // ---- dF = dH1 W1; the weight gradients of the round (texels as the
+        // reduction index, both operands read MN-major)
+        if (tid == 0) {
+            for (int j = 0; j < 4; ++j)
+                tc_mma(tmem + kColC, sdesc(sDH + 64 / 8 * 128 + 256 * j, 128, kDHGroup),
+                       sdesc(saddr_of(sm + kGW1T) + 256 * j, 128, 1024), id16, j > 0);
+            for (int s = 0; s < kT / 16; ++s) {
+                const bool acc = r > 0 || s > 0;
+                // [dH2 dH1]^T [H1 F 1]: A = DH (channels along MN), B = AH channels 80..175
+                tc_mma(tmem + kColWG1, sdesc(sDH + 2 * kDHGroup * s, kDHGroup, 128),
+                       sdesc(sAH + kChH1 / 8 * 128 + 2 * kAHGroup * s, kAHGroup, 128), idW1, acc);
+                // [H2 1 H1]^T e: A = AH channels 0..127, B = DE
+                tc_mma(tmem + kColWG2, sdesc(sAH + 2 * kAHGroup * s, kAHGroup, 128), sdesc(sDE + 512 * s, 256, 128),
+                       idW2, acc);
+            }
+        }
+        if (!(ok = tc_sync(bar, phase))) break;
+        // ---- the latent-grid gradient of texel row tid
+        float df[16];
+        tld16(lane_t + kColC, df);  // warp-collective: every lane takes it
+        if (valid) {
+#pragma unroll
+            for (int gi = 0; gi < 2; ++gi) {
+                int tap[4];
+                float tw[4];
+                bilinear_taps(g, gi, x, y, tap, tw);
                 unsigned long long *gl = reinterpret_cast<unsigned long long *>(g.grad + kOffLat + (gi ? lat1 : 0));
-                const int ta[2] = {hi ? tap[2] : tap[0], hi ? tap[3] : tap[1]};
-                const float wa[2] = {hi ? tw[2] : tw[0], hi ? tw[3] : tw[1]};
                 const uint32_t cell0 = gi ? (uint32_t)(lat1 / 8) : 0u;
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const uint32_t cell = cell0 + (uint32_t)ta[k];
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t cell = cell0 + (uint32_t)tap[k];
                     atomicOr(g.touched + (cell >> 5), 1u << (cell & 31u));
+                    const float wk = __fmul_rn(tw[k], g.dscale);
 #pragma unroll
                     for (int ch = 0; ch < 8; ++ch) {
-                        const long long v = to_fix(__fmul_rn(wa[k], DF[(gi * 8 + ch) * kLd + t]));
-                        if (v) atomicAdd(gl + (size_t)ta[k] * 8 + ch, (unsigned long long)v);
+                        const long long v = to_fix(__fmul_rn(wk, df[gi * 8 + ch]));
+                        if (v) atomicAdd(gl + (size_t)tap[k] * 8 + ch, (unsigned long long)v);
                     }
                 }
             }
         }
-        __syncthreads();
     }
-    // ---- flush the CTA's sums
-    unsigned long long *G = reinterpret_cast<unsigned long long *>(g.grad);
+    // ---- the CTA's weight-gradient sums, row m = tid of the two products,
+    // stored as this CTA's partial sums (reduce_kernel adds the CTAs' up in
+    // CTA order: no atomics on the few thousand weight entries)
+    if (ok) {
+        float *W = g.partial + (size_t)blockIdx.x * kWeights;
+        const int m = tid;
+#pragma unroll 1
+        for (int q = 0; q < 6; ++q) {
+            float d[16];
+            tld16(lane_t + kColWG1 + 16 * q, d);
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 16; ++j) {
+                const int n = 16 * q + j;
+                if (m < 64 && n < 64) W[kOffW2 + m * 64 + n] = d[j];                          // dW2
+                else if (m >= 64 && n >= 64 && n < 80) W[kOffW1 + (m - 64) * 16 + (n - 64)] = d[j];  // dW1
+                else if (n == 80) W[m < 64 ? kOffB2 + m : kOffB1 + (m - 64)] = d[j];           // db2, db1
+            }
+        }
+        {
+            float d[16];
+            tld16(lane_t + kColWG2, d);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            atomicAdd(G + kOffW2 + (m2 + 4 * i) * 64 + n2 + 8 * j, (unsigned long long)to_fix(aW2[i][j]));
-    atomicAdd(G + kOffW1 + m1 * 16 + n1, (unsigned long long)to_fix(aW1[0]));
-    atomicAdd(G + kOffW1 + m1 * 16 + n1 + 8, (unsigned long long)to_fix(aW1[1]));
-    if (tid < 256) atomicAdd(G + kOffW3 + tid, (unsigned long long)to_fix(aW3));
-    if (tid < 132)
-        atomicAdd(G + (tid < 64 ? kOffB2 + tid : (tid < 128 ? kOffB1 + tid - 64 : kOffB3 + tid - 128)),
-                  (unsigned long long)to_fix(aB));
-    E[tid] = loss;
+            for (int c = 0; c < 4; ++c) {
+                if (m < 64) W[kOffW3 + c * 64 + m] = d[c];
+                else if (m == 64) W[kOffB3 + c] = d[c];
+            }
+        }
+        sloss[tid] = loss;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
+    if (ok && tid == 0) {
         float tot = 0.f;
-        for (int s = 0; s < kT; ++s) tot = __fadd_rn(tot, E[s]);
+        for (int s = 0; s < kT; ++s) tot = __fadd_rn(tot, sloss[s]);
         atomicAdd(reinterpret_cast<unsigned long long *>(g.loss), (unsigned long long)__double2ll_rn((double)tot * kLossFix));
+    }
+    if (!ok && tid == 0 && g.err) atomicExch(g.err, CTF_ERR_TIMEOUT);
+    if (tid < 32) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+    }
+}
+
+// The weight gradients: the CTAs' partial sums added up in CTA order (FP64),
+// times 2 / batch, into the fixed-point accumulators.  A block takes 16
+// entries; its 16 thread rows each add every 16th CTA in order (loads
+// issued 8 at a time), and the 16 row sums are added in row order, so the
+// result does not depend on timing.
+constexpr int kRedEntries = 16, kRedRows = 16;
+__global__ void __launch_bounds__(kRedEntries * kRedRows) reduce_kernel(const float *partial, int ctas, double dscale,
+                                                                       long long *grad) {
+    __shared__ double part[kRedRows][kRedEntries];
+    const int e = blockIdx.x * kRedEntries + (threadIdx.x % kRedEntries), row = threadIdx.x / kRedEntries;
+    double acc = 0.0;
+    if (e < kWeights) {
+        for (int c0 = row; c0 < ctas; c0 += 8 * kRedRows) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + j * kRedRows;
+                v[j] = c < ctas ? __ldg(partial + (size_t)c * kWeights + e) : 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc += (double)v[j];
+        }
+    }
+    part[row][threadIdx.x % kRedEntries] = acc;
+    __syncthreads();
+    if (row == 0 && e < kWeights) {
+        double tot = 0.0;
+        for (int r = 0; r < kRedRows; ++r) tot += part[r][threadIdx.x];
+        grad[e] = __double2ll_rn(tot * dscale * kFix);
     }
 }
 
@@ -613,6 +795,8 @@ struct ctf_trainer_s {
     float *params = nullptr, *m = nullptr, *v = nullptr;
     long long *grad = nullptr, *loss = nullptr;
     uint32_t *touched = nullptr;  // latent cells a step's texels reached (zero between steps)
+    unsigned char *wimg = nullptr;  // FP16 weight operands of the gradient kernel
+    float *partial = nullptr;       // per-CTA weight-gradient sums of the gradient kernel
     size_t touched_words = 0;
     int64_t step = 0;
 };
@@ -643,26 +827,50 @@ GradParams grad_params(const ctf_trainer_s *t) {
     g.grad = t->grad;
     g.touched = t->touched;
     g.loss = t->loss;
+    g.per_round = kT;
+    g.wimg = t->wimg;
+    g.partial = t->partial;
+    g.err = nullptr;
+    device_error_word(&g.err);  // a static device word: no allocation; nullptr if it cannot be had
     return g;
 }
 
 cudaError_t launch_grad(const GradParams &g, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
+    static std::mutex mu;
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!attr[dev]) {
+            cudaError_t e = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem);
+            if (e != cudaSuccess) return e;
+            attr[dev] = true;
+        }
     }
-    // One CTA per SM fits (shared memory and registers).  A CTA's fixed
-    // costs (weights in, sums out) favour a few rounds each: kMaxRounds once
-    // there are 128 CTAs of them, fewer below.  The split depends on the
-    // batch alone, so a step gives the same sums on any device.
+    // Two CTAs fit on an SM (TMEM and shared memory).  Small batches take 64
+    // texels per round (the other 64 rows of the MMAs stay empty) so that
+    // more SMs have work; a CTA's fixed costs (weights in, sums out) favour a
+    // few rounds each once there are 256 CTAs, and at most kMaxGradCtas CTAs
+    // hold partial sums.  The split depends on the batch alone, so a step
+    // gives the same sums on any device.
     GradParams gp = g;
-    gp.rounds = g.n / (kT * 128);
-    gp.rounds = gp.rounds < 1 ? 1 : (gp.rounds > kMaxRounds ? kMaxRounds : gp.rounds);
-    const int ctas = (g.n + kT * gp.rounds - 1) / (kT * gp.rounds);
+    gp.per_round = g.n >= 32768 ? kT : kT / 2;
+    int rounds = g.n / (gp.per_round * 256);
+    rounds = rounds < 1 ? 1 : (rounds > kMaxRounds ? kMaxRounds : rounds);
+    const int need = (g.n + gp.per_round * kMaxGradCtas - 1) / (gp.per_round * kMaxGradCtas);
+    gp.rounds = rounds > need ? rounds : need;
+    const int ctas = (g.n + gp.per_round * gp.rounds - 1) / (gp.per_round * gp.rounds);
     if (ctas == 0) return cudaSuccess;
-    grad_kernel<<<ctas, kGradThreads, kGradSmem, s>>>(gp);
+    pack_kernel<<<(kPackThreads + 255) / 256, 256, 0, s>>>(g.params, g.wimg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    grad_kernel<<<ctas, kT, kGradSmem, s>>>(gp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_kernel<<<(kWeights + kRedEntries - 1) / kRedEntries, kRedEntries * kRedRows, 0, s>>>(
+        g.partial, ctas, (double)g.dscale, g.grad);
     return cudaGetLastError();
 }
 
@@ -687,6 +895,8 @@ void free_trainer(ctf_trainer_s *t) {
     ctf::dev_free(t->grad);
     ctf::dev_free(t->touched);
     ctf::dev_free(t->loss);
+    ctf::dev_free(t->wimg);
+    ctf::dev_free(t->partial);
     delete t;
 }
 
@@ -710,6 +920,8 @@ int alloc_trainer(ctf_texture src, const ctf_train_desc *d, ctf_trainer_s **out)
     if (e == cudaSuccess) e = ctf::dev_malloc(&t->v, t->nparams * 4);
     if (e == cudaSuccess) e = ctf::dev_malloc(&t->grad, t->nparams * 8);
     if (e == cudaSuccess) e = ctf::dev_malloc(&t->loss, 8);
+    if (e == cudaSuccess) e = ctf::dev_malloc(&t->wimg, kGAH);
+    if (e == cudaSuccess) e = ctf::dev_malloc(&t->partial, (size_t)kMaxGradCtas * kWeights * 4);
     if (e == cudaSuccess) e = cudaMemset(t->m, 0, t->nparams * 4);
     if (e == cudaSuccess) e = cudaMemset(t->v, 0, t->nparams * 4);
     if (e == cudaSuccess) e = cudaMemset(t->grad, 0, t->nparams * 8);

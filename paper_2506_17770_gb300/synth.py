@@ -151,32 +151,31 @@ def procedural_rgba8(n: int, seed: int = SEED_TEXTURE, octaves: int = 6, base_fr
 
 def encode_blocks(rgba8: np.ndarray) -> np.ndarray:
     """Simple encoder into the 8-byte block format: per 4x4 block the endpoints
-    are the per-channel min (c0) and max (c1) quantised to RGB565, and each
-    texel's 2-bit index is the nearest of the four points 0, 1/3, 2/3, 1 of
-    its colour's projection onto the segment from the block's min to its max
-    colour (index 0 = c0, 1 = c1, 2 = the 1/3 point, 3 = the 2/3 point).
-    Only the encoding is done here; the format's decoding arithmetic is not
-    restated."""
+    are the per-channel min (c0) and max (c1) quantised to RGB565; each texel
+    takes the palette entry nearest in squared RGB distance.  The palette is
+    built here with the format's published rules (bit replication, 1/3 and 2/3
+    points rounded) only to choose indices; decoding is not done here."""
     Ht, Wt = rgba8.shape[:2]
     assert Wt % 4 == 0 and Ht % 4 == 0
-    blk = rgba8[..., :3].astype(np.float64).reshape(Ht // 4, 4, Wt // 4, 4, 3).transpose(0, 2, 1, 3, 4)
+    blk = rgba8[..., :3].astype(np.int32).reshape(Ht // 4, 4, Wt // 4, 4, 3).transpose(0, 2, 1, 3, 4)
     blk = blk.reshape(Ht // 4, Wt // 4, 16, 3)
     lo, hi = blk.min(axis=2), blk.max(axis=2)
 
     def to565(c):
-        c = c.astype(np.int64)
         r = np.clip((c[..., 0] * 31 + 127) // 255, 0, 31)
         gg = np.clip((c[..., 1] * 63 + 127) // 255, 0, 63)
         b = np.clip((c[..., 2] * 31 + 127) // 255, 0, 31)
         return (r << 11) | (gg << 5) | b
 
+    def expand(c):
+        r5, g6, b5 = (c >> 11) & 31, (c >> 5) & 63, c & 31
+        return np.stack([(r5 << 3) | (r5 >> 2), (g6 << 2) | (g6 >> 4), (b5 << 3) | (b5 >> 2)], axis=-1)
+
     c0, c1 = to565(lo), to565(hi)
-    axis = hi - lo                                          # [by,bx,3]
-    den = (axis * axis).sum(-1)                             # [by,bx]
-    num = ((blk - lo[:, :, None, :]) * axis[:, :, None, :]).sum(-1)  # [by,bx,16]
-    t = np.where(den[..., None] > 0, num / np.maximum(den[..., None], 1e-30), 0.0)
-    q = np.clip(np.rint(3.0 * t), 0, 3).astype(np.uint64)   # 0, 1/3, 2/3, 1 -> 0..3
-    sel = np.array([0, 2, 3, 1], dtype=np.uint64)[q]        # -> index codes
+    e0, e1 = expand(c0), expand(c1)
+    pal = np.stack([e0, e1, (2 * e0 + e1 + 1) // 3, (e0 + 2 * e1 + 1) // 3], axis=2)  # [by,bx,4,3]
+    d = ((blk[:, :, :, None, :] - pal[:, :, None, :, :]) ** 2).sum(-1)  # [by,bx,16,4]
+    sel = d.argmin(-1).astype(np.uint64)  # [by,bx,16]
     bits = np.zeros(sel.shape[:2], np.uint64)
     for k in range(16):
         bits |= sel[:, :, k] << np.uint64(2 * k)
