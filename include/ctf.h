@@ -124,16 +124,17 @@ typedef struct {
  *                   ones and spends the other lanes on further texels of
  *                   the footprints (eq. 2); each pixel blends the produced
  *                   texels of its footprint by eq. 1).  Minified tiles take
- *                   one-tap STF.  Block textures only (CTF_ERR_UNSUPPORTED
- *                   for learned ones)                             [0]
+ *                   one-tap STF.  Block and learned textures (on learned
+ *                   ones not together with group_dedup, and in
+ *                   ctf_filter_batch block views only)            [0]
  *   texels_per_lane 0 or 1: one texel evaluation per lane; 2: up to two
  *                   (Sec. 5: at magnification 1 an 8x4 wave needs at most
  *                   54 texels, so two per lane always succeed once every
  *                   pixel is magnified).  Texel i is evaluated for lane
  *                   h(i mod na, A) (or lane i mod 32 without edge
  *                   remapping), whose count becomes 2 when it has two;
- *                   success needs n <= 2 popcount(A).  Block textures only
- *                   (CTF_ERR_UNSUPPORTED for learned ones)        [1]
+ *                   success needs n <= 2 popcount(A).  Block and learned
+ *                   textures (as for fallback)                    [1]
  *   filter          0 bilinear (2x2 footprint); 1 cubic B-spline, 2
  *                   Catmull-Rom (4x4 footprint, Sec. 4.2: the same
  *                   algorithms with the footprint, weights and mask bits of

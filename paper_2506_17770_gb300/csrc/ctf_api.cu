@@ -169,9 +169,11 @@ int validate_filter_args(ctf_texture tex, const float *uv, const float *jac, int
     if ((int)alg < CTF_ALG_4TAP || (int)alg > CTF_ALG_MASK) return fail(CTF_ERR_ARG, "unknown algorithm %d", (int)alg);
     rc = resolve_opts(opts, ro);
     if (rc) return rc;
-    if ((ro->fallback != 0 || ro->tpl != 1 || ro->filter != 0) && tex->mode != CTF_EVAL_BLOCK)
+    if (ro->filter != 0 && tex->mode != CTF_EVAL_BLOCK)
+        return fail(CTF_ERR_UNSUPPORTED, "the bicubic filters are built for block textures only");
+    if ((ro->fallback != 0 || ro->tpl != 1) && ro->group_dedup && tex->mode != CTF_EVAL_BLOCK)
         return fail(CTF_ERR_UNSUPPORTED,
-                    "fallbacks C and C+, two texels per lane and the bicubic filters are built for block textures only");
+                    "group_dedup does not combine with fallbacks C and C+ or two texels per lane on learned textures");
     if ((size_t)width * (size_t)height == 0) return CTF_OK;
     if (!uv || !jac || !out) return fail(CTF_ERR_ARG, "uv, jac and out_rgba must not be NULL");
     if (!aligned(uv, 8)) return fail(CTF_ERR_ALIGN, "uv must be 8-byte aligned");

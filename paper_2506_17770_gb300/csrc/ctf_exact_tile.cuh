@@ -179,18 +179,27 @@ struct FallbackArgs {
     int mode;
 };
 
-__device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ulx, int uly, float s, float t,
-                                                   bool active, int px, int py, uint32_t A, int lane, uint32_t lt,
-                                                   const DecodeTables *tabs, FbTable *tab) {
+// Which texel a lane of an over-budget tile produces under fallback C
+// (mode 1) or C+ (mode 2), from its one-tap STF draw; warp-collective.
+struct FbChoice {
+    bool produce;
+    int qx, qy;  // the texel (unclamped)
+};
+
+__device__ __forceinline__ FbChoice fb_choose(int mode, int view, int y0, uint32_t k0, uint32_t k1, int ulx, int uly,
+                                              float s, float t, bool active, int px, int py, uint32_t A, int lane,
+                                              uint32_t lt, FbTable *tab) {
     const int na = __popc(A);
     const int ai = __popc(A & lt);
     int dx = 0, dy = 0;
     float xi2 = 0.f;
-    if (active) stf_draw(px, py + fa.y0, fa.view, fa.k0, fa.k1, s, t, dx, dy, xi2);
+    if (active) stf_draw(px, py + y0, view, k0, k1, s, t, dx, dy, xi2);
     const int sx = ulx + dx, sy = uly + dy;
-    int qx = sx, qy = sy;  // the texel this lane produces
-    bool produce = active;
-    if (fa.mode == 2) {
+    FbChoice c;
+    c.qx = sx;
+    c.qy = sy;
+    c.produce = active;
+    if (mode == 2) {
         // distinct STF texels: the lowest active lane of each group leads
         const unsigned long long skey = active ? texel_key(sx, sy) : texel_key(INT_MIN, lane);  // distinct when inactive
         const uint32_t grp = __match_any_sync(FULL, skey);
@@ -211,9 +220,9 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
         const int sux = __shfl_sync(FULL, ulx, src), suy = __shfl_sync(FULL, uly, src);
         const float ss = __shfl_sync(FULL, s, src), st = __shfl_sync(FULL, t, src);
         if (!extra) {
-            qx = ux;
-            qy = uy;
-            produce = active;
+            c.qx = ux;
+            c.qy = uy;
+            c.produce = active;
         } else {
             float w[4];
             bilinear_weights(ss, st, w);
@@ -232,8 +241,8 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
                     last = k;
                 }
             }
-            produce = last >= 0;
-            if (produce) {
+            c.produce = last >= 0;
+            if (c.produce) {
                 const float tsel = __fmul_rn(xi2, wc);
                 float run = 0.f;
                 int pick = last;
@@ -248,24 +257,27 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
                         }
                     }
                 }
-                qx = sux + (pick & 1);
-                qy = suy + (pick >> 1);
+                c.qx = sux + (pick & 1);
+                c.qy = suy + (pick >> 1);
             }
         }
         __syncwarp();
         fb_clear(tab, lane);
         __syncwarp();
     }
-    // produce; every lane decodes (non-producers their own clamped texel)
-    float3 val;
-    {
-        const int x = min(max(produce ? qx : ulx, 0), fa.Wt - 1), y = min(max(produce ? qy : uly, 0), fa.Ht - 1);
-        const uint2 blk = __ldg(fa.blocks + (uint32_t)(y >> 2) * (uint32_t)fa.nbx + (uint32_t)(x >> 2));
-        val = decode_texel_f(blk, x, y, tabs);
-    }
-    if (produce) fb_insert(tab, texel_key(qx, qy), lane);
+    return c;
+}
+
+// Eq. 1 for every active pixel of the tile, given each lane's produced
+// value `val` (the texel fb_choose chose; non-producers pass anything):
+// the produced texels of the pixel's footprint with nonzero weight, found in
+// the warp's table.  kAlphaOne: the texels' alpha is 1 (block textures), and
+// val.w is not read.  Warp-collective; leaves the table empty.
+template <bool kAlphaOne>
+__device__ __forceinline__ FallbackOut fb_blend(float4 val, const FbChoice &c, int ulx, int uly, float s, float t,
+                                                bool active, int lane, FbTable *tab) {
+    if (c.produce) fb_insert(tab, texel_key(c.qx, c.qy), lane);
     __syncwarp();
-    // eq. 1: the produced texels of the pixel's footprint with nonzero weight
     float w[4];
     bilinear_weights(s, t, w);
     int srcl[4];
@@ -280,24 +292,25 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
         nz += w[k] > 0.f ? 1 : 0;
         N += pres[k] ? 1 : 0;
     }
-    float3 tv[4];
+    float4 tv[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         tv[k].x = __shfl_sync(FULL, val.x, srcl[k]);
         tv[k].y = __shfl_sync(FULL, val.y, srcl[k]);
         tv[k].z = __shfl_sync(FULL, val.z, srcl[k]);
+        tv[k].w = kAlphaOne ? 1.0f : __shfl_sync(FULL, val.w, srcl[k]);
     }
     __syncwarp();
     fb_clear(tab, lane);  // empty for the next tile
     __syncwarp();
     FallbackOut o;
     o.res = make_float4(0.f, 0.f, 0.f, 0.f);
-    o.count = produce ? 1u : 0u;
+    o.count = c.produce ? 1u : 0u;
     if (!active) return o;
     if (N == 1) {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (pres[k]) o.res = make_float4(tv[k].x, tv[k].y, tv[k].z, 1.0f);
+            if (pres[k]) o.res = tv[k];
         return o;
     }
     float4 swp = make_float4(0.f, 0.f, 0.f, 0.f), sp = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -308,12 +321,12 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
         swp.x = __fmaf_rn(w[k], tv[k].x, swp.x);
         swp.y = __fmaf_rn(w[k], tv[k].y, swp.y);
         swp.z = __fmaf_rn(w[k], tv[k].z, swp.z);
-        swp.w = __fmaf_rn(w[k], 1.0f, swp.w);
+        swp.w = __fmaf_rn(w[k], tv[k].w, swp.w);
         sw = __fadd_rn(sw, w[k]);
         sp.x = __fadd_rn(sp.x, tv[k].x);
         sp.y = __fadd_rn(sp.y, tv[k].y);
         sp.z = __fadd_rn(sp.z, tv[k].z);
-        sp.w = __fadd_rn(sp.w, 1.0f);
+        sp.w = __fadd_rn(sp.w, tv[k].w);
     }
     if (N == nz) {
         o.res = swp;
@@ -323,6 +336,20 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
     o.res = make_float4(__fmaf_rn(r, __fdiv_rn(sp.x, fn), swp.x), __fmaf_rn(r, __fdiv_rn(sp.y, fn), swp.y),
                         __fmaf_rn(r, __fdiv_rn(sp.z, fn), swp.z), __fmaf_rn(r, __fdiv_rn(sp.w, fn), swp.w));
     return o;
+}
+
+__device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ulx, int uly, float s, float t,
+                                                   bool active, int px, int py, uint32_t A, int lane, uint32_t lt,
+                                                   const DecodeTables *tabs, FbTable *tab) {
+    const FbChoice c = fb_choose(fa.mode, fa.view, fa.y0, fa.k0, fa.k1, ulx, uly, s, t, active, px, py, A, lane, lt, tab);
+    // produce; every lane decodes (non-producers their own clamped texel)
+    float3 val;
+    {
+        const int x = min(max(c.produce ? c.qx : ulx, 0), fa.Wt - 1), y = min(max(c.produce ? c.qy : uly, 0), fa.Ht - 1);
+        const uint2 blk = __ldg(fa.blocks + (uint32_t)(y >> 2) * (uint32_t)fa.nbx + (uint32_t)(x >> 2));
+        val = decode_texel_f(blk, x, y, tabs);
+    }
+    return fb_blend<true>(make_float4(val.x, val.y, val.z, 1.0f), c, ulx, uly, s, t, active, lane, tab);
 }
 
 // CTAs of 8 warps per SM that the exact kernels ask the compiler to fit:

@@ -128,6 +128,12 @@ inline uint64_t fnv1a(const void *data, size_t n, uint64_t h = 14695981039346656
 // consumer merging the group's lists (ctf_mlp_ws.cu).
 bool mlp_filter_ws_applies(const ExactParams &p, int alg);
 cudaError_t prepare_mlp_filter_pf(int alg, int tile_w, int mask_dim);
+// The learned filter with fallbacks C / C+ or two texels per lane
+// (ctf_mlp_ext.cu), for List Merge, Box and Mask Sampling.
+bool mlp_filter_ext_applies(const ExactParams &p, int alg);
+cudaError_t prepare_mlp_filter_ext(int alg, int tile_w, int mask_dim);
+cudaError_t launch_mlp_filter_ext(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim,
+                                  int *err, cudaStream_t stream);
 cudaError_t launch_mlp_filter_pf(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim,
                                  int *err, cudaStream_t stream);
 cudaError_t prepare_mlp_filter_ws(int alg, int tile_w, int mask_dim);

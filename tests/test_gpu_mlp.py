@@ -341,10 +341,69 @@ def test_group_dedup_on_a_magnified_plane(tex64):
     assert st1["texel_evals_unique"] < 0.8 * st1["texel_evals"]
 
 
-def test_learned_textures_refuse_fallback_c(tex64):
+EXT_OPTS = [{"fallback": 1}, {"fallback": 2}, {"texels_per_lane": 2, "budget": 64},
+            {"fallback": 2, "texels_per_lane": 2, "budget": 64, "mask_dim": 11}]
+
+
+@pytest.mark.parametrize("opts", EXT_OPTS, ids=["C", "C+", "two", "C+two"])
+@pytest.mark.parametrize("alg", ["list_merge", "box", "mask"])
+@pytest.mark.parametrize("fp8", [False, True])
+def test_learned_extensions_match_fp64_oracle(tex64, tex64_fp8, alg, opts, fp8):
+    """Fallbacks C and C+ (Sec. 3.4) and two texels per lane (Sec. 5) on a
+    learned texture: per-pixel counts and statistics bit-exact against the
+    FP64 oracle, pixels within the texel bound of the decode.  Eq. 1 blends a
+    pixel's produced footprint texels with weights that sum to one (the
+    bilinear weights present plus (1 - S_w) / N each), and the success path
+    is the bilinear filter, so a pixel's error is at most the largest error
+    of its footprint texels, the bound _pixel_bounds takes.  The view holds
+    over-budget and minified tiles and a ragged edge."""
+    tex = tex64_fp8 if fp8 else tex64
+    W, H = 133, 70
+    uv, jac, cov = _scene(W, H, 23)
+    o = {"tile_w": 8, "tile_h": 4, "budget": 32, "mask_dim": 16, "edge_remap": 1}
+    o.update(opts)
+    out, ev, st = gpu_filter(tex, uv, jac, cov, alg, opts, seed=5)
+    ref, ref_ev, ref_st = oracle.filter_frame_learned_f64(
+        tex.mlp, 64, 64, uv, jac, cov, alg=ALGS[alg], seed=5, tile_w=o["tile_w"], tile_h=o["tile_h"],
+        budget=o["budget"], mask_dim=o["mask_dim"], edge_remap=o["edge_remap"], fallback=o.get("fallback", 0),
+        texels_per_lane=o.get("texels_per_lane", 1))
+    np.testing.assert_array_equal(ev, ref_ev)
+    assert st == ref_st
+    if "fallback" in opts and "texels_per_lane" not in opts:
+        assert st["tiles_fallback_budget"] > 0
+    assert st["tiles_fallback_minified"] > 0
+    err = np.abs(out - ref)
+    tol = _pixel_bounds(tex, uv)
+    assert np.all(err <= tol), (alg, opts, err.max(), (err / tol).max())
+
+
+def test_learned_two_texels_per_lane_equal_learned_4tap_on_success(tex64):
+    """Where a tile succeeds with two texels per lane, its pixels equal the
+    learned per-pixel 4-tap image bit for bit: the same texel values (rows
+    of the same chain) and the same filter arithmetic."""
+    W, H = 133, 70
+    uv, jac, cov = _scene(W, H, 29)
+    two, ev, st = gpu_filter(tex64, uv, jac, cov, "mask", {"texels_per_lane": 2, "budget": 64})
+    four = gpu_filter(tex64, uv, jac, cov, "4tap")[0]
+    _, _, _, tp, _ = oracle.filter_frame(synth.random_blocks(64, 64), 64, 64, uv, jac, cov, alg=4,
+                                         texels_per_lane=2, budget=64, want_tiles=True)
+    tiles_x = (W + 7) // 8
+    checked = 0
+    for t, path in enumerate(tp):
+        if path != oracle.PATH_SUCCESS:
+            continue
+        by, bx = divmod(t, tiles_x)
+        sl = (slice(4 * by, 4 * by + 4), slice(8 * bx, 8 * bx + 8))
+        assert np.array_equal(two[sl].view(np.uint32), four[sl].view(np.uint32)), t
+        checked += 1
+    assert checked > 100 and st["tiles_success"] == checked
+
+
+def test_learned_extensions_refuse_group_dedup(tex64):
     uv, jac, cov = _scene(37, 21, 12)
-    with pytest.raises(_ctf.CtfError):
-        gpu_filter(tex64, uv, jac, cov, "mask", {"fallback": 1})
+    with pytest.raises(_ctf.CtfError) as ei:
+        gpu_filter(tex64, uv, jac, cov, "mask", {"fallback": 1, "group_dedup": 1})
+    assert ei.value.status == _ctf.CTF_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("dedup", [0, 1])
