@@ -533,20 +533,25 @@ def learned_others(args, dev, stream, flush, sc, texs, exact, peak_tf, peak_kind
     _ctf.ctf_filter(exact, uv, jac, cov, W, H, 0, "4tap", 0, None, ref_exact, ev, stream=stream)
     k = max(3, min(args.steps, 20))
     runs = {}
+    ref4 = {}
     opts11 = {"mask_dim": 11}
     for tname in ("fp16", "fp8"):
         tex = texs[tname]
-        for name in ("4tap", "stf", "mask", "mask_group_dedup", "box", "list_merge"):
+        for name in ("4tap", "stf", "mask", "mask_group_dedup", "box", "list_merge", "mask_fallback_cplus",
+                     "mask_two_texels_per_lane"):
             if tname == "fp8" and name in ("stf", "box", "list_merge"):
                 continue
             alg = "mask" if name.startswith("mask") else name
-            o = opts11 if name == "mask" else ({"mask_dim": 11, "group_dedup": 1} if name == "mask_group_dedup"
-                                              else None)
+            o = {"mask": opts11, "mask_group_dedup": {"mask_dim": 11, "group_dedup": 1},
+                 "mask_fallback_cplus": {"mask_dim": 11, "fallback": 2},
+                 "mask_two_texels_per_lane": {"mask_dim": 11, "texels_per_lane": 2, "budget": 64}}.get(name)
             ms = _timed_views(lambda: _ctf.ctf_filter(tex, uv, jac, cov, W, H, 0, alg, 0, o, out, ev,
                                                      stream=stream), k, 2, flush, stream)
             st = _ctf.ctf_filter(tex, uv, jac, cov, W, H, 0, alg, 0, o, out, ev, stats=True, stream=stream)
             _ctf.ctf_sync_check(stream)
             mse = torch.mean((out[..., :3] - ref_exact[..., :3]) ** 2).item()
+            if name == "4tap":
+                ref4[tname] = out.clone()
             t = ms / k * 1e-3
             flops = st["texel_evals_unique"] * MLP_FLOP_PER_EVAL  # evaluations done
             peak = peak_tf * (2.0 if tname == "fp8" else 1.0)
@@ -556,6 +561,7 @@ def learned_others(args, dev, stream, flush, sc, texs, exact, peak_tf, peak_kind
                 "evaluations_done_per_pixel": st["texel_evals_unique"] / max(1, st["pixels_active"]),
                 "texel_evals_per_s": st["texel_evals"] / t,
                 "psnr_vs_exact_4tap_db": -10 * math.log10(max(mse, 1e-30)),
+                "psnr_vs_learned_4tap_db": (_psnr(out, ref4[tname]) if name != "4tap" else None),
                 "tensor": {"achieved_tflops": flops / t / 1e12, "peak_tflops": peak,
                            "frac": flops / t / 1e12 / peak,
                            "peak_kind": peak_kind + (" x2 (nominal fp8/fp16 ratio)" if tname == "fp8" else "")},
