@@ -55,7 +55,8 @@ typedef enum {
     CTF_ERR_OOM = -4,         /* device allocation failed */
     CTF_ERR_CUDA = -5,        /* CUDA runtime error */
     CTF_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
-    CTF_ERR_CORRUPT = -7      /* corrupt or mismatched file */
+    CTF_ERR_CORRUPT = -7,     /* corrupt or mismatched file */
+    CTF_ERR_BOUNDS = -8       /* debug build: a kernel index fell outside its buffer */
 } ctf_status;
 
 /* Filtering algorithm.
@@ -271,8 +272,9 @@ int ctf_mlp_decode(ctf_texture tex, const int32_t *xy, int n, float *out_rgba, v
 
 /* Wait for the stream and report any failure of work queued on it:
  * CTF_ERR_CUDA for CUDA errors, CTF_ERR_TIMEOUT if a kernel of this library
- * on the current device gave up a bounded wait since the last check (the
- * record is then cleared). */
+ * on the current device gave up a bounded wait since the last check,
+ * CTF_ERR_BOUNDS if (debug build) a kernel index fell outside its buffer
+ * (the record is then cleared). */
 int ctf_sync_check(void *stream);
 
 /* The same as ctf_sync_check, under the name of the problem statement's
@@ -304,6 +306,26 @@ int ctf_selftest_bounded_wait(uint32_t polls, void *stream);
 int64_t ctf_debug_device_allocations(void);
 int64_t ctf_debug_live_allocations(void);
 int ctf_debug_fail_allocations(int skip, int n);
+
+/* Debug build.  The library also builds as libctf_debug.so (compiled with
+ * -DCTF_DEBUG): the same entry points and results, and every data-dependent
+ * index its kernels use to reach a texel (block or latent cell), a pixel of
+ * the view, or an entry of a shared-memory table (decode tables, rank
+ * slots, List Merge and fallback tables, texel lists, chain rows, per-pixel
+ * words) is checked against its buffer first.  An index outside it is
+ * recorded in the device error word and replaced by 0, so the access stays
+ * inside the buffer and the kernel runs on to its end (no trap); the next
+ * ctf_sync_check returns CTF_ERR_BOUNDS, and ctf_last_error names the site,
+ * the index and the bound of the first record.
+ * ctf_debug_build returns 1 in that library and 0 in the release one.
+ * ctf_debug_selftest_bounds(index, stream) has one thread read element
+ * `index` of a 32-int shared array through the same check: in the debug
+ * library an index outside [0, 32) is recorded (site "self-test") and 0 is
+ * read instead, so the next ctf_sync_check returns CTF_ERR_BOUNDS; the
+ * release library does no unchecked read and returns CTF_ERR_UNSUPPORTED
+ * without launching.  Otherwise returns the launch status. */
+int ctf_debug_build(void);
+int ctf_debug_selftest_bounds(int index, void *stream);
 
 /* Training of the learned decode on texels of an exact block texture (the
  * decoder the network stands in for, which also judges its error).  A

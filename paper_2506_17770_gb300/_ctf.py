@@ -13,10 +13,15 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libctf.so")
+RELEASE_LIB_PATH = os.path.join(_HERE, "_build", "libctf.so")
+DEBUG_LIB_PATH = os.path.join(_HERE, "_build", "libctf_debug.so")
+# CTF_LIBRARY=debug in the environment loads the debug build (index checks
+# in every kernel, reported as CTF_ERR_BOUNDS) instead of the release one.
+LIB_PATH = DEBUG_LIB_PATH if os.environ.get("CTF_LIBRARY", "") == "debug" else RELEASE_LIB_PATH
 
 CTF_OK, CTF_ERR_ARG, CTF_ERR_ALIGN, CTF_ERR_UNSUPPORTED = 0, -1, -2, -3
 CTF_ERR_OOM, CTF_ERR_CUDA, CTF_ERR_TIMEOUT, CTF_ERR_CORRUPT = -4, -5, -6, -7
+CTF_ERR_BOUNDS = -8
 CTF_ALG_4TAP, CTF_ALG_STF, CTF_ALG_LIST_MERGE, CTF_ALG_BOX, CTF_ALG_MASK = 0, 1, 2, 3, 4
 CTF_EVAL_BLOCK, CTF_EVAL_MLP_FP16, CTF_EVAL_MLP_FP8 = 0, 1, 2
 ALGORITHMS = {"4tap": 0, "stf": 1, "list_merge": 2, "box": 3, "mask": 4}
@@ -59,7 +64,7 @@ def load() -> ctypes.CDLL:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
                 raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
-                                  "(run paper_2506_17770_gb300.build.build())")
+                                  "(run paper_2506_17770_gb300.build.build(debug=...))")
             lib = ctypes.CDLL(LIB_PATH)
             P, I, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
             lib.ctf_version.restype = ctypes.c_char_p
@@ -127,6 +132,8 @@ def _bind_optional(lib):
         "ctf_debug_device_allocations": ([], ctypes.c_int64),
         "ctf_debug_live_allocations": ([], ctypes.c_int64),
         "ctf_debug_fail_allocations": ([I, I], I),
+        "ctf_debug_build": ([], I),
+        "ctf_debug_selftest_bounds": ([I, P], I),
     }
     for name, (argtypes, restype) in table.items():
         if hasattr(lib, name):
@@ -334,6 +341,19 @@ def ctf_debug_fail_allocations(n, skip=0):
     """Let the library's next `skip` device allocations through, then make
     the n after them fail (CTF_ERR_OOM); n = 0 disarms."""
     _check(load().ctf_debug_fail_allocations(int(skip), int(n)))
+
+
+def ctf_debug_build() -> bool:
+    """True when the loaded library is the debug build (index checks)."""
+    return bool(load().ctf_debug_build())
+
+
+def ctf_debug_selftest_bounds(index, stream=None):
+    """One thread reads element `index` of a 32-int shared array through the
+    debug build's index check; an index outside [0, 32) is recorded and the
+    next ctf_sync_check raises CTF_ERR_BOUNDS.  The release library refuses
+    (CTF_ERR_UNSUPPORTED)."""
+    _check(load().ctf_debug_selftest_bounds(int(index), _stream(stream)))
 
 
 # ---------------------------------------------------------------------------

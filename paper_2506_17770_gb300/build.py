@@ -1,6 +1,11 @@
 """Build the CUDA library in-tree: every .cu under csrc/ compiled for sm_103a
 with nvcc (one process per translation unit, in parallel) and linked into
-_build/libctf.so.  Only nvcc and the CUDA runtime are needed (no cmake)."""
+_build/libctf.so.  Only nvcc and the CUDA runtime are needed (no cmake).
+
+build(debug=True) makes the debug library _build/libctf_debug.so from the
+same sources with -DCTF_DEBUG: every data-dependent index of its kernels is
+checked against its buffer and an index outside it is reported through the
+device error word (CTF_ERR_BOUNDS) instead of being used."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -13,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libctf.so")
+DEBUG_LIB = os.path.join(BUILD, "libctf_debug.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -33,16 +39,22 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def _paths(debug: bool):
+    """(library, object directory) of the release or the debug build."""
+    return (DEBUG_LIB, os.path.join(BUILD, "debug")) if debug else (LIB, BUILD)
+
+
+def needs_build(debug: bool = False) -> bool:
+    lib = _paths(debug)[0]
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    cmd = [nvcc()] + ARCH + NVCC_FLAGS + ["-I", INCLUDE, "-c", src, "-o", obj]
+def _compile(src: str, verbose: bool, debug: bool) -> str:
+    obj = os.path.join(_paths(debug)[1], os.path.basename(src) + ".o")
+    cmd = [nvcc()] + ARCH + NVCC_FLAGS + (["-DCTF_DEBUG"] if debug else []) + ["-I", INCLUDE, "-c", src, "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,22 +65,23 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib, objdir = _paths(debug)
+    if not force and not needs_build(debug):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    tmp = LIB + f".{os.getpid()}.tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose, debug), srcs))
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcuda"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -14,6 +14,7 @@
 
 #include "../../include/ctf.h"
 #include "ctf_internal.h"
+#include "ctf_debug.cuh"
 
 namespace {
 
@@ -214,15 +215,16 @@ int run_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t
     p.out = reinterpret_cast<float4 *>(out);
     p.evals = evals;
     p.stats = dstats;
+    int *err = nullptr;
+    int rc = ctf::device_error_word(&err);
+    if (rc) return rc;
+    p.err = err;
     cudaError_t e;
     if (tex->mode == CTF_EVAL_BLOCK && ro.filter != 0) {
         e = ctf::launch_bicubic_filter(p, (int)alg, ro.tile_w, ro.mask_dim, ro.filter, stream);
     } else if (tex->mode == CTF_EVAL_BLOCK) {
         e = ctf::launch_exact_filter(p, (int)alg, ro.tile_w, ro.mask_dim, stream);
     } else {
-        int *err = nullptr;
-        int rc = ctf::device_error_word(&err);
-        if (rc) return rc;
         e = ctf::launch_mlp_filter(p, ctf::mlp_device_view(tex), (int)alg, ro.tile_w, ro.mask_dim, err, stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "filter launch");
@@ -307,7 +309,9 @@ void clear_error() { g_last_error.clear(); }
 // The error word lives in the module's own device memory (zero at load), so
 // no call that needs it allocates.  Host code only holds the symbol's
 // host-side stand-in; its device address is looked up once per device.
-static __device__ int g_device_error_word;
+// Word 0 is the status a kernel recorded; a CTF_ERR_BOUNDS record of the
+// debug build adds the site, the index and the bound in words 1-3.
+static __device__ int g_device_error_word[4];
 
 int device_error_word(int **out) {
     int dev = 0;
@@ -323,6 +327,41 @@ int device_error_word(int **out) {
     }
     *out = s.err;
     return CTF_OK;
+}
+
+const char *bounds_site_name(int site) {
+    switch (site) {
+    case kBndPixel: return "the view's pixels";
+    case kBndBlock: return "the texture's blocks";
+    case kBndDecodeTable: return "the decode tables";
+    case kBndRanks: return "a warp's rank slots";
+    case kBndListTable: return "a warp's List Merge table";
+    case kBndFbTable: return "a warp's fallback table";
+    case kBndLatent: return "a latent grid";
+    case kBndTexList: return "a group's texel lists";
+    case kBndRow: return "a chain's rows";
+    case kBndPixSlot: return "a group's per-pixel words";
+    case kBndLane: return "a shuffle's source lane";
+    case kBndBatch: return "a batch plan";
+    case kBndTrain: return "the trainer's buffers";
+    case kBndSelfTest: return "the self-test";
+    default: return "an unknown site";
+    }
+}
+
+namespace {
+// One thread reads element `index` of a 32-int shared array through ck().
+__global__ void bounds_selftest_kernel(int index, int *err) {
+    __shared__ volatile int a[32];
+    a[threadIdx.x] = (int)threadIdx.x;
+    __syncwarp();
+    if (threadIdx.x == 0) (void)a[ck(index, 32, err, kBndSelfTest)];
+}
+}  // namespace
+
+cudaError_t launch_bounds_selftest(int index, int *err, cudaStream_t stream) {
+    bounds_selftest_kernel<<<1, 32, 0, stream>>>(index, err);
+    return cudaGetLastError();
 }
 
 std::mutex g_alloc_mutex;
@@ -416,6 +455,7 @@ const char *ctf_status_string(int status) {
     case CTF_ERR_CUDA: return "CTF_ERR_CUDA";
     case CTF_ERR_TIMEOUT: return "CTF_ERR_TIMEOUT";
     case CTF_ERR_CORRUPT: return "CTF_ERR_CORRUPT";
+    case CTF_ERR_BOUNDS: return "CTF_ERR_BOUNDS";
     default: return "CTF_ERR_UNKNOWN";
     }
 }
@@ -430,13 +470,30 @@ int ctf_sync_check(void *stream) {
     int *err = nullptr;
     int rc = ctf::device_error_word(&err);
     if (rc) return rc;
-    int h = 0;
-    e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    int h[4] = {0, 0, 0, 0};
+    e = cudaMemcpy(h, err, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "reading the error word");
-    if (h != 0) {
-        cudaMemset(err, 0, sizeof(int));
-        return fail(h, "a device wait gave up (status %d recorded by a kernel)", h);
+    if (h[0] != 0) {
+        cudaMemset(err, 0, sizeof(h));
+        if (h[0] == CTF_ERR_BOUNDS)
+            return fail(h[0], "index %d outside [0, %d) at %s (site %d), recorded by a kernel of the debug build",
+                        h[2], h[3], ctf::bounds_site_name(h[1]), h[1]);
+        return fail(h[0], "a device wait gave up (status %d recorded by a kernel)", h[0]);
     }
+    return CTF_OK;
+}
+
+int ctf_debug_build(void) { return ctf::kDebugBuild ? 1 : 0; }
+
+int ctf_debug_selftest_bounds(int index, void *stream) {
+    g_last_error.clear();
+    if (!ctf::kDebugBuild)
+        return fail(CTF_ERR_UNSUPPORTED, "the release library has no index checks (load libctf_debug.so)");
+    int *err = nullptr;
+    int rc = ctf::device_error_word(&err);
+    if (rc) return rc;
+    cudaError_t e = ctf::launch_bounds_selftest(index, err, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
     return CTF_OK;
 }
 

@@ -59,6 +59,7 @@ struct BatchParams {
     const int *index;             // views of this kind
     const long long *item_begin;  // nkind + 1 prefix
     int nkind;
+    int nviews;                   // entries of the view table
     long long total_items;
     int items_per_fetch;
     unsigned long long *counter;
@@ -129,11 +130,11 @@ __global__ void __launch_bounds__(kBlockWarps * 32, batch_min_blocks<ALG>()) bat
         const long long item = __shfl_sync(FULL, next, 0);
         if (item >= b.total_items) break;
         if (lane == 0) next = (long long)atomicAdd(b.counter, 1ull);
-        const int k = find_view(b.item_begin, sb, b.nkind, item);
+        const int k = ck(find_view(b.item_begin, sb, b.nkind, item), b.nkind, b.err, kBndBatch);
         if (k != cur_k) {
             // the view's parameters into this warp's shared-memory slot
             __syncwarp();
-            const uint4 *src = reinterpret_cast<const uint4 *>(&b.views[__ldg(b.index + k)].p);
+            const uint4 *src = reinterpret_cast<const uint4 *>(&b.views[ck(__ldg(b.index + k), b.nviews, b.err, kBndBatch)].p);
             uint4 *dst = reinterpret_cast<uint4 *>(&s_params[warp]);
             if (lane < (int)(sizeof(ExactParams) / 16)) dst[lane] = __ldg(src + lane);
             __syncwarp();
@@ -228,11 +229,11 @@ __global__ void __launch_bounds__(kRows, 4) batch_mlp_kernel(const BatchParams b
         for (int k = 0; k < b.items_per_fetch && ok; ++k) {
             const long long item = first + k;
             if (item >= b.total_items) break;
-            const int v = find_view(b.item_begin, sb, b.nkind, item);
+            const int v = ck(find_view(b.item_begin, sb, b.nkind, item), b.nkind, b.err, kBndBatch);
             if (v != s_view_k) {
                 // parameters of the new view into shared memory (CTA-uniform branch)
                 __syncthreads();
-                const uint4 *src = reinterpret_cast<const uint4 *>(b.views + __ldg(b.index + v));
+                const uint4 *src = reinterpret_cast<const uint4 *>(b.views + ck(__ldg(b.index + v), b.nviews, b.err, kBndBatch));
                 uint4 *dst = reinterpret_cast<uint4 *>(&s_view);
                 for (int i = threadIdx.x; i < (int)(sizeof(BatchViewDev) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
                 if (threadIdx.x == 0) s_view_k = v;
@@ -414,6 +415,7 @@ int make_plan(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t see
         p.evals = v.out_evals;
         p.stats = nullptr;
         p.tables = v.tex->tables;
+        if (int rc = device_error_word(&p.err)) return rc;
         d.learned = v.tex->mode != CTF_EVAL_BLOCK;
         if (d.learned && (r.fallback || r.tpl != 1))
             return report(CTF_ERR_UNSUPPORTED,
@@ -509,6 +511,7 @@ cudaError_t launch_plan(const Plan &plan, const DevPlan &dp, int alg, const Reso
         b.index = dp.index[k];
         b.item_begin = dp.begin[k];
         b.nkind = (int)plan.index[k].size();
+        b.nviews = (int)plan.views.size();
         b.total_items = plan.items[k];
         b.items_per_fetch = r.items_per_fetch;
         b.counter = dp.counter + k;

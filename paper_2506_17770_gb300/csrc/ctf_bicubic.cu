@@ -223,8 +223,8 @@ __global__ void __launch_bounds__(kThreads) bicubic_filter_kernel(const ExactPar
                         const uint32_t newm = __ballot_sync(FULL, inserted);
                         if (inserted) {
                             const int index = base + __popc(newm & lt);
-                            T->index[slot] = (unsigned char)index;
-                            if (index < 64) T->list[index] = key;
+                            T->index[ck(slot, 256, p.err, kBndListTable)] = (unsigned char)index;
+                            if (index < 64) T->list[ck(index, 64, p.err, kBndListTable)] = key;
                         }
                         base += __popc(newm);
                         __syncwarp();
@@ -309,11 +309,11 @@ __global__ void __launch_bounds__(kThreads) bicubic_filter_kernel(const ExactPar
                 for (int k = 0; k < 16; ++k) {
                     const int t = t00 + (k >> 2) * bw + (k & 3);
                     src[k] = mask_rank<NW>(Bw, pre, t);
-                    if (ps.active) ranks[src[k]] = t;
+                    if (ps.active) ranks[ck(src[k], 32, p.err, kBndRanks)] = t;
                 }
                 __syncwarp();
                 if (my_i < n) {
-                    const int t = ranks[my_i];
+                    const int t = ranks[ck(my_i, 32, p.err, kBndRanks)];
                     const int q = div_small(t, bw);
                     qx = minx + (t - q * bw);
                     qy = miny + q;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kThreads) bicubic_filter_kernel(const ExactPar
                         for (int probe = 0; probe < 256; ++probe) {
                             const unsigned long long kk = T->keys[h];
                             if (kk == key) {
-                                jk = T->index[h];
+                                jk = ck((int)T->index[h], 64, p.err, kBndListTable);
                                 break;
                             }
                             if (kk == kEmpty) break;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kThreads) bicubic_filter_kernel(const ExactPar
                     src[k] = jk;
                 }
                 if (my_i < n) {
-                    const unsigned long long key = T->list[my_i];
+                    const unsigned long long key = T->list[ck(my_i, 64, p.err, kBndListTable)];
                     qx = minx + (int)(uint32_t)key;
                     qy = miny + (int)(uint32_t)(key >> 32);
                 }

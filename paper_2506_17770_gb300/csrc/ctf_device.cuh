@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ctf_debug.cuh"
+
 namespace ctf {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -84,12 +86,13 @@ __device__ __forceinline__ uint32_t decode_block_texel(uint2 blk, int x, int y) 
     return r | (g << 8) | (b << 16) | 0xff000000u;
 }
 
-// Clamp-to-edge texel fetch of packed RGBA8.
+// Clamp-to-edge texel fetch of packed RGBA8 (err: the device error word of
+// the debug build's index check, or nullptr).
 __device__ __forceinline__ uint32_t fetch_block_texel(const uint2 *__restrict__ blocks, int nbx, int Wt, int Ht,
-                                                      int x, int y) {
+                                                      int x, int y, int *err = nullptr) {
     x = min(max(x, 0), Wt - 1);
     y = min(max(y, 0), Ht - 1);
-    uint2 blk = __ldg(blocks + (size_t)(y >> 2) * (size_t)nbx + (x >> 2));
+    uint2 blk = __ldg(blocks + ck((size_t)(y >> 2) * (size_t)nbx + (x >> 2), (long long)nbx * (Ht / 4), err, kBndBlock));
     return decode_block_texel(blk, x, y);
 }
 

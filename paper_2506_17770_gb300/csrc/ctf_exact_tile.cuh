@@ -26,6 +26,7 @@ __device__ __forceinline__ Inputs load_inputs(const ExactParams &p, bool inside,
     in.jac = make_float4(0.f, 0.f, 0.f, 0.f);
     in.covered = inside;
     if (inside) {
+        idx = ck(idx, view_pixels(p), p.err, kBndPixel);
         in.uv = __ldcs(p.uv + idx);
         if (kJac) in.jac = __ldcs(p.jac + idx);
         if (p.cov) in.covered = __ldcs(p.cov + idx) != 0;
@@ -38,7 +39,7 @@ __device__ __forceinline__ Inputs load_inputs(const ExactParams &p, bool inside,
 template <bool kJac>
 __device__ __forceinline__ Inputs load_inputs_any(const ExactParams &p, bool inside, uint32_t idx) {
     Inputs in;
-    const uint32_t i = inside ? idx : 0u;
+    const uint32_t i = ck(inside ? idx : 0u, view_pixels(p), p.err, kBndPixel);
     in.uv = __ldcs(p.uv + i);
     in.jac = kJac ? __ldcs(p.jac + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     in.covered = inside && (p.cov == nullptr || __ldcs(p.cov + i) != 0);
@@ -46,6 +47,7 @@ __device__ __forceinline__ Inputs load_inputs_any(const ExactParams &p, bool ins
 }
 
 __device__ __forceinline__ void store_pixel(const ExactParams &p, uint32_t idx, float4 v, uint8_t count) {
+    idx = ck(idx, view_pixels(p), p.err, kBndPixel);
     __stcs(p.out + idx, v);
     if (p.evals) p.evals[idx] = count;
 }
@@ -61,24 +63,27 @@ __device__ __forceinline__ void load_decode_tables(DecodeTables *t, const Decode
 
 // RGB of texel (x, y) of a block (alpha is 1): palette c0, c1,
 // (2c0+c1+1)/3, (c0+2c1+1)/3, 2-bit index at bits 2*(4*(y&3)+(x&3)).
-__device__ __forceinline__ float3 decode_texel_f(uint2 blk, int x, int y, const DecodeTables *T) {
+__device__ __forceinline__ float3 decode_texel_f(uint2 blk, int x, int y, const DecodeTables *T, int *err) {
     const uint32_t sel = (blk.y >> ((((uint32_t)y & 3u) << 3) | (((uint32_t)x & 3u) << 1))) & 3u;
     const uint32_t c0 = blk.x & 0xffffu, c1 = blk.x >> 16;
-    const uint32_t e0 = T->rg[c0 >> 5] | T->b[c0 & 31u];
-    const uint32_t e1 = T->rg[c1 >> 5] | T->b[c1 & 31u];
+    const uint32_t e0 = T->rg[ck(c0 >> 5, 2048, err, kBndDecodeTable)] | T->b[ck(c0 & 31u, 32, err, kBndDecodeTable)];
+    const uint32_t e1 = T->rg[ck(c1 >> 5, 2048, err, kBndDecodeTable)] | T->b[ck(c1 & 31u, 32, err, kBndDecodeTable)];
     const bool odd = (sel & 1u) != 0, mid = (sel & 2u) != 0;
     const uint32_t a = odd ? e1 : e0, b = odd ? e0 : e1;
     // per field 2a + b + 1 + 256 <= 1022: no carry between the fields
     const uint32_t v = mid ? (2u * a + b + 0x10140501u) : a;
-    return make_float3(T->val[v & 0x3ffu], T->val[(v >> 10) & 0x3ffu], T->val[v >> 20]);
+    return make_float3(T->val[ck(v & 0x3ffu, 1024, err, kBndDecodeTable)],
+                       T->val[ck((v >> 10) & 0x3ffu, 1024, err, kBndDecodeTable)],
+                       T->val[ck(v >> 20, 1024, err, kBndDecodeTable)]);
 }
 
 // Clamp-to-edge fetch and decode of texel (x, y).
 __device__ __forceinline__ float3 fetch_decode(const ExactParams &p, int x, int y, const DecodeTables *T) {
     x = min(max(x, 0), p.Wt - 1);
     y = min(max(y, 0), p.Ht - 1);
-    const uint2 blk = __ldg(p.blocks + (uint32_t)(y >> 2) * (uint32_t)p.nbx + (uint32_t)(x >> 2));
-    return decode_texel_f(blk, x, y, T);
+    const uint2 blk = __ldg(p.blocks + ck((uint32_t)(y >> 2) * (uint32_t)p.nbx + (uint32_t)(x >> 2),
+                                          texture_blocks(p), p.err, kBndBlock));
+    return decode_texel_f(blk, x, y, T, p.err);
 }
 
 // acc = fma(w_k, p_k, acc) from 0, k = 0..3; alpha of every block texel is
@@ -177,6 +182,7 @@ struct FallbackArgs {
     int y0;  // row of the whole view at which the frame starts
     uint32_t k0, k1;
     int mode;
+    int *err;  // device error word (index checks of the debug build)
 };
 
 // Which texel a lane of an over-budget tile produces under fallback C
@@ -346,8 +352,9 @@ __device__ __noinline__ FallbackOut fallback_blend(const FallbackArgs fa, int ul
     float3 val;
     {
         const int x = min(max(c.produce ? c.qx : ulx, 0), fa.Wt - 1), y = min(max(c.produce ? c.qy : uly, 0), fa.Ht - 1);
-        const uint2 blk = __ldg(fa.blocks + (uint32_t)(y >> 2) * (uint32_t)fa.nbx + (uint32_t)(x >> 2));
-        val = decode_texel_f(blk, x, y, tabs);
+        const uint2 blk = __ldg(fa.blocks + ck((uint32_t)(y >> 2) * (uint32_t)fa.nbx + (uint32_t)(x >> 2),
+                                               (long long)fa.nbx * (fa.Ht / 4), fa.err, kBndBlock));
+        val = decode_texel_f(blk, x, y, tabs, fa.err);
     }
     return fb_blend<true>(make_float4(val.x, val.y, val.z, 1.0f), c, ulx, uly, s, t, active, lane, tab);
 }
@@ -418,6 +425,7 @@ __device__ __forceinline__ void filter_tile(const ExactParams &p, const Inputs &
             fa.k0 = p.k0;
             fa.k1 = p.k1;
             fa.mode = p.fallback;
+            fa.err = p.err;
             const FallbackOut fo =
                 fallback_blend(fa, ps.ulx, ps.uly, ps.s, ps.t, ps.active, px, py, sel.A, lane, lt, tabs, fbtab);
             if (kStats) {  // select_tile counted one evaluation per active lane

@@ -78,7 +78,13 @@ struct __align__(16) ExactParams {
     float4 *out;
     uint8_t *evals;       // nullable
     unsigned long long *stats;  // kNumStats counters or nullptr
+    int *err;             // device error word (index checks of the debug build)
 };
+
+// Pixels of the view and blocks of the texture: the bounds of the debug
+// build's index checks.
+__host__ __device__ inline long long view_pixels(const ExactParams &p) { return (long long)p.W * p.H; }
+__host__ __device__ inline long long texture_blocks(const ExactParams &p) { return (long long)p.nbx * (p.Ht / 4); }
 
 // Launch the exact-decode filter.  alg: ctf_algorithm; tile_w in {4, 8, 16};
 // mask_dim in {11, 16}.  Returns cudaSuccess or the launch error.
@@ -105,6 +111,11 @@ cudaError_t prepare_mlp_filter(int alg, int tile_w, int mask_dim);
 
 // One CTA whose bounded mbarrier wait runs out and records CTF_ERR_TIMEOUT.
 cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t stream);
+// One thread reads element `index` of a 32-int shared array through the
+// debug build's index check (ctf_api.cu).
+cudaError_t launch_bounds_selftest(int index, int *err, cudaStream_t stream);
+// Name of a BoundsSite (ctf_debug.cuh) for error messages.
+const char *bounds_site_name(int site);
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                               cudaStream_t stream);
 MlpDevice mlp_device_view(const ctf_texture_s *t);

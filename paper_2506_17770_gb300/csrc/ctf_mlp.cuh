@@ -53,6 +53,7 @@ struct MlpDevice {
     float sx[2], sy[2];    // grid texels per texture texel
     const uint4 *img;      // operand image (kImgBytes)
     int fp8;               // 0: FP16 operands, 1: E4M3 operands
+    int *err;              // device error word (index checks of the debug build)
 };
 
 }  // namespace ctf

@@ -101,10 +101,11 @@ __device__ __forceinline__ void texel_features(const MlpDevice &m, int x, int y,
         const int xa = min(max(x0, 0), m.gw[g] - 1), xb = min(max(x0 + 1, 0), m.gw[g] - 1);
         const int ya = min(max(y0, 0), m.gh[g] - 1), yb = min(max(y0 + 1, 0), m.gh[g] - 1);
         const uint4 *L = reinterpret_cast<const uint4 *>(m.lat[g]);
-        const uint4 q00 = __ldg(L + (size_t)ya * m.gw[g] + xa);
-        const uint4 q10 = __ldg(L + (size_t)ya * m.gw[g] + xb);
-        const uint4 q01 = __ldg(L + (size_t)yb * m.gw[g] + xa);
-        const uint4 q11 = __ldg(L + (size_t)yb * m.gw[g] + xb);
+        const long long cells = (long long)m.gw[g] * m.gh[g];
+        const uint4 q00 = __ldg(L + ck((size_t)ya * m.gw[g] + xa, cells, m.err, kBndLatent));
+        const uint4 q10 = __ldg(L + ck((size_t)ya * m.gw[g] + xb, cells, m.err, kBndLatent));
+        const uint4 q01 = __ldg(L + ck((size_t)yb * m.gw[g] + xa, cells, m.err, kBndLatent));
+        const uint4 q11 = __ldg(L + ck((size_t)yb * m.gw[g] + xb, cells, m.err, kBndLatent));
         const float ofx = __fsub_rn(1.f, fx), ofy = __fsub_rn(1.f, fy);
         const float w00 = __fmul_rn(ofx, ofy), w10 = __fmul_rn(fx, ofy), w01 = __fmul_rn(ofx, fy),
                     w11 = __fmul_rn(fx, fy);
@@ -396,7 +397,8 @@ __device__ __forceinline__ bool mlp_warp_tile(const ExactParams &p, const MlpDev
     const int by = valid ? (int)(t32 / tiles_x) : 0, bx = valid ? (int)(t32 - (uint32_t)by * tiles_x) : 0;
     const int px = bx * TW + tx, py = by * TH + ty;
     const bool inside = valid && px < p.W && py < p.H;
-    const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
+    const uint32_t idx = ck(inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u, view_pixels(p), p.err,
+                            kBndPixel);
     PixelSetup ps;
     float2 uv = make_float2(0.f, 0.f);
     float4 jac = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -551,7 +553,8 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
         if (valid) tile_pos(tp, g, bx, by);
         const int px = bx * TW + tx, py = by * TH + ty;
         const bool inside = valid && px < p.W && py < p.H;
-        const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
+        const uint32_t idx = ck(inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u, view_pixels(p), p.err,
+                                kBndPixel);
         float2 uv = make_float2(0.f, 0.f);
         float4 jac = make_float4(0.f, 0.f, 0.f, 0.f);
         bool covered = inside;
@@ -574,7 +577,7 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
             sel.my_rank = 0;
         }
         if (sel.produce)
-            texlist[32 * g + sel.my_rank] =
+            texlist[32 * g + ck(sel.my_rank, 32, p.err, kBndTexList)] =
                 make_int2(min(max(sel.tx, 0), p.Wt - 1), min(max(sel.ty, 0), p.Ht - 1));
         const bool succ = sel.path == PATH_SUCCESS;
         if (lane == 0) count[g] = succ ? sel.n : __popc(sel.A);
@@ -641,7 +644,7 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             if (won[c]) {
-                const int row = atomicAdd(nuniq, 1);
+                const int row = ck(atomicAdd(nuniq, 1), 2 * kRows, p.err, kBndRow);
                 hrow[slot[c]] = (unsigned char)row;
                 uxy[row] = t2[c];
             }
@@ -677,7 +680,7 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
                         b = start[k];
                     }
                 }
-                xy[c] = texlist[32 * g + (row - b)];
+                xy[c] = texlist[32 * g + ck(row - b, 32, p.err, kBndTexList)];
             }
         }
     }
@@ -699,7 +702,7 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
         }
         float4 v;
         if (!mlp_chain(ch, m.fp8, v, err)) return false;
-        outrow[row] = v;
+        outrow[ck(row, 2 * kRows, p.err, kBndRow)] = v;
     }
     __syncthreads();
 
@@ -711,11 +714,14 @@ __device__ __forceinline__ bool mlp_group(const ExactParams &p, const MlpDevice 
         if (!((info >> 24) & 1u)) continue;  // outside the frame (or no tile)
         int bx, by;
         tile_pos(tp, g, bx, by);
-        const uint32_t idx = (uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx);
+        const uint32_t idx =
+            ck((uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx), view_pixels(p), p.err, kBndPixel);
         const int b = h == 0 ? my_base[0] : my_base[1];
         const bool dedup = p.group_dedup != 0;
         // row of list entry i of this tile
-        auto row_of = [&](uint32_t i) { return dedup ? (int)rowmap[32 * g + (int)i] : b + (int)i; };
+        auto row_of = [&](uint32_t i) {
+            return ck(dedup ? (int)rowmap[32 * g + (int)i] : b + (int)i, 2 * kRows, p.err, kBndRow);
+        };
         float4 result = make_float4(0.f, 0.f, 0.f, 0.f);
         uint8_t cv = 0;
         if ((info >> 23) & 1u) {

@@ -39,10 +39,14 @@
 namespace ctf {
 namespace {
 
-// The warps' fallback tables reuse the packed-group buffers of the chain's
-// layout (this kernel has no packed groups).
+// The warps' fallback tables and rank slots reuse the packed-group buffers
+// of the chain's layout (this kernel has no packed groups).  With two texels
+// per lane a Mask tile may hold up to 64 texels, so each warp has 64 rank
+// slots (the chain layout's own rank slots hold 32).
 constexpr int kSmFb = kSmPixST;
-static_assert(kSmFb + 4 * (int)sizeof(FbTable) <= kSmCount, "fallback tables inside the group buffers");
+constexpr int kSmExtRanks = kSmFb + 4 * (int)sizeof(FbTable);  // 4 warps x 64 ints
+static_assert(kSmExtRanks % 16 == 0 && kSmExtRanks + 4 * 64 * 4 <= kSmCount,
+              "fallback tables and rank slots inside the group buffers");
 
 template <int ALG, int TW, int MD>
 __device__ __forceinline__ bool ext_warp_tile(const ExactParams &p, const MlpDevice &m, Chain &ch, long long tile,
@@ -56,7 +60,8 @@ __device__ __forceinline__ bool ext_warp_tile(const ExactParams &p, const MlpDev
     const int by = valid ? (int)(t32 / tiles_x) : 0, bx = valid ? (int)(t32 - (uint32_t)by * tiles_x) : 0;
     const int px = bx * TW + tx, py = by * TH + ty;
     const bool inside = valid && px < p.W && py < p.H;
-    const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
+    const uint32_t idx = ck(inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u, view_pixels(p), p.err,
+                            kBndPixel);
     float2 uv = make_float2(0.f, 0.f);
     float4 jac = make_float4(0.f, 0.f, 0.f, 0.f);
     bool covered = inside;
@@ -128,8 +133,9 @@ __device__ __forceinline__ bool ext_warp_tile(const ExactParams &p, const MlpDev
         float4 tap[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int l = sel.src[k] & 31;
-            const bool r = sel.src[k] >= 32;
+            const int sk = sel.src[k];  // lane + 32 x round (checked in select_tile)
+            const int l = sk & 31;
+            const bool r = sk >= 32;
             const float ax = __shfl_sync(FULL, val0.x, l), bx1 = __shfl_sync(FULL, val1.x, l);
             const float ay = __shfl_sync(FULL, val0.y, l), by1 = __shfl_sync(FULL, val1.y, l);
             const float az = __shfl_sync(FULL, val0.z, l), bz1 = __shfl_sync(FULL, val1.z, l);
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(kRows, 3) mlp_filter_ext_kernel(const ExactPar
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ListTable *T = reinterpret_cast<ListTable *>(sm + kSmList) + warp;
     FbTable *fbt = reinterpret_cast<FbTable *>(sm + kSmFb) + warp;
-    int *ranks = reinterpret_cast<int *>(sm + kSmRanks) + 32 * warp;
+    int *ranks = reinterpret_cast<int *>(sm + kSmExtRanks) + 64 * warp;
     if (ALG == ALG_LIST) {
 #pragma unroll
         for (int s = 0; s < 8; ++s) T->keys[lane * 8 + s] = kEmpty;

@@ -102,6 +102,8 @@ MlpDevice mlp_device_view(const ctf_texture_s *t) {
     }
     m.img = static_cast<const uint4 *>(t->img);
     m.fp8 = t->mode == CTF_EVAL_MLP_FP8 ? 1 : 0;
+    m.err = nullptr;
+    if (device_error_word(&m.err) != CTF_OK) m.err = nullptr;  // the index checks then only clamp
     return m;
 }
 

@@ -266,7 +266,8 @@ __device__ __forceinline__ void ws_step1(const ExactParams &p, long long first, 
     if (valid) tile_pos(tile_pos0(p, first), g, bx, by);
     const int px = bx * TW + tx, py = by * TH + ty;
     const bool inside = valid && px < p.W && py < p.H;
-    const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
+    const uint32_t idx = ck(inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u, view_pixels(p), p.err,
+                            kBndPixel);
     float2 uv = make_float2(0.f, 0.f);
     float4 jac = make_float4(0.f, 0.f, 0.f, 0.f);
     bool covered = inside;
@@ -289,7 +290,8 @@ __device__ __forceinline__ void ws_step1(const ExactParams &p, long long first, 
         sel.my_rank = 0;
     }
     if (sel.produce)
-        texlist[32 * g + sel.my_rank] = make_int2(min(max(sel.tx, 0), p.Wt - 1), min(max(sel.ty, 0), p.Ht - 1));
+        texlist[32 * g + ck(sel.my_rank, 32, p.err, kBndTexList)] =
+            make_int2(min(max(sel.tx, 0), p.Wt - 1), min(max(sel.ty, 0), p.Ht - 1));
     const bool succ = sel.path == PATH_SUCCESS;
     if (lane == 0) count[g] = succ ? sel.n : __popc(sel.A);
     uint32_t info = 0;
@@ -318,10 +320,11 @@ __device__ __forceinline__ void ws_gather(const ExactParams &p, long long first,
     // already belong to a later group)
     const int base = reinterpret_cast<const int *>(st + kWsBase)[g];
     const unsigned char *rowmap = st + kWsRowMap + 32 * g;
-    auto row_of = [&](uint32_t i) { return dedup ? (int)rowmap[i] : base + (int)i; };
+    auto row_of = [&](uint32_t i) { return ck(dedup ? (int)rowmap[i] : base + (int)i, 2 * kRows, p.err, kBndRow); };
     int bx, by;
     tile_pos(tile_pos0(p, first), g, bx, by);
-    const uint32_t idx = (uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx);
+    const uint32_t idx =
+        ck((uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx), view_pixels(p), p.err, kBndPixel);
     float4 result = make_float4(0.f, 0.f, 0.f, 0.f);
     uint8_t cv = 0;
     if ((info >> 23) & 1u) {
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(kWsThreads, 4) mlp_filter_ws_kernel(const Exac
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     if (won[c]) {
-                        const int row = atomicAdd(nuniq, 1);
+                        const int row = ck(atomicAdd(nuniq, 1), 2 * kRows, p.err, kBndRow);
                         hrow[slot[c]] = (unsigned char)row;
                         texlist[row] = t2[c];  // the distinct texels reuse the list space
                     }
@@ -476,7 +479,7 @@ __global__ void __launch_bounds__(kWsThreads, 4) mlp_filter_ws_kernel(const Exac
                         int b = start[0];
 #pragma unroll
                         for (int k = 1; k < kGroupTiles; ++k) b = k == g ? start[k] : b;
-                        xy[c] = texlist[32 * g + (row - b)];
+                        xy[c] = texlist[32 * g + ck(row - b, 32, p.err, kBndTexList)];
                     }
                 }
                 if (tid < kGroupTiles) reinterpret_cast<int *>(st + kWsBase)[tid] = start[tid];
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(kWsThreads, 4) mlp_filter_ws_kernel(const Exac
                 }
                 float4 v;
                 ok = ws_chain(ch, m.fp8, v, err);
-                if (ok) outrow[row] = v;
+                if (ok) outrow[ck(row, 2 * kRows, p.err, kBndRow)] = v;
             }
             if (!ok) break;
             cons_sync();  // every row value is written

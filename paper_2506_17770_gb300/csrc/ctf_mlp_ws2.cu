@@ -288,7 +288,8 @@ __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp,
     if (valid) tile_pos(tp, g, bx, by);
     const int px = bx * TW + tx, py = by * TH + ty;
     const bool inside = valid && px < p.W && py < p.H;
-    const uint32_t idx = inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u;
+    const uint32_t idx = ck(inside ? (uint32_t)py * (uint32_t)p.W + (uint32_t)px : 0u, view_pixels(p), p.err,
+                            kBndPixel);
     float2 uv = make_float2(0.f, 0.f);
     float4 jac = make_float4(0.f, 0.f, 0.f, 0.f);
     bool covered = inside;
@@ -311,7 +312,8 @@ __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp,
         sel.my_rank = 0;
     }
     if (sel.produce)
-        list[32 * g + sel.my_rank] = make_int2(min(max(sel.tx, 0), p.Wt - 1), min(max(sel.ty, 0), p.Ht - 1));
+        list[32 * g + ck(sel.my_rank, 32, p.err, kBndTexList)] =
+            make_int2(min(max(sel.tx, 0), p.Wt - 1), min(max(sel.ty, 0), p.Ht - 1));
     const bool succ = sel.path == PATH_SUCCESS;
     const int n = succ ? sel.n : __popc(sel.A);
     if (lane == 0) reinterpret_cast<int *>(st + kPCount)[g] = n;
@@ -334,10 +336,14 @@ __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp
     const int tx = lane % TW, ty = lane / TW;
     const uint32_t info = reinterpret_cast<const uint32_t *>(st + kPInfo)[32 * g + lane];
     if (!((info >> 24) & 1u)) return;  // outside the frame (or no tile)
-    const float4 *outrow = reinterpret_cast<const float4 *>(st + kPX) + reinterpret_cast<const int *>(st + kPBase)[g];
+    const float4 *outrow = reinterpret_cast<const float4 *>(st + kPX);
+    const int base = reinterpret_cast<const int *>(st + kPBase)[g];
+    // row of list entry i of this tile (the row values fill the stage's first 4 KB: 256 rows)
+    auto row_of = [&](uint32_t i) { return ck(base + (int)i, 2 * kRows, p.err, kBndRow); };
     int bx, by;
     tile_pos(tp, g, bx, by);
-    const uint32_t idx = (uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx);
+    const uint32_t idx =
+        ck((uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx), view_pixels(p), p.err, kBndPixel);
     float4 result = make_float4(0.f, 0.f, 0.f, 0.f);
     uint8_t cv = 0;
     if ((info >> 23) & 1u) {
@@ -348,7 +354,7 @@ __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp
             float2 rg = make_float2(0.f, 0.f), ba = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float4 t = outrow[(info >> (5 * k)) & 31u];
+                const float4 t = outrow[row_of((info >> (5 * k)) & 31u)];
                 const float2 wk = make_float2(w[k], w[k]);
                 rg = __ffma2_rn(wk, make_float2(t.x, t.y), rg);
                 ba = __ffma2_rn(wk, make_float2(t.z, t.w), ba);
@@ -356,7 +362,7 @@ __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp
             result = make_float4(rg.x, rg.y, ba.x, ba.y);
             cv = (uint8_t)((info >> 20) & 7u);
         } else {
-            result = outrow[info & 31u];
+            result = outrow[row_of(info & 31u)];
             cv = 1;
         }
     }
@@ -430,7 +436,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 // chain c's outputs overwrite operand rows of chain 0, which its
                 // layer-1 MMA has read; chain 1's operand rows (bytes 4096 on)
                 // are untouched
-                if (ok && live) outrow[kRows * c + tid] = v;
+                if (ok && live) outrow[ck(kRows * c + tid, 2 * kRows, p.err, kBndRow)] = v;
                 cons_bar();
             }
             if (!ok) break;
@@ -491,10 +497,11 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 for (int c = 0; c < kPFeatRounds; ++c) {
                     const int row = pt + kPProducerThreads * c;
                     if (row >= R) break;
-                    const int2 t = c == 0 ? list[32 * g0 + (row - b0)] : list[32 * g1 + (row - b1)];
+                    const int2 t = c == 0 ? list[32 * g0 + ck(row - b0, 32, p.err, kBndTexList)]
+                                          : list[32 * g1 + ck(row - b1, 32, p.err, kBndTexList)];
                     float f[kMlpIn];
                     texel_features(m, t.x, t.y, f);
-                    store_x_row_at(st + kPX, row, f, fp8, inv_a1);
+                    store_x_row_at(st + kPX, ck(row, 2 * kRows, p.err, kBndRow), f, fp8, inv_a1);
                 }
                 tc::fence_proxy_async();  // generic-proxy writes -> the MMAs' async proxy
                 __syncwarp();

@@ -105,6 +105,7 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                                                  int px, int py, int lane, uint32_t lt, ListTable *T, int *ranks,
                                                  Counters &cnt) {
     constexpr int NW = (MD * MD + 31) / 32;
+    constexpr int kRanksN = kTwo ? 64 : 32;  // rank slots the caller provides
     const float fW = (float)p.Wt, fH = (float)p.Ht;
     Selection sel;
     sel.A = __ballot_sync(FULL, ps.active);
@@ -204,8 +205,8 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                     const uint32_t newm = __ballot_sync(FULL, inserted);
                     if (inserted) {
                         const int index = base + __popc(newm & lt);
-                        T->index[slot] = (unsigned char)index;
-                        if (index < 64) T->list[index] = key;
+                        T->index[ck(slot, 256, p.err, kBndListTable)] = (unsigned char)index;
+                        if (index < 64) T->list[ck(index, 64, p.err, kBndListTable)] = key;
                     }
                     base += __popc(newm);
                     __syncwarp();
@@ -297,14 +298,14 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                 j[1] = j[0] + 1;
                 j[3] = j[2] + 1;
                 if (ps.active) {
-                    ranks[j[0]] = t00;
-                    ranks[j[1]] = t00 + 1;
-                    ranks[j[2]] = t01;
-                    ranks[j[3]] = t01 + 1;
+                    ranks[ck(j[0], kRanksN, p.err, kBndRanks)] = t00;
+                    ranks[ck(j[1], kRanksN, p.err, kBndRanks)] = t00 + 1;
+                    ranks[ck(j[2], kRanksN, p.err, kBndRanks)] = t01;
+                    ranks[ck(j[3], kRanksN, p.err, kBndRanks)] = t01 + 1;
                 }
                 __syncwarp();
-                pos0 = lane < n ? ranks[lane] : -1;
-                pos1 = lane + 32 < n ? ranks[lane + 32] : -1;
+                pos0 = lane < n ? ranks[ck(lane, kRanksN, p.err, kBndRanks)] : -1;
+                pos1 = lane + 32 < n ? ranks[ck(lane + 32, kRanksN, p.err, kBndRanks)] : -1;
                 __syncwarp();
             } else {  // List Merge: list indices of the taps, list order
 #pragma unroll
@@ -317,7 +318,7 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                         for (int probe = 0; probe < 256; ++probe) {
                             const unsigned long long kk = T->keys[h];
                             if (kk == key) {
-                                j[k] = T->index[h];
+                                j[k] = ck((int)T->index[h], 64, p.err, kBndListTable);
                                 break;
                             }
                             if (kk == kEmpty) break;
@@ -326,13 +327,13 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                     }
                 }
                 if (lane < n) {
-                    const unsigned long long key = T->list[lane];
+                    const unsigned long long key = T->list[ck(lane, 64, p.err, kBndListTable)];
                     sel.produce = true;
                     sel.tx = minx + (int)(uint32_t)key;
                     sel.ty = miny + (int)(uint32_t)(key >> 32);
                 }
                 if (lane + 32 < n) {
-                    const unsigned long long key = T->list[lane + 32];
+                    const unsigned long long key = T->list[ck(lane + 32, 64, p.err, kBndListTable)];
                     sel.produce2 = true;
                     sel.tx2 = minx + (int)(uint32_t)key;
                     sel.ty2 = miny + (int)(uint32_t)(key >> 32);
@@ -354,8 +355,10 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                     sel.ty2 = miny + q;
                 }
             }
+            // lane + 32 x round; inactive pixels carry arbitrary indices, whose
+            // shuffled values they drop
 #pragma unroll
-            for (int k = 0; k < 4; ++k) sel.src[k] = j[k];
+            for (int k = 0; k < 4; ++k) sel.src[k] = ps.active ? ck(j[k], 64, p.err, kBndLane) : j[k];
             if (ALG == ALG_LIST) {
                 __syncwarp();
 #pragma unroll
@@ -413,13 +416,14 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                 // larger masks are filled by the pixels, each at the ranks of
                 // its taps.
                 if (mcls == 2) {
-                    if ((Bw[0] >> lane) & 1u) ranks[__popc(Bw[0] & lt)] = lane;
-                    if ((Bw[1] >> lane) & 1u) ranks[pre[1] + __popc(Bw[1] & lt)] = lane + 32;
+                    if ((Bw[0] >> lane) & 1u) ranks[ck(__popc(Bw[0] & lt), kRanksN, p.err, kBndRanks)] = lane;
+                    if ((Bw[1] >> lane) & 1u)
+                        ranks[ck(pre[1] + __popc(Bw[1] & lt), kRanksN, p.err, kBndRanks)] = lane + 32;
                 } else if (ps.active) {
-                    ranks[j[0]] = t00;
-                    ranks[j[1]] = t00 + 1;
-                    ranks[j[2]] = t01;
-                    ranks[j[3]] = t01 + 1;
+                    ranks[ck(j[0], kRanksN, p.err, kBndRanks)] = t00;
+                    ranks[ck(j[1], kRanksN, p.err, kBndRanks)] = t00 + 1;
+                    ranks[ck(j[2], kRanksN, p.err, kBndRanks)] = t01;
+                    ranks[ck(j[3], kRanksN, p.err, kBndRanks)] = t01 + 1;
                 }
                 __syncwarp();
             } else {
@@ -433,7 +437,7 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                         for (int probe = 0; probe < 256; ++probe) {
                             const unsigned long long kk = T->keys[h];
                             if (kk == key) {
-                                j[k] = T->index[h];
+                                j[k] = ck((int)T->index[h], 64, p.err, kBndListTable);
                                 break;
                             }
                             if (kk == kEmpty) break;
@@ -445,12 +449,12 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
             if (my_i < n) {
                 int x, y;
                 if (ALG == ALG_MASK) {
-                    const int t = ranks[my_i];  // bit position dy * bw + dx
+                    const int t = ranks[ck(my_i, kRanksN, p.err, kBndRanks)];  // bit position dy * bw + dx
                     const int q = div_small(t, bw);
                     x = minx + (t - q * bw);
                     y = miny + q;
                 } else {
-                    const unsigned long long key = T->list[my_i];
+                    const unsigned long long key = T->list[ck(my_i, 64, p.err, kBndListTable)];
                     x = minx + (int)(uint32_t)key;
                     y = miny + (int)(uint32_t)(key >> 32);
                 }
@@ -467,8 +471,9 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                 for (int k = 0; k < 4; ++k) j[k] = nth_set_lane(A, j[k]);
             }
         }
+        // (inactive pixels carry arbitrary lanes, whose shuffled values they drop)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sel.src[k] = j[k];
+        for (int k = 0; k < 4; ++k) sel.src[k] = ps.active ? ck(j[k], 32, p.err, kBndLane) : j[k];
     }
     if (ALG == ALG_LIST) {
         __syncwarp();

@@ -216,10 +216,11 @@ __device__ __forceinline__ void bilinear_taps(const GradParams &g, int grid, int
     const int x0 = (int)fx0, y0 = (int)fy0;
     const int xa = min(max(x0, 0), gw - 1), xb = min(max(x0 + 1, 0), gw - 1);
     const int ya = min(max(y0, 0), gh - 1), yb = min(max(y0 + 1, 0), gh - 1);
-    idx[0] = ya * gw + xa;
-    idx[1] = ya * gw + xb;
-    idx[2] = yb * gw + xa;
-    idx[3] = yb * gw + xb;
+    const long long cells = (long long)gw * gh;
+    idx[0] = ck(ya * gw + xa, cells, g.err, kBndLatent);
+    idx[1] = ck(ya * gw + xb, cells, g.err, kBndLatent);
+    idx[2] = ck(yb * gw + xa, cells, g.err, kBndLatent);
+    idx[3] = ck(yb * gw + xb, cells, g.err, kBndLatent);
     const float ofx = __fsub_rn(1.f, fx), ofy = __fsub_rn(1.f, fy);
     w[0] = __fmul_rn(ofx, ofy);
     w[1] = __fmul_rn(fx, ofy);
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kT, 2) grad_kernel(const GradParams g) {
         // ---- the texel of row tid, its features and its target
         int x, y;
         if (g.xy) {
-            const int2 c = valid ? g.xy[i] : make_int2(0, 0);
+            const int2 c = valid ? g.xy[ck(i, g.n, g.err, kBndTrain)] : make_int2(0, 0);
             x = min(max(c.x, 0), g.Wt - 1);
             y = min(max(c.y, 0), g.Ht - 1);
         } else {
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(kT, 2) grad_kernel(const GradParams g) {
         }
         float tgt[4];
         {
-            const uint32_t px = fetch_block_texel(g.blocks, g.nbx, g.Wt, g.Ht, x, y);
+            const uint32_t px = fetch_block_texel(g.blocks, g.nbx, g.Wt, g.Ht, x, y, g.err);
 #pragma unroll
             for (int c = 0; c < 4; ++c) tgt[c] = __fdiv_rn((float)((px >> (8 * c)) & 0xffu), 255.f);
         }
@@ -518,7 +519,7 @@ __global__ void __launch_bounds__(kT, 2) grad_kernel(const GradParams g) {
     // stored as this CTA's partial sums (reduce_kernel adds the CTAs' up in
     // CTA order: no atomics on the few thousand weight entries)
     if (ok) {
-        float *W = g.partial + (size_t)blockIdx.x * kWeights;
+        float *W = g.partial + (size_t)ck((int)blockIdx.x, kMaxGradCtas, g.err, kBndTrain) * kWeights;
         const int m = tid;
 #pragma unroll 1
         for (int q = 0; q < 6; ++q) {

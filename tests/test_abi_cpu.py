@@ -146,3 +146,32 @@ def test_allocation_hook_checks_its_arguments_without_gpu(lib):
     _ctf.ctf_debug_fail_allocations(0)
     assert _ctf.ctf_debug_device_allocations() >= 0
     assert _ctf.ctf_debug_live_allocations() >= 0
+
+
+def test_debug_build_exports_the_same_entry_points_without_gpu(lib):
+    """The debug library (index checks in every kernel) builds from the same
+    sources, exports every declared function and says which build it is;
+    the release library refuses the bounds self-test before any CUDA call."""
+    from paper_2506_17770_gb300 import _ctf, build
+    dbg = ctypes.CDLL(build.build(debug=True))
+    missing = [n for n in _declared_functions() if not hasattr(dbg, n)]
+    assert not missing, missing
+    assert dbg.ctf_debug_build() == 1
+    assert lib.ctf_debug_build() == 0
+    assert _ctf.ctf_status_string(_ctf.CTF_ERR_BOUNDS) == "CTF_ERR_BOUNDS"
+    with pytest.raises(_ctf.CtfError) as ei:
+        _ctf.ctf_debug_selftest_bounds(40)
+    assert ei.value.status == _ctf.CTF_ERR_UNSUPPORTED
+
+
+def test_debug_index_checks_cover_the_kernels_sources():
+    """Every translation unit with kernels that index texels, pixels or
+    shared tables goes through the debug build's check (ck) somewhere, and
+    the release definition of ck is the index itself."""
+    csrc = os.path.join(ROOT, "paper_2506_17770_gb300", "csrc")
+    for name in ("ctf_exact_tile.cuh", "ctf_select.cuh", "ctf_mlp_chain.cuh", "ctf_mlp_ws2.cu", "ctf_mlp_ext.cu",
+                 "ctf_bicubic.cu", "ctf_batch.cu", "ctf_train.cu", "ctf_device.cuh"):
+        assert "ck(" in open(os.path.join(csrc, name)).read(), name
+    dbg = open(os.path.join(csrc, "ctf_debug.cuh")).read()
+    release = dbg[dbg.index("#else"):dbg.index("#endif")]
+    assert "return i;" in release and "atomic" not in release

@@ -399,6 +399,31 @@ def test_learned_two_texels_per_lane_equal_learned_4tap_on_success(tex64):
     assert checked > 100 and st["tiles_success"] == checked
 
 
+@pytest.mark.parametrize("md", [16, 11])
+def test_learned_two_texels_per_lane_on_rotated_quads(tex64, md):
+    """Two texels per lane on head-on quads rotated by 0..90 degrees just
+    above magnification 1 (Sec. 5): Mask tiles of up to 54 texels whose
+    bounding boxes span more than 64 positions, so the texel ranks 32..63
+    (the second round) are in use.  Counts and statistics equal the FP64
+    oracle's, the pixels lie within the decode bound, and every tile
+    succeeds."""
+    q = synth.rotated_quad_tiles(1.001, np.arange(0, 91, 3.0), 8, Wt=64, Ht=64)
+    # the quads sit near texel 1024; move them to the middle of the 64^2 texture
+    uv = (q.uv.astype(np.float64) - 996.0 / 64.0).astype(np.float32)
+    jac = q.jac.astype(np.float32)
+    opts = {"texels_per_lane": 2, "budget": 64, "mask_dim": md}
+    out, ev, st = gpu_filter(tex64, uv, jac, None, "mask", opts)
+    ref, ref_ev, ref_st = oracle.filter_frame_learned_f64(tex64.mlp, 64, 64, uv, jac, None, alg=ALGS["mask"], seed=0,
+                                                          budget=64, mask_dim=md, texels_per_lane=2)
+    np.testing.assert_array_equal(ev, ref_ev)
+    assert st == ref_st
+    assert st["tiles_success"] == st["tiles_total"]
+    per_tile = ev.reshape(-1, 4, 8).sum(axis=(1, 2))
+    assert per_tile.max() > 32 and np.count_nonzero(per_tile > 32) >= 20
+    err = np.abs(out - ref)
+    assert np.all(err <= _pixel_bounds(tex64, uv)), err.max()
+
+
 def test_learned_extensions_refuse_group_dedup(tex64):
     uv, jac, cov = _scene(37, 21, 12)
     with pytest.raises(_ctf.CtfError) as ei:
