@@ -8,27 +8,32 @@
 //     runs step 1 of the collaborative flow (Sec. 3) on its tiles, packs the
 //     texel lists of the group into consecutive rows (tile order, list order
 //     within a tile), and writes the features of its own rows straight into
-//     the group's layer-1 operand buffer in the tensor cores' layout; later
-//     it gathers, filters and stores the group's pixels from the row values;
+//     the group's layer-1 operand buffer in the tensor cores' layout;
 //   - warpgroup 0 (warps 0-3, the consumer) owns the 128 TMEM lanes and runs
 //     the tcgen05 MLP chain(s) over the group's rows: three MMA layers, the
 //     two hidden epilogues (bias, ReLU, conversion to the next operand) and
-//     the output epilogue into the row values.
+//     the output epilogue into the row values; then it gathers, filters and
+//     stores the group's pixels from the row values (warp w the tiles w and
+//     4 + w).
 // One consumer thread issues the MMAs and polls their barrier; the other
 // consumer threads wait at a named barrier (no polling).  Warps whose 32
-// rows all lie past the group's last row skip their epilogues.
-// Two stages of group buffers (operand rows, whose first 4 KB the row values
-// overwrite once the rows have been consumed, per-pixel words, counts and
-// first rows) alternate between consecutive groups.  The producers hand a
-// stage over with a full barrier (four arrivals) and get it back with a done
-// barrier (one arrival); a named barrier among the producers at the start
-// of each group orders their own reuse of a stage.  Every wait is bounded; a
-// wait that gives up records CTF_ERR_TIMEOUT and both roles leave.
-// The CTA starts with 64 registers per thread; setmaxnreg gives the
+// rows all lie past the group's last row skip their epilogues.  The hidden
+// activations stay in tensor memory: each epilogue writes them next to the
+// accumulator, and the next layer's MMAs read their A operand from there.
+// Three stages of group buffers (operand rows, whose first 4 KB the row
+// values overwrite once the rows have been consumed, per-pixel words, counts
+// and first rows) rotate over consecutive groups, so the producers may run
+// two groups ahead of the consumer.  The producers hand a stage over with a
+// full barrier (four arrivals) and get it back with a done barrier (one
+// arrival, after the gather); a named barrier among the producers at the
+// start of each group orders their reuse of the texel lists.  Every wait is
+// bounded; a wait that gives up records CTF_ERR_TIMEOUT and both roles
+// leave.  The CTA starts with 64 registers per thread; setmaxnreg gives the
 // producers 72 and the consumer 56 (128 x 72 + 128 x 56 = 256 x 64).
 // Each pixel gets the same texels, texel values, image and counts as the
 // other learned kernels: the rows of an MMA are independent, so where a
-// texel's row sits does not change its value.
+// texel's row sits does not change its value, and an MMA's result does not
+// depend on whether its A operand comes from shared or tensor memory.
 #include <cstdint>
 #include <mutex>
 #include <set>
@@ -62,14 +67,15 @@ static_assert(kGroupTiles % kPProducerWarps == 0 && 2 * kRows % kPProducerThread
 constexpr int kPFeatRounds = 2 * kRows / kPProducerThreads;  // rows per producer thread, at most
 
 // Shared memory (bytes).  The operand image sits at 0 with the offsets of
-// ctf_mlp.cuh; then the hidden-layer operand H, the MMA barrier and TMEM
-// slot, the stage hand-over barriers, the producers' Mask rank slots and
-// texel lists, and two stages.
-constexpr int kPH = kImgBytes;                   // 128 rows x 128 B
-constexpr int kPBar = kPH + 16384;               // MMA barrier (8 B), TMEM base (4 B)
+// ctf_mlp.cuh; then the MMA barrier and TMEM slot, the stage hand-over
+// barriers, the producers' Mask rank slots and texel lists, and the stages.
+// Tensor memory (128 columns): every layer's accumulator D at columns
+// [0, 64), the hidden activations at [64, 96).
+constexpr int kPStages = 3;
+constexpr int kPBar = kImgBytes;                 // MMA barrier (8 B), TMEM base (4 B)
 constexpr int kPTmem = kPBar + 8;
-constexpr int kPHand = kPBar + 16;               // full[2], done[2]
-constexpr int kPRanks = kPHand + 32;             // producer warps x 32 ints
+constexpr int kPHand = kPBar + 16;               // full[kPStages], done[kPStages]
+constexpr int kPRanks = kPHand + 16 * kPStages;             // producer warps x 32 ints
 constexpr int kPList = kPRanks + kPProducerWarps * 32 * 4;  // 8 slots x 32 int2 texel lists
 constexpr int kPStage0 = kPList + kGroupTiles * 32 * 8;
 // one stage
@@ -80,8 +86,8 @@ constexpr int kPCount = kPInfo + 1024;           // 8 x int texels per tile
 constexpr int kPBase = kPCount + 32;             // 8 x int first row per tile
 constexpr int kPRows = kPBase + 32;              // int: rows of the group
 constexpr int kPStageBytes = kPRows + 16;
-constexpr int kPBytes = kPStage0 + 2 * kPStageBytes;
-static_assert(kPH % 16 == 0 && kPStage0 % 16 == 0 && kPStageBytes % 16 == 0, "16-byte operand buffers");
+constexpr int kPBytes = kPStage0 + kPStages * kPStageBytes;
+static_assert(kPStage0 % 16 == 0 && kPStageBytes % 16 == 0, "16-byte operand buffers");
 // kPCtasPerSm CTAs per SM fit, and no more than four (4 x 128 TMEM columns)
 static_assert(kPCtasPerSm * (kPBytes + 1024 + 128) <= 228 * 1024, "the CTAs of an SM fit in shared memory");
 static_assert(65536 / (kPThreads * kPLaunchRegs) <= 4, "at most four CTAs share an SM's TMEM");
@@ -91,7 +97,7 @@ __device__ __forceinline__ uint64_t *p_full(unsigned char *sm, int s) {
     return reinterpret_cast<uint64_t *>(sm + kPHand) + s;
 }
 __device__ __forceinline__ uint64_t *p_done(unsigned char *sm, int s) {
-    return reinterpret_cast<uint64_t *>(sm + kPHand) + 2 + s;
+    return reinterpret_cast<uint64_t *>(sm + kPHand) + kPStages + s;
 }
 
 __device__ __forceinline__ void p_arrive(uint64_t *bar) {
@@ -119,36 +125,30 @@ __device__ __forceinline__ bool bar_or(bool v) {
 }
 
 // Hidden epilogue of a warp's 32 rows: TMEM columns [taddr, taddr + 64) of
-// this thread's row -> bias, ReLU -> row `row` of H (FP16; or E4M3 with the
-// output scale and the bias of an FP8 texture already multiplied on the host
-// by the inverse activation scale of the next layer's input).  The same
-// operations, in the same order, as the other learned kernels' epilogue.
-__device__ __forceinline__ void p_hidden_epilogue(unsigned char *H, uint32_t taddr, const float *bias,
-                                                  const float *oscale, bool fp8, int row) {
+// this thread's row -> bias, ReLU -> the next layer's A operand, written to
+// TMEM columns from hcol on (FP16 pairs, or E4M3 quadruples, per 32-bit
+// column in K order).
+__device__ __forceinline__ void p_hidden_epilogue(uint32_t hcol, uint32_t taddr, const float *bias,
+                                                  const float *oscale, bool fp8) {
     const float4 *b4 = reinterpret_cast<const float4 *>(bias);
     const float4 *o4 = reinterpret_cast<const float4 *>(oscale);
-    // 16 columns at a time (an FP16 pair of core-matrix rows, or one E4M3 one)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         float d[16];
         tc::tmem_ld16(taddr + 16 * q, d);
         tc::tmem_wait_ld();
         if (!fp8) {
+            uint32_t w[8];
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                uint32_t w[4];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int k = 8 * c + 4 * i;  // columns 16 q + k .. + 3
-                    const float4 b = b4[(16 * q + k) / 4];
-                    const float2 t0 = __fadd2_rn(make_float2(d[k], d[k + 1]), make_float2(b.x, b.y));
-                    const float2 t1 = __fadd2_rn(make_float2(d[k + 2], d[k + 3]), make_float2(b.z, b.w));
-                    w[2 * i] = relu_half2(t0.x, t0.y);
-                    w[2 * i + 1] = relu_half2(t1.x, t1.y);
-                }
-                *reinterpret_cast<uint4 *>(H + core_offset(row, 16 * q + 8 * c, 64, 2)) =
-                    make_uint4(w[0], w[1], w[2], w[3]);
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * i;
+                const float4 b = b4[(16 * q + k) / 4];
+                const float2 t0 = __fadd2_rn(make_float2(d[k], d[k + 1]), make_float2(b.x, b.y));
+                const float2 t1 = __fadd2_rn(make_float2(d[k + 2], d[k + 3]), make_float2(b.z, b.w));
+                w[2 * i] = relu_half2(t0.x, t0.y);
+                w[2 * i + 1] = relu_half2(t1.x, t1.y);
             }
+            tc::tmem_st8(hcol + 8 * q, w);
         } else {
             uint32_t w[4];
 #pragma unroll
@@ -160,9 +160,10 @@ __device__ __forceinline__ void p_hidden_epilogue(unsigned char *H, uint32_t tad
                     __ffma2_rn(make_float2(d[k + 2], d[k + 3]), make_float2(o.z, o.w), make_float2(b.z, b.w));
                 w[i] = (uint32_t)relu_e4m3x2(t0.x, t0.y) | ((uint32_t)relu_e4m3x2(t1.x, t1.y) << 16);
             }
-            *reinterpret_cast<uint4 *>(H + core_offset(row, 16 * q, 64, 1)) = make_uint4(w[0], w[1], w[2], w[3]);
+            tc::tmem_st4(hcol + 4 * q, w);
         }
     }
+    tc::tmem_wait_st();
 }
 
 // One MMA layer's completion: thread 0 polls the barrier, the other
@@ -183,12 +184,12 @@ __device__ __forceinline__ bool p_layer_done(uint64_t *bar, uint32_t &phase, int
 }
 
 // The three layers for the 128 rows of chain c of a stage (layer-1 operand
-// at sX).  `live`: this warp has rows below the group's row count (else it
-// skips its epilogues, whose rows nobody reads).  Consumer threads only.
+// at sX).  TMEM columns: D (every layer's accumulator) at [0, 64), the
+// hidden activations H at [64, 96).  `live`: this warp has rows below the
+// group's row count (else it skips its epilogues).  Consumer threads only.
 __device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64_t *bar, uint32_t &phase,
                                         uint32_t sX, bool fp8, bool live, float4 &out, int *err) {
     const int tid = threadIdx.x, warp = tid >> 5;
-    unsigned char *H = sm + kPH;
     const float *b1 = reinterpret_cast<const float *>(sm + kImgB1);
     const float *b2 = reinterpret_cast<const float *>(sm + kImgB2);
     const float *b3 = reinterpret_cast<const float *>(sm + kImgB3);
@@ -196,7 +197,6 @@ __device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64
     const float *s2 = reinterpret_cast<const float *>(sm + kImgS2);
     const float *s3 = reinterpret_cast<const float *>(sm + kImgS3);
     const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-    const uint32_t sH = tc::smem_addr(H);
     const uint32_t sW1 = tc::smem_addr(sm + kImgW1), sW2 = tc::smem_addr(sm + kImgW2),
                    sW3 = tc::smem_addr(sm + kImgW3);
     const uint32_t kstep = 256;              // 32 bytes of K per 8-row group
@@ -205,10 +205,9 @@ __device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64
     const int nk = fp8 ? 2 : 4;              // MMAs over K = 64
     const uint32_t id64 = fp8 ? tc::idesc_e4m3(128, 64) : tc::idesc_f16(128, 64);
     const uint32_t id16 = fp8 ? tc::idesc_e4m3(128, 16) : tc::idesc_f16(128, 16);
+    const uint32_t tH = tmem + 64;
 
-    // ---- layer 1: D[0..64) = X W1^T (the producers made X visible to the
-    // tensor cores before the full barrier; the last chain's TMEM reads are
-    // ordered before this issue by the barrier that ended it)
+    // ---- layer 1: D = X W1^T
     if (tid == 0) {
         tc::fence_after_sync();
         const uint64_t a = tc::smem_desc(sX, 128, sboX), b = tc::smem_desc(sW1, 128, sboX);
@@ -217,35 +216,31 @@ __device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64
         tc::commit(bar);
     }
     if (!p_layer_done(bar, phase, err)) return false;
-    if (live) p_hidden_epilogue(H, lane_base + 0, b1, s1, fp8, tid);
-    tc::fence_proxy_async();
+    if (live) p_hidden_epilogue(lane_base + 64, lane_base + 0, b1, s1, fp8);
     tc::fence_before_sync();
     cons_bar();
-    // ---- layer 2: D[64..128) = H1 W2^T
+    // ---- layer 2: D = H1 W2^T (D1 has been read)
     if (tid == 0) {
         tc::fence_after_sync();
         for (int j = 0; j < nk; ++j) {
-            const uint64_t a = tc::smem_desc(sH + j * kstep, 128, sboH);
             const uint64_t b = tc::smem_desc(sW2 + j * kstep, 128, sboH);
-            if (fp8) tc::mma_e4m3(tmem + 64, a, b, id64, j > 0);
-            else tc::mma_f16(tmem + 64, a, b, id64, j > 0);
+            if (fp8) tc::mma_e4m3_ts(tmem, tH + 8 * j, b, id64, j > 0);
+            else tc::mma_f16_ts(tmem, tH + 8 * j, b, id64, j > 0);
         }
         tc::commit(bar);
     }
     if (!p_layer_done(bar, phase, err)) return false;
     // the layer-2 MMAs have read H1, so H2 may overwrite it
-    if (live) p_hidden_epilogue(H, lane_base + 64, b2, s2, fp8, tid);
-    tc::fence_proxy_async();
+    if (live) p_hidden_epilogue(lane_base + 64, lane_base + 0, b2, s2, fp8);
     tc::fence_before_sync();
     cons_bar();
     // ---- layer 3: D[0..16) = H2 W3^T
     if (tid == 0) {
         tc::fence_after_sync();
         for (int j = 0; j < nk; ++j) {
-            const uint64_t a = tc::smem_desc(sH + j * kstep, 128, sboH);
             const uint64_t b = tc::smem_desc(sW3 + j * kstep, 128, sboH);
-            if (fp8) tc::mma_e4m3(tmem, a, b, id16, j > 0);
-            else tc::mma_f16(tmem, a, b, id16, j > 0);
+            if (fp8) tc::mma_e4m3_ts(tmem, tH + 8 * j, b, id16, j > 0);
+            else tc::mma_f16_ts(tmem, tH + 8 * j, b, id16, j > 0);
         }
         tc::commit(bar);
     }
@@ -263,8 +258,6 @@ __device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64
         }
         out = make_float4(o[0], o[1], o[2], o[3]);
     }
-    // the next chain's layer 1 overwrites D[0..64): every TMEM read of this
-    // chain is ordered before it by the caller's consumer barrier
     tc::fence_before_sync();
     return true;
 }
@@ -274,7 +267,8 @@ __device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64
 // 0-19 the list indices of its 4 taps on success, else of its own texel;
 // 20-22 its count; 23 active; 24 inside; 25 success), the slot's texel count,
 // and the slot's texel list (clamped) at list[32 g + rank].
-template <int ALG, int TW, int MD>
+// kStats: the variant that keeps the outcome counters (p.stats set).
+template <int ALG, int TW, int MD, bool kStats>
 __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp, long long first, int g,
                                         unsigned char *st, int2 *list, int lane, uint32_t lt, int *ranks,
                                         Counters &cnt) {
@@ -303,7 +297,7 @@ __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp,
     setup_coords(uv, (float)p.Wt, (float)p.Ht, ps);
     Selection sel;
     if (valid) {
-        sel = select_tile<ALG, MD, true, false>(p, ps, jac, px, py, lane, lt, nullptr, ranks, cnt);
+        sel = select_tile<ALG, MD, kStats, false>(p, ps, jac, px, py, lane, lt, nullptr, ranks, cnt);
     } else {
         sel.path = PATH_EMPTY;
         sel.A = 0;
@@ -327,8 +321,8 @@ __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp,
     pix_info[32 * g + lane] = info;
 }
 
-// Producer: step 3 for tile slot g of the group at `first` from stage st
-// (row values written by the consumer): gather, filter, store.
+// Consumer: step 3 for tile slot g of the group at `first` from stage st
+// (its row values in place): gather, filter, store; `lane` is the pixel.
 template <int TW>
 __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp, int g, const unsigned char *st,
                                          int lane) {
@@ -370,7 +364,7 @@ __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp
     if (p.evals) p.evals[idx] = cv;
 }
 
-template <int ALG, int TW, int MD>
+template <int ALG, int TW, int MD, bool kStats>
 __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(const ExactParams p, const MlpDevice m, int *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned long long block_stats[kNumStats];
@@ -385,7 +379,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
     }
     if (threadIdx.x == 0) {
         tc::mbar_init(mma_bar, 1);
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kPStages; ++s) {
             tc::mbar_init(p_full(sm, s), kPProducerWarps);
             tc::mbar_init(p_done(sm, s), 1);
         }
@@ -415,8 +409,8 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
         for (long long j = 0;; ++j) {
             const long long grp = blockIdx.x + j * G;
             if (grp >= n_groups) break;
-            const int s = (int)(j & 1);
-            const uint32_t par = (uint32_t)((j >> 1) & 1);
+            const int s = (int)(j % kPStages);
+            const uint32_t par = (uint32_t)((j / kPStages) & 1);
             unsigned char *st = p_stage(sm, s);
             bool ok = true;
             if (tid == 0) ok = tc::mbar_wait(p_full(sm, s), par, kMaxTries);
@@ -440,6 +434,14 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 cons_bar();
             }
             if (!ok) break;
+            {
+                // step 3 for the group: warp w the tiles w and 4 + w
+                const TilePos tpc = tile_pos0(p, grp * kGroupTiles);
+#pragma unroll 1
+                for (int k = 0; k < 2; ++k) p_gather<TW>(p, tpc, 4 * k + warp, st, tid & 31);
+            }
+            __syncwarp();
+            cons_bar();  // every consumer warp has read the stage
             if (tid == 0) p_arrive(p_done(sm, s));
         }
     } else {
@@ -453,19 +455,28 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
         for (long long j = 0;; ++j) {
             const long long grp = blockIdx.x + j * G;
             const bool have = grp < n_groups;  // uniform over the CTA
-            if (have) {
-                const int s = (int)(j & 1);
+            if (!have) break;
+            {
+                const int s = (int)(j % kPStages);
                 unsigned char *st = p_stage(sm, s);
-                // every producer warp has gathered group j - 2 from this stage
-                // (the consumer was done with it before that gather began) and
-                // read the texel lists of group j - 1
+                if (j >= kPStages) {
+                    // the consumer has gathered group j - kPStages from this stage
+                    bool okd = true;
+                    if (lane == 0) okd = tc::mbar_wait(p_done(sm, s), (uint32_t)(((j - kPStages) / kPStages) & 1), kMaxTries);
+                    __syncwarp();
+                    if (bar_or<2, kPProducerThreads>(!okd)) {
+                        if (threadIdx.x == 128) atomicExch(err, CTF_ERR_TIMEOUT);
+                        break;
+                    }
+                }
+                // every producer warp has read the texel lists of group j - 1
                 __syncwarp();
                 prod_bar();
                 const long long first = grp * kGroupTiles;
                 const TilePos tp = tile_pos0(p, first);
 #pragma unroll 1
                 for (int k = 0; k < kPSlots; ++k)
-                    p_step1<ALG, TW, MD>(p, tp, first, kPSlots * pw + k, st, list, lane, lt, ranks, cnt);
+                    p_step1<ALG, TW, MD, kStats>(p, tp, first, kPSlots * pw + k, st, list, lane, lt, ranks, cnt);
                 __syncwarp();
                 prod_bar();  // every slot's list and count is in place
                 // rows: slot g owns [start_g, start_g + count_g) in slot order;
@@ -489,7 +500,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 if (pt < kGroupTiles) reinterpret_cast<int *>(st + kPBase)[pt] = mybase;
                 if (pt == 0) {
                     *reinterpret_cast<int *>(st + kPRows) = R;
-                    cnt.v[kStatTexelEvalsUnique] += R;
+                    if (kStats) cnt.v[kStatTexelEvalsUnique] += R;
                 }
                 // features of rows pt and pt + kPProducerThreads, in the tensor
                 // cores' operand layout
@@ -507,26 +518,10 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 __syncwarp();
                 if (lane == 0) p_arrive(p_full(sm, s));
             }
-            if (j >= 1) {
-                // gather group j - 1 once its row values are written
-                const int s1 = (int)((j - 1) & 1);
-                const uint32_t par1 = (uint32_t)(((j - 1) >> 1) & 1);
-                bool ok = true;
-                if (lane == 0) ok = tc::mbar_wait(p_done(sm, s1), par1, kMaxTries);
-                __syncwarp();
-                if (bar_or<2, kPProducerThreads>(!ok)) {
-                    if (threadIdx.x == 128) atomicExch(err, CTF_ERR_TIMEOUT);
-                    break;
-                }
-                const TilePos tp1 = tile_pos0(p, (grp - G) * kGroupTiles);
-#pragma unroll 1
-                for (int k = 0; k < kPSlots; ++k) p_gather<TW>(p, tp1, kPSlots * pw + k, p_stage(sm, s1), lane);
-            }
-            if (!have) break;
         }
     }
 
-    if (p.stats && lane == 0) {
+    if (kStats && p.stats && lane == 0) {
 #pragma unroll
         for (int i = 0; i < kNumStats; ++i)
             if (cnt.v[i]) atomicAdd(&block_stats[i], (unsigned long long)cnt.v[i]);
@@ -544,21 +539,21 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
 
 using PfFn = void (*)(const ExactParams, const MlpDevice, int *);
 
-template <int TW>
+template <int TW, bool kStats>
 PfFn pf_pick(int alg, int md) {
     switch (alg) {
-    case ALG_STF: return mlp_filter_pf_kernel<ALG_STF, TW, 16>;
-    case ALG_BOX: return mlp_filter_pf_kernel<ALG_BOX, TW, 16>;
-    case ALG_MASK: return md == 11 ? mlp_filter_pf_kernel<ALG_MASK, TW, 11> : mlp_filter_pf_kernel<ALG_MASK, TW, 16>;
+    case ALG_STF: return mlp_filter_pf_kernel<ALG_STF, TW, 16, kStats>;
+    case ALG_BOX: return mlp_filter_pf_kernel<ALG_BOX, TW, 16, kStats>;
+    case ALG_MASK: return md == 11 ? mlp_filter_pf_kernel<ALG_MASK, TW, 11, kStats> : mlp_filter_pf_kernel<ALG_MASK, TW, 16, kStats>;
     default: return nullptr;
     }
 }
 
-PfFn pf_kernel(int alg, int tile_w, int mask_dim) {
+PfFn pf_kernel(int alg, int tile_w, int mask_dim, bool st = true) {
     switch (tile_w) {
-    case 8: return pf_pick<8>(alg, mask_dim);
-    case 4: return pf_pick<4>(alg, mask_dim);
-    case 16: return pf_pick<16>(alg, mask_dim);
+    case 8: return st ? pf_pick<8, true>(alg, mask_dim) : pf_pick<8, false>(alg, mask_dim);
+    case 4: return st ? pf_pick<4, true>(alg, mask_dim) : pf_pick<4, false>(alg, mask_dim);
+    case 16: return st ? pf_pick<16, true>(alg, mask_dim) : pf_pick<16, false>(alg, mask_dim);
     default: return nullptr;
     }
 }
@@ -585,13 +580,15 @@ cudaError_t pf_prepare(PfFn fn) {
 }  // namespace
 
 cudaError_t prepare_mlp_filter_pf(int alg, int tile_w, int mask_dim) {
-    PfFn fn = pf_kernel(alg, tile_w, mask_dim);
-    return fn ? pf_prepare(fn) : cudaErrorInvalidValue;
+    PfFn fn = pf_kernel(alg, tile_w, mask_dim, true), fn0 = pf_kernel(alg, tile_w, mask_dim, false);
+    if (!fn || !fn0) return cudaErrorInvalidValue;
+    cudaError_t e = pf_prepare(fn);
+    return e == cudaSuccess ? pf_prepare(fn0) : e;
 }
 
 cudaError_t launch_mlp_filter_pf(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                                  cudaStream_t stream) {
-    PfFn fn = pf_kernel(alg, tile_w, mask_dim);
+    PfFn fn = pf_kernel(alg, tile_w, mask_dim, p.stats != nullptr);
     if (!fn) return cudaErrorInvalidValue;
     if (p.n_tiles == 0) return cudaSuccess;
     if (p.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile positions use 32-bit arithmetic
