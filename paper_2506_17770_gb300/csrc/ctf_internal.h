@@ -138,6 +138,9 @@ inline uint64_t fnv1a(const void *data, size_t n, uint64_t h = 14695981039346656
 // computed by the selecting warps (ctf_mlp_ws2.cu), and with group_dedup the
 // consumer merging the group's lists (ctf_mlp_ws.cu).
 bool mlp_filter_ws_applies(const ExactParams &p, int alg);
+// Box and Mask with fallback C / C+ and one texel per lane run the
+// fallback variant of the packed-group kernel (ctf_mlp_ws2.cu).
+bool mlp_filter_pf_fallback_applies(const ExactParams &p, int alg);
 cudaError_t prepare_mlp_filter_pf(int alg, int tile_w, int mask_dim);
 // The learned filter with fallbacks C / C+ or two texels per lane
 // (ctf_mlp_ext.cu), for List Merge, Box and Mask Sampling.

@@ -199,6 +199,8 @@ cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t 
 
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                               cudaStream_t stream) {
+    // fallbacks C / C+ with one texel per lane on Box and Mask: the packed-group kernel's fallback variant
+    if (mlp_filter_pf_fallback_applies(p, alg)) return launch_mlp_filter_pf(p, m, alg, tile_w, mask_dim, err, stream);
     if (mlp_filter_ext_applies(p, alg)) return launch_mlp_filter_ext(p, m, alg, tile_w, mask_dim, err, stream);
     if (mlp_filter_ws_applies(p, alg))
         return p.group_dedup ? launch_mlp_filter_ws(p, m, alg, tile_w, mask_dim, err, stream)

@@ -48,6 +48,7 @@
 #include "ctf_select.cuh"
 #include "tc_ops.cuh"
 #include "ctf_mlp_chain.cuh"
+#include "ctf_exact_tile.cuh"
 
 namespace ctf {
 namespace {
@@ -68,16 +69,17 @@ constexpr int kPFeatRounds = 2 * kRows / kPProducerThreads;  // rows per produce
 
 // Shared memory (bytes).  The operand image sits at 0 with the offsets of
 // ctf_mlp.cuh; then the MMA barrier and TMEM slot, the stage hand-over
-// barriers, the producers' Mask rank slots and texel lists, and the stages.
+// barriers, the producers' Mask rank slots and texel lists, in the variant
+// with fallbacks C / C+ one texel table per warp, and the stages.
 // Tensor memory (128 columns): every layer's accumulator D at columns
 // [0, 64), the hidden activations at [64, 96).
-constexpr int kPStages = 3;
+constexpr int kPMaxStages = 3;
 constexpr int kPBar = kImgBytes;                 // MMA barrier (8 B), TMEM base (4 B)
 constexpr int kPTmem = kPBar + 8;
-constexpr int kPHand = kPBar + 16;               // full[kPStages], done[kPStages]
-constexpr int kPRanks = kPHand + 16 * kPStages;             // producer warps x 32 ints
+constexpr int kPHand = kPBar + 16;               // full[kPMaxStages], done[kPMaxStages]
+constexpr int kPRanks = kPHand + 16 * kPMaxStages;          // producer warps x 32 ints
 constexpr int kPList = kPRanks + kPProducerWarps * 32 * 4;  // 8 slots x 32 int2 texel lists
-constexpr int kPStage0 = kPList + kGroupTiles * 32 * 8;
+constexpr int kPFbTab = kPList + kGroupTiles * 32 * 8;      // fallback variant: 8 warps' texel tables
 // one stage
 constexpr int kPX = 0;                           // 256 rows x 32 B layer-1 operand; row values overlay 0..4095
 constexpr int kPST = kPX + 8192;                 // 256 x float2 (s, t)
@@ -85,19 +87,32 @@ constexpr int kPInfo = kPST + 2048;              // 256 x uint32 per-pixel words
 constexpr int kPCount = kPInfo + 1024;           // 8 x int texels per tile
 constexpr int kPBase = kPCount + 32;             // 8 x int first row per tile
 constexpr int kPRows = kPBase + 32;              // int: rows of the group
-constexpr int kPStageBytes = kPRows + 16;
-constexpr int kPBytes = kPStage0 + kPStages * kPStageBytes;
-static_assert(kPStage0 % 16 == 0 && kPStageBytes % 16 == 0, "16-byte operand buffers");
-// kPCtasPerSm CTAs per SM fit, and no more than four (4 x 128 TMEM columns)
-static_assert(kPCtasPerSm * (kPBytes + 1024 + 128) <= 228 * 1024, "the CTAs of an SM fit in shared memory");
+constexpr int kPQ = kPRows + 16;                 // fallback variant: 256 x int2 texel a pixel's lane produces
+constexpr int kPUL = kPQ + 2048;                 // fallback variant: 256 x int2 upper-left texel of the footprint
+
+// kFb: the variant with fallbacks C / C+ (two stages, to make room for the
+// texel tables and the per-pixel texels the blend of eq. 1 needs).
+template <bool kFb>
+struct PLayout {
+    static constexpr int kStages = kFb ? 2 : 3;
+    static constexpr int kStage0 = kFb ? kPFbTab + 8 * (int)sizeof(FbTable) : kPFbTab;
+    static constexpr int kStageBytes = kFb ? kPUL + 2048 : kPRows + 16;
+    static constexpr int kBytes = kStage0 + kStages * kStageBytes;
+    static_assert(kStage0 % 16 == 0 && kStageBytes % 16 == 0 && kPFbTab % 16 == 0, "16-byte operand buffers");
+    // kPCtasPerSm CTAs per SM fit, and no more than four (4 x 128 TMEM columns)
+    static_assert(kPCtasPerSm * (kBytes + 1024 + 128) <= 228 * 1024, "the CTAs of an SM fit in shared memory");
+};
 static_assert(65536 / (kPThreads * kPLaunchRegs) <= 4, "at most four CTAs share an SM's TMEM");
 
-__device__ __forceinline__ unsigned char *p_stage(unsigned char *sm, int s) { return sm + kPStage0 + s * kPStageBytes; }
+template <bool kFb>
+__device__ __forceinline__ unsigned char *p_stage(unsigned char *sm, int s) {
+    return sm + PLayout<kFb>::kStage0 + s * PLayout<kFb>::kStageBytes;
+}
 __device__ __forceinline__ uint64_t *p_full(unsigned char *sm, int s) {
     return reinterpret_cast<uint64_t *>(sm + kPHand) + s;
 }
 __device__ __forceinline__ uint64_t *p_done(unsigned char *sm, int s) {
-    return reinterpret_cast<uint64_t *>(sm + kPHand) + kPStages + s;
+    return reinterpret_cast<uint64_t *>(sm + kPHand) + kPMaxStages + s;
 }
 
 __device__ __forceinline__ void p_arrive(uint64_t *bar) {
@@ -268,10 +283,16 @@ __device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64
 // 20-22 its count; 23 active; 24 inside; 25 success), the slot's texel count,
 // and the slot's texel list (clamped) at list[32 g + rank].
 // kStats: the variant that keeps the outcome counters (p.stats set).
-template <int ALG, int TW, int MD, bool kStats>
+// kFb: the variant with fallbacks C / C+: an over-budget magnified tile
+// takes its texels from fb_choose (the exact path's choice, with the warp's
+// table fbt); each lane's produced texel gets the rank of the lane among
+// the producing lanes, and the pixel's word carries bit 26 (fallback tile)
+// and bit 27 (this lane produces); the produced texel and the footprint's
+// upper-left texel go to the stage for the blend of eq. 1.
+template <int ALG, int TW, int MD, bool kStats, bool kFb>
 __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp, long long first, int g,
                                         unsigned char *st, int2 *list, int lane, uint32_t lt, int *ranks,
-                                        Counters &cnt) {
+                                        Counters &cnt, FbTable *fbt) {
     constexpr int TH = 32 / TW;
     const int tx = lane % TW, ty = lane / TW;
     float2 *pix_st = reinterpret_cast<float2 *>(st + kPST);
@@ -305,6 +326,25 @@ __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp,
         sel.count = 0;
         sel.my_rank = 0;
     }
+    if (kFb && p.fallback != 0 && sel.path == PATH_FALLBACK_BUDGET) {  // warp-uniform
+        const FbChoice c = fb_choose(p.fallback, p.view, p.y0, p.k0, p.k1, ps.ulx, ps.uly, ps.s, ps.t, ps.active, px,
+                                     py, sel.A, lane, lt, fbt);
+        const uint32_t pm = __ballot_sync(FULL, c.produce);
+        const int rank = __popc(pm & lt), n = __popc(pm);
+        if (c.produce)
+            list[32 * g + ck(rank, 32, p.err, kBndTexList)] =
+                make_int2(min(max(c.qx, 0), p.Wt - 1), min(max(c.qy, 0), p.Ht - 1));
+        if (lane == 0) reinterpret_cast<int *>(st + kPCount)[g] = n;
+        // select_tile counted one evaluation per active lane
+        if (kStats) cnt.v[kStatTexelEvals] += n - __popc(sel.A);
+        const uint32_t info = (uint32_t)rank | ((c.produce ? 1u : 0u) << 20) | (ps.active ? 1u << 23 : 0u) |
+                              (inside ? 1u << 24 : 0u) | (1u << 26) | (c.produce ? 1u << 27 : 0u);
+        pix_st[32 * g + lane] = make_float2(ps.s, ps.t);
+        pix_info[32 * g + lane] = info;
+        reinterpret_cast<int2 *>(st + kPQ)[32 * g + lane] = make_int2(c.qx, c.qy);
+        reinterpret_cast<int2 *>(st + kPUL)[32 * g + lane] = make_int2(ps.ulx, ps.uly);
+        return;
+    }
     if (sel.produce)
         list[32 * g + ck(sel.my_rank, 32, p.err, kBndTexList)] =
             make_int2(min(max(sel.tx, 0), p.Wt - 1), min(max(sel.ty, 0), p.Ht - 1));
@@ -323,21 +363,41 @@ __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp,
 
 // Consumer: step 3 for tile slot g of the group at `first` from stage st
 // (its row values in place): gather, filter, store; `lane` is the pixel.
-template <int TW>
+template <int TW, bool kFb>
 __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp, int g, const unsigned char *st,
-                                         int lane) {
+                                         int lane, FbTable *fbt) {
     constexpr int TH = 32 / TW;
     const int tx = lane % TW, ty = lane / TW;
     const uint32_t info = reinterpret_cast<const uint32_t *>(st + kPInfo)[32 * g + lane];
-    if (!((info >> 24) & 1u)) return;  // outside the frame (or no tile)
     const float4 *outrow = reinterpret_cast<const float4 *>(st + kPX);
     const int base = reinterpret_cast<const int *>(st + kPBase)[g];
     // row of list entry i of this tile (the row values fill the stage's first 4 KB: 256 rows)
     auto row_of = [&](uint32_t i) { return ck(base + (int)i, 2 * kRows, p.err, kBndRow); };
     int bx, by;
     tile_pos(tp, g, bx, by);
-    const uint32_t idx =
-        ck((uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx), view_pixels(p), p.err, kBndPixel);
+    const bool inside = ((info >> 24) & 1u) != 0;  // (pixels outside the frame take part in the blend only)
+    const uint32_t idx = ck(inside ? (uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx) : 0u,
+                            view_pixels(p), p.err, kBndPixel);
+    if (kFb && ((info >> 26) & 1u)) {
+        // fallback C / C+ (the whole warp: the blend is warp-collective):
+        // eq. 1 over the produced texels of the footprint, their values the
+        // rows of the tile's list
+        FbChoice c;
+        c.produce = ((info >> 27) & 1u) != 0;
+        const int2 q = reinterpret_cast<const int2 *>(st + kPQ)[32 * g + lane];
+        const int2 ul = reinterpret_cast<const int2 *>(st + kPUL)[32 * g + lane];
+        const float2 s = reinterpret_cast<const float2 *>(st + kPST)[32 * g + lane];
+        c.qx = q.x;
+        c.qy = q.y;
+        const float4 val = c.produce ? outrow[row_of(info & 31u)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const FallbackOut fo = fb_blend<false>(val, c, ul.x, ul.y, s.x, s.y, ((info >> 23) & 1u) != 0, lane, fbt);
+        if (inside) {
+            __stcs(p.out + idx, fo.res);
+            if (p.evals) p.evals[idx] = (uint8_t)fo.count;
+        }
+        return;
+    }
+    if (!inside) return;  // outside the frame (or no tile)
     float4 result = make_float4(0.f, 0.f, 0.f, 0.f);
     uint8_t cv = 0;
     if ((info >> 23) & 1u) {
@@ -364,11 +424,15 @@ __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp
     if (p.evals) p.evals[idx] = cv;
 }
 
-template <int ALG, int TW, int MD, bool kStats>
+template <int ALG, int TW, int MD, bool kStats, bool kFb>
 __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(const ExactParams p, const MlpDevice m, int *err) {
+    constexpr int kPStages = PLayout<kFb>::kStages;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned long long block_stats[kNumStats];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // fallback variant: warp w's texel table (empty between tiles)
+    FbTable *fbt = kFb ? reinterpret_cast<FbTable *>(sm + kPFbTab) + warp : nullptr;
+    if (kFb) fb_clear(fbt, lane);
     uint64_t *mma_bar = reinterpret_cast<uint64_t *>(sm + kPBar);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kPTmem);
     if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
@@ -411,7 +475,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
             if (grp >= n_groups) break;
             const int s = (int)(j % kPStages);
             const uint32_t par = (uint32_t)((j / kPStages) & 1);
-            unsigned char *st = p_stage(sm, s);
+            unsigned char *st = p_stage<kFb>(sm, s);
             bool ok = true;
             if (tid == 0) ok = tc::mbar_wait(p_full(sm, s), par, kMaxTries);
             __syncwarp();
@@ -438,7 +502,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 // step 3 for the group: warp w the tiles w and 4 + w
                 const TilePos tpc = tile_pos0(p, grp * kGroupTiles);
 #pragma unroll 1
-                for (int k = 0; k < 2; ++k) p_gather<TW>(p, tpc, 4 * k + warp, st, tid & 31);
+                for (int k = 0; k < 2; ++k) p_gather<TW, kFb>(p, tpc, 4 * k + warp, st, tid & 31, fbt);
             }
             __syncwarp();
             cons_bar();  // every consumer warp has read the stage
@@ -458,7 +522,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
             if (!have) break;
             {
                 const int s = (int)(j % kPStages);
-                unsigned char *st = p_stage(sm, s);
+                unsigned char *st = p_stage<kFb>(sm, s);
                 if (j >= kPStages) {
                     // the consumer has gathered group j - kPStages from this stage
                     bool okd = true;
@@ -476,7 +540,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 const TilePos tp = tile_pos0(p, first);
 #pragma unroll 1
                 for (int k = 0; k < kPSlots; ++k)
-                    p_step1<ALG, TW, MD, kStats>(p, tp, first, kPSlots * pw + k, st, list, lane, lt, ranks, cnt);
+                    p_step1<ALG, TW, MD, kStats, kFb>(p, tp, first, kPSlots * pw + k, st, list, lane, lt, ranks, cnt, fbt);
                 __syncwarp();
                 prod_bar();  // every slot's list and count is in place
                 // rows: slot g owns [start_g, start_g + count_g) in slot order;
@@ -539,26 +603,33 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
 
 using PfFn = void (*)(const ExactParams, const MlpDevice, int *);
 
-template <int TW, bool kStats>
+template <int TW, bool kStats, bool kFb>
 PfFn pf_pick(int alg, int md) {
     switch (alg) {
-    case ALG_STF: return mlp_filter_pf_kernel<ALG_STF, TW, 16, kStats>;
-    case ALG_BOX: return mlp_filter_pf_kernel<ALG_BOX, TW, 16, kStats>;
-    case ALG_MASK: return md == 11 ? mlp_filter_pf_kernel<ALG_MASK, TW, 11, kStats> : mlp_filter_pf_kernel<ALG_MASK, TW, 16, kStats>;
+    case ALG_STF: return kFb ? nullptr : mlp_filter_pf_kernel<ALG_STF, TW, 16, kStats, false>;
+    case ALG_BOX: return mlp_filter_pf_kernel<ALG_BOX, TW, 16, kStats, kFb>;
+    case ALG_MASK:
+        return md == 11 ? mlp_filter_pf_kernel<ALG_MASK, TW, 11, kStats, kFb> : mlp_filter_pf_kernel<ALG_MASK, TW, 16, kStats, kFb>;
     default: return nullptr;
     }
 }
 
-PfFn pf_kernel(int alg, int tile_w, int mask_dim, bool st = true) {
+template <int TW>
+PfFn pf_pick_tw(int alg, int md, bool st, bool fb) {
+    return fb ? (st ? pf_pick<TW, true, true>(alg, md) : pf_pick<TW, false, true>(alg, md))
+              : (st ? pf_pick<TW, true, false>(alg, md) : pf_pick<TW, false, false>(alg, md));
+}
+
+PfFn pf_kernel(int alg, int tile_w, int mask_dim, bool st, bool fb) {
     switch (tile_w) {
-    case 8: return st ? pf_pick<8, true>(alg, mask_dim) : pf_pick<8, false>(alg, mask_dim);
-    case 4: return st ? pf_pick<4, true>(alg, mask_dim) : pf_pick<4, false>(alg, mask_dim);
-    case 16: return st ? pf_pick<16, true>(alg, mask_dim) : pf_pick<16, false>(alg, mask_dim);
+    case 8: return pf_pick_tw<8>(alg, mask_dim, st, fb);
+    case 4: return pf_pick_tw<4>(alg, mask_dim, st, fb);
+    case 16: return pf_pick_tw<16>(alg, mask_dim, st, fb);
     default: return nullptr;
     }
 }
 
-cudaError_t pf_prepare(PfFn fn) {
+cudaError_t pf_prepare(PfFn fn, int smem_bytes) {
     static std::mutex mu;
     static std::set<std::pair<int, const void *>> done;
     int dev = 0;
@@ -572,32 +643,45 @@ cudaError_t pf_prepare(PfFn fn) {
     cudaError_t e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return e;
     if (kPSplitRegs ? fa.numRegs != kPLaunchRegs : fa.numRegs > kPLaunchRegs) return cudaErrorInvalidDeviceFunction;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kPBytes);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e == cudaSuccess) done.insert(key);
     return e;
 }
 
+int pf_smem(bool fb) { return fb ? PLayout<true>::kBytes : PLayout<false>::kBytes; }
+
 }  // namespace
 
+bool mlp_filter_pf_fallback_applies(const ExactParams &p, int alg) {
+    return (alg == ALG_BOX || alg == ALG_MASK) && p.fallback != 0 && p.tpl == 1 && !p.group_dedup;
+}
+
 cudaError_t prepare_mlp_filter_pf(int alg, int tile_w, int mask_dim) {
-    PfFn fn = pf_kernel(alg, tile_w, mask_dim, true), fn0 = pf_kernel(alg, tile_w, mask_dim, false);
-    if (!fn || !fn0) return cudaErrorInvalidValue;
-    cudaError_t e = pf_prepare(fn);
-    return e == cudaSuccess ? pf_prepare(fn0) : e;
+    for (int v = 0; v < 4; ++v) {
+        const bool st = (v & 1) != 0, fb = (v & 2) != 0;
+        if (fb && alg == ALG_STF) continue;
+        PfFn fn = pf_kernel(alg, tile_w, mask_dim, st, fb);
+        if (!fn) return cudaErrorInvalidValue;
+        const cudaError_t e = pf_prepare(fn, pf_smem(fb));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_mlp_filter_pf(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                                  cudaStream_t stream) {
-    PfFn fn = pf_kernel(alg, tile_w, mask_dim, p.stats != nullptr);
+    const bool fb = p.fallback != 0;
+    if (fb && !mlp_filter_pf_fallback_applies(p, alg)) return cudaErrorInvalidValue;
+    PfFn fn = pf_kernel(alg, tile_w, mask_dim, p.stats != nullptr, fb);
     if (!fn) return cudaErrorInvalidValue;
     if (p.n_tiles == 0) return cudaSuccess;
     if (p.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile positions use 32-bit arithmetic
-    cudaError_t e = pf_prepare(fn);
+    cudaError_t e = pf_prepare(fn, pf_smem(fb));
     if (e != cudaSuccess) return e;
     const long long groups = (p.n_tiles + kGroupTiles - 1) / kGroupTiles;
     const long long cap = (long long)device_sm_count() * kPCtasPerSm;
     const int grid = (int)(groups < cap ? groups : cap);
-    fn<<<grid, kPThreads, kPBytes, stream>>>(p, m, err);
+    fn<<<grid, kPThreads, pf_smem(fb), stream>>>(p, m, err);
     return cudaGetLastError();
 }
 
