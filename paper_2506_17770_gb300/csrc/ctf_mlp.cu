@@ -178,6 +178,10 @@ cudaError_t launch_mlp_decode(const MlpDevice &m, int Wt, int Ht, const int2 *xy
 }
 
 cudaError_t prepare_mlp_filter(int alg, int tile_w, int mask_dim) {
+    if (alg == ALG_LIST) {
+        cudaError_t e = prepare_mlp_filter_pf(alg, tile_w, mask_dim);
+        if (e != cudaSuccess) return e;
+    }
     if (alg == ALG_STF || alg == ALG_BOX || alg == ALG_MASK) {
         cudaError_t e = prepare_mlp_filter_pf(alg, tile_w, mask_dim);
         return e == cudaSuccess ? prepare_mlp_filter_ws(alg, tile_w, mask_dim) : e;
@@ -201,6 +205,9 @@ cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg,
                               cudaStream_t stream) {
     // fallbacks C / C+ with one texel per lane on Box and Mask: the packed-group kernel's fallback variant
     if (mlp_filter_pf_fallback_applies(p, alg)) return launch_mlp_filter_pf(p, m, alg, tile_w, mask_dim, err, stream);
+    // List Merge without extensions or group_dedup: the packed-group kernel's List Merge variant
+    if (alg == ALG_LIST && p.fallback == 0 && p.tpl == 1 && !p.group_dedup)
+        return launch_mlp_filter_pf(p, m, alg, tile_w, mask_dim, err, stream);
     if (mlp_filter_ext_applies(p, alg)) return launch_mlp_filter_ext(p, m, alg, tile_w, mask_dim, err, stream);
     if (mlp_filter_ws_applies(p, alg))
         return p.group_dedup ? launch_mlp_filter_ws(p, m, alg, tile_w, mask_dim, err, stream)

@@ -91,11 +91,15 @@ constexpr int kPQ = kPRows + 16;                 // fallback variant: 256 x int2
 constexpr int kPUL = kPQ + 2048;                 // fallback variant: 256 x int2 upper-left texel of the footprint
 
 // kFb: the variant with fallbacks C / C+ (two stages, to make room for the
-// texel tables and the per-pixel texels the blend of eq. 1 needs).
-template <bool kFb>
+// texel tables and the per-pixel texels the blend of eq. 1 needs); kList:
+// List Merge (two stages and a List Merge table per producer warp, at the
+// place of the fallback tables).
+template <bool kFb, bool kList = false>
 struct PLayout {
-    static constexpr int kStages = kFb ? 2 : 3;
-    static constexpr int kStage0 = kFb ? kPFbTab + 8 * (int)sizeof(FbTable) : kPFbTab;
+    static_assert(!(kFb && kList), "List Merge with fallbacks runs on the extension kernel");
+    static constexpr int kStages = (kFb || kList) ? 2 : 3;
+    static constexpr int kStage0 = kFb ? kPFbTab + 8 * (int)sizeof(FbTable)
+                                       : (kList ? kPFbTab + kPProducerWarps * (int)sizeof(ListTable) : kPFbTab);
     static constexpr int kStageBytes = kFb ? kPUL + 2048 : kPRows + 16;
     static constexpr int kBytes = kStage0 + kStages * kStageBytes;
     static_assert(kStage0 % 16 == 0 && kStageBytes % 16 == 0 && kPFbTab % 16 == 0, "16-byte operand buffers");
@@ -104,9 +108,9 @@ struct PLayout {
 };
 static_assert(65536 / (kPThreads * kPLaunchRegs) <= 4, "at most four CTAs share an SM's TMEM");
 
-template <bool kFb>
+template <bool kFb, bool kList>
 __device__ __forceinline__ unsigned char *p_stage(unsigned char *sm, int s) {
-    return sm + PLayout<kFb>::kStage0 + s * PLayout<kFb>::kStageBytes;
+    return sm + PLayout<kFb, kList>::kStage0 + s * PLayout<kFb, kList>::kStageBytes;
 }
 __device__ __forceinline__ uint64_t *p_full(unsigned char *sm, int s) {
     return reinterpret_cast<uint64_t *>(sm + kPHand) + s;
@@ -292,7 +296,7 @@ __device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64
 template <int ALG, int TW, int MD, bool kStats, bool kFb>
 __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp, long long first, int g,
                                         unsigned char *st, int2 *list, int lane, uint32_t lt, int *ranks,
-                                        Counters &cnt, FbTable *fbt) {
+                                        Counters &cnt, FbTable *fbt, ListTable *T) {
     constexpr int TH = 32 / TW;
     const int tx = lane % TW, ty = lane / TW;
     float2 *pix_st = reinterpret_cast<float2 *>(st + kPST);
@@ -318,7 +322,7 @@ __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp,
     setup_coords(uv, (float)p.Wt, (float)p.Ht, ps);
     Selection sel;
     if (valid) {
-        sel = select_tile<ALG, MD, kStats, false>(p, ps, jac, px, py, lane, lt, nullptr, ranks, cnt);
+        sel = select_tile<ALG, MD, kStats, false>(p, ps, jac, px, py, lane, lt, T, ranks, cnt);
     } else {
         sel.path = PATH_EMPTY;
         sel.A = 0;
@@ -426,13 +430,20 @@ __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp
 
 template <int ALG, int TW, int MD, bool kStats, bool kFb>
 __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(const ExactParams p, const MlpDevice m, int *err) {
-    constexpr int kPStages = PLayout<kFb>::kStages;
+    constexpr bool kList = ALG == ALG_LIST;
+    constexpr int kPStages = PLayout<kFb, kList>::kStages;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned long long block_stats[kNumStats];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // fallback variant: warp w's texel table (empty between tiles)
     FbTable *fbt = kFb ? reinterpret_cast<FbTable *>(sm + kPFbTab) + warp : nullptr;
     if (kFb) fb_clear(fbt, lane);
+    // List Merge: producer warp w - 4's table (empty between tiles)
+    ListTable *T = kList && warp >= 4 ? reinterpret_cast<ListTable *>(sm + kPFbTab) + (warp - 4) : nullptr;
+    if (kList && warp >= 4) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) T->keys[lane * 8 + q] = kEmpty;
+    }
     uint64_t *mma_bar = reinterpret_cast<uint64_t *>(sm + kPBar);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kPTmem);
     if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
@@ -475,7 +486,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
             if (grp >= n_groups) break;
             const int s = (int)(j % kPStages);
             const uint32_t par = (uint32_t)((j / kPStages) & 1);
-            unsigned char *st = p_stage<kFb>(sm, s);
+            unsigned char *st = p_stage<kFb, kList>(sm, s);
             bool ok = true;
             if (tid == 0) ok = tc::mbar_wait(p_full(sm, s), par, kMaxTries);
             __syncwarp();
@@ -522,7 +533,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
             if (!have) break;
             {
                 const int s = (int)(j % kPStages);
-                unsigned char *st = p_stage<kFb>(sm, s);
+                unsigned char *st = p_stage<kFb, kList>(sm, s);
                 if (j >= kPStages) {
                     // the consumer has gathered group j - kPStages from this stage
                     bool okd = true;
@@ -540,7 +551,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 const TilePos tp = tile_pos0(p, first);
 #pragma unroll 1
                 for (int k = 0; k < kPSlots; ++k)
-                    p_step1<ALG, TW, MD, kStats, kFb>(p, tp, first, kPSlots * pw + k, st, list, lane, lt, ranks, cnt, fbt);
+                    p_step1<ALG, TW, MD, kStats, kFb>(p, tp, first, kPSlots * pw + k, st, list, lane, lt, ranks, cnt, fbt, T);
                 __syncwarp();
                 prod_bar();  // every slot's list and count is in place
                 // rows: slot g owns [start_g, start_g + count_g) in slot order;
@@ -607,6 +618,7 @@ template <int TW, bool kStats, bool kFb>
 PfFn pf_pick(int alg, int md) {
     switch (alg) {
     case ALG_STF: return kFb ? nullptr : mlp_filter_pf_kernel<ALG_STF, TW, 16, kStats, false>;
+    case ALG_LIST: return kFb ? nullptr : mlp_filter_pf_kernel<ALG_LIST, TW, 16, kStats, false>;
     case ALG_BOX: return mlp_filter_pf_kernel<ALG_BOX, TW, 16, kStats, kFb>;
     case ALG_MASK:
         return md == 11 ? mlp_filter_pf_kernel<ALG_MASK, TW, 11, kStats, kFb> : mlp_filter_pf_kernel<ALG_MASK, TW, 16, kStats, kFb>;
@@ -648,7 +660,9 @@ cudaError_t pf_prepare(PfFn fn, int smem_bytes) {
     return e;
 }
 
-int pf_smem(bool fb) { return fb ? PLayout<true>::kBytes : PLayout<false>::kBytes; }
+int pf_smem(bool fb, int alg) {
+    return fb ? PLayout<true>::kBytes : (alg == ALG_LIST ? PLayout<false, true>::kBytes : PLayout<false>::kBytes);
+}
 
 }  // namespace
 
@@ -659,10 +673,10 @@ bool mlp_filter_pf_fallback_applies(const ExactParams &p, int alg) {
 cudaError_t prepare_mlp_filter_pf(int alg, int tile_w, int mask_dim) {
     for (int v = 0; v < 4; ++v) {
         const bool st = (v & 1) != 0, fb = (v & 2) != 0;
-        if (fb && alg == ALG_STF) continue;
+        if (fb && (alg == ALG_STF || alg == ALG_LIST)) continue;
         PfFn fn = pf_kernel(alg, tile_w, mask_dim, st, fb);
         if (!fn) return cudaErrorInvalidValue;
-        const cudaError_t e = pf_prepare(fn, pf_smem(fb));
+        const cudaError_t e = pf_prepare(fn, pf_smem(fb, alg));
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -676,12 +690,12 @@ cudaError_t launch_mlp_filter_pf(const ExactParams &p, const MlpDevice &m, int a
     if (!fn) return cudaErrorInvalidValue;
     if (p.n_tiles == 0) return cudaSuccess;
     if (p.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile positions use 32-bit arithmetic
-    cudaError_t e = pf_prepare(fn, pf_smem(fb));
+    cudaError_t e = pf_prepare(fn, pf_smem(fb, alg));
     if (e != cudaSuccess) return e;
     const long long groups = (p.n_tiles + kGroupTiles - 1) / kGroupTiles;
     const long long cap = (long long)device_sm_count() * kPCtasPerSm;
     const int grid = (int)(groups < cap ? groups : cap);
-    fn<<<grid, kPThreads, pf_smem(fb), stream>>>(p, m, err);
+    fn<<<grid, kPThreads, pf_smem(fb, alg), stream>>>(p, m, err);
     return cudaGetLastError();
 }
 
