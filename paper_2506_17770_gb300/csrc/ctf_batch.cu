@@ -45,13 +45,6 @@ constexpr int kMaxViews = 4096;
 constexpr int kSmViews = 1024;         // item prefixes cached in shared memory up to this many views
 constexpr int kSmViewsMlp = 256;       // the same for the learned kernel (4 CTAs of it share an SM)
 
-struct __align__(16) BatchViewDev {
-    ExactParams p;
-    MlpDevice m;
-    int learned;
-};
-static_assert(sizeof(BatchViewDev) % 16 == 0, "copied in 16-byte pieces");
-static_assert(sizeof(ExactParams) % 16 == 0 && sizeof(ExactParams) <= 32 * 16, "copied in 16-byte pieces");
 
 // One kind of views: their indices in the view table and item prefix.
 struct BatchParams {
@@ -518,6 +511,13 @@ cudaError_t launch_plan(const Plan &plan, const DevPlan &dp, int alg, const Reso
         b.stats = stats;
         b.err = err;
         b.tables = k == 0 ? plan.views[plan.index[0][0]].p.tables : nullptr;
+        if (k == 1 && mlp_batch_pf_applies(alg, r.group_dedup)) {
+            // learned views on the packed-group kernel (one group per fetch)
+            e = launch_mlp_batch_pf(dp.views, (int)plan.views.size(), dp.index[1], dp.begin[1], b.nkind, b.total_items,
+                                    b.counter, stats, err, plan.views[plan.index[1][0]].m, alg, r.tile_w, r.mask_dim, s);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         if (k == 1) {
             e = prepare_batch(fn);
             if (e != cudaSuccess) return e;
@@ -620,6 +620,8 @@ int ctf_batch_graph_create(const ctf_view *views, int nviews, ctf_algorithm alg,
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     // the kernel attributes must be set before capture
     if (e == cudaSuccess && plan.items[1]) e = prepare_batch(pick(true, (int)alg, r.tile_w, r.mask_dim, false));
+    if (e == cudaSuccess && plan.items[1] && mlp_batch_pf_applies((int)alg, r.group_dedup))
+        e = prepare_mlp_batch_pf((int)alg, r.tile_w, r.mask_dim);
     for (int i : plan.solo)
         if (e == cudaSuccess && plan.views[i].learned) e = prepare_mlp_filter((int)alg, r.tile_w, r.mask_dim);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);

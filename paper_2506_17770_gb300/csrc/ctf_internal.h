@@ -154,6 +154,26 @@ cudaError_t prepare_mlp_filter_ws(int alg, int tile_w, int mask_dim);
 cudaError_t launch_mlp_filter_ws(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim,
                                  int *err, cudaStream_t stream);
 
+// One view of a batch plan on the device (ctf_batch.cu).
+struct __align__(16) BatchViewDev {
+    ExactParams p;
+    MlpDevice m;
+    int learned;
+};
+static_assert(sizeof(BatchViewDev) % 16 == 0, "copied in 16-byte pieces");
+static_assert(sizeof(ExactParams) % 16 == 0 && sizeof(ExactParams) <= 32 * 16, "copied in 16-byte pieces");
+
+// The learned views of a batch (other than per-pixel 4-tap and group_dedup)
+// on the packed-group kernel (ctf_mlp_ws2.cu): the views index[0..nkind)
+// of the table of nviews views, whose items (groups of 8 tiles) are numbered from
+// item_begin[k]; the CTAs take items from *counter (zero at launch).  m0 is
+// the first view's network, which the CTAs load first.
+bool mlp_batch_pf_applies(int alg, int group_dedup);
+cudaError_t prepare_mlp_batch_pf(int alg, int tile_w, int mask_dim);
+cudaError_t launch_mlp_batch_pf(const BatchViewDev *views, int nviews, const int *index, const long long *item_begin,
+                                int nkind, long long total_items, unsigned long long *counter, unsigned long long *stats,
+                                int *err, const MlpDevice &m0, int alg, int tile_w, int mask_dim, cudaStream_t s);
+
 // Error reporting shared by the C ABI translation units (ctf_api.cu).
 int report(int status, const char *fmt, ...);
 int report_cuda(cudaError_t e, const char *what);

@@ -94,13 +94,19 @@ constexpr int kPUL = kPQ + 2048;                 // fallback variant: 256 x int2
 // texel tables and the per-pixel texels the blend of eq. 1 needs); kList:
 // List Merge (two stages and a List Merge table per producer warp, at the
 // place of the fallback tables).
-template <bool kFb, bool kList = false>
+// kBatch: the persistent batch kernel, whose stages also carry the group's
+// view (at kPBat: its slot, the group's first tile, copies of its
+// parameters and network).
+constexpr int kPBat = kPRows + 16;
+constexpr int kPBatBytes = 16 + (int)sizeof(ExactParams) + (((int)sizeof(MlpDevice) + 15) & ~15);
+template <bool kFb, bool kList = false, bool kBatch = false>
 struct PLayout {
     static_assert(!(kFb && kList), "List Merge with fallbacks runs on the extension kernel");
+    static_assert(!(kFb && kBatch), "batches take no fallbacks on learned views");
     static constexpr int kStages = (kFb || kList) ? 2 : 3;
     static constexpr int kStage0 = kFb ? kPFbTab + 8 * (int)sizeof(FbTable)
                                        : (kList ? kPFbTab + kPProducerWarps * (int)sizeof(ListTable) : kPFbTab);
-    static constexpr int kStageBytes = kFb ? kPUL + 2048 : kPRows + 16;
+    static constexpr int kStageBytes = kFb ? kPUL + 2048 : kPRows + 16 + (kBatch ? kPBatBytes : 0);
     static constexpr int kBytes = kStage0 + kStages * kStageBytes;
     static_assert(kStage0 % 16 == 0 && kStageBytes % 16 == 0 && kPFbTab % 16 == 0, "16-byte operand buffers");
     // kPCtasPerSm CTAs per SM fit, and no more than four (4 x 128 TMEM columns)
@@ -108,9 +114,9 @@ struct PLayout {
 };
 static_assert(65536 / (kPThreads * kPLaunchRegs) <= 4, "at most four CTAs share an SM's TMEM");
 
-template <bool kFb, bool kList>
+template <bool kFb, bool kList, bool kBatch = false>
 __device__ __forceinline__ unsigned char *p_stage(unsigned char *sm, int s) {
-    return sm + PLayout<kFb, kList>::kStage0 + s * PLayout<kFb, kList>::kStageBytes;
+    return sm + PLayout<kFb, kList, kBatch>::kStage0 + s * PLayout<kFb, kList, kBatch>::kStageBytes;
 }
 __device__ __forceinline__ uint64_t *p_full(unsigned char *sm, int s) {
     return reinterpret_cast<uint64_t *>(sm + kPHand) + s;
@@ -612,6 +618,244 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
         atomicAdd(p.stats + threadIdx.x, block_stats[threadIdx.x]);
 }
 
+// Last view whose first item is <= item (views without items share the
+// next view's first item, so they are skipped).
+__device__ __forceinline__ int find_batch_view(const long long *begin, int nviews, long long item) {
+    int lo = 0, hi = nviews - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(begin + mid) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The learned views of a batch: the packed-group kernel made persistent.
+// The producers take groups (items of 8 tiles) from a global counter, find
+// the group's view, copy its parameters and network into the stage and run
+// step 1 and the features as for one view; the consumer runs the chains and
+// the gather with the stage's copies, and reloads the operand image when a
+// group's network is not the one in shared memory (between chains, when no
+// MMA is in flight).  A stage whose view slot is -1 ends the CTA's work.
+struct PfBatch {
+    const BatchViewDev *views;
+    const int *index;
+    const long long *item_begin;
+    int nkind, nviews;
+    long long total_items;
+    unsigned long long *counter;
+    unsigned long long *stats;
+    int *err;
+};
+
+template <int ALG, int TW, int MD, bool kStats>
+__global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_batch_pf_kernel(const PfBatch b, const MlpDevice m0) {
+    constexpr bool kList = ALG == ALG_LIST;
+    constexpr int kPStages = PLayout<false, kList, true>::kStages;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ unsigned long long block_stats[kNumStats];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ListTable *T = kList && warp >= 4 ? reinterpret_cast<ListTable *>(sm + kPFbTab) + (warp - 4) : nullptr;
+    if (kList && warp >= 4) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) T->keys[lane * 8 + q] = kEmpty;
+    }
+    uint64_t *mma_bar = reinterpret_cast<uint64_t *>(sm + kPBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kPTmem);
+    if (threadIdx.x < kNumStats) block_stats[threadIdx.x] = 0;
+    {
+        const uint4 *src = m0.img;
+        uint4 *dst = reinterpret_cast<uint4 *>(sm + kImgW1);
+        for (int i = threadIdx.x; i < kImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    if (threadIdx.x == 0) {
+        tc::mbar_init(mma_bar, 1);
+        for (int s = 0; s < kPStages; ++s) {
+            tc::mbar_init(p_full(sm, s), kPProducerWarps);
+            tc::mbar_init(p_done(sm, s), 1);
+        }
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    Counters cnt;
+#pragma unroll
+    for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
+    int *err = b.err;
+
+    if (warp < 4) {
+        // ---------------- consumer ----------------
+        if (kPSplitRegs) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kPConsumerRegs));
+        const int tid = threadIdx.x;
+        uint32_t phase = 0;
+        const uint4 *loaded = m0.img;
+        for (long long j = 0;; ++j) {
+            const int s = (int)(j % kPStages);
+            const uint32_t par = (uint32_t)((j / kPStages) & 1);
+            unsigned char *st = p_stage<false, kList, true>(sm, s);
+            bool ok = true;
+            if (tid == 0) ok = tc::mbar_wait(p_full(sm, s), par, kMaxTries);
+            __syncwarp();
+            if (bar_or<1, kRows>(!ok)) {
+                if (tid == 0) atomicExch(err, CTF_ERR_TIMEOUT);
+                break;
+            }
+            const int *bm = reinterpret_cast<const int *>(st + kPBat);
+            if (bm[0] < 0) break;  // no more groups
+            const long long first = *reinterpret_cast<const long long *>(st + kPBat + 8);
+            const ExactParams &p = *reinterpret_cast<const ExactParams *>(st + kPBat + 16);
+            const MlpDevice &m = *reinterpret_cast<const MlpDevice *>(st + kPBat + 16 + sizeof(ExactParams));
+            if (m.img != loaded) {
+                // another network: its operand image (every MMA of the last chain is done)
+                const uint4 *src = m.img;
+                uint4 *dst = reinterpret_cast<uint4 *>(sm + kImgW1);
+                for (int i = tid; i < kImgBytes / 16; i += kRows) dst[i] = __ldg(src + i);
+                tc::fence_proxy_async();  // generic-proxy writes -> the MMAs' async proxy
+                cons_bar();
+                loaded = m.img;
+            }
+            const bool fp8 = m.fp8 != 0;
+            const int R = *reinterpret_cast<const int *>(st + kPRows);
+            const int passes = (R + kRows - 1) / kRows;
+            float4 *outrow = reinterpret_cast<float4 *>(st + kPX);
+            const uint32_t sX = tc::smem_addr(st + kPX);
+            for (int c = 0; c < passes && ok; ++c) {
+                const bool live = kRows * c + 32 * warp < R;
+                float4 v;
+                ok = p_chain(sm, tmem, mma_bar, phase, sX + 4096u * (uint32_t)c, fp8, live, v, err);
+                if (ok && live) outrow[ck(kRows * c + tid, 2 * kRows, err, kBndRow)] = v;
+                cons_bar();
+            }
+            if (!ok) break;
+            {
+                const TilePos tpc = tile_pos0(p, first);
+#pragma unroll 1
+                for (int k = 0; k < 2; ++k) p_gather<TW, false>(p, tpc, 4 * k + warp, st, tid & 31, nullptr);
+            }
+            __syncwarp();
+            cons_bar();  // every consumer warp has read the stage
+            if (tid == 0) p_arrive(p_done(sm, s));
+        }
+    } else {
+        // ---------------- producers ----------------
+        if (kPSplitRegs) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kPProducerRegs));
+        const int pw = warp - 4;
+        const uint32_t lt = lanemask_lt();
+        int *ranks = reinterpret_cast<int *>(sm + kPRanks) + 32 * pw;
+        int2 *list = reinterpret_cast<int2 *>(sm + kPList);
+        const int pt = threadIdx.x - kRows;  // producer thread
+        for (long long j = 0;; ++j) {
+            const int s = (int)(j % kPStages);
+            unsigned char *st = p_stage<false, kList, true>(sm, s);
+            if (j >= kPStages) {
+                // the consumer has gathered group j - kPStages from this stage
+                bool okd = true;
+                if (lane == 0) okd = tc::mbar_wait(p_done(sm, s), (uint32_t)(((j - kPStages) / kPStages) & 1), kMaxTries);
+                __syncwarp();
+                if (bar_or<2, kPProducerThreads>(!okd)) {
+                    if (threadIdx.x == 128) atomicExch(err, CTF_ERR_TIMEOUT);
+                    break;
+                }
+            }
+            // every producer warp has read the texel lists of the last group
+            __syncwarp();
+            prod_bar();
+            int *bm = reinterpret_cast<int *>(st + kPBat);
+            if (pt == 0) *reinterpret_cast<long long *>(st + kPBat + 8) = (long long)atomicAdd(b.counter, 1ull);
+            prod_bar();
+            const long long item = *reinterpret_cast<volatile long long *>(st + kPBat + 8);
+            if (item >= b.total_items) {
+                if (pt == 0) bm[0] = -1;
+                __syncwarp();
+                if (lane == 0) p_arrive(p_full(sm, s));
+                break;
+            }
+            const int vk = ck(find_batch_view(b.item_begin, b.nkind, item), b.nkind, err, kBndBatch);
+            const BatchViewDev *V = b.views + ck(__ldg(b.index + vk), b.nviews, err, kBndBatch);
+            {
+                // the view's parameters and network into the stage
+                const uint4 *src = reinterpret_cast<const uint4 *>(&V->p);
+                uint4 *dst = reinterpret_cast<uint4 *>(st + kPBat + 16);
+                if (pt < (int)(sizeof(ExactParams) / 16)) dst[pt] = __ldg(src + pt);
+                const uint2 *msrc = reinterpret_cast<const uint2 *>(&V->m);
+                uint2 *mdst = reinterpret_cast<uint2 *>(st + kPBat + 16 + sizeof(ExactParams));
+                if (pt < (int)(sizeof(MlpDevice) / 8)) mdst[pt] = __ldg(msrc + pt);
+            }
+            const long long first = (item - __ldg(b.item_begin + vk)) * kGroupTiles;
+            prod_bar();  // the copies are in place
+            if (pt == 0) {
+                bm[0] = vk;
+                *reinterpret_cast<long long *>(st + kPBat + 8) = first;
+            }
+            const ExactParams &p = *reinterpret_cast<const ExactParams *>(st + kPBat + 16);
+            const MlpDevice &m = *reinterpret_cast<const MlpDevice *>(st + kPBat + 16 + sizeof(ExactParams));
+            const bool fp8 = m.fp8 != 0;
+            const float *inv_a1 = reinterpret_cast<const float *>(reinterpret_cast<const unsigned char *>(m.img) + kImgA1);
+            const TilePos tp = tile_pos0(p, first);
+#pragma unroll 1
+            for (int k = 0; k < kPSlots; ++k)
+                p_step1<ALG, TW, MD, kStats, false>(p, tp, first, kPSlots * pw + k, st, list, lane, lt, ranks, cnt,
+                                                    nullptr, T);
+            __syncwarp();
+            prod_bar();  // every slot's list and count is in place
+            const int *count = reinterpret_cast<const int *>(st + kPCount);
+            int R = 0, g0 = 0, b0 = 0, g1 = 0, b1 = 0, mybase = 0;
+#pragma unroll
+            for (int g = 0; g < kGroupTiles; ++g) {
+                if (pt >= R) {
+                    g0 = g;
+                    b0 = R;
+                }
+                if (pt + kPProducerThreads >= R) {
+                    g1 = g;
+                    b1 = R;
+                }
+                if (pt == g) mybase = R;
+                R += count[g];
+            }
+            if (pt < kGroupTiles) reinterpret_cast<int *>(st + kPBase)[pt] = mybase;
+            if (pt == 0) {
+                *reinterpret_cast<int *>(st + kPRows) = R;
+                if (kStats) cnt.v[kStatTexelEvalsUnique] += R;
+            }
+#pragma unroll 1
+            for (int c = 0; c < kPFeatRounds; ++c) {
+                const int row = pt + kPProducerThreads * c;
+                if (row >= R) break;
+                const int2 t = c == 0 ? list[32 * g0 + ck(row - b0, 32, err, kBndTexList)]
+                                      : list[32 * g1 + ck(row - b1, 32, err, kBndTexList)];
+                float f[kMlpIn];
+                texel_features(m, t.x, t.y, f);
+                store_x_row_at(st + kPX, ck(row, 2 * kRows, err, kBndRow), f, fp8, inv_a1);
+            }
+            tc::fence_proxy_async();  // generic-proxy writes -> the MMAs' async proxy
+            __syncwarp();
+            if (lane == 0) p_arrive(p_full(sm, s));
+        }
+    }
+
+    if (kStats && b.stats && lane == 0) {
+#pragma unroll
+        for (int i = 0; i < kNumStats; ++i)
+            if (cnt.v[i]) atomicAdd(&block_stats[i], (unsigned long long)cnt.v[i]);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();  // tcgen05.dealloc needs the whole warp
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
+    if (kStats && b.stats && threadIdx.x < kNumStats && block_stats[threadIdx.x])
+        atomicAdd(b.stats + threadIdx.x, block_stats[threadIdx.x]);
+}
+
 using PfFn = void (*)(const ExactParams, const MlpDevice, int *);
 
 template <int TW, bool kStats, bool kFb>
@@ -696,6 +940,72 @@ cudaError_t launch_mlp_filter_pf(const ExactParams &p, const MlpDevice &m, int a
     const long long cap = (long long)device_sm_count() * kPCtasPerSm;
     const int grid = (int)(groups < cap ? groups : cap);
     fn<<<grid, kPThreads, pf_smem(fb, alg), stream>>>(p, m, err);
+    return cudaGetLastError();
+}
+
+namespace {
+using BatchPfFn = void (*)(const PfBatch, const MlpDevice);
+
+template <int TW, bool kStats>
+BatchPfFn batch_pf_pick(int alg, int md) {
+    switch (alg) {
+    case ALG_STF: return mlp_batch_pf_kernel<ALG_STF, TW, 16, kStats>;
+    case ALG_LIST: return mlp_batch_pf_kernel<ALG_LIST, TW, 16, kStats>;
+    case ALG_BOX: return mlp_batch_pf_kernel<ALG_BOX, TW, 16, kStats>;
+    case ALG_MASK: return md == 11 ? mlp_batch_pf_kernel<ALG_MASK, TW, 11, kStats> : mlp_batch_pf_kernel<ALG_MASK, TW, 16, kStats>;
+    default: return nullptr;
+    }
+}
+
+BatchPfFn batch_pf_kernel(int alg, int tile_w, int md, bool st) {
+    switch (tile_w) {
+    case 8: return st ? batch_pf_pick<8, true>(alg, md) : batch_pf_pick<8, false>(alg, md);
+    case 4: return st ? batch_pf_pick<4, true>(alg, md) : batch_pf_pick<4, false>(alg, md);
+    case 16: return st ? batch_pf_pick<16, true>(alg, md) : batch_pf_pick<16, false>(alg, md);
+    default: return nullptr;
+    }
+}
+
+int batch_pf_smem(int alg) {
+    return alg == ALG_LIST ? PLayout<false, true, true>::kBytes : PLayout<false, false, true>::kBytes;
+}
+}  // namespace
+
+bool mlp_batch_pf_applies(int alg, int group_dedup) {
+    return (alg == ALG_STF || alg == ALG_LIST || alg == ALG_BOX || alg == ALG_MASK) && !group_dedup;
+}
+
+cudaError_t prepare_mlp_batch_pf(int alg, int tile_w, int mask_dim) {
+    for (int st = 0; st < 2; ++st) {
+        BatchPfFn fn = batch_pf_kernel(alg, tile_w, mask_dim, st != 0);
+        if (!fn) return cudaErrorInvalidValue;
+        const cudaError_t e = pf_prepare(reinterpret_cast<PfFn>(fn), batch_pf_smem(alg));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_mlp_batch_pf(const BatchViewDev *views, int nviews, const int *index, const long long *item_begin,
+                                int nkind, long long total_items, unsigned long long *counter, unsigned long long *stats,
+                                int *err, const MlpDevice &m0, int alg, int tile_w, int mask_dim, cudaStream_t s) {
+    BatchPfFn fn = batch_pf_kernel(alg, tile_w, mask_dim, stats != nullptr);
+    if (!fn) return cudaErrorInvalidValue;
+    if (total_items <= 0) return cudaSuccess;
+    cudaError_t e = pf_prepare(reinterpret_cast<PfFn>(fn), batch_pf_smem(alg));
+    if (e != cudaSuccess) return e;
+    PfBatch b;
+    b.views = views;
+    b.index = index;
+    b.item_begin = item_begin;
+    b.nkind = nkind;
+    b.nviews = nviews;
+    b.total_items = total_items;
+    b.counter = counter;
+    b.stats = stats;
+    b.err = err;
+    const long long cap = (long long)device_sm_count() * kPCtasPerSm;
+    const int grid = (int)(total_items < cap ? total_items : cap);
+    fn<<<grid, kPThreads, batch_pf_smem(alg), s>>>(b, m0);
     return cudaGetLastError();
 }
 
