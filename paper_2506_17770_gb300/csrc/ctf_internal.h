@@ -141,6 +141,9 @@ bool mlp_filter_ws_applies(const ExactParams &p, int alg);
 // Box and Mask with fallback C / C+ and one texel per lane run the
 // fallback variant of the packed-group kernel (ctf_mlp_ws2.cu).
 bool mlp_filter_pf_fallback_applies(const ExactParams &p, int alg);
+// List Merge, Box and Mask with two texels per lane and no fallback: its
+// variant with groups of 4 tiles.
+bool mlp_filter_pf_two_applies(const ExactParams &p, int alg);
 cudaError_t prepare_mlp_filter_pf(int alg, int tile_w, int mask_dim);
 // The learned filter with fallbacks C / C+ or two texels per lane
 // (ctf_mlp_ext.cu), for List Merge, Box and Mask Sampling.

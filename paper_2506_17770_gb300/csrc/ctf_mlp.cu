@@ -204,7 +204,8 @@ cudaError_t launch_bounded_wait_selftest(uint32_t polls, int *err, cudaStream_t 
 cudaError_t launch_mlp_filter(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                               cudaStream_t stream) {
     // fallbacks C / C+ with one texel per lane on Box and Mask: the packed-group kernel's fallback variant
-    if (mlp_filter_pf_fallback_applies(p, alg)) return launch_mlp_filter_pf(p, m, alg, tile_w, mask_dim, err, stream);
+    if (mlp_filter_pf_fallback_applies(p, alg) || mlp_filter_pf_two_applies(p, alg))
+        return launch_mlp_filter_pf(p, m, alg, tile_w, mask_dim, err, stream);
     // List Merge without extensions or group_dedup: the packed-group kernel's List Merge variant
     if (alg == ALG_LIST && p.fallback == 0 && p.tpl == 1 && !p.group_dedup)
         return launch_mlp_filter_pf(p, m, alg, tile_w, mask_dim, err, stream);

@@ -77,8 +77,9 @@ constexpr int kPMaxStages = 3;
 constexpr int kPBar = kImgBytes;                 // MMA barrier (8 B), TMEM base (4 B)
 constexpr int kPTmem = kPBar + 8;
 constexpr int kPHand = kPBar + 16;               // full[kPMaxStages], done[kPMaxStages]
-constexpr int kPRanks = kPHand + 16 * kPMaxStages;          // producer warps x 32 ints
-constexpr int kPList = kPRanks + kPProducerWarps * 32 * 4;  // 8 slots x 32 int2 texel lists
+// producer warps x 64 rank slots (two texels per lane may rank 64 texels a tile)
+constexpr int kPRanks = kPHand + 16 * kPMaxStages;
+constexpr int kPList = kPRanks + kPProducerWarps * 64 * 4;  // 8 slots x 32 (or 4 x 64) int2 texel lists
 constexpr int kPFbTab = kPList + kGroupTiles * 32 * 8;      // fallback variant: 8 warps' texel tables
 // one stage
 constexpr int kPX = 0;                           // 256 rows x 32 B layer-1 operand; row values overlay 0..4095
@@ -299,7 +300,11 @@ __device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64
 // the producing lanes, and the pixel's word carries bit 26 (fallback tile)
 // and bit 27 (this lane produces); the produced texel and the footprint's
 // upper-left texel go to the stage for the blend of eq. 1.
-template <int ALG, int TW, int MD, bool kStats, bool kFb>
+// kTwo: the variant with two texels per lane (groups of 4 tiles of up to 64
+// texels): the tile's list at list[64 g + rank]; the pixel's word holds the
+// 6-bit list indices of its taps (bits 0-23, or of its own texel), its count
+// (24-25), active (26), inside (27) and success (28).
+template <int ALG, int TW, int MD, bool kStats, bool kFb, bool kTwo = false>
 __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp, long long first, int g,
                                         unsigned char *st, int2 *list, int lane, uint32_t lt, int *ranks,
                                         Counters &cnt, FbTable *fbt, ListTable *T) {
@@ -328,13 +333,29 @@ __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp,
     setup_coords(uv, (float)p.Wt, (float)p.Ht, ps);
     Selection sel;
     if (valid) {
-        sel = select_tile<ALG, MD, kStats, false>(p, ps, jac, px, py, lane, lt, T, ranks, cnt);
+        sel = select_tile<ALG, MD, kStats, false, kTwo>(p, ps, jac, px, py, lane, lt, T, ranks, cnt);
     } else {
         sel.path = PATH_EMPTY;
         sel.A = 0;
-        sel.produce = false;
+        sel.produce = sel.produce2 = false;
         sel.count = 0;
-        sel.my_rank = 0;
+        sel.my_rank = sel.my_rank2 = 0;
+    }
+    if (kTwo) {
+        auto clamp_xy = [&](int x, int y) { return make_int2(min(max(x, 0), p.Wt - 1), min(max(y, 0), p.Ht - 1)); };
+        if (sel.produce) list[64 * g + ck(sel.my_rank, 64, p.err, kBndTexList)] = clamp_xy(sel.tx, sel.ty);
+        if (sel.produce2) list[64 * g + ck(sel.my_rank2, 64, p.err, kBndTexList)] = clamp_xy(sel.tx2, sel.ty2);
+        const bool succ = sel.path == PATH_SUCCESS;
+        if (lane == 0) reinterpret_cast<int *>(st + kPCount)[g] = succ ? sel.n : __popc(sel.A);
+        uint32_t info = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) info |= ((uint32_t)sel.rk[k] & 63u) << (6 * k);
+        info = succ ? info : ((uint32_t)sel.my_rank & 63u);
+        info |= ((uint32_t)sel.count << 24) | (ps.active ? 1u << 26 : 0u) | (inside ? 1u << 27 : 0u) |
+                (succ ? 1u << 28 : 0u);
+        reinterpret_cast<float2 *>(st + kPST)[32 * g + lane] = make_float2(ps.s, ps.t);
+        reinterpret_cast<uint32_t *>(st + kPInfo)[32 * g + lane] = info;
+        return;
     }
     if (kFb && p.fallback != 0 && sel.path == PATH_FALLBACK_BUDGET) {  // warp-uniform
         const FbChoice c = fb_choose(p.fallback, p.view, p.y0, p.k0, p.k1, ps.ulx, ps.uly, ps.s, ps.t, ps.active, px,
@@ -373,7 +394,7 @@ __device__ __forceinline__ void p_step1(const ExactParams &p, const TilePos &tp,
 
 // Consumer: step 3 for tile slot g of the group at `first` from stage st
 // (its row values in place): gather, filter, store; `lane` is the pixel.
-template <int TW, bool kFb>
+template <int TW, bool kFb, bool kTwo = false>
 __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp, int g, const unsigned char *st,
                                          int lane, FbTable *fbt) {
     constexpr int TH = 32 / TW;
@@ -385,7 +406,11 @@ __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp
     auto row_of = [&](uint32_t i) { return ck(base + (int)i, 2 * kRows, p.err, kBndRow); };
     int bx, by;
     tile_pos(tp, g, bx, by);
-    const bool inside = ((info >> 24) & 1u) != 0;  // (pixels outside the frame take part in the blend only)
+    // the word's fields (kTwo: 6-bit list indices)
+    constexpr int kIdxBits = kTwo ? 6 : 5, kCnt = kTwo ? 24 : 20, kAct = kTwo ? 26 : 23, kIns = kTwo ? 27 : 24,
+                  kSucc = kTwo ? 28 : 25;
+    constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u, kCntMask = kTwo ? 3u : 7u;
+    const bool inside = ((info >> kIns) & 1u) != 0;  // (pixels outside the frame take part in the blend only)
     const uint32_t idx = ck(inside ? (uint32_t)(by * TH + ty) * (uint32_t)p.W + (uint32_t)(bx * TW + tx) : 0u,
                             view_pixels(p), p.err, kBndPixel);
     if (kFb && ((info >> 26) & 1u)) {
@@ -410,23 +435,23 @@ __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp
     if (!inside) return;  // outside the frame (or no tile)
     float4 result = make_float4(0.f, 0.f, 0.f, 0.f);
     uint8_t cv = 0;
-    if ((info >> 23) & 1u) {
-        if ((info >> 25) & 1u) {
+    if ((info >> kAct) & 1u) {
+        if ((info >> kSucc) & 1u) {
             const float2 s = reinterpret_cast<const float2 *>(st + kPST)[32 * g + lane];
             float w[4];
             bilinear_weights(s.x, s.y, w);
             float2 rg = make_float2(0.f, 0.f), ba = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float4 t = outrow[row_of((info >> (5 * k)) & 31u)];
+                const float4 t = outrow[row_of((info >> (kIdxBits * k)) & kIdxMask)];
                 const float2 wk = make_float2(w[k], w[k]);
                 rg = __ffma2_rn(wk, make_float2(t.x, t.y), rg);
                 ba = __ffma2_rn(wk, make_float2(t.z, t.w), ba);
             }
             result = make_float4(rg.x, rg.y, ba.x, ba.y);
-            cv = (uint8_t)((info >> 20) & 7u);
+            cv = (uint8_t)((info >> kCnt) & kCntMask);
         } else {
-            result = outrow[row_of(info & 31u)];
+            result = outrow[row_of(info & kIdxMask)];
             cv = 1;
         }
     }
@@ -434,10 +459,14 @@ __device__ __forceinline__ void p_gather(const ExactParams &p, const TilePos &tp
     if (p.evals) p.evals[idx] = cv;
 }
 
-template <int ALG, int TW, int MD, bool kStats, bool kFb>
+template <int ALG, int TW, int MD, bool kStats, bool kFb, bool kTwo>
 __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(const ExactParams p, const MlpDevice m, int *err) {
+    static_assert(!(kFb && kTwo), "fallbacks with two texels per lane run on the extension kernel");
     constexpr bool kList = ALG == ALG_LIST;
     constexpr int kPStages = PLayout<kFb, kList>::kStages;
+    // tiles per group: two texels per lane may need 64 rows a tile
+    constexpr int kGT = kTwo ? kGroupTiles / 2 : kGroupTiles;
+    constexpr int kSlots = kGT / kPProducerWarps;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ unsigned long long block_stats[kNumStats];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -478,7 +507,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
     Counters cnt;
 #pragma unroll
     for (int i = 0; i < kNumStats; ++i) cnt.v[i] = 0;
-    const long long n_groups = (p.n_tiles + kGroupTiles - 1) / kGroupTiles;
+    const long long n_groups = (p.n_tiles + kGT - 1) / kGT;
     const long long G = gridDim.x;
     const bool fp8 = m.fp8 != 0;
 
@@ -517,9 +546,9 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
             if (!ok) break;
             {
                 // step 3 for the group: warp w the tiles w and 4 + w
-                const TilePos tpc = tile_pos0(p, grp * kGroupTiles);
+                const TilePos tpc = tile_pos0(p, grp * kGT);
 #pragma unroll 1
-                for (int k = 0; k < 2; ++k) p_gather<TW, kFb>(p, tpc, 4 * k + warp, st, tid & 31, fbt);
+                for (int k = 0; k < kSlots; ++k) p_gather<TW, kFb, kTwo>(p, tpc, 4 * k + warp, st, tid & 31, fbt);
             }
             __syncwarp();
             cons_bar();  // every consumer warp has read the stage
@@ -530,7 +559,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
         if (kPSplitRegs) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kPProducerRegs));
         const int pw = warp - 4;
         const uint32_t lt = lanemask_lt();
-        int *ranks = reinterpret_cast<int *>(sm + kPRanks) + 32 * pw;
+        int *ranks = reinterpret_cast<int *>(sm + kPRanks) + 64 * pw;
         int2 *list = reinterpret_cast<int2 *>(sm + kPList);
         const int pt = threadIdx.x - kRows;  // producer thread
         for (long long j = 0;; ++j) {
@@ -553,11 +582,12 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 // every producer warp has read the texel lists of group j - 1
                 __syncwarp();
                 prod_bar();
-                const long long first = grp * kGroupTiles;
+                const long long first = grp * kGT;
                 const TilePos tp = tile_pos0(p, first);
 #pragma unroll 1
-                for (int k = 0; k < kPSlots; ++k)
-                    p_step1<ALG, TW, MD, kStats, kFb>(p, tp, first, kPSlots * pw + k, st, list, lane, lt, ranks, cnt, fbt, T);
+                for (int k = 0; k < kSlots; ++k)
+                    p_step1<ALG, TW, MD, kStats, kFb, kTwo>(p, tp, first, kSlots * pw + k, st, list, lane, lt, ranks,
+                                                            cnt, fbt, T);
                 __syncwarp();
                 prod_bar();  // every slot's list and count is in place
                 // rows: slot g owns [start_g, start_g + count_g) in slot order;
@@ -566,7 +596,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 const int *count = reinterpret_cast<const int *>(st + kPCount);
                 int R = 0, g0 = 0, b0 = 0, g1 = 0, b1 = 0, mybase = 0;
 #pragma unroll
-                for (int g = 0; g < kGroupTiles; ++g) {
+                for (int g = 0; g < kGT; ++g) {
                     if (pt >= R) {
                         g0 = g;
                         b0 = R;
@@ -578,7 +608,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                     if (pt == g) mybase = R;
                     R += count[g];
                 }
-                if (pt < kGroupTiles) reinterpret_cast<int *>(st + kPBase)[pt] = mybase;
+                if (pt < kGT) reinterpret_cast<int *>(st + kPBase)[pt] = mybase;
                 if (pt == 0) {
                     *reinterpret_cast<int *>(st + kPRows) = R;
                     if (kStats) cnt.v[kStatTexelEvalsUnique] += R;
@@ -589,8 +619,9 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
                 for (int c = 0; c < kPFeatRounds; ++c) {
                     const int row = pt + kPProducerThreads * c;
                     if (row >= R) break;
-                    const int2 t = c == 0 ? list[32 * g0 + ck(row - b0, 32, p.err, kBndTexList)]
-                                          : list[32 * g1 + ck(row - b1, 32, p.err, kBndTexList)];
+                    constexpr int kLs = kTwo ? 64 : 32;  // list entries a tile
+                    const int2 t = c == 0 ? list[kLs * g0 + ck(row - b0, kLs, p.err, kBndTexList)]
+                                          : list[kLs * g1 + ck(row - b1, kLs, p.err, kBndTexList)];
                     float f[kMlpIn];
                     texel_features(m, t.x, t.y, f);
                     store_x_row_at(st + kPX, ck(row, 2 * kRows, p.err, kBndRow), f, fp8, inv_a1);
@@ -747,7 +778,7 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_batch_pf_kernel(co
         if (kPSplitRegs) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kPProducerRegs));
         const int pw = warp - 4;
         const uint32_t lt = lanemask_lt();
-        int *ranks = reinterpret_cast<int *>(sm + kPRanks) + 32 * pw;
+        int *ranks = reinterpret_cast<int *>(sm + kPRanks) + 64 * pw;
         int2 *list = reinterpret_cast<int2 *>(sm + kPList);
         const int pt = threadIdx.x - kRows;  // producer thread
         for (long long j = 0;; ++j) {
@@ -858,29 +889,39 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_batch_pf_kernel(co
 
 using PfFn = void (*)(const ExactParams, const MlpDevice, int *);
 
-template <int TW, bool kStats, bool kFb>
+// Variants: kPlain, kFallback (C / C+ on Box and Mask), kTwoTexels (two
+// texels per lane on List Merge, Box and Mask).
+enum { kPlain = 0, kFallback = 1, kTwoTexels = 2 };
+
+template <int TW, bool kStats, int kVar>
 PfFn pf_pick(int alg, int md) {
+    constexpr bool kFb = kVar == kFallback, kTwo = kVar == kTwoTexels;
     switch (alg) {
-    case ALG_STF: return kFb ? nullptr : mlp_filter_pf_kernel<ALG_STF, TW, 16, kStats, false>;
-    case ALG_LIST: return kFb ? nullptr : mlp_filter_pf_kernel<ALG_LIST, TW, 16, kStats, false>;
-    case ALG_BOX: return mlp_filter_pf_kernel<ALG_BOX, TW, 16, kStats, kFb>;
+    case ALG_STF: return kVar == kPlain ? mlp_filter_pf_kernel<ALG_STF, TW, 16, kStats, false, false> : nullptr;
+    case ALG_LIST: return kFb ? nullptr : mlp_filter_pf_kernel<ALG_LIST, TW, 16, kStats, false, kTwo>;
+    case ALG_BOX: return mlp_filter_pf_kernel<ALG_BOX, TW, 16, kStats, kFb, kTwo>;
     case ALG_MASK:
-        return md == 11 ? mlp_filter_pf_kernel<ALG_MASK, TW, 11, kStats, kFb> : mlp_filter_pf_kernel<ALG_MASK, TW, 16, kStats, kFb>;
+        return md == 11 ? mlp_filter_pf_kernel<ALG_MASK, TW, 11, kStats, kFb, kTwo>
+                        : mlp_filter_pf_kernel<ALG_MASK, TW, 16, kStats, kFb, kTwo>;
     default: return nullptr;
     }
 }
 
-template <int TW>
-PfFn pf_pick_tw(int alg, int md, bool st, bool fb) {
-    return fb ? (st ? pf_pick<TW, true, true>(alg, md) : pf_pick<TW, false, true>(alg, md))
-              : (st ? pf_pick<TW, true, false>(alg, md) : pf_pick<TW, false, false>(alg, md));
+template <int TW, bool kStats>
+PfFn pf_pick_var(int alg, int md, int var) {
+    switch (var) {
+    case kPlain: return pf_pick<TW, kStats, kPlain>(alg, md);
+    case kFallback: return pf_pick<TW, kStats, kFallback>(alg, md);
+    case kTwoTexels: return pf_pick<TW, kStats, kTwoTexels>(alg, md);
+    default: return nullptr;
+    }
 }
 
-PfFn pf_kernel(int alg, int tile_w, int mask_dim, bool st, bool fb) {
+PfFn pf_kernel(int alg, int tile_w, int mask_dim, bool st, int var) {
     switch (tile_w) {
-    case 8: return pf_pick_tw<8>(alg, mask_dim, st, fb);
-    case 4: return pf_pick_tw<4>(alg, mask_dim, st, fb);
-    case 16: return pf_pick_tw<16>(alg, mask_dim, st, fb);
+    case 8: return st ? pf_pick_var<8, true>(alg, mask_dim, var) : pf_pick_var<8, false>(alg, mask_dim, var);
+    case 4: return st ? pf_pick_var<4, true>(alg, mask_dim, var) : pf_pick_var<4, false>(alg, mask_dim, var);
+    case 16: return st ? pf_pick_var<16, true>(alg, mask_dim, var) : pf_pick_var<16, false>(alg, mask_dim, var);
     default: return nullptr;
     }
 }
@@ -904,8 +945,9 @@ cudaError_t pf_prepare(PfFn fn, int smem_bytes) {
     return e;
 }
 
-int pf_smem(bool fb, int alg) {
-    return fb ? PLayout<true>::kBytes : (alg == ALG_LIST ? PLayout<false, true>::kBytes : PLayout<false>::kBytes);
+int pf_smem(int var, int alg) {
+    return var == kFallback ? PLayout<true>::kBytes
+                            : (alg == ALG_LIST ? PLayout<false, true>::kBytes : PLayout<false>::kBytes);
 }
 
 }  // namespace
@@ -914,32 +956,38 @@ bool mlp_filter_pf_fallback_applies(const ExactParams &p, int alg) {
     return (alg == ALG_BOX || alg == ALG_MASK) && p.fallback != 0 && p.tpl == 1 && !p.group_dedup;
 }
 
+bool mlp_filter_pf_two_applies(const ExactParams &p, int alg) {
+    return (alg == ALG_LIST || alg == ALG_BOX || alg == ALG_MASK) && p.fallback == 0 && p.tpl == 2 && !p.group_dedup;
+}
+
 cudaError_t prepare_mlp_filter_pf(int alg, int tile_w, int mask_dim) {
-    for (int v = 0; v < 4; ++v) {
-        const bool st = (v & 1) != 0, fb = (v & 2) != 0;
-        if (fb && (alg == ALG_STF || alg == ALG_LIST)) continue;
-        PfFn fn = pf_kernel(alg, tile_w, mask_dim, st, fb);
-        if (!fn) return cudaErrorInvalidValue;
-        const cudaError_t e = pf_prepare(fn, pf_smem(fb, alg));
-        if (e != cudaSuccess) return e;
+    for (int var = kPlain; var <= kTwoTexels; ++var) {
+        for (int st = 0; st < 2; ++st) {
+            PfFn fn = pf_kernel(alg, tile_w, mask_dim, st != 0, var);
+            if (!fn) continue;  // no such variant for this algorithm
+            const cudaError_t e = pf_prepare(fn, pf_smem(var, alg));
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
 
 cudaError_t launch_mlp_filter_pf(const ExactParams &p, const MlpDevice &m, int alg, int tile_w, int mask_dim, int *err,
                                  cudaStream_t stream) {
-    const bool fb = p.fallback != 0;
-    if (fb && !mlp_filter_pf_fallback_applies(p, alg)) return cudaErrorInvalidValue;
-    PfFn fn = pf_kernel(alg, tile_w, mask_dim, p.stats != nullptr, fb);
+    const int var = p.fallback != 0 ? kFallback : (p.tpl == 2 ? kTwoTexels : kPlain);
+    if (var == kFallback && !mlp_filter_pf_fallback_applies(p, alg)) return cudaErrorInvalidValue;
+    if (var == kTwoTexels && !mlp_filter_pf_two_applies(p, alg)) return cudaErrorInvalidValue;
+    PfFn fn = pf_kernel(alg, tile_w, mask_dim, p.stats != nullptr, var);
     if (!fn) return cudaErrorInvalidValue;
     if (p.n_tiles == 0) return cudaSuccess;
     if (p.n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile positions use 32-bit arithmetic
-    cudaError_t e = pf_prepare(fn, pf_smem(fb, alg));
+    cudaError_t e = pf_prepare(fn, pf_smem(var, alg));
     if (e != cudaSuccess) return e;
-    const long long groups = (p.n_tiles + kGroupTiles - 1) / kGroupTiles;
+    const int gt = var == kTwoTexels ? kGroupTiles / 2 : kGroupTiles;
+    const long long groups = (p.n_tiles + gt - 1) / gt;
     const long long cap = (long long)device_sm_count() * kPCtasPerSm;
     const int grid = (int)(groups < cap ? groups : cap);
-    fn<<<grid, kPThreads, pf_smem(fb, alg), stream>>>(p, m, err);
+    fn<<<grid, kPThreads, pf_smem(var, alg), stream>>>(p, m, err);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,7 @@ struct Selection {
     int tx2, ty2;    // that texel (unclamped)
     int rk[4];       // success path: index of tap k in the warp's texel list
     int my_rank;     // index of this lane's texel in that list (when produce)
+    int my_rank2;    // two texels per lane: index of this lane's second texel (when produce2)
     uint8_t count;   // texel evaluations of this lane
 };
 
@@ -115,6 +116,7 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
     sel.ty = ps.uly;
     sel.count = 0;  // sel.src and sel.rk are set on the success path only
     sel.my_rank = 0;
+    sel.my_rank2 = 0;
     sel.produce2 = false;
     sel.tx2 = sel.ty2 = 0;
     if (kStats) cnt.v[kStatTilesTotal] += 1;
@@ -354,6 +356,21 @@ __device__ __forceinline__ Selection select_tile(const ExactParams &p, const Pix
                     sel.tx2 = minx + (pos1 - q * bw);
                     sel.ty2 = miny + q;
                 }
+            }
+            // the dense ranks of the taps and of this lane's texels in the
+            // tile's texel list (what the learned decode packs): the index
+            // itself but for the small masks, whose indices are box positions
+            if (ALG == ALG_MASK && mcls <= 2) {
+                const unsigned long long B = ((unsigned long long)(mcls == 2 ? Bw[1] : 0u) << 32) | Bw[0];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) sel.rk[k] = __popcll(B & ((1ull << (j[k] & 63)) - 1ull));
+                sel.my_rank = __popcll(B & ((1ull << lane) - 1ull));
+                sel.my_rank2 = __popcll(B & ((1ull << (lane + 32)) - 1ull));
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) sel.rk[k] = j[k];
+                sel.my_rank = lane;
+                sel.my_rank2 = lane + 32;
             }
             // lane + 32 x round; inactive pixels carry arbitrary indices, whose
             // shuffled values they drop
