@@ -629,6 +629,39 @@ def e2e_host(tex, sc, alg, opts, k, stream):
     return s, h2d, d2h
 
 
+def link_roof(h2d, d2h, s, reps=5):
+    """The host link's rate for one step's bytes: h2d bytes copied from
+    page-locked host memory to the device and d2h bytes back, on two streams
+    at once (copy engines, CUDA events, best of reps), beside the rate the
+    end-to-end call achieved for the same bytes in s seconds."""
+    import torch
+    h_in = torch.empty(h2d, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(d2h, dtype=torch.uint8).pin_memory()
+    d_in = torch.empty(h2d, dtype=torch.uint8, device="cuda")
+    d_out = torch.zeros(d2h, dtype=torch.uint8, device="cuda")
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    best = float("inf")
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cur = torch.cuda.current_stream()
+        e0.record(cur)
+        for st, dst, src in ((s_in, d_in, h_in), (s_out, h_out, d_out)):
+            st.wait_event(e0)
+            with torch.cuda.stream(st):
+                dst.copy_(src, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(st)
+            cur.wait_event(done)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    link = (h2d + d2h) / best / 1e9
+    achieved = (h2d + d2h) / s / 1e9
+    return {"achieved_GBps": achieved, "link_GBps": link, "frac": achieved / link,
+            "how": "copy engines, both directions at once on two streams, the step's h2d and d2h bytes"}
+
+
 E2E_NOTE = ("page-locked host buffers: inputs read and the image written in place by the kernel over "
             "NVLink-C2C, the counts copied back in one copy; three buffer sets in turn (above L2)")
 
@@ -711,7 +744,7 @@ def exact_section(args, dev, stream, flush, name, rank, world, headline):
                        "algorithmic_bytes_per_launch": abytes, "kernel": "exact_filter_kernel<MASK, 8x4, 11>"}
     s, h2d, d2h = e2e_host(tex, sc, alg, opts, max(3, min(args.steps, 200)), stream)
     res["e2e"] = {"value": npix / s, "unit": "pixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                  "entry_point": "ctf_filter_host", "transfer": E2E_NOTE}
+                  "entry_point": "ctf_filter_host", "transfer": E2E_NOTE, "link": link_roof(h2d, d2h, s)}
     res["_tex"] = (tex, blocks)
     if not args.no_cpu_baseline and world == 1:
         arrays = {"uv": sc.uv, "jac": sc.jac, "blocks": blocks}
@@ -767,13 +800,24 @@ def learned_section(args, dev, stream, flush, rank, world):
                        "peak_kind": peak_kind, "algorithmic_flop_per_launch": flop,
                        "flop_per_evaluation": MLP_FLOP_PER_EVAL,
                        "kernel": "mlp_filter_pf_kernel<MASK, 8x4, 11> (FP16 operands, FP32 accumulation in TMEM)"}
+    # The same launch against the HBM roof: the per-pixel streams (uv, Jacobian,
+    # coverage in; RGBA and count out) take longer at the measured copy rate
+    # than the evaluations' FLOP at the tensor peak, so by the roofline model
+    # this is the binding roof; the latents' lines are not counted.
+    hbm_peak, hbm_kind = measured_peaks()
+    pbytes = npix * (8 + 16 + (1 if cov is not None else 0) + 16 + 1)
+    hbm_achieved = pbytes / (res["ms_per_step"] * 1e-3) / 1e9
+    res["roofline_hbm"] = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": hbm_achieved / hbm_peak, "peak_kind": hbm_kind,
+                           "algorithmic_bytes_per_launch": pbytes,
+                           "roof_us": {"hbm": pbytes / hbm_peak / 1e3, "tensor": flop / peak / 1e6}}
     if not args.no_extras:
         res["learned"] = learned_others(args, dev, stream, flush, sc, texs, exact, peak, peak_kind)
         f = res["learned"]["filter_3840x2160"]
         res["vs_4tap"] = (npix / (res["ms_per_step"] * 1e-3)) / f["fp16_4tap"]["pixels_per_s"]
     s, h2d, d2h = e2e_host(tex, sc, alg, opts, max(3, min(args.steps, 50)), stream)
     res["e2e"] = {"value": npix / s, "unit": "pixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                  "entry_point": "ctf_filter_host", "transfer": E2E_NOTE}
+                  "entry_point": "ctf_filter_host", "transfer": E2E_NOTE, "link": link_roof(h2d, d2h, s)}
     if not args.no_cpu_baseline and world == 1:
         arrays = {"uv": sc.uv, "jac": sc.jac, "cov": sc.coverage}
         arrays.update(oracle_mlp_arrays(tex, "fp16"))
@@ -987,6 +1031,8 @@ def ours_arm(args):
         line["dtype_note"] = ("FP16 operands with FP32 accumulation for the learned decode; FP32 coordinate "
                               "setup, selection and filter")
         line["training"] = head["training"]
+        if "roofline_hbm" in head:
+            line["roofline_hbm"] = head["roofline_hbm"]
         if "learned" in head:
             line["learned"] = head["learned"]
         if exact:
