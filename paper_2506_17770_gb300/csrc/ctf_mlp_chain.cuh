@@ -203,6 +203,7 @@ __device__ __forceinline__ void hidden_epilogue(unsigned char *sm, uint32_t tadd
 #pragma unroll
     for (int q = 0; q < 4; ++q) tc::tmem_ld16(taddr + 16 * q, d + 16 * q);
     tc::tmem_wait_ld();
+    tc::regs_after_wait<64>(d);
     unsigned char *H = sm + kSmH;
     // Bias and scale in packed pairs; the ReLU is applied by the conversion
     // (the rounding of a negative value is not positive, and the positive
@@ -327,6 +328,7 @@ __device__ __forceinline__ bool mlp_chain(Chain &ch, bool fp8, float4 &out, int 
     float d[16];
     tc::tmem_ld16(lane_base + 0, d);
     tc::tmem_wait_ld();
+    tc::regs_after_wait<16>(d);
     float o[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {

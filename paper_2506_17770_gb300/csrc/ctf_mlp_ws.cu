@@ -112,6 +112,7 @@ __device__ __forceinline__ void ws_hidden_epilogue(unsigned char *sm, uint32_t t
         tc::tmem_ld16(taddr + 32 * half, d);
         tc::tmem_ld16(taddr + 32 * half + 16, d + 16);
         tc::tmem_wait_ld();
+        tc::regs_after_wait<32>(d);
         if (!fp8) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -231,6 +232,7 @@ __device__ __forceinline__ bool ws_chain(Chain &ch, bool fp8, float4 &out, int *
     float d[16];
     tc::tmem_ld16(lane_base + 0, d);
     tc::tmem_wait_ld();
+    tc::regs_after_wait<16>(d);
     float o[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {

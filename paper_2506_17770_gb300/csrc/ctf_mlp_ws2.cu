@@ -163,6 +163,7 @@ __device__ __forceinline__ void p_hidden_epilogue(uint32_t hcol, uint32_t taddr,
         float d[16];
         tc::tmem_ld16(taddr + 16 * q, d);
         tc::tmem_wait_ld();
+        tc::regs_after_wait<16>(d);
         if (!fp8) {
             uint32_t w[8];
 #pragma unroll
@@ -275,6 +276,7 @@ __device__ __forceinline__ bool p_chain(unsigned char *sm, uint32_t tmem, uint64
         uint32_t r[4];
         tc::tmem_ld4(lane_base + 0, r);
         tc::tmem_wait_ld();
+        tc::regs_after_wait<4>(r);
         float o[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {

@@ -201,6 +201,10 @@ __device__ __forceinline__ void tld16(uint32_t taddr, float v[16]) {
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    // the loaded registers pass through an empty asm after the wait, so that
+    // no use of them can be scheduled before it
+#pragma unroll
+    for (int i = 0; i < 16; ++i) asm volatile("" : "+r"(r[i]));
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }

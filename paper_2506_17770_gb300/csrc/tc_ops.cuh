@@ -157,16 +157,15 @@ __device__ __forceinline__ void commit(uint64_t *bar) {
 }
 
 // Each thread of the warp reads 16 consecutive fp32 columns of its TMEM lane.
+// (The .b32 load writes the fp32 registers directly, so that nothing reads
+// them before the caller's tcgen05.wait::ld.)
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-    uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+          "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
         : "r"(taddr)
         : "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Each thread of the warp reads 32 consecutive 32-bit columns of its TMEM lane.
@@ -191,6 +190,21 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t r[4]) {
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// The registers a tcgen05.ld writes hold their values only after
+// tcgen05.wait::ld.  Passing them through an empty asm placed after the wait
+// makes every later use depend on it, so the compiler cannot move arithmetic
+// on them above the wait (no instruction is emitted).
+template <int N>
+__device__ __forceinline__ void regs_after_wait(float *v) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+f"(v[i]));
+}
+template <int N>
+__device__ __forceinline__ void regs_after_wait(uint32_t *v) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+r"(v[i]));
+}
 
 }  // namespace tc
 }  // namespace ctf
