@@ -528,6 +528,7 @@ int ctf_selftest_bounded_wait(uint32_t polls, void *stream) {
 }
 
 int ctf_texture_create(const ctf_texture_desc *desc, ctf_texture *out) {
+    ctf::NvtxRange nvtx_range("ctf_texture_create");
     g_last_error.clear();
     if (!desc || !out) return fail(CTF_ERR_ARG, "desc and out must not be NULL");
     *out = nullptr;
@@ -580,6 +581,7 @@ int ctf_texture_destroy(ctf_texture tex) {
 int ctf_filter(ctf_texture tex, const float *uv, const float *jac, const uint8_t *coverage, int width, int height,
                int view_id, ctf_algorithm alg, uint64_t seed, const ctf_filter_opts *opts, float *out_rgba,
                uint8_t *out_evals, ctf_stats *stats, void *stream) {
+    ctf::NvtxRange nvtx_range("ctf_filter");
     g_last_error.clear();
     ResolvedOpts ro;
     int rc = validate_filter_args(tex, uv, jac, width, height, alg, out_rgba, &ro, opts);
@@ -625,6 +627,7 @@ int ctf_filter_host(ctf_texture tex, const float *uv_host, const float *jac_host
                     int width, int height, int view_id, ctf_algorithm alg, uint64_t seed,
                     const ctf_filter_opts *opts, float *out_rgba_host, uint8_t *out_evals_host, ctf_stats *stats,
                     void *stream) {
+    ctf::NvtxRange nvtx_range("ctf_filter_host");
     g_last_error.clear();
     ResolvedOpts ro;
     int rc = validate_filter_args(tex, uv_host, jac_host, width, height, alg, out_rgba_host, &ro, opts);

@@ -558,6 +558,7 @@ extern "C" {
 
 int ctf_filter_batch(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t seed, const ctf_batch_opts *opts,
                      ctf_stats *stats, void *stream) {
+    ctf::NvtxRange nvtx_range("ctf_filter_batch");
     using namespace ctf;
     clear_error();
     ResolvedBatch r;
@@ -644,6 +645,7 @@ int ctf_batch_graph_create(const ctf_view *views, int nviews, ctf_algorithm alg,
 }
 
 int ctf_batch_graph_launch(ctf_batch_graph g, void *stream) {
+    ctf::NvtxRange nvtx_range("ctf_batch_graph_launch");
     using namespace ctf;
     clear_error();
     if (!g) return report(CTF_ERR_ARG, "graph is NULL");
@@ -665,6 +667,7 @@ int ctf_batch_graph_destroy(ctf_batch_graph g) {
 
 int ctf_batch_autotune(const ctf_view *views, int nviews, ctf_algorithm alg, uint64_t seed, const ctf_batch_opts *base,
                        ctf_batch_opts *best, double *best_ms, void *stream) {
+    ctf::NvtxRange nvtx_range("ctf_batch_autotune");
     using namespace ctf;
     clear_error();
     if (!best) return report(CTF_ERR_ARG, "best is NULL");

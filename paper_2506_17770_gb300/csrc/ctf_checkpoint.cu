@@ -210,6 +210,7 @@ int ctf_checkpoint_load(const char *path, ctf_texture *out) {
 
 int ctf_mlp_train(ctf_texture exact_src, const ctf_train_desc *desc, ctf_eval_mode mode, ctf_texture *out_mlp,
                   ctf_train_report *rep, void *stream) {
+    ctf::NvtxRange nvtx_range("ctf_mlp_train");
     using namespace ctf;
     clear_error();
     if (!desc || !out_mlp) return report(CTF_ERR_ARG, "desc and out_mlp must not be NULL");

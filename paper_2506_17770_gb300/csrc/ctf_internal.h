@@ -6,10 +6,23 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ctf.h"
 #include "ctf_mlp.cuh"
 
 namespace ctf {
+// A named range on the host timeline around one entry point's work (NVTX:
+// a profiler attached to the process shows the range and can filter the
+// kernels queued inside it, e.g. ncu --nvtx --nvtx-include "ctf_filter/";
+// with no tool attached it costs a pointer test).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Decode tables of the exact block decode, one copy per device in global
 // memory (made on the host, ctf_api.cu) and copied into shared memory by
 // every CTA: the two endpoints of a block expand to 8-bit channels laid out

@@ -112,6 +112,7 @@ MlpDevice mlp_device_view(const ctf_texture_s *t) {
 extern "C" {
 
 int ctf_texture_create_mlp(const ctf_mlp_desc *d, ctf_texture *out) {
+    ctf::NvtxRange nvtx_range("ctf_texture_create_mlp");
     using namespace ctf;
     clear_error();
     if (!d || !out) return report(CTF_ERR_ARG, "desc and out must not be NULL");

@@ -70,6 +70,7 @@ extern "C" int ctf_filter_host_noalloc(ctf_texture tex, const float *uv_host, co
                                        ctf_algorithm alg, uint64_t seed, const ctf_filter_opts *opts,
                                        float *out_rgba_host, uint8_t *out_evals_host, ctf_stats *stats,
                                        void *stream) {
+    ctf::NvtxRange nvtx_range("ctf_filter_host_noalloc");
     using namespace ctf;
     // Argument checks first (they queue nothing and touch no device memory).
     int rc = noalloc_validate(tex, uv_host, jac_host, width, height, alg, opts, out_rgba_host);

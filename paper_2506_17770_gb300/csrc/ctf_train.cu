@@ -999,6 +999,7 @@ int ctf_trainer_destroy(ctf_trainer t) {
 int64_t ctf_trainer_steps_done(ctf_trainer t) { return t ? t->step : -1; }
 
 int ctf_trainer_step(ctf_trainer t, int64_t steps, void *stream) {
+    ctf::NvtxRange nvtx_range("ctf_trainer_step");
     using namespace ctf;
     clear_error();
     if (!t) return report(CTF_ERR_ARG, "trainer is NULL");
