@@ -351,6 +351,9 @@ __device__ __forceinline__ void chain_setup(Chain &ch, unsigned char *sm, const 
     uint4 *dst = reinterpret_cast<uint4 *>(sm + kSmImg);
     if (src)
         for (int i = threadIdx.x; i < kImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    // every thread's part of the image, written through the generic proxy,
+    // ordered before the MMAs that read it through the async proxy
+    tc::fence_proxy_async();
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kSmBar);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kSmTmem);
     if (threadIdx.x == 0) {

@@ -488,6 +488,9 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_filter_pf_kernel(c
         const uint4 *src = m.img;
         uint4 *dst = reinterpret_cast<uint4 *>(sm + kImgW1);
         for (int i = threadIdx.x; i < kImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+        // every thread's part of the image, written through the generic
+        // proxy, ordered before the MMAs that read it through the async proxy
+        tc::fence_proxy_async();
     }
     if (threadIdx.x == 0) {
         tc::mbar_init(mma_bar, 1);
@@ -700,6 +703,9 @@ __global__ void __launch_bounds__(kPThreads, kPCtasPerSm) mlp_batch_pf_kernel(co
         const uint4 *src = m0.img;
         uint4 *dst = reinterpret_cast<uint4 *>(sm + kImgW1);
         for (int i = threadIdx.x; i < kImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+        // every thread's part of the image, written through the generic
+        // proxy, ordered before the MMAs that read it through the async proxy
+        tc::fence_proxy_async();
     }
     if (threadIdx.x == 0) {
         tc::mbar_init(mma_bar, 1);
